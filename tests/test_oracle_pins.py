@@ -1,0 +1,503 @@
+"""Pins of the CPU oracle to facts outside itself (closed forms, library
+routines, brute force, hand-worked values, invariants).  CPU only."""
+import math
+import os
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+import scipy.interpolate
+import scipy.stats
+
+from oracle import nvc as O
+from oracle import philox as PH
+import nvc_synth as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox --
+
+def test_philox_round_structure_matches_numpy_philox4x64():
+    """numpy's Philox bit generator (an independent implementation of
+    Philox-4x64-10) pins the round function, word permutation and key
+    schedule; numpy increments its counter before the first block."""
+    rng = np.random.default_rng(5)
+    cases = [([0, 0, 0, 0], [0, 0]),
+             ([2**64 - 1, 0, 0, 0], [1, 2]),       # carry into word 1
+             ([5, 7, 9, 11], [123, 456])]
+    for _ in range(5):
+        cases.append((list(map(int, rng.integers(0, 2**63, 4))),
+                      list(map(int, rng.integers(0, 2**63, 2)))))
+    for ctr, key in cases:
+        bg = np.random.Philox(counter=np.array(ctr, dtype=np.uint64),
+                             key=np.array(key, dtype=np.uint64))
+        got = [int(v) for v in bg.random_raw(4)]
+        c = ctr[0] + (ctr[1] << 64) + (ctr[2] << 128) + (ctr[3] << 192) + 1
+        c1 = [(c >> (64 * i)) & (2**64 - 1) for i in range(4)]
+        want = PH.philox_generic(c1, key, width=64, mult=PH.M4x64, weyl=PH.W64)
+        assert got == list(want)
+
+
+def test_philox_weyl_constants_closed_form():
+    """Key increments = fractional parts of the golden ratio and sqrt(3)."""
+    getcontext().prec = 80
+    phi_frac = (Decimal(5).sqrt() - 1) / 2
+    s3_frac = Decimal(3).sqrt() - 1
+    for bits, W in ((32, PH.W32), (64, PH.W64)):
+        assert W[0] == int(phi_frac * (2**bits))
+        assert W[1] == int(s3_frac * (2**bits))
+
+
+def test_philox4x32_vectorised_matches_generic():
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, (64, 4), dtype=np.uint64).astype(np.uint32)
+    key = (0xDEADBEEF, 0x01234567)
+    vec = PH.philox4x32(ctr, key)
+    for i in range(64):
+        assert tuple(int(v) for v in vec[i]) == PH.philox_generic(ctr[i], key)
+
+
+def test_philox_uniformity_chi2():
+    r = PH.stream_words(np.arange(1 << 16), 3, 1, PH.TAG_WRS, 16, seed=42)
+    u = PH.uniform24(r).ravel()
+    assert u.min() >= 0.0 and u.max() < 1.0
+    hist = np.bincount((u * 256).astype(np.int64), minlength=256)
+    assert scipy.stats.chisquare(hist).pvalue > 1e-4
+    # consecutive words of one stream are uncorrelated
+    assert abs(np.corrcoef(u[:-1], u[1:])[0, 1]) < 0.01
+
+
+def test_uniform24_exact():
+    r = np.array([0, 0xFF, 0x100, 0xFFFFFFFF], np.uint32)
+    assert list(PH.uniform24(r)) == [0.0, 0.0, 2.0**-24, 1.0 - 2.0**-24]
+
+
+# ------------------------------------------------------------------- hash --
+
+def test_hash_hand_worked_vectors():
+    rows = np.loadtxt(os.path.join(GOLDEN, "hash_vectors.txt"), dtype=np.int64)
+    for x, y, z, _, _, h, h14, h19 in rows:
+        assert O.hash_index(x, y, z, 1 << 14) == h14
+        assert O.hash_index(x, y, z, 1 << 19) == h19
+        assert O.hash_index(x, y, z, 1 << 32) == h
+
+
+def test_hash_axis_properties():
+    x = np.arange(1000)
+    # the x axis carries prime 1: identity below T
+    assert np.array_equal(O.hash_index(x, 0, 0, 1 << 14), x)
+    # XOR-separable over the axes
+    y, z = x * 7 + 3, x * 13 + 5
+    T = 1 << 19
+    assert np.array_equal(O.hash_index(x, y, z, T),
+                          O.hash_index(x, 0, 0, T) ^ O.hash_index(0, y, 0, T)
+                          ^ O.hash_index(0, 0, z, T))
+
+
+# ----------------------------------------------------------------- encode --
+
+def _cfg(**kw):
+    base = dict(name="t", n_levels=4, n_features=2, log2_table_size=14,
+                base_resolution=4, growth=2.0, hidden=(8,), n_outputs=3)
+    base.update(kw)
+    return S.NVCConfig(**base)
+
+
+def test_level_resolutions():
+    assert O.level_resolutions(4, 2.0, 4) == [4, 8, 16, 32]
+    assert O.level_resolutions(4, 1.5, 8) == [4, 6, 9, 13, 20, 30, 45, 68]
+    assert O.level_resolutions(16, 1.447, 3) == [16, 23, 33]
+
+
+def test_encode_grid_vertices_return_stored_entries():
+    """At power-of-two resolutions vertex k / N_l is exact in float32 and
+    the encoding returns the stored row bit-for-bit."""
+    cfg = _cfg()
+    rng = np.random.default_rng(0)
+    table = rng.standard_normal((4, 1 << 14, 2))
+    for l, n_l in enumerate([4, 8, 16, 32]):
+        k = rng.integers(0, n_l + 1, (200, 3))
+        k[0] = (n_l, n_l, n_l)          # the far corner (x_hat = 1)
+        k[1] = (0, 0, 0)
+        pos = (k / n_l).astype(np.float32)
+        feat = O.encode(cfg, table, pos)
+        rows = O.hash_index(k[:, 0], k[:, 1], k[:, 2], 1 << 14)
+        assert np.array_equal(feat[:, 2 * l:2 * l + 2], table[l, rows])
+
+
+def _collision_free_level(n_l, T):
+    v = np.stack(np.meshgrid(*[np.arange(n_l + 1)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    rows = O.hash_index(v[:, 0], v[:, 1], v[:, 2], T)
+    return v, rows, len(np.unique(rows)) == len(rows)
+
+
+def test_encode_reproduces_affine_functions():
+    """Trilinear interpolation is exact on affine functions of position: a
+    wrong corner weight (f vs 1-f) or offset breaks this."""
+    cfg = _cfg(n_levels=1, base_resolution=5, growth=1.0)
+    T = 1 << 14
+    v, rows, ok = _collision_free_level(5, T)
+    assert ok
+    a, b = np.array([0.3, -1.7, 2.9]), 0.25
+    table = np.zeros((1, T, 2))
+    table[0, rows, 0] = (v / 5.0) @ a + b
+    table[0, rows, 1] = 1.0
+    # dyadic positions: x_hat * N_l is exact in float32, so the blend is
+    # evaluated at the query itself
+    pos = (np.random.default_rng(1).integers(0, 1025, (500, 3)) / 1024.0).astype(np.float32)
+    feat = O.encode(cfg, table, pos)
+    np.testing.assert_allclose(feat[:, 0], pos.astype(np.float64) @ a + b, atol=1e-12)
+    np.testing.assert_allclose(feat[:, 1], 1.0, atol=1e-14)   # partition of unity
+
+
+def test_encode_matches_scipy_trilinear_interpolator():
+    cfg = _cfg(n_levels=1, base_resolution=7, growth=1.0, n_features=1)
+    T = 1 << 14
+    v, rows, ok = _collision_free_level(7, T)
+    assert ok
+    vals = np.random.default_rng(2).standard_normal(len(v))
+    table = np.zeros((1, T, 1))
+    table[0, rows, 0] = vals
+    grid = np.zeros((8, 8, 8))
+    grid[v[:, 0], v[:, 1], v[:, 2]] = vals
+    ax = np.arange(8) / 7.0
+    interp = scipy.interpolate.RegularGridInterpolator((ax, ax, ax), grid)
+    pos = (np.random.default_rng(3).integers(0, 4097, (400, 3)) / 4096.0).astype(np.float32)
+    np.testing.assert_allclose(O.encode(cfg, table, pos)[:, 0],
+                               interp(pos.astype(np.float64)), atol=1e-12)
+
+
+def test_encode_clamps_outside_bounds_and_normalises():
+    cfg = _cfg(bounds_min=(-2.0, 0.0, 1.0), bounds_max=(2.0, 4.0, 3.0))
+    table = np.random.default_rng(4).standard_normal((4, 1 << 14, 2))
+    inside = np.array([[-2.0, 0.0, 1.0], [2.0, 4.0, 3.0], [0.0, 2.0, 2.0]], np.float32)
+    outside = np.array([[-9.0, -1.0, 0.0], [5.0, 8.0, 9.0], [0.0, 2.0, 2.0]], np.float32)
+    np.testing.assert_array_equal(O.encode(cfg, table, inside), O.encode(cfg, table, outside))
+    unit = _cfg()
+    np.testing.assert_array_equal(
+        O.encode(cfg, table, inside),
+        O.encode(unit, table, np.array([[0, 0, 0], [1, 1, 1], [.5, .5, .5]], np.float32)))
+
+
+def test_encode_backward_is_the_adjoint():
+    """<encode(table), g> == <table, encode_backward(g)> (linear in table)."""
+    cfg = _cfg(log2_table_size=8)          # small T: many collisions
+    rng = np.random.default_rng(5)
+    table = rng.standard_normal((4, 256, 2))
+    pos = rng.uniform(0, 1, (300, 3)).astype(np.float32)
+    feat, aux = O.encode(cfg, table, pos, with_aux=True)
+    g = rng.standard_normal(feat.shape)
+    lhs = np.sum(feat * g)
+    rhs = np.sum(table * O.encode_backward(cfg, aux, g))
+    assert abs(lhs - rhs) < 1e-9 * max(1.0, abs(lhs))
+
+
+# -------------------------------------------------------------------- MLP --
+
+def test_mlp_hand_computed():
+    # 2 -> 2 -> 1, slope 0.25: x = (1, 1); z = (-1, 1.5); h = (-0.25, 1.5)
+    W1 = np.array([[1.0, -2.0], [0.5, 1.0]])
+    Wo = np.array([[1.0, -1.0]])
+    out, acts, zs = O.mlp_forward([W1, Wo], np.array([[1.0, 1.0]]), 0.25)
+    assert out[0, 0] == -1.75
+    assert list(acts[1][0]) == [-0.25, 1.5]
+    # 3 -> 2 -> 2 -> 2 ReLU: x = (2, 0, -1)
+    A = np.array([[1.0, 0.5, 2.0], [-1.0, 1.0, 0.0]])   # z = (0, -2) -> (0, 0)
+    B = np.array([[1.0, 1.0], [2.0, -1.0]])
+    C = np.array([[3.0, 0.0], [0.0, 1.0]])
+    out, _, _ = O.mlp_forward([A, B, C], np.array([[2.0, 0.0, -1.0]]), 0.0)
+    assert list(out[0]) == [0.0, 0.0]
+    out, _, _ = O.mlp_forward([A, B, C], np.array([[2.0, 4.0, 0.0]]), 0.0)
+    # z1 = (4, 2); z2 = (6, 6); out = (18, 6)
+    assert list(out[0]) == [18.0, 6.0]
+    assert O.sigmoid(0.0) == 0.5
+    np.testing.assert_allclose(O.sigmoid(np.log(3.0)), 0.75)
+
+
+# ------------------------------------------------------- loss / backward --
+
+@pytest.mark.parametrize("loss,slope", [("bce", 0.01), ("l2", 0.0), ("bce", 0.0)])
+def test_gradients_match_central_finite_differences(loss, slope):
+    """Analytic gradient vs central differences (h = 1e-3, float64) on 128
+    parameters with nonzero gradient, relative error <= 1e-6."""
+    cfg = _cfg(n_levels=3, log2_table_size=10, hidden=(16, 16), n_outputs=4,
+               leaky_slope=slope, loss=loss, table_init=4.0, growth=1.5)
+    p = S.init_params(cfg, seed=3).astype(np.float64)
+    rng = np.random.default_rng(6)
+    pos = rng.uniform(0, 1, (256, 3)).astype(np.float32)
+    y = (rng.uniform(0, 1, (256, 4)) < 0.5).astype(np.float64)
+    table, Ws = O.split_params(cfg, p)
+    _, _, zs = O.mlp_forward(Ws, O.encode(cfg, table, pos), slope)
+    # keep the samples away from the activation kinks, which a 1e-3 step
+    # could cross
+    keep = np.all([np.min(np.abs(z), axis=1) > 1e-2 for z in zs], axis=0)
+    pos, y = pos[keep], y[keep]
+    assert len(pos) >= 8
+    _, g = O.gradients(cfg, p, pos, y)
+    cand = np.flatnonzero(np.abs(g) > 1e-4 * np.abs(g).max())
+    pick = rng.choice(cand, 128, replace=False)
+    h = 1e-3
+    worst = 0.0
+    for i in pick:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (O.gradients(cfg, pp, pos, y)[0] - O.gradients(cfg, pm, pos, y)[0]) / (2 * h)
+        worst = max(worst, abs(fd - g[i]) / max(abs(fd), abs(g[i])))
+    assert worst <= 1e-6, worst
+
+
+def test_bce_and_l2_closed_forms():
+    z = np.array([[-3.0, 0.0, 2.0]])
+    y = np.array([[1.0, 0.0, 1.0]])
+    s = 1 / (1 + np.exp(-z))
+    lb, gb = O.loss_and_grad("bce", z, y)
+    np.testing.assert_allclose(lb, np.mean(-y * np.log(s) - (1 - y) * np.log(1 - s)))
+    np.testing.assert_allclose(gb, (s - y) / 3)
+    l2, g2 = O.loss_and_grad("l2", z, y)
+    np.testing.assert_allclose(l2, np.mean((s - y) ** 2))
+    # large logits: BCE stays finite
+    lb, _ = O.loss_and_grad("bce", np.array([[800.0, -800.0]]), np.array([[0.0, 1.0]]))
+    np.testing.assert_allclose(lb, 800.0)
+
+
+# ------------------------------------------------------------------- Adam --
+
+def test_adam_first_step_closed_form():
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    th = np.array([1.0, 1.0, 1.0, 1.0])
+    t1, m, v = O.adam_update(th, g, np.zeros(4), np.zeros(4), 1, 0.01, 0.9, 0.99, 1e-15)
+    # m_hat = g, v_hat = g^2: step = -lr * g / (|g| + eps)
+    np.testing.assert_allclose(t1, th - 0.01 * g / (np.abs(g) + 1e-15), rtol=0, atol=1e-15)
+    # a constant gradient keeps m_hat = g, v_hat = g^2 on step 2 as well
+    t2, _, _ = O.adam_update(t1, g, m, v, 2, 0.01, 0.9, 0.99, 1e-15)
+    np.testing.assert_allclose(t2, t1 - 0.01 * np.sign(g), atol=1e-12)
+
+
+def test_adam_matches_torch_optim():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    th0 = rng.standard_normal(50)
+    grads = [rng.standard_normal(50) * 10 ** rng.uniform(-3, 1) for _ in range(6)]
+    p = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([p], lr=0.02, betas=(0.9, 0.99), eps=1e-15)
+    th, m, v = th0.copy(), np.zeros(50), np.zeros(50)
+    for t, g in enumerate(grads, 1):
+        p.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        th, m, v = O.adam_update(th, g, m, v, t, 0.02, 0.9, 0.99, 1e-15)
+    np.testing.assert_allclose(th, p.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_learning_rate_schedules():
+    paper = S.config_by_name("paper")
+    assert O.learning_rate(paper, 1) == 0.05
+    assert abs(O.learning_rate(paper, 101) - 0.0255) < 1e-15
+    assert abs(O.learning_rate(paper, 201) - 0.001) < 1e-15
+    assert abs(O.learning_rate(paper, 5000) - 0.001) < 1e-15
+    assert O.learning_rate(S.config_by_name("tiny_fp32"), 77) == 0.01
+
+
+# ------------------------------------------------------------- visibility --
+
+LIGHT = np.array([[0.0, 0.0, 10.0, 1.0]])
+ORIGIN = np.array([[0.0, 0.0, 0.0]])
+NOBOX = np.zeros((0, 6))
+NOSPH = np.zeros((0, 4))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_visibility_sphere_special_cases(dt):
+    V = lambda pos, sph: O.visibility(pos, LIGHT, np.array(sph, float).reshape(-1, 4), NOBOX, dt)[0, 0]
+    assert V(ORIGIN, []) == 1.0
+    assert V(ORIGIN, [0, 0, 5, 1]) == 0.0                 # on the axis
+    assert V(ORIGIN, [1.5, 0, 5, 1]) == 1.0               # beside it
+    assert V(ORIGIN, [0, 0, 12, 1]) == 1.0                # beyond the light
+    assert V(ORIGIN, [0, 0, -3, 1]) == 1.0                # behind the point
+    assert V(ORIGIN, [0.2, 0, 0.1, 0.5]) == 0.0           # point inside
+    assert V(ORIGIN, [0, 0.1, 10, 0.5]) == 0.0            # light inside
+    if dt == np.float64:
+        assert V(ORIGIN, [1 + 1e-6, 0, 5, 1]) == 1.0      # just tangent
+        assert V(ORIGIN, [1 - 1e-6, 0, 5, 1]) == 0.0      # just inside
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_visibility_box_special_cases(dt):
+    V = lambda pos, box: O.visibility(np.array(pos, float).reshape(1, 3), LIGHT, NOSPH,
+                                      np.array(box, float).reshape(-1, 6), dt)[0, 0]
+    assert V([0, 0, 0], [-1, -1, 4, 1, 1, 6]) == 0.0      # axis-aligned through
+    assert V([0, 0, 0], [0.5, -1, 4, 2, 1, 6]) == 1.0     # parallel, outside in x
+    assert V([0, 0, 0], [0.0, -1, 4, 2, 1, 6]) == 0.0     # touching face: closed
+    assert V([0, 0, 0], [-1, -1, -1, 1, 1, 1]) == 0.0     # point inside
+    assert V([0, 0, 0], [-1, -1, 11, 1, 1, 12]) == 1.0    # beyond the light
+    assert V([3, 0, 0], [1, -1, 4, 2, 1, 6]) == 0.0       # oblique ray through
+    assert V([3, 0, 0], [-1, -1, 4, 1, 1, 6]) == 1.0      # oblique ray passes by
+    assert V([3, 0, 0], [2.5, 0.5, 1, 3, 1, 2]) == 1.0    # oblique ray misses
+
+
+def test_visibility_matches_dense_segment_sampling():
+    """Brute force: march 20001 points along each segment and test each
+    against every occluder; configurations whose minimum clearance is
+    within 2e-3 of a surface are skipped as ambiguous for the marcher."""
+    rng = np.random.default_rng(8)
+    sc = S.scene_heightfield(seed=3, n_lights=6, n_spheres=10, n_boxes=10)
+    pos = rng.uniform(0, 10, (60, 3))
+    V = O.visibility(pos, sc.lights, sc.spheres, sc.boxes, np.float64)
+    ts = np.linspace(O.SEG_T0, O.SEG_T1, 20001)
+    checked = 0
+    for a in range(len(pos)):
+        for i in range(len(sc.lights)):
+            P = pos[a] + ts[:, None] * (sc.lights[i, :3].astype(float) - pos[a])
+            clear = np.inf
+            for s in sc.spheres.astype(float):
+                clear = min(clear, np.min(np.linalg.norm(P - s[:3], axis=1) - s[3]))
+            for b in sc.boxes.astype(float):
+                lo, hi = b[:3], b[3:]
+                out = np.maximum(np.maximum(lo - P, P - hi), 0)
+                inside_depth = np.min(np.minimum(P - lo, hi - P), axis=1)
+                sd = np.where(np.all((P >= lo) & (P <= hi), 1), -inside_depth,
+                              np.linalg.norm(out, axis=1))
+                clear = min(clear, np.min(sd))
+            if abs(clear) < 2e-3:
+                continue
+            checked += 1
+            assert V[a, i] == (1.0 if clear > 0 else 0.0)
+    assert checked > 300
+
+
+# -------------------------------------------------- contributions and WRS --
+
+def test_contribution_closed_forms():
+    L = np.array([[0.0, 0.0, 2.0, 8.0], [2.0, 0.0, 2 * math.sqrt(3.0), 4.0],
+                  [0.0, 0.0, -1.0, 5.0]])
+    c = O.contributions(np.zeros((1, 3)), np.array([[0.0, 0.0, 1.0]]), L)[0]
+    np.testing.assert_allclose(c, [8 / (math.pi * 4), 4 * math.cos(math.pi / 6) / (math.pi * 16), 0.0])
+    c32 = O.contributions(np.zeros((1, 3)), np.array([[0.0, 0.0, 1.0]]), L, np.float32)[0]
+    np.testing.assert_allclose(c32, c, rtol=1e-6)
+    # light on the point: zero-length direction gives 0 (no NaN)
+    c0 = O.contributions(np.zeros((1, 3)), np.array([[0.0, 0.0, 1.0]]),
+                         np.array([[0.0, 0.0, 0.0, 1.0]]), np.float32)
+    assert c0[0, 0] == 0.0
+
+
+def test_fp32_constants():
+    assert O.INV_PI_F32 == np.float32(1 / math.pi)
+    assert O.VIS_CLAMP_F32.view(np.uint32) == 0x3A83126F
+
+
+def test_quantize_weights_range_and_ratio():
+    rng = np.random.default_rng(9)
+    w = (rng.uniform(0, 1, (1000, 32)) * 10.0 ** rng.uniform(-30, 30, (1000, 1))).astype(np.float32)
+    w[:, 5] = 0
+    q = O.quantize_weights(w)
+    assert np.all(q[:, 5] == 0)
+    assert np.all((q.max(1) >= 2**23) & (q.max(1) < 2**24))
+    pos = w > 0
+    assert np.all(q[pos] >= 1)
+    law = O.selection_law(w)
+    ref = w / w.astype(np.float64).sum(1, keepdims=True)
+    big = ref > 1e-4
+    np.testing.assert_allclose(law[big], ref[big], rtol=2e-3)
+    np.testing.assert_allclose(law[ref > 1e-2], ref[ref > 1e-2], rtol=1e-5)
+
+
+@pytest.mark.parametrize("weights", [
+    [1.0, 2.0, 3.0, 4.0],
+    [0.0, 5.0, 0.0, 1e-3, 2.0, 0.0, 7.0, 0.5],
+    [1e-30, 3e-30, 2e-30, 0.0],
+])
+def test_wrs_frequencies_chi2(weights):
+    """Selection frequencies of the streaming reservoir match w_i / sum w."""
+    w = np.tile(np.array(weights, np.float32), (200_000, 1))
+    idx, pdf, wsum = O.wrs_select(w, np.arange(len(w)), seed=11, frame=0, view=0)
+    w64 = np.array(weights, np.float32).astype(np.float64)
+    p = w64 / w64.sum()
+    counts = np.bincount(idx, minlength=len(weights))
+    assert np.all(counts[p == 0] == 0)
+    nz = p > 0
+    stat = scipy.stats.chisquare(counts[nz], p[nz] * len(w))
+    assert stat.pvalue > 1e-4
+    np.testing.assert_allclose(pdf, p[idx], rtol=1e-12)
+
+
+def test_wrs_degenerate_rows():
+    w = np.array([[0, 0, 0], [0, 2, 0], [1, 0, 0]], np.float32)
+    idx, pdf, wsum = O.wrs_select(w, np.arange(3), seed=0, frame=0, view=0)
+    assert list(idx) == [-1, 1, 0]
+    assert list(pdf) == [0.0, 1.0, 1.0]
+    assert list(wsum) == [0.0, 2.0, 1.0]
+
+
+def test_estimator_unbiased_with_clamp_and_biased_without():
+    """E[V c / p] = exact DI when every light with c > 0 has p > 0: the
+    sample mean over many frames is within 4 sigma of sum V c."""
+    sc = S.scene_unit_cube(seed=0)
+    gb = S.gbuffer_points(1, 8, 8)
+    V = O.visibility(gb.pos, sc.lights, sc.spheres, sc.boxes)
+    c32 = O.contributions(gb.pos, gb.nrm, sc.lights, np.float32)
+    vis_pred = np.where(V > 0, 0.9, 0.0).astype(np.float32)   # a confident cache
+    vis_pred[:, 0] = 0.0                                       # ... wrong on light 0
+    w = O.light_weights_f32(vis_pred, c32)
+    p = O.selection_law(w)
+    E, var = O.estimator_moments(V, c32, p)
+    np.testing.assert_allclose(E, O.exact_di(V, c32), rtol=1e-12)
+    frames = 4000
+    acc = np.zeros(len(gb.pos))
+    ids = np.arange(len(gb.pos))
+    for f in range(frames):
+        idx, pdf, _ = O.wrs_select(w, ids, seed=3, frame=f, view=0)
+        ok = idx >= 0
+        j = np.maximum(idx, 0)
+        acc += np.where(ok, V[ids, j] * c32[ids, j] / np.where(ok, p[ids, j], 1), 0)
+    mean = acc / frames
+    sigma = np.sqrt(np.maximum(var, 0) / frames)
+    assert np.all(np.abs(mean - E) <= 4 * sigma + 1e-9)
+    # without the clamp, light 0 can never be picked: biased low
+    p_noclamp = O.selection_law(vis_pred * c32)
+    E_nc, _ = O.estimator_moments(V, c32, p_noclamp)
+    lost = V[:, 0] * c32[:, 0]
+    np.testing.assert_allclose(E - E_nc, lost, atol=1e-9)
+    assert lost.sum() > 0
+
+
+# ------------------------------------------------------- training samples --
+
+def test_training_positions_split_and_ranges():
+    sc = S.scene_heightfield(seed=1, n_lights=4, n_spheres=2, n_boxes=2)
+    gb = S.gbuffer_points(2, 16, 16, lo=(1, 2, 3), hi=(2, 3, 4))
+    pos = O.training_positions(64, sc.world_min, sc.world_max, gb.pos, 5, 9)
+    assert pos.dtype == np.float32 and pos.shape == (64, 3)
+    assert np.all((pos[:32] >= 0) & (pos[:32] < 10))
+    rows = {tuple(r) for r in gb.pos}
+    assert all(tuple(r) in rows for r in pos[32:])
+    assert not np.array_equal(pos, O.training_positions(64, sc.world_min, sc.world_max, gb.pos, 5, 10))
+    allw = O.training_positions(64, sc.world_min, sc.world_max, None, 5, 9)
+    np.testing.assert_array_equal(allw[:32], pos[:32])
+
+
+# ------------------------------------------------------------ learned part --
+
+def test_oracle_training_converges_to_brute_force_visibility_and_gains():
+    """Online training on the tiny scene: the cache's prediction approaches
+    brute-force ray-cast visibility, and sampling with it lowers the
+    estimator variance below sampling without a cache (v = 1)."""
+    cfg = S.config_by_name("tiny_fp32").with_(loss="bce", leaky_slope=0.01, batch_positions=512)
+    sc = S.scene_unit_cube(seed=0)
+    st = O.TrainState.fresh(S.init_params(cfg, seed=0))
+    test_pts = S.gbuffer_points(77, 32, 32)
+    Vt = O.visibility(test_pts.pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    mae0 = np.mean(np.abs(O.infer(cfg, st.params, test_pts.pos) - Vt))
+    maes = []
+    for f in range(300):
+        view = S.gbuffer_points(1000 + f, 16, 16)
+        O.train_step(cfg, st, sc, view.pos, seed=1, frame=f)
+        if f % 50 == 49:
+            maes.append(np.mean(np.abs(O.infer(cfg, st.params, test_pts.pos) - Vt)))
+    assert st.step == 300 and st.skipped == 0
+    assert maes[-1] < 0.5 * mae0 and maes[-1] < 0.12, (mae0, maes)
+    c = O.contributions(test_pts.pos, test_pts.nrm, sc.lights, np.float32)
+    vis = O.infer(cfg, st.params, test_pts.pos).astype(np.float32)
+    _, var_cache = O.estimator_moments(Vt, c, O.selection_law(O.light_weights_f32(vis, c)))
+    _, var_none = O.estimator_moments(Vt, c, O.selection_law(O.light_weights_f32(np.ones_like(vis), c)))
+    assert var_cache.mean() < 0.8 * var_none.mean()
