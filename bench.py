@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Throughput of the neural visibility cache hot path on synthetic frames.
+
+One step = one frame of the 1080p workload: an online training step (8192
+positions x 32 shadow rays against 64 occluders, forward, loss, backward,
+Adam over all 16.8M parameters) followed by inference + WRS + Neural DI of
+all 1920x1080 pixels, replayed as one CUDA graph.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank renders and trains its own view (weak
+scaling, no data-path collective); rank 0 prints the max-over-ranks time.
+--impl reference times the CPU oracle (float64 numpy) on a bounded sample
+of the same frame, extrapolated to the whole frame.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Mpixels/s encode+MLP+WRS and ms/frame incl. train step at 1080p/32 lights; "
+          "% roofline")
+WORKLOAD = "frame_1080p"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None, help="override the inference precision")
+    ap.add_argument("--pretrain", type=int, default=500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return dict(hbm=p["hbm_gbs"], bf16=p["bf16_tflops"],
+                    bf16_sustained=p["bf16_tflops_sustained"], src="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sustained=1700.0, src="fallback")
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx = float(c[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- workload --
+
+_WORKLOAD_CACHE = {}
+
+
+def workload(precision=None):
+    import nvc_synth as S
+    if "base" not in _WORKLOAD_CACHE:
+        cfg = S.config_by_name(WORKLOAD)
+        sc = S.scene_heightfield(seed=1, n_lights=32, n_spheres=32, n_boxes=32)
+        gb = S.gbuffer_heightfield(seed=1, width=1920, height=1080)
+        _WORKLOAD_CACHE["base"] = (cfg, sc, gb)
+    cfg, sc, gb = _WORKLOAD_CACHE["base"]
+    if precision:
+        cfg = cfg.with_(precision=precision)
+    return cfg, sc, gb
+
+
+def algorithmic(cfg, n_pixels):
+    """Algorithmic work of the stages (the roofline numerators)."""
+    F, Lv, L, W = cfg.n_features, cfg.n_levels, cfg.n_outputs, cfg.hidden[0]
+    dims = [cfg.n_inputs, *cfg.hidden, L]
+    macs = sum(a * b for a, b in zip(dims[:-1], dims[1:]))
+    n_params = cfg.n_levels * cfg.table_size * F + macs
+    return dict(
+        shade_flops=2.0 * macs * n_pixels,                  # MLP contraction
+        shade_hbm_bytes=40.0 * n_pixels,                    # pos+nrm in, idx/pdf/wsum/DI out
+        shade_gather_bytes=Lv * 8 * F * 4.0 * n_pixels,     # useful table bytes gathered
+        adam_bytes=32.0 * n_params,                         # read theta,m,v,g; write theta,m,v,g=0
+        n_params=n_params, macs_per_px=macs)
+
+
+# ------------------------------------------------------------- our arm ----
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_05930_gb300.build import build
+    build()
+    from paper_2506_05930_gb300 import nvc
+    import nvc_synth as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    cfg, sc, gb = workload(args.precision)
+    P = gb.n
+    scene = nvc.Scene.from_synth(sc)
+    pos = torch.from_numpy(gb.pos).cuda()
+    nrm = torch.from_numpy(gb.nrm).cuda()
+    cache = nvc.VisibilityCache(cfg)
+    cache.set_params(S.init_params(cfg, seed=0))
+    fused = cfg.precision != "fp32"
+    if not fused:
+        nvc.nvc_set_staging(cache.handle, P)
+    view = nvc.View(pos, nrm, rank, torch.empty(P, dtype=torch.int32, device="cuda"),
+                    torch.empty(P, device="cuda"), torch.empty(P, device="cuda"),
+                    torch.empty(P, device="cuda"))
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    seed = 1234 + rank
+    use_graph = not args.no_graph
+    # pretraining (untimed): 500 frames of online training on this view
+    for f in range(args.pretrain):
+        nvc.nvc_train_step(cache.handle, scene, pos, seed, f, loss)
+    torch.cuda.synchronize()
+    frame0 = args.pretrain
+
+    def frame(f):
+        nvc.nvc_frame(cache.handle, scene, [view], 0, seed, f, loss, use_graph=use_graph)
+
+    for w in range(args.warmup):
+        frame(frame0 + w)
+    nvc.nvc_stage_times(cache.handle)        # reset counters
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        frame(frame0 + args.warmup + k)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms_total = t0.elapsed_time(t1)
+    clk = clocks.stop() if clocks else None
+    _, launches = nvc.nvc_stage_times(cache.handle)
+    if world > 1:
+        tt = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_frame = ms_total / args.steps
+    value = world * P / (ms_frame * 1e-3) / 1e6
+
+    # per-stage attribution with CUDA events around each stage (eager frames)
+    nvc.nvc_set_profiling(cache.handle, True)
+    nvc.nvc_stage_times(cache.handle)
+    f0 = frame0 + args.warmup + args.steps
+    ta = torch.cuda.Event(enable_timing=True)
+    tb = torch.cuda.Event(enable_timing=True)
+    ta.record(stream)
+    for k in range(args.steps):
+        nvc.nvc_frame(cache.handle, scene, [view], 0, seed, f0 + k, loss, use_graph=False)
+    tb.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = ta.elapsed_time(tb) / args.steps
+    stage_ms, _ = nvc.nvc_stage_times(cache.handle)
+    nvc.nvc_set_profiling(cache.handle, False)
+    stage_ms = [m / args.steps for m in stage_ms]
+
+    # end to end through the public API with host buffers
+    pin_pos = torch.from_numpy(gb.pos).pin_memory()
+    pin_nrm = torch.from_numpy(gb.nrm).pin_memory()
+    out_h = [torch.empty(P, dtype=torch.int32).pin_memory()] + \
+        [torch.empty(P).pin_memory() for _ in range(3)]
+    h2d = pin_pos.numel() * 4 + pin_nrm.numel() * 4
+    d2h = sum(t.numel() * 4 for t in out_h)
+
+    def e2e_step(f):
+        pos.copy_(pin_pos, non_blocking=True)
+        nrm.copy_(pin_nrm, non_blocking=True)
+        frame(f)
+        for src, dst in zip((view.idx, view.pdf, view.wsum, view.radiance), out_h):
+            dst.copy_(src, non_blocking=True)
+        stream.synchronize()
+
+    f1 = f0 + args.steps
+    for w in range(2):
+        e2e_step(f1 + w)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e_steps = max(5, args.steps // 2)
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for k in range(e_steps):
+        e2e_step(f1 + 2 + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1) / e_steps
+    if world > 1:
+        tt = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_ms = float(tt.item())
+
+    # the plain float32 separate-kernel path, same frame (the baseline to beat)
+    base = None
+    if fused and rank == 0:
+        cache32 = nvc.VisibilityCache(cfg.with_(precision="fp32"))
+        cache32.set_params(cache.state()[0])
+        nvc.nvc_set_staging(cache32.handle, P)
+        for w in range(3):
+            nvc.nvc_frame(cache32.handle, scene, [view], 0, seed, f1 + w, loss, use_graph=use_graph)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for k in range(args.steps):
+            nvc.nvc_frame(cache32.handle, scene, [view], 0, seed, f1 + 3 + k, loss,
+                          use_graph=use_graph)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bm = b0.elapsed_time(b1) / args.steps
+        base = {"ms_per_step": bm, "value": P / (bm * 1e-3) / 1e6}
+        cache32.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    pk = peaks()
+    alg = algorithmic(cfg, P)
+    shade_s = stage_ms[3] * 1e-3
+    adam_s = stage_ms[2] * 1e-3
+    # the dominant stage sets the reported roofline
+    if stage_ms[3] >= stage_ms[2]:
+        achieved = alg["shade_flops"] / shade_s / 1e12
+        if fused:
+            roof = {"kernel": "shade (fused encode+MLP+WRS+DI)", "bound": "tensor",
+                    "achieved": achieved, "peak": pk["bf16_sustained"], "unit": "TFLOP/s"}
+        else:
+            roof = {"kernel": "shade (encode, MLP, WRS+DI kernels)", "bound": "hbm",
+                    "achieved": alg["shade_hbm_bytes"] / shade_s / 1e9, "peak": pk["hbm"],
+                    "unit": "GB/s"}
+    else:
+        roof = {"kernel": "adam", "bound": "hbm", "achieved": alg["adam_bytes"] / adam_s / 1e9,
+                "peak": pk["hbm"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["peak_source"] = pk["src"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_frame,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": cfg.precision, "data": "synthetic",
+        "config": {"workload": "frame_1080p: 1920x1080 heightfield+boxes view, 32 point lights, "
+                               "32 spheres + 32 boxes; hash grid 16 levels x 2 features x 2^19, "
+                               "MLP 32-64-64-64-32; training 8192 positions x 32 lights per frame",
+                   "global_batch": world * P, "pixels_per_gpu": P,
+                   "train_positions_per_frame": cfg.batch_positions, "parallelism": f"replica{world}",
+                   "graph": use_graph,
+                   "l2": "no flush: per-frame working set (G-buffer 50 MB, table+Adam state 270 MB) "
+                         "exceeds L2"},
+        "roofline": roof,
+        "stages_ms": {"train_data": stage_ms[0], "train_fwd_bwd": stage_ms[1],
+                      "adam": stage_ms[2], "shade": stage_ms[3], "eager_frame": eager_ms},
+        "infer_mpixels_s": P / shade_s / 1e6 if shade_s > 0 else None,
+        "train_ms": stage_ms[0] + stage_ms[1] + stage_ms[2],
+        "e2e": {"value": world * P / (e_ms * 1e-3) / 1e6, "unit": "Mpixels/s",
+                "ms_per_step": e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if base:
+        line["fp32_unfused_baseline"] = base
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(seconds_target=15.0)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------- the oracle on the CPU --
+
+def oracle_frame_sample(n_pixels=16384, n_positions=1024, seed=0):
+    """Time the oracle on a sample of the frame and extrapolate to the whole
+    frame: shading scales with pixels, training forward/backward with
+    positions, the dense Adam update is timed over every parameter."""
+    import numpy as np
+    from oracle import nvc as O
+    import nvc_synth as S
+    cfg, sc, gb = workload()
+    p = S.init_params(cfg, seed=seed)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(gb.n, n_pixels, replace=False)
+    t0 = time.perf_counter()
+    O.shade(cfg, p, gb.pos[pick], gb.nrm[pick], sc.lights, seed=1, frame=0)
+    t1 = time.perf_counter()
+    pos = O.training_positions(n_positions, sc.world_min, sc.world_max, gb.pos, 1, 0)
+    y = O.visibility(pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    _, g = O.gradients(cfg, p, pos, y)
+    t2 = time.perf_counter()
+    st = O.TrainState.fresh(p)
+    O.adam_update(st.params, g, st.m, st.v, 1, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps)
+    t3 = time.perf_counter()
+    frame_s = ((t1 - t0) * gb.n / n_pixels + (t2 - t1) * cfg.batch_positions / n_positions
+               + (t3 - t2))
+    return frame_s, t3 - t0, gb.n
+
+
+def cpu_baseline(seconds_target=15.0):
+    """Run the oracle in a child process with one BLAS thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "f, w, P = bench.oracle_frame_sample(131072, 4096); print(json.dumps([f, w, P]))" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    frame_s, wall, P = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": P / frame_s / 1e6, "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
+            "ms_per_frame": frame_s * 1e3, "wall_s": wall,
+            "sample": "131,072 random pixels of the 1080p frame shaded (inference+WRS+DI), "
+                      "training forward/backward on 4,096 of the 8,192 positions, one dense Adam "
+                      "update of all parameters; extrapolated linearly to the full frame"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_frame_sample(n_pixels=4096, n_positions=256)
+    frames, walls = [], []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        f, w, P = oracle_frame_sample(n_pixels=4096, n_positions=256, seed=k)
+        frames.append(f)
+        walls.append(w)
+    frame_s = sum(frames) / len(frames)
+    value = P / frame_s / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "frame_1080p (CPU float64 oracle, extrapolated from a sample)"},
+        "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step 4,096 pixels shaded, training forward/backward on "
+                                   "256 positions, one dense Adam update; extrapolated to the "
+                                   "1080p frame", "wall_s_per_step": sum(walls) / len(walls)},
+        "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

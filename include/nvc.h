@@ -1,0 +1,312 @@
+/*
+ * nvc.h -- C ABI of the neural visibility cache hot path (libnvc.so).
+ *
+ * The method (Bokshansky & Meister, "Neural Visibility Cache for Real-Time
+ * Light Sampling", JCGT 14(2), 2025): every shading point is encoded by a
+ * multi-resolution hash grid (Sections 3.1, 3.3), a small MLP predicts one
+ * sigmoid visibility per light (Section 3.3), weighted reservoir sampling
+ * picks one light per pixel with weights visibility x unshadowed
+ * contribution (Section 3.1), or the Neural-DI variant sums them
+ * (Section 3.2); the network is trained online every frame against
+ * shadow-ray targets (Section 3.4).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named in the comments as "device" point to GPU memory owned
+ *     by the caller, row-major and densely packed, float32 unless stated.
+ *     The library never frees or retains them past the call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every
+ *     compute call is asynchronous on it, allocates nothing and never
+ *     synchronises the host, unless its comment says otherwise.
+ *   - Argument errors are detected on the host before any work is queued
+ *     and returned as NVC_ERR_INVALID_ARG / NVC_ERR_UNSUPPORTED; launch
+ *     failures as NVC_ERR_CUDA.  nvc_last_error() gives a message.  Errors
+ *     found on the device (non-finite gradients, a bounded wait that ran
+ *     out) are recorded in the handle's device status and read by
+ *     nvc_sync_status().
+ *   - A handle is not thread-safe: calls on one handle must not overlap on
+ *     the host.  Calls on one handle queued on different streams must be
+ *     ordered by the caller.
+ *   - Positions are in world space; the encoding normalises them with the
+ *     configuration's bounds and clamps to [0,1]^3.
+ */
+#ifndef NVC_H
+#define NVC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NVC_VERSION 1
+
+#define NVC_MAX_LEVELS 32
+#define NVC_MAX_FEATURES 8
+#define NVC_MAX_HIDDEN_LAYERS 8
+#define NVC_MAX_WIDTH 128
+#define NVC_MAX_LIGHTS 256
+#define NVC_MAX_OCCLUDERS 2048
+
+typedef enum nvc_status {
+  NVC_OK = 0,
+  NVC_ERR_INVALID_ARG = 1,
+  NVC_ERR_UNSUPPORTED = 2,
+  NVC_ERR_CUDA = 3,
+  NVC_ERR_NONFINITE = 4,
+  NVC_ERR_TIMEOUT = 5
+} nvc_status;
+
+typedef enum nvc_precision {
+  NVC_PREC_FP32 = 0,   /* SIMT float32 */
+  NVC_PREC_FP16 = 1,   /* tensor cores, fp16 operands, fp32 accumulation */
+  NVC_PREC_BF16 = 2,   /* tensor cores, bf16 operands, fp32 accumulation */
+  NVC_PREC_FP8 = 3     /* tensor cores, e4m3 operands with per-tensor scale */
+} nvc_precision;
+
+typedef enum nvc_loss { NVC_LOSS_L2 = 0, NVC_LOSS_BCE = 1 } nvc_loss;
+
+typedef enum nvc_lr_schedule {
+  NVC_LR_CONSTANT = 0,
+  NVC_LR_RAMP = 1      /* lr -> lr_end linearly over lr_ramp_steps (Section 3.4) */
+} nvc_lr_schedule;
+
+/* Hyper-parameters of one cache (Sections 3.3 and 3.4). */
+typedef struct nvc_config {
+  int32_t n_levels;          /* hash-grid levels, 1..NVC_MAX_LEVELS */
+  int32_t n_features;        /* features per level: 1, 2, 4 or 8 */
+  int32_t log2_table_size;   /* T = 2^log2_table_size rows per level, 4..24 */
+  int32_t base_resolution;   /* N_min >= 1; level l has floor(N_min*growth^l) cells */
+  double growth;             /* >= 1 */
+  int32_t n_hidden;          /* hidden layers, 1..NVC_MAX_HIDDEN_LAYERS */
+  int32_t hidden_width;      /* neurons per hidden layer, multiple of 16, <= 128 */
+  int32_t n_outputs;         /* lights = output neurons, 1..NVC_MAX_LIGHTS */
+  float leaky_slope;         /* hidden activation slope for z <= 0 (0 = ReLU) */
+  int32_t precision;         /* nvc_precision of the inference MLP */
+  int32_t train_precision;   /* nvc_precision of training (FP32 or FP16) */
+  int32_t loss;              /* nvc_loss */
+  int32_t lr_schedule;       /* nvc_lr_schedule */
+  float lr;                  /* base / initial learning rate */
+  float lr_end;              /* final learning rate of NVC_LR_RAMP */
+  int32_t lr_ramp_steps;
+  float beta1, beta2, eps;   /* Adam */
+  float loss_scale;          /* static loss scale (1 = none) */
+  int32_t batch_positions;   /* training positions per step (each traced to every light) */
+  float bounds_min[3];       /* encoding domain */
+  float bounds_max[3];
+} nvc_config;
+
+/* Analytic scene: point lights and occluders (all device pointers). */
+typedef struct nvc_scene {
+  const float* lights;       /* [n_lights][4]: x, y, z, intensity */
+  int32_t n_lights;          /* must equal the configuration's n_outputs */
+  const float* spheres;      /* [n_spheres][4]: cx, cy, cz, radius; may be NULL if 0 */
+  int32_t n_spheres;
+  const float* boxes;        /* [n_boxes][6]: lo x, y, z, hi x, y, z; may be NULL if 0 */
+  int32_t n_boxes;
+  float world_min[3];        /* box that world-space training positions are drawn from */
+  float world_max[3];
+} nvc_scene;
+
+/* Device-side status, read by nvc_sync_status. */
+typedef struct nvc_counters {
+  int32_t step;              /* Adam updates applied */
+  int32_t skipped;           /* training steps skipped for non-finite gradients */
+  int32_t error_flags;       /* bit 0: non-finite seen; bit 1: bounded wait ran out */
+  int32_t frames;            /* nvc_frame calls queued */
+} nvc_counters;
+
+typedef struct nvc_handle nvc_handle;
+
+/* ---- lifetime ---------------------------------------------------------- */
+
+/* Validates `cfg`, allocates the handle's device state (FP32 master
+ * parameters, Adam moments, gradients, low-precision copies, training
+ * workspace for cfg->batch_positions positions) on the current device and
+ * zero-initialises it.  Parameters must then be set with nvc_set_state.
+ * Synchronous.  On failure *out is NULL and nvc_last_error(NULL) explains. */
+nvc_status nvc_create(const nvc_config* cfg, nvc_handle** out);
+
+/* Frees everything nvc_create allocated; waits for the device first.
+ * NULL is ignored. */
+void nvc_destroy(nvc_handle* h);
+
+/* Message of the last failed call on `h`, or of the last failed
+ * nvc_create on this thread when h is NULL.  Never NULL. */
+const char* nvc_last_error(const nvc_handle* h);
+
+/* Number of float32 parameters of a configuration (the flat layout is
+ * [table: levels x T x F][W_1: width x n_in][W_2..][W_out: L x width], every
+ * matrix row-major [out][in], no biases), or -1 if `cfg` is invalid. */
+int64_t nvc_param_count(const nvc_config* cfg);
+
+/* Level resolution N_l = floor(N_min * growth^l) (computed in double), or
+ * -1 for an invalid level.  Exposed so callers can check the encoding. */
+int32_t nvc_level_resolution(const nvc_config* cfg, int32_t level);
+
+/* ---- state ------------------------------------------------------------- */
+
+/* Copies parameters (device [n_params]) into the handle and refreshes the
+ * low-precision copies.  adam_m / adam_v (device [n_params]) may be NULL,
+ * meaning zero moments; `step` is the number of updates already applied. */
+nvc_status nvc_set_state(nvc_handle* h, const float* params, const float* adam_m,
+                         const float* adam_v, int32_t step, void* stream);
+
+/* Copies parameters and moments out (device [n_params] each; any may be
+ * NULL).  Asynchronous; the step count is read by nvc_sync_status. */
+nvc_status nvc_get_state(nvc_handle* h, float* params, float* adam_m, float* adam_v,
+                         void* stream);
+
+/* Capacity, in pixels, of the buffers the separate-kernel shading path
+ * (nvc_shade with fused = 0, and FP32 nvc_infer) stages encoded features and
+ * visibility in; larger inputs are processed in chunks of this size.  The
+ * default is 65,536.  Synchronous; reallocates. */
+nvc_status nvc_set_staging(nvc_handle* h, int64_t max_pixels);
+
+/* Synchronises `stream`, then reads the device status into *out (host). */
+nvc_status nvc_sync_status(nvc_handle* h, void* stream, nvc_counters* out);
+
+/* ---- inference (Sections 3.1, 3.3) -------------------------------------- */
+
+/* Hash-grid encoding: feat (device [n][levels*F], level-major) of pos
+ * (device [n][3]).  Per level, the 8 corners of the cell containing
+ * x_hat * N_l are hashed (x*1 ^ y*2654435761 ^ z*805459861 mod 2^32, mod T)
+ * and trilinearly blended.  n = 0 is a no-op. */
+nvc_status nvc_encode(nvc_handle* h, const float* pos, int64_t n, float* feat,
+                      void* stream);
+
+/* Predicted visibility (device [n][L]) = sigmoid(MLP(encode(pos))), in the
+ * configuration's inference precision. */
+nvc_status nvc_infer(nvc_handle* h, const float* pos, int64_t n, float* vis,
+                     void* stream);
+
+/* ---- light sampling (Sections 3.1, 3.2) -------------------------------- */
+
+/* Light weights: c (device [n][L]) = unshadowed contribution of each point
+ * light to a Lambertian (albedo 1) point with normal nrm,
+ * c = I * max(0, n.w) / (pi * max(|d|^2, 1e-6)), d = light - pos,
+ * w = d / |d|; evaluated as ((I * (1/pi)) * (n.d)) / (sqrt(d.d) *
+ * max(d.d, 1e-6)) for n.d > 0 (else 0), every operation a correctly
+ * rounded float32 one, dot products summed x, y then z.  w (device
+ * [n][L], may be NULL) = max(vis, 0.001) * c, the weights the sampler uses
+ * (the Section 3.1 clamp).  vis may be NULL when w is NULL. */
+nvc_status nvc_light_weights(const nvc_scene* scene, const float* pos, const float* nrm,
+                             const float* vis, int64_t n, float* c, float* w,
+                             void* stream);
+
+/* Weighted reservoir sampling of one light per row of w (device [n][n_lights],
+ * float32 >= 0).  Integer form: q_i = max(1, floor(w_i * 2^(23-e))) for
+ * w_i > 0 (e = floor(log2 max w)), Q_i = q_1 + .. + q_i; candidate i
+ * replaces the reservoir iff r_i * Q_i < q_i * 2^32 with r_i word i of the
+ * Philox-4x32-10 stream counter (pixel_offset + row, frame, view,
+ * (i/4) << 4 | 0), key (seed low, seed high).  Outputs (device [n], any may
+ * be NULL): idx (-1 if all weights are 0), pdf = w_idx / sum w, wsum. */
+nvc_status nvc_wrs_from_weights(const float* w, int64_t n, int32_t n_lights, uint64_t seed,
+                                uint32_t frame, uint32_t view, int64_t pixel_offset,
+                                int32_t* idx, float* pdf, float* wsum, void* stream);
+
+/* Inference + light weights + WRS for n pixels (pos, nrm device [n][3]). */
+nvc_status nvc_wrs_sample(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                          const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
+                          uint32_t view, int64_t pixel_offset, int32_t* idx, float* pdf,
+                          float* wsum, void* stream);
+
+/* Neural direct illumination (Section 3.2): radiance (device [n]) =
+ * sum_i vis_i * c_i with the raw predicted visibility, no shadow rays. */
+nvc_status nvc_direct_illum(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                            const float* nrm, int64_t n, float* radiance, void* stream);
+
+/* The per-pixel hot path in one pass: inference, WRS and Neural DI.
+ * Outputs (device [n], any may be NULL) as nvc_wrs_sample and
+ * nvc_direct_illum.  fused != 0 runs the single fused kernel of the
+ * configuration's precision; fused == 0 runs the separate FP32 kernels
+ * (encode, MLP, sampling) with visibility staged in the handle. */
+nvc_status nvc_shade(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                     const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
+                     uint32_t view, int64_t pixel_offset, int32_t* idx, float* pdf,
+                     float* wsum, float* radiance, int32_t fused, void* stream);
+
+/* ---- training (Section 3.4) -------------------------------------------- */
+
+/* Binary visibility vis (device [n][n_lights], 0 or 1) of every light from
+ * every position: the segment x + t (l - x), t in [1e-4, 1 - 1e-4], is
+ * blocked by a sphere whose centre is closer than its radius to the segment
+ * or by a box the segment touches (slab test); float32 arithmetic. */
+nvc_status nvc_trace_visibility(const nvc_scene* scene, const float* pos, int64_t n,
+                                float* vis, void* stream);
+
+/* Training positions (device [batch][3]): the first half (all of them when
+ * screen_pos is NULL or n_screen = 0) uniform in the scene's world box,
+ * x = lo + u * (hi - lo), u the top 24 bits of Philox stream
+ * (j, frame, 0, 1) times 2^-24; the rest are G-buffer pixels
+ * screen_pos[floor(r * n_screen / 2^32)], r from stream (j, frame, 0, 2). */
+nvc_status nvc_training_positions(const nvc_scene* scene, const float* screen_pos,
+                                  int64_t n_screen, int64_t batch, uint64_t seed,
+                                  uint32_t frame, float* pos, void* stream);
+
+/* One online training step: batch_positions positions (as
+ * nvc_training_positions), shadow-ray targets, forward, loss (L2 or BCE,
+ * mean over positions x lights), hand-written backward, Adam (bias
+ * corrected; lr from the schedule).  A non-finite gradient skips the
+ * update and is counted.  loss_out (device double, may be NULL) receives
+ * the unscaled loss. */
+nvc_status nvc_train_step(nvc_handle* h, const nvc_scene* scene, const float* screen_pos,
+                          int64_t n_screen, uint64_t seed, uint32_t frame, double* loss_out,
+                          void* stream);
+
+/* The training step without the update: grad (device [n_params]) receives
+ * d loss / d params (unscaled) for the same batch nvc_train_step would use. */
+nvc_status nvc_train_gradient(nvc_handle* h, const nvc_scene* scene, const float* screen_pos,
+                              int64_t n_screen, uint64_t seed, uint32_t frame, float* grad,
+                              double* loss_out, void* stream);
+
+/* Differentiable forward for autograd wrappers: logits (device [n][L]) of
+ * pos (device [n][3]), n <= batch_positions; activations are kept in the
+ * handle for the next nvc_mlp_backward. */
+nvc_status nvc_mlp_forward(nvc_handle* h, const float* pos, int64_t n, float* logits,
+                           void* stream);
+
+/* Adjoint of the last nvc_mlp_forward: grad (device [n_params]) receives
+ * sum_{b,i} dlogits[b][i] * d logits[b][i] / d params (overwritten). */
+nvc_status nvc_mlp_backward(nvc_handle* h, const float* pos, int64_t n,
+                            const float* dlogits, float* grad, void* stream);
+
+/* ---- one frame ---------------------------------------------------------- */
+
+/* One view of a frame: its G-buffer and its outputs (device [n_pixels];
+ * idx/pdf/wsum/radiance may be NULL). */
+typedef struct nvc_view {
+  const float* pos;
+  const float* nrm;
+  int64_t n_pixels;
+  uint32_t view_id;
+  int32_t* idx;
+  float* pdf;
+  float* wsum;
+  float* radiance;
+} nvc_view;
+
+#define NVC_FRAME_WORLD_ONLY (-1) /* train_view: world-space training positions only */
+#define NVC_FRAME_NO_TRAINING (-2) /* train_view: no training step this frame */
+
+/* One frame: a training step (Section 3.4: one step per frame) whose
+ * screen-space positions come from view `train_view` (or see the two
+ * constants above), then inference + WRS + Neural DI of every view.
+ * use_graph != 0 records the frame's launches as a CUDA graph and replays
+ * it, updating the recorded graph in place when arguments change. */
+nvc_status nvc_frame(nvc_handle* h, const nvc_scene* scene, const nvc_view* views,
+                     int32_t n_views, int32_t train_view, uint64_t seed, uint32_t frame,
+                     double* loss_out, int32_t use_graph, void* stream);
+
+/* ---- profiling ---------------------------------------------------------- */
+
+/* When enabled, the handle records CUDA events around each stage it
+ * launches; nvc_stage_times (synchronising) returns the summed milliseconds
+ * per stage since the last reset: [0] training data, [1] training
+ * forward+backward, [2] Adam, [3] shade (inference+WRS+DI). */
+nvc_status nvc_set_profiling(nvc_handle* h, int32_t enable);
+nvc_status nvc_stage_times(nvc_handle* h, double* ms_out, int32_t n_out, int64_t* launches_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NVC_H */

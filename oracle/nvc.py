@@ -206,9 +206,12 @@ def contributions(pos, nrm, lights, dtype=np.float64) -> np.ndarray:
     """Unshadowed contribution c_i of every point light, [n, L].
 
     Lambertian BRDF (albedo 1) times the clamped cosine, times the light's
-    intensity over the squared distance: c_i = I_i * max(0, n.w_i) / pi /
-    max(d_i^2, 1e-6).  With dtype=float32 the operations are taken in the
-    order the light-weight decision uses, each rounded to float32.
+    intensity over the squared distance (the integrand of Eq. 1 without
+    visibility, for a point light): with d = l_i - x,
+        c_i = I_i * max(0, n.d / |d|) / pi / max(|d|^2, 1e-6)
+            = ((I_i / pi) * (n.d)) / (|d| * max(|d|^2, 1e-6))   for n.d > 0.
+    With dtype=float32 the second form is evaluated operation by operation,
+    each rounded to float32, which is the order the light weights use.
     """
     t = np.dtype(dtype)
     P = np.asarray(pos, t)[:, None, :]
@@ -218,12 +221,12 @@ def contributions(pos, nrm, lights, dtype=np.float64) -> np.ndarray:
     d = Lp - P
     d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
     ndl = (N[..., 0] * d[..., 0] + N[..., 1] * d[..., 1]) + N[..., 2] * d[..., 2]
-    dist = np.sqrt(d2)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        cos = np.where(ndl > 0, ndl / np.where(dist > 0, dist, t.type(1)), t.type(0))
     inv_pi = INV_PI_F32 if t == np.float32 else 1.0 / math.pi
     d2min = D2_MIN_F32 if t == np.float32 else 1e-6
-    return ((I * cos) * t.type(inv_pi)) / np.maximum(d2, t.type(d2min))
+    num = (I * t.type(inv_pi)) * ndl
+    den = np.sqrt(d2) * np.maximum(d2, t.type(d2min))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(ndl > 0, num / np.where(ndl > 0, den, t.type(1)), t.type(0))
 
 
 def light_weights_f32(vis, c32) -> np.ndarray:

@@ -1,0 +1,753 @@
+// C ABI of libnvc: argument checks, device-state lifetime and the order in
+// which the kernels of each entry point are queued.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nvc_internal.cuh"
+
+using namespace nvc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+nvc_status fail(nvc_handle* h, nvc_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h)
+    h->err = buf;
+  else
+    g_create_error = buf;
+  return st;
+}
+
+nvc_status cuda_fail(nvc_handle* h, cudaError_t e, const char* what) {
+  return fail(h, NVC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define NVC_CUDA(h, expr)                                   \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #expr); \
+  } while (0)
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int level_res(const nvc_config* c, int l) {
+  return (int)std::floor((double)c->base_resolution * std::pow(c->growth, (double)l));
+}
+
+nvc_status check_config(const nvc_config* c, std::string* why) {
+  auto bad = [&](const char* m) {
+    *why = m;
+    return NVC_ERR_INVALID_ARG;
+  };
+  if (!c) return bad("config is NULL");
+  if (c->n_levels < 1 || c->n_levels > NVC_MAX_LEVELS) return bad("n_levels out of range");
+  if (c->n_features != 1 && c->n_features != 2 && c->n_features != 4 && c->n_features != 8)
+    return bad("n_features must be 1, 2, 4 or 8");
+  if (c->log2_table_size < 4 || c->log2_table_size > 24) return bad("log2_table_size out of range");
+  if (c->base_resolution < 1) return bad("base_resolution must be >= 1");
+  if (!(c->growth >= 1.0) || !std::isfinite(c->growth)) return bad("growth must be >= 1");
+  if (level_res(c, c->n_levels - 1) > (1 << 22)) return bad("finest level resolution above 2^22");
+  if (c->n_hidden < 1 || c->n_hidden > NVC_MAX_HIDDEN_LAYERS) return bad("n_hidden out of range");
+  if (c->hidden_width < 16 || c->hidden_width > NVC_MAX_WIDTH || c->hidden_width % 16)
+    return bad("hidden_width must be a multiple of 16 in [16, 128]");
+  if (c->n_outputs < 1 || c->n_outputs > NVC_MAX_LIGHTS) return bad("n_outputs out of range");
+  if (c->n_levels * c->n_features > NVC_MAX_WIDTH) return bad("encoded width above 128");
+  if (!(c->leaky_slope >= 0.0f && c->leaky_slope < 1.0f)) return bad("leaky_slope not in [0,1)");
+  if (c->precision < NVC_PREC_FP32 || c->precision > NVC_PREC_FP8) return bad("bad precision");
+  if (c->train_precision != NVC_PREC_FP32 && c->train_precision != NVC_PREC_FP16)
+    return bad("train_precision must be FP32 or FP16");
+  if (c->loss != NVC_LOSS_L2 && c->loss != NVC_LOSS_BCE) return bad("bad loss");
+  if (c->lr_schedule != NVC_LR_CONSTANT && c->lr_schedule != NVC_LR_RAMP)
+    return bad("bad lr_schedule");
+  if (c->lr_schedule == NVC_LR_RAMP && c->lr_ramp_steps < 1) return bad("lr_ramp_steps < 1");
+  if (!(c->lr > 0.0f) || !std::isfinite(c->lr)) return bad("lr must be > 0");
+  if (!(c->beta1 >= 0.0f && c->beta1 < 1.0f) || !(c->beta2 >= 0.0f && c->beta2 < 1.0f))
+    return bad("betas must be in [0,1)");
+  if (!(c->eps >= 0.0f)) return bad("eps must be >= 0");
+  if (!(c->loss_scale > 0.0f) || !std::isfinite(c->loss_scale)) return bad("loss_scale must be > 0");
+  if (c->batch_positions < 1 || c->batch_positions > (1 << 24)) return bad("batch_positions out of range");
+  for (int d = 0; d < 3; ++d)
+    if (!(c->bounds_max[d] > c->bounds_min[d]) || !std::isfinite(c->bounds_max[d]) ||
+        !std::isfinite(c->bounds_min[d]))
+      return bad("bounds_max must exceed bounds_min");
+  return NVC_OK;
+}
+
+nvc_status check_scene(nvc_handle* h, const nvc_scene* sc, int expect_lights) {
+  if (!sc) return fail(h, NVC_ERR_INVALID_ARG, "scene is NULL");
+  if (!sc->lights || !aligned(sc->lights, 16))
+    return fail(h, NVC_ERR_INVALID_ARG, "scene lights NULL or not 16-byte aligned");
+  if (sc->n_lights < 1 || sc->n_lights > NVC_MAX_LIGHTS)
+    return fail(h, NVC_ERR_INVALID_ARG, "n_lights out of range");
+  if (expect_lights > 0 && sc->n_lights != expect_lights)
+    return fail(h, NVC_ERR_INVALID_ARG, "n_lights (%d) != n_outputs (%d)", sc->n_lights,
+                expect_lights);
+  if (sc->n_spheres < 0 || sc->n_boxes < 0 ||
+      sc->n_spheres + sc->n_boxes > NVC_MAX_OCCLUDERS)
+    return fail(h, NVC_ERR_INVALID_ARG, "occluder counts out of range");
+  if (sc->n_spheres > 0 && (!sc->spheres || !aligned(sc->spheres, 16)))
+    return fail(h, NVC_ERR_INVALID_ARG, "spheres NULL or not 16-byte aligned");
+  if (sc->n_boxes > 0 && (!sc->boxes || !aligned(sc->boxes, 4)))
+    return fail(h, NVC_ERR_INVALID_ARG, "boxes NULL or misaligned");
+  for (int d = 0; d < 3; ++d)
+    if (!(sc->world_max[d] >= sc->world_min[d]))
+      return fail(h, NVC_ERR_INVALID_ARG, "world_max below world_min");
+  return NVC_OK;
+}
+
+nvc_status check_ptr(nvc_handle* h, const void* p, const char* name, size_t align = 4) {
+  if (!p) return fail(h, NVC_ERR_INVALID_ARG, "%s is NULL", name);
+  if (!aligned(p, align)) return fail(h, NVC_ERR_INVALID_ARG, "%s is misaligned", name);
+  return NVC_OK;
+}
+
+#define NVC_TRY(expr)              \
+  do {                             \
+    nvc_status st_ = (expr);       \
+    if (st_ != NVC_OK) return st_; \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e == cudaSuccess) e = cudaMemset(*p, 0, sizeof(T) * count);
+  return e;
+}
+
+__global__ void set_status_kernel(int32_t* status, int step) {
+  status[kStStep] = step;
+  status[kStNonFinite] = 0;
+}
+
+__global__ void bump_frames_kernel(int32_t* status) { status[kStFrames] += 1; }
+
+// ---- profiling: event pairs resolved when the caller asks ------------------
+struct ProfEvents {
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, int>> open;  // (stage, index of start event)
+  size_t next = 0;
+};
+
+}  // namespace
+
+// Per-handle profiling state lives beside the handle (kept out of the struct
+// shared with the kernels' translation units).
+namespace {
+struct ProfTable {
+  nvc_handle* h;
+  ProfEvents ev;
+};
+std::vector<ProfTable*> g_prof;
+ProfEvents* prof_of(nvc_handle* h) {
+  for (auto* t : g_prof)
+    if (t->h == h) return &t->ev;
+  return nullptr;
+}
+
+struct StageScope {
+  nvc_handle* h;
+  cudaStream_t s;
+  int stage;
+  int start = -1;
+  StageScope(nvc_handle* hh, cudaStream_t ss, int st) : h(hh), s(ss), stage(st) {
+    if (!h->profiling) return;
+    ProfEvents* pe = prof_of(h);
+    if (!pe || pe->next + 2 > pe->pool.size()) return;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    start = (int)pe->next;
+    pe->next += 2;
+    cudaEventRecord(pe->pool[start], s);
+  }
+  ~StageScope() {
+    if (start < 0) return;
+    ProfEvents* pe = prof_of(h);
+    cudaEventRecord(pe->pool[start + 1], s);
+    pe->open.push_back({stage, start});
+  }
+};
+
+void count_launches(nvc_handle* h, int n) { h->launches += n; }
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+int64_t nvc_param_count(const nvc_config* cfg) {
+  std::string why;
+  if (check_config(cfg, &why) != NVC_OK) return -1;
+  const int64_t din = (int64_t)cfg->n_levels * cfg->n_features;
+  int64_t n = (int64_t)cfg->n_levels * ((int64_t)1 << cfg->log2_table_size) * cfg->n_features;
+  n += din * cfg->hidden_width;
+  n += (int64_t)(cfg->n_hidden - 1) * cfg->hidden_width * cfg->hidden_width;
+  n += (int64_t)cfg->n_outputs * cfg->hidden_width;
+  return n;
+}
+
+int32_t nvc_level_resolution(const nvc_config* cfg, int32_t level) {
+  std::string why;
+  if (check_config(cfg, &why) != NVC_OK || level < 0 || level >= cfg->n_levels) return -1;
+  return level_res(cfg, level);
+}
+
+const char* nvc_last_error(const nvc_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+nvc_status nvc_create(const nvc_config* cfg, nvc_handle** out) {
+  if (!out) return fail(nullptr, NVC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (check_config(cfg, &why) != NVC_OK) return fail(nullptr, NVC_ERR_INVALID_ARG, "%s", why.c_str());
+  nvc_handle* h = new (std::nothrow) nvc_handle();
+  if (!h) return fail(nullptr, NVC_ERR_CUDA, "out of host memory");
+  h->cfg = *cfg;
+  h->L = cfg->n_outputs;
+  h->F = cfg->n_features;
+  h->T = 1 << cfg->log2_table_size;
+  h->din = cfg->n_levels * cfg->n_features;
+  h->width = cfg->hidden_width;
+  h->n_hidden = cfg->n_hidden;
+  h->n_layers = cfg->n_hidden + 1;
+  for (int l = 0; l < cfg->n_levels; ++l) h->res[l] = level_res(cfg, l);
+  h->n_table = (int64_t)cfg->n_levels * h->T * h->F;
+  int64_t off = h->n_table;
+  for (int k = 0; k < h->n_layers; ++k) {
+    h->w_in[k] = k == 0 ? h->din : h->width;
+    h->w_out[k] = k == h->n_layers - 1 ? h->L : h->width;
+    h->w_off[k] = off;
+    off += (int64_t)h->w_in[k] * h->w_out[k];
+  }
+  h->n_params = off;
+  h->B = cfg->batch_positions;
+
+  auto cleanup_fail = [&](cudaError_t e, const char* what) {
+    nvc_status st = fail(nullptr, NVC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    nvc_destroy(h);
+    return st;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return cleanup_fail(e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) !=
+      cudaSuccess)
+    return cleanup_fail(e, "cudaDeviceGetAttribute");
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (mlp_fwd_smem_bytes(h) > (size_t)smem_optin) {
+    nvc_status st = fail(nullptr, NVC_ERR_UNSUPPORTED,
+                         "MLP of this shape needs %zu B of shared memory (limit %d)",
+                         mlp_fwd_smem_bytes(h), smem_optin);
+    nvc_destroy(h);
+    return st;
+  }
+  const size_t np4 = (size_t)((h->n_params + 3) / 4) * 4;
+  const int maxdim = h->width > h->L ? h->width : h->L;
+  const size_t B = (size_t)h->B;
+  if ((e = dalloc(&h->params, np4)) || (e = dalloc(&h->grad, np4)) ||
+      (e = dalloc(&h->adam_m, np4)) || (e = dalloc(&h->adam_v, np4)) ||
+      (e = dalloc(&h->t_pos, B * 3)) || (e = dalloc(&h->t_target, B * h->L)) ||
+      (e = dalloc(&h->t_feat, B * h->din)) ||
+      (e = dalloc(&h->t_act, (size_t)h->n_hidden * B * h->width)) ||
+      (e = dalloc(&h->t_logits, B * h->L)) ||
+      (e = dalloc(&h->t_delta, (size_t)h->n_layers * B * maxdim)) ||
+      (e = dalloc(&h->t_dfeat, B * h->din)) || (e = dalloc(&h->loss_partials, 256)) ||
+      (e = dalloc(&h->status, kStWords)) || (e = dalloc(&h->adam_scalars, 1)))
+    return cleanup_fail(e, "cudaMalloc");
+  h->n_loss_partials = 256;
+  h->mlp_packed_bytes = mlp_packed_bytes(h);
+  if (h->mlp_packed_bytes) {
+    if ((e = cudaMalloc(&h->mlp_packed, h->mlp_packed_bytes)) != cudaSuccess)
+      return cleanup_fail(e, "cudaMalloc");
+    cudaMemset(h->mlp_packed, 0, h->mlp_packed_bytes);
+  }
+  h->stage_pixels = 65536;
+  if ((e = dalloc(&h->s_feat, (size_t)h->stage_pixels * h->din)) ||
+      (e = dalloc(&h->s_vis, (size_t)h->stage_pixels * h->L)))
+    return cleanup_fail(e, "cudaMalloc");
+  if ((e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cleanup_fail(e, "cudaStreamCreate");
+  ProfTable* pt = new ProfTable{h, {}};
+  g_prof.push_back(pt);
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup_fail(e, "cudaDeviceSynchronize");
+  *out = h;
+  return NVC_OK;
+}
+
+void nvc_destroy(nvc_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  cudaFree(h->params);
+  cudaFree(h->grad);
+  cudaFree(h->adam_m);
+  cudaFree(h->adam_v);
+  cudaFree(h->mlp_packed);
+  cudaFree(h->t_pos);
+  cudaFree(h->t_target);
+  cudaFree(h->t_feat);
+  cudaFree(h->t_act);
+  cudaFree(h->t_logits);
+  cudaFree(h->t_delta);
+  cudaFree(h->t_dfeat);
+  cudaFree(h->loss_partials);
+  cudaFree(h->status);
+  cudaFree(h->adam_scalars);
+  cudaFree(h->s_feat);
+  cudaFree(h->s_vis);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  for (size_t i = 0; i < g_prof.size(); ++i)
+    if (g_prof[i]->h == h) {
+      for (cudaEvent_t ev : g_prof[i]->ev.pool) cudaEventDestroy(ev);
+      delete g_prof[i];
+      g_prof.erase(g_prof.begin() + i);
+      break;
+    }
+  delete h;
+}
+
+nvc_status nvc_set_staging(nvc_handle* h, int64_t max_pixels) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (max_pixels < 128 || max_pixels > ((int64_t)1 << 26))
+    return fail(h, NVC_ERR_INVALID_ARG, "max_pixels out of range");
+  NVC_CUDA(h, cudaDeviceSynchronize());
+  cudaFree(h->s_feat);
+  cudaFree(h->s_vis);
+  h->s_feat = h->s_vis = nullptr;
+  h->stage_pixels = 0;
+  NVC_CUDA(h, dalloc(&h->s_feat, (size_t)max_pixels * h->din));
+  NVC_CUDA(h, dalloc(&h->s_vis, (size_t)max_pixels * h->L));
+  h->stage_pixels = max_pixels;
+  return NVC_OK;
+}
+
+nvc_status nvc_set_state(nvc_handle* h, const float* params, const float* adam_m,
+                         const float* adam_v, int32_t step, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  NVC_TRY(check_ptr(h, params, "params"));
+  if (step < 0) return fail(h, NVC_ERR_INVALID_ARG, "step < 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(float) * (size_t)h->n_params;
+  NVC_CUDA(h, cudaMemcpyAsync(h->params, params, bytes, cudaMemcpyDeviceToDevice, s));
+  if (adam_m)
+    NVC_CUDA(h, cudaMemcpyAsync(h->adam_m, adam_m, bytes, cudaMemcpyDeviceToDevice, s));
+  else
+    NVC_CUDA(h, cudaMemsetAsync(h->adam_m, 0, bytes, s));
+  if (adam_v)
+    NVC_CUDA(h, cudaMemcpyAsync(h->adam_v, adam_v, bytes, cudaMemcpyDeviceToDevice, s));
+  else
+    NVC_CUDA(h, cudaMemsetAsync(h->adam_v, 0, bytes, s));
+  NVC_CUDA(h, cudaMemsetAsync(h->grad, 0, bytes, s));
+  set_status_kernel<<<1, 1, 0, s>>>(h->status, step);
+  NVC_CUDA(h, cudaGetLastError());
+  NVC_CUDA(h, launch_pack_mlp(h, s));
+  return NVC_OK;
+}
+
+nvc_status nvc_get_state(nvc_handle* h, float* params, float* adam_m, float* adam_v,
+                         void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(float) * (size_t)h->n_params;
+  if (params) NVC_CUDA(h, cudaMemcpyAsync(params, h->params, bytes, cudaMemcpyDeviceToDevice, s));
+  if (adam_m) NVC_CUDA(h, cudaMemcpyAsync(adam_m, h->adam_m, bytes, cudaMemcpyDeviceToDevice, s));
+  if (adam_v) NVC_CUDA(h, cudaMemcpyAsync(adam_v, h->adam_v, bytes, cudaMemcpyDeviceToDevice, s));
+  return NVC_OK;
+}
+
+nvc_status nvc_sync_status(nvc_handle* h, void* stream, nvc_counters* out) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (!out) return fail(h, NVC_ERR_INVALID_ARG, "out is NULL");
+  NVC_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
+  int32_t st[kStWords];
+  NVC_CUDA(h, cudaMemcpy(st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+  out->step = st[kStStep];
+  out->skipped = st[kStSkipped];
+  out->error_flags = st[kStFlags];
+  out->frames = st[kStFrames];
+  return NVC_OK;
+}
+
+nvc_status nvc_encode(nvc_handle* h, const float* pos, int64_t n, float* feat, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(h, NVC_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(h, pos, "pos"));
+  NVC_TRY(check_ptr(h, feat, "feat", h->F % 2 == 0 ? 8 : 4));
+  NVC_CUDA(h, launch_encode_fwd(h, pos, n, feat, (cudaStream_t)stream));
+  count_launches(h, 1);
+  return NVC_OK;
+}
+
+nvc_status nvc_infer(nvc_handle* h, const float* pos, int64_t n, float* vis, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0) return fail(h, NVC_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(h, pos, "pos"));
+  NVC_TRY(check_ptr(h, vis, "vis"));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->cfg.precision != NVC_PREC_FP32) {
+    std::string why;
+    if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
+    NVC_CUDA(h, launch_shade_fused(h, nullptr, pos, nullptr, n, 0, 0, 0, 0, nullptr, nullptr,
+                                   nullptr, nullptr, vis, s));
+    count_launches(h, 1);
+    return NVC_OK;
+  }
+  for (int64_t o = 0; o < n; o += h->stage_pixels) {
+    const int64_t m = n - o < h->stage_pixels ? n - o : h->stage_pixels;
+    NVC_CUDA(h, launch_encode_fwd(h, pos + 3 * o, m, h->s_feat, s));
+    NVC_CUDA(h, launch_mlp_fwd_fp32(h, h->s_feat, m, vis + o * h->L, true, nullptr, s));
+    count_launches(h, 2);
+  }
+  return NVC_OK;
+}
+
+nvc_status nvc_light_weights(const nvc_scene* scene, const float* pos, const float* nrm,
+                             const float* vis, int64_t n, float* c, float* w, void* stream) {
+  NVC_TRY(check_scene(nullptr, scene, 0));
+  if (n < 0) return fail(nullptr, NVC_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(nullptr, pos, "pos"));
+  NVC_TRY(check_ptr(nullptr, nrm, "nrm"));
+  if (w) NVC_TRY(check_ptr(nullptr, vis, "vis"));
+  NVC_CUDA(nullptr, launch_light_weights(scene, pos, nrm, vis, n, c, w, (cudaStream_t)stream));
+  return NVC_OK;
+}
+
+nvc_status nvc_wrs_from_weights(const float* w, int64_t n, int32_t n_lights, uint64_t seed,
+                                uint32_t frame, uint32_t view, int64_t pixel_offset,
+                                int32_t* idx, float* pdf, float* wsum, void* stream) {
+  if (n < 0 || pixel_offset < 0) return fail(nullptr, NVC_ERR_INVALID_ARG, "n or offset < 0");
+  if (n_lights < 1 || n_lights > NVC_MAX_LIGHTS)
+    return fail(nullptr, NVC_ERR_INVALID_ARG, "n_lights out of range");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(nullptr, w, "w"));
+  NVC_CUDA(nullptr, launch_wrs_from_weights(w, n, n_lights, seed, frame, view, pixel_offset, idx,
+                                            pdf, wsum, (cudaStream_t)stream));
+  return NVC_OK;
+}
+
+static nvc_status shade_impl(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                             const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
+                             uint32_t view, int64_t pixel_offset, int32_t* idx, float* pdf,
+                             float* wsum, float* radiance, int fused, cudaStream_t s) {
+  if (fused) {
+    std::string why;
+    if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
+    StageScope sc(h, s, 3);
+    NVC_CUDA(h, launch_shade_fused(h, scene, pos, nrm, n, seed, frame, view, pixel_offset, idx,
+                                   pdf, wsum, radiance, nullptr, s));
+    count_launches(h, 1);
+    return NVC_OK;
+  }
+  StageScope sc(h, s, 3);
+  for (int64_t o = 0; o < n; o += h->stage_pixels) {
+    const int64_t m = n - o < h->stage_pixels ? n - o : h->stage_pixels;
+    NVC_CUDA(h, launch_encode_fwd(h, pos + 3 * o, m, h->s_feat, s));
+    NVC_CUDA(h, launch_mlp_fwd_fp32(h, h->s_feat, m, h->s_vis, true, nullptr, s));
+    NVC_CUDA(h, launch_shade_from_vis(scene, pos + 3 * o, nrm + 3 * o, h->s_vis, m, seed, frame,
+                                      view, pixel_offset + o, idx ? idx + o : nullptr,
+                                      pdf ? pdf + o : nullptr, wsum ? wsum + o : nullptr,
+                                      radiance ? radiance + o : nullptr, s));
+    count_launches(h, 3);
+  }
+  return NVC_OK;
+}
+
+static nvc_status shade_checks(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                               const float* nrm, int64_t n, int64_t pixel_offset) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  NVC_TRY(check_scene(h, scene, h->L));
+  if (n < 0 || pixel_offset < 0) return fail(h, NVC_ERR_INVALID_ARG, "n or offset < 0");
+  if (pixel_offset + n > ((int64_t)1 << 32))
+    return fail(h, NVC_ERR_INVALID_ARG, "pixel ids must fit in 32 bits");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(h, pos, "pos"));
+  NVC_TRY(check_ptr(h, nrm, "nrm"));
+  return NVC_OK;
+}
+
+nvc_status nvc_shade(nvc_handle* h, const nvc_scene* scene, const float* pos, const float* nrm,
+                     int64_t n, uint64_t seed, uint32_t frame, uint32_t view,
+                     int64_t pixel_offset, int32_t* idx, float* pdf, float* wsum,
+                     float* radiance, int32_t fused, void* stream) {
+  NVC_TRY(shade_checks(h, scene, pos, nrm, n, pixel_offset));
+  if (n == 0) return NVC_OK;
+  return shade_impl(h, scene, pos, nrm, n, seed, frame, view, pixel_offset, idx, pdf, wsum,
+                    radiance, fused, (cudaStream_t)stream);
+}
+
+nvc_status nvc_wrs_sample(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                          const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
+                          uint32_t view, int64_t pixel_offset, int32_t* idx, float* pdf,
+                          float* wsum, void* stream) {
+  NVC_TRY(shade_checks(h, scene, pos, nrm, n, pixel_offset));
+  if (n == 0) return NVC_OK;
+  return shade_impl(h, scene, pos, nrm, n, seed, frame, view, pixel_offset, idx, pdf, wsum,
+                    nullptr, h->cfg.precision != NVC_PREC_FP32, (cudaStream_t)stream);
+}
+
+nvc_status nvc_direct_illum(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                            const float* nrm, int64_t n, float* radiance, void* stream) {
+  NVC_TRY(shade_checks(h, scene, pos, nrm, n, 0));
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(h, radiance, "radiance"));
+  return shade_impl(h, scene, pos, nrm, n, 0, 0, 0, 0, nullptr, nullptr, nullptr, radiance,
+                    h->cfg.precision != NVC_PREC_FP32, (cudaStream_t)stream);
+}
+
+nvc_status nvc_trace_visibility(const nvc_scene* scene, const float* pos, int64_t n, float* vis,
+                                void* stream) {
+  NVC_TRY(check_scene(nullptr, scene, 0));
+  if (n < 0) return fail(nullptr, NVC_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(nullptr, pos, "pos"));
+  NVC_TRY(check_ptr(nullptr, vis, "vis"));
+  NVC_CUDA(nullptr, launch_trace_visibility(scene, pos, n, vis, (cudaStream_t)stream));
+  return NVC_OK;
+}
+
+nvc_status nvc_training_positions(const nvc_scene* scene, const float* screen_pos,
+                                  int64_t n_screen, int64_t batch, uint64_t seed, uint32_t frame,
+                                  float* pos, void* stream) {
+  NVC_TRY(check_scene(nullptr, scene, 0));
+  if (batch < 0 || n_screen < 0 || n_screen > ((int64_t)1 << 32))
+    return fail(nullptr, NVC_ERR_INVALID_ARG, "batch or n_screen out of range");
+  if (batch > ((int64_t)1 << 32)) return fail(nullptr, NVC_ERR_INVALID_ARG, "batch above 2^32");
+  if (batch == 0) return NVC_OK;
+  NVC_TRY(check_ptr(nullptr, pos, "pos"));
+  if (n_screen > 0 && screen_pos) NVC_TRY(check_ptr(nullptr, screen_pos, "screen_pos"));
+  NVC_CUDA(nullptr, launch_training_positions(scene, screen_pos, n_screen, batch, seed, frame, pos,
+                                              (cudaStream_t)stream));
+  return NVC_OK;
+}
+
+// Forward + backward of one training batch into h->grad (scaled by the loss
+// scale); positions are generated unless `given_pos` is set.
+static nvc_status train_forward_backward(nvc_handle* h, const nvc_scene* scene,
+                                         const float* screen_pos, int64_t n_screen,
+                                         uint64_t seed, uint32_t frame, cudaStream_t s) {
+  const int64_t B = h->B;
+  {
+    StageScope sc(h, s, 0);
+    NVC_CUDA(h, launch_training_positions(scene, screen_pos, n_screen, B, seed, frame, h->t_pos, s));
+    NVC_CUDA(h, launch_trace_visibility(scene, h->t_pos, B, h->t_target, s));
+    count_launches(h, 2);
+  }
+  StageScope sc(h, s, 1);
+  NVC_CUDA(h, launch_encode_fwd(h, h->t_pos, B, h->t_feat, s));
+  NVC_CUDA(h, launch_mlp_fwd_fp32(h, h->t_feat, B, h->t_logits, false, h->t_act, s));
+  NVC_CUDA(h, launch_loss_grad(h, B, s));
+  NVC_CUDA(h, launch_mlp_bwd_fp32(h, B, nullptr, h->grad, h->status, s));
+  NVC_CUDA(h, launch_encode_bwd(h, h->t_pos, B, h->t_dfeat, h->grad, h->status, s));
+  count_launches(h, 4 + 1 + h->n_layers);
+  return NVC_OK;
+}
+
+static nvc_status train_checks(nvc_handle* h, const nvc_scene* scene, const float* screen_pos,
+                               int64_t n_screen) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  NVC_TRY(check_scene(h, scene, h->L));
+  if (n_screen < 0 || n_screen > ((int64_t)1 << 32))
+    return fail(h, NVC_ERR_INVALID_ARG, "n_screen out of range");
+  if (n_screen > 0 && screen_pos) NVC_TRY(check_ptr(h, screen_pos, "screen_pos"));
+  return NVC_OK;
+}
+
+static nvc_status train_step_impl(nvc_handle* h, const nvc_scene* scene, const float* screen_pos,
+                                  int64_t n_screen, uint64_t seed, uint32_t frame,
+                                  double* loss_out, cudaStream_t s) {
+  NVC_TRY(train_forward_backward(h, scene, screen_pos, n_screen, seed, frame, s));
+  StageScope sc(h, s, 2);
+  NVC_CUDA(h, launch_adam(h, loss_out, true, s));
+  NVC_CUDA(h, launch_pack_mlp(h, s));
+  count_launches(h, 2 + (h->mlp_packed ? 1 : 0));
+  return NVC_OK;
+}
+
+nvc_status nvc_train_step(nvc_handle* h, const nvc_scene* scene, const float* screen_pos,
+                          int64_t n_screen, uint64_t seed, uint32_t frame, double* loss_out,
+                          void* stream) {
+  NVC_TRY(train_checks(h, scene, screen_pos, n_screen));
+  if (loss_out) NVC_TRY(check_ptr(h, loss_out, "loss_out", 8));
+  return train_step_impl(h, scene, screen_pos, n_screen, seed, frame, loss_out,
+                         (cudaStream_t)stream);
+}
+
+nvc_status nvc_train_gradient(nvc_handle* h, const nvc_scene* scene, const float* screen_pos,
+                              int64_t n_screen, uint64_t seed, uint32_t frame, float* grad,
+                              double* loss_out, void* stream) {
+  NVC_TRY(train_checks(h, scene, screen_pos, n_screen));
+  NVC_TRY(check_ptr(h, grad, "grad"));
+  if (loss_out) NVC_TRY(check_ptr(h, loss_out, "loss_out", 8));
+  cudaStream_t s = (cudaStream_t)stream;
+  NVC_TRY(train_forward_backward(h, scene, screen_pos, n_screen, seed, frame, s));
+  NVC_CUDA(h, launch_finish_gradient(h, grad, loss_out, s));
+  return NVC_OK;
+}
+
+nvc_status nvc_mlp_forward(nvc_handle* h, const float* pos, int64_t n, float* logits,
+                           void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0 || n > h->B) return fail(h, NVC_ERR_INVALID_ARG, "n must be in [0, batch_positions]");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(h, pos, "pos"));
+  NVC_TRY(check_ptr(h, logits, "logits"));
+  cudaStream_t s = (cudaStream_t)stream;
+  NVC_CUDA(h, launch_encode_fwd(h, pos, n, h->t_feat, s));
+  NVC_CUDA(h, launch_mlp_fwd_fp32(h, h->t_feat, n, logits, false, h->t_act, s));
+  return NVC_OK;
+}
+
+__global__ void copy_rows_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+__global__ void take_grad_unscaled_kernel(float* __restrict__ grad, float* __restrict__ out,
+                                          int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    out[e] = grad[e];
+    grad[e] = 0.0f;
+  }
+}
+
+nvc_status nvc_mlp_backward(nvc_handle* h, const float* pos, int64_t n, const float* dlogits,
+                            float* grad, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0 || n > h->B) return fail(h, NVC_ERR_INVALID_ARG, "n must be in [0, batch_positions]");
+  NVC_TRY(check_ptr(h, grad, "grad"));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n > 0) {
+    NVC_TRY(check_ptr(h, pos, "pos"));
+    NVC_TRY(check_ptr(h, dlogits, "dlogits"));
+    const int maxdim = h->width > h->L ? h->width : h->L;
+    float* dtop = h->t_delta + (int64_t)(h->n_layers - 1) * h->B * maxdim;
+    copy_rows_kernel<<<h->num_sms * 4, 256, 0, s>>>(dlogits, dtop, n * h->L);
+    NVC_CUDA(h, cudaGetLastError());
+    NVC_CUDA(h, launch_mlp_bwd_fp32(h, n, nullptr, h->grad, h->status, s));
+    NVC_CUDA(h, launch_encode_bwd(h, pos, n, h->t_dfeat, h->grad, h->status, s));
+  }
+  take_grad_unscaled_kernel<<<h->num_sms * 4, 256, 0, s>>>(h->grad, grad, h->n_params);
+  NVC_CUDA(h, cudaGetLastError());
+  return NVC_OK;
+}
+
+static nvc_status frame_body(nvc_handle* h, const nvc_scene* scene, const nvc_view* views,
+                             int32_t n_views, int32_t train_view, uint64_t seed, uint32_t frame,
+                             double* loss_out, cudaStream_t s) {
+  if (train_view != NVC_FRAME_NO_TRAINING) {
+    const nvc_view* tv = train_view >= 0 ? &views[train_view] : nullptr;
+    NVC_TRY(train_step_impl(h, scene, tv ? tv->pos : nullptr, tv ? tv->n_pixels : 0, seed,
+                            frame, loss_out, s));
+  }
+  const bool fused = h->cfg.precision != NVC_PREC_FP32;
+  for (int v = 0; v < n_views; ++v) {
+    const nvc_view& vw = views[v];
+    if (vw.n_pixels == 0) continue;
+    NVC_TRY(shade_impl(h, scene, vw.pos, vw.nrm, vw.n_pixels, seed, frame, vw.view_id, 0, vw.idx,
+                       vw.pdf, vw.wsum, vw.radiance, fused, s));
+  }
+  bump_frames_kernel<<<1, 1, 0, s>>>(h->status);
+  NVC_CUDA(h, cudaGetLastError());
+  count_launches(h, 1);
+  return NVC_OK;
+}
+
+nvc_status nvc_frame(nvc_handle* h, const nvc_scene* scene, const nvc_view* views,
+                     int32_t n_views, int32_t train_view, uint64_t seed, uint32_t frame,
+                     double* loss_out, int32_t use_graph, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  NVC_TRY(check_scene(h, scene, h->L));
+  if (n_views < 0 || (n_views > 0 && !views)) return fail(h, NVC_ERR_INVALID_ARG, "bad views");
+  if (train_view >= n_views || train_view < NVC_FRAME_NO_TRAINING)
+    return fail(h, NVC_ERR_INVALID_ARG, "train_view out of range");
+  for (int v = 0; v < n_views; ++v) {
+    NVC_TRY(shade_checks(h, scene, views[v].pos, views[v].nrm, views[v].n_pixels, 0));
+  }
+  if (loss_out) NVC_TRY(check_ptr(h, loss_out, "loss_out", 8));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!use_graph) return frame_body(h, scene, views, n_views, train_view, seed, frame, loss_out, s);
+
+  const bool was_profiling = h->profiling;
+  h->profiling = false;
+  NVC_CUDA(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+  nvc_status st = frame_body(h, scene, views, n_views, train_view, seed, frame, loss_out,
+                             h->capture_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &g);
+  h->profiling = was_profiling;
+  if (st != NVC_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
+  if (h->graph_exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(h->graph_exec, g, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(h->graph_exec);
+      h->graph_exec = nullptr;
+    }
+  }
+  if (!h->graph_exec) {
+    ce = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(h, ce, "cudaGraphInstantiate");
+    }
+  }
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->graph = g;
+  NVC_CUDA(h, cudaGraphLaunch(h->graph_exec, s));
+  return NVC_OK;
+}
+
+nvc_status nvc_set_profiling(nvc_handle* h, int32_t enable) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  ProfEvents* pe = prof_of(h);
+  if (enable && pe && pe->pool.empty()) {
+    pe->pool.resize(8192);
+    for (auto& ev : pe->pool) NVC_CUDA(h, cudaEventCreate(&ev));
+  }
+  h->profiling = enable != 0;
+  return NVC_OK;
+}
+
+nvc_status nvc_stage_times(nvc_handle* h, double* ms_out, int32_t n_out, int64_t* launches_out) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  ProfEvents* pe = prof_of(h);
+  if (pe && !pe->open.empty()) {
+    NVC_CUDA(h, cudaEventSynchronize(pe->pool[pe->open.back().second + 1]));
+    for (auto& o : pe->open) {
+      float ms = 0.f;
+      NVC_CUDA(h, cudaEventElapsedTime(&ms, pe->pool[o.second], pe->pool[o.second + 1]));
+      h->stage_ms[o.first] += ms;
+    }
+    pe->open.clear();
+    pe->next = 0;
+  }
+  for (int i = 0; i < n_out && i < 4; ++i) ms_out[i] = h->stage_ms[i];
+  if (launches_out) *launches_out = h->launches;
+  for (double& v : h->stage_ms) v = 0.0;
+  h->launches = 0;
+  return NVC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,198 @@
+// Multi-resolution hash-grid encoding (Sections 3.1 and 3.3 of the paper,
+// after Mueller et al. 2022) and its adjoint.
+//
+// One thread per (position, level), level fastest, so a warp covers two
+// positions x 16 levels and its feature stores are contiguous.  Each
+// thread hashes the 8 corners of its cell and gathers F float32 features
+// per corner (one 8-byte load for F = 2) from the level's table; at the
+// table sizes used here the tables stay resident in L2.
+#include "nvc_internal.cuh"
+
+namespace nvc {
+
+EncodeParams encode_params(const nvc_handle* h) {
+  EncodeParams ep{};
+  ep.n_levels = h->cfg.n_levels;
+  ep.log2_table = h->cfg.log2_table_size;
+  for (int d = 0; d < 3; ++d) {
+    ep.lo[d] = h->cfg.bounds_min[d];
+    ep.ext[d] = h->cfg.bounds_max[d] - h->cfg.bounds_min[d];  // host float32 subtraction
+  }
+  for (int l = 0; l < h->cfg.n_levels; ++l) ep.res[l] = h->res[l];
+  return ep;
+}
+
+template <int F>
+struct FeatVec {
+  float v[F];
+};
+
+template <int F>
+__device__ __forceinline__ FeatVec<F> load_feat(const float* p) {
+  FeatVec<F> r;
+  if constexpr (F == 1) {
+    r.v[0] = __ldg(p);
+  } else if constexpr (F == 2) {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+    r.v[0] = a.x;
+    r.v[1] = a.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < F; k += 4) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(p + k));
+      r.v[k] = a.x;
+      r.v[k + 1] = a.y;
+      r.v[k + 2] = a.z;
+      r.v[k + 3] = a.w;
+    }
+  }
+  return r;
+}
+
+// Corner rows and trilinear weights of one (position, level).
+struct Corners {
+  uint32_t row[8];
+  float w[8];
+};
+
+__device__ __forceinline__ void level_corners(const EncodeParams& ep, int l, float x, float y,
+                                              float z, Corners& cr) {
+  const int n = ep.res[l];
+  int cx, cy, cz;
+  float fx, fy, fz;
+  grid_cell(x, n, cx, fx);
+  grid_cell(y, n, cy, fy);
+  grid_cell(z, n, cz, fz);
+  const uint32_t mask = (1u << ep.log2_table) - 1u;
+  const float gx[2] = {1.0f - fx, fx}, gy[2] = {1.0f - fy, fy}, gz[2] = {1.0f - fz, fz};
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+    cr.row[d] = grid_hash((uint32_t)(cx + dx), (uint32_t)(cy + dy), (uint32_t)(cz + dz)) & mask;
+    cr.w[d] = gx[dx] * gy[dy] * gz[dz];
+  }
+}
+
+template <int F>
+__global__ void __launch_bounds__(256) encode_fwd_kernel(const float* __restrict__ pos,
+                                                         int64_t n, const float* __restrict__ table,
+                                                         EncodeParams ep,
+                                                         float* __restrict__ feat) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = ep.n_levels;
+  if (t >= n * L) return;
+  const int64_t i = t / L;
+  const int l = (int)(t - i * L);
+  const float x = normalise(__ldg(pos + 3 * i + 0), ep.lo[0], ep.ext[0]);
+  const float y = normalise(__ldg(pos + 3 * i + 1), ep.lo[1], ep.ext[1]);
+  const float z = normalise(__ldg(pos + 3 * i + 2), ep.lo[2], ep.ext[2]);
+  Corners cr;
+  level_corners(ep, l, x, y, z, cr);
+  const float* tab = table + ((int64_t)l << ep.log2_table) * F;
+  float acc[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const FeatVec<F> v = load_feat<F>(tab + (int64_t)cr.row[d] * F);
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = fmaf(cr.w[d], v.v[f], acc[f]);
+  }
+  float* out = feat + i * (int64_t)L * F + l * F;
+#pragma unroll
+  for (int f = 0; f < F; ++f) out[f] = acc[f];
+}
+
+template <int F>
+__global__ void __launch_bounds__(256) encode_bwd_kernel(const float* __restrict__ pos, int64_t n,
+                                                         const float* __restrict__ dfeat,
+                                                         EncodeParams ep, float* grad,
+                                                         int32_t* status) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = ep.n_levels;
+  if (t >= n * L) return;
+  const int64_t i = t / L;
+  const int l = (int)(t - i * L);
+  float g[F];
+  bool finite = true;
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    g[f] = __ldg(dfeat + i * (int64_t)L * F + l * F + f);
+    finite = finite && isfinite(g[f]);
+  }
+  if (!finite) {
+    atomicOr(status + kStNonFinite, 1);
+    return;
+  }
+  const float x = normalise(__ldg(pos + 3 * i + 0), ep.lo[0], ep.ext[0]);
+  const float y = normalise(__ldg(pos + 3 * i + 1), ep.lo[1], ep.ext[1]);
+  const float z = normalise(__ldg(pos + 3 * i + 2), ep.lo[2], ep.ext[2]);
+  Corners cr;
+  level_corners(ep, l, x, y, z, cr);
+  float* tab = grad + ((int64_t)l << ep.log2_table) * F;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    float* dst = tab + (int64_t)cr.row[d] * F;
+    if constexpr (F == 2) {
+      atomicAdd(reinterpret_cast<float2*>(dst), make_float2(cr.w[d] * g[0], cr.w[d] * g[1]));
+    } else if constexpr (F % 4 == 0) {
+#pragma unroll
+      for (int k = 0; k < F; k += 4)
+        atomicAdd(reinterpret_cast<float4*>(dst + k),
+                  make_float4(cr.w[d] * g[k], cr.w[d] * g[k + 1], cr.w[d] * g[k + 2],
+                              cr.w[d] * g[k + 3]));
+    } else {
+#pragma unroll
+      for (int f = 0; f < F; ++f) atomicAdd(dst + f, cr.w[d] * g[f]);
+    }
+  }
+}
+
+template <int F>
+static cudaError_t enc_fwd(const nvc_handle* h, const float* pos, int64_t n, float* feat,
+                           cudaStream_t s) {
+  const int64_t total = n * h->cfg.n_levels;
+  const int threads = 256;
+  const int64_t blocks = (total + threads - 1) / threads;
+  encode_fwd_kernel<F><<<(unsigned)blocks, threads, 0, s>>>(pos, n, h->params, encode_params(h),
+                                                              feat);
+  return cudaGetLastError();
+}
+
+template <int F>
+static cudaError_t enc_bwd(const nvc_handle* h, const float* pos, int64_t n, const float* dfeat,
+                           float* grad, int32_t* status, cudaStream_t s) {
+  const int64_t total = n * h->cfg.n_levels;
+  const int threads = 256;
+  const int64_t blocks = (total + threads - 1) / threads;
+  encode_bwd_kernel<F><<<(unsigned)blocks, threads, 0, s>>>(pos, n, dfeat, encode_params(h), grad,
+                                                              status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_fwd(const nvc_handle* h, const float* pos, int64_t n, float* feat,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  switch (h->F) {
+    case 1: return enc_fwd<1>(h, pos, n, feat, s);
+    case 2: return enc_fwd<2>(h, pos, n, feat, s);
+    case 4: return enc_fwd<4>(h, pos, n, feat, s);
+    case 8: return enc_fwd<8>(h, pos, n, feat, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_encode_bwd(const nvc_handle* h, const float* pos, int64_t n,
+                              const float* dfeat, float* grad_table, int32_t* status,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  switch (h->F) {
+    case 1: return enc_bwd<1>(h, pos, n, dfeat, grad_table, status, s);
+    case 2: return enc_bwd<2>(h, pos, n, dfeat, grad_table, status, s);
+    case 4: return enc_bwd<4>(h, pos, n, dfeat, grad_table, status, s);
+    case 8: return enc_bwd<8>(h, pos, n, dfeat, grad_table, status, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nvc

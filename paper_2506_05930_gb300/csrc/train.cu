@@ -1,0 +1,295 @@
+// Online training (Section 3.4 of the paper): training positions, binary
+// shadow-ray targets, the loss and its gradient at the logits, and Adam.
+#include "nvc_internal.cuh"
+
+namespace nvc {
+
+namespace {
+
+// ---- training positions ---------------------------------------------------
+// Samples [0, n_world) are uniform in the world box (stream tag 1); the rest
+// copy G-buffer pixel floor(r * n_screen / 2^32) (stream tag 2).
+__global__ void training_positions_kernel(float3 lo, float3 ext, const float* __restrict__ screen,
+                                          int64_t n_screen, int64_t batch, int64_t n_world,
+                                          uint32_t k0, uint32_t k1, uint32_t frame,
+                                          float* __restrict__ pos) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= batch) return;
+  float x, y, z;
+  if (j < n_world) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)j, frame, 0u, kTagWorld), k0, k1);
+    x = __fadd_rn(lo.x, __fmul_rn(uniform24(r.x), ext.x));
+    y = __fadd_rn(lo.y, __fmul_rn(uniform24(r.y), ext.y));
+    z = __fadd_rn(lo.z, __fmul_rn(uniform24(r.z), ext.z));
+  } else {
+    const uint32_t s = (uint32_t)(j - n_world);
+    const uint4 r = philox4x32_10(make_uint4(s, frame, 0u, kTagScreen), k0, k1);
+    const int64_t pix = (int64_t)(((uint64_t)r.x * (uint64_t)n_screen) >> 32);
+    x = screen[3 * pix];
+    y = screen[3 * pix + 1];
+    z = screen[3 * pix + 2];
+  }
+  pos[3 * j] = x;
+  pos[3 * j + 1] = y;
+  pos[3 * j + 2] = z;
+}
+
+// ---- shadow rays ------------------------------------------------------------
+// One thread per (position, light); occluders staged in shared memory.  The
+// arithmetic is correctly rounded float32 in a fixed order, so the binary
+// decision is reproducible operation by operation.
+__device__ __forceinline__ bool sphere_blocks(float px, float py, float pz, float dx, float dy,
+                                              float dz, float dd, float4 s) {
+  const float t0 = bits_f(kSegT0Bits), t1 = bits_f(kSegT1Bits);
+  const float ox = __fsub_rn(s.x, px), oy = __fsub_rn(s.y, py), oz = __fsub_rn(s.z, pz);
+  float tc = dd > 0.0f ? __fdiv_rn(dot3_rn(ox, oy, oz, dx, dy, dz), dd) : t0;
+  tc = fminf(fmaxf(tc, t0), t1);
+  const float ex = __fsub_rn(s.x, __fadd_rn(px, __fmul_rn(tc, dx)));
+  const float ey = __fsub_rn(s.y, __fadd_rn(py, __fmul_rn(tc, dy)));
+  const float ez = __fsub_rn(s.z, __fadd_rn(pz, __fmul_rn(tc, dz)));
+  return dot3_rn(ex, ey, ez, ex, ey, ez) < __fmul_rn(s.w, s.w);
+}
+
+__device__ __forceinline__ void slab(float xa, float da, float lo, float hi, float& tmin,
+                                     float& tmax, bool& miss) {
+  if (da == 0.0f) {
+    miss = miss || xa < lo || xa > hi;
+    return;
+  }
+  const float ta = __fdiv_rn(__fsub_rn(lo, xa), da);
+  const float tb = __fdiv_rn(__fsub_rn(hi, xa), da);
+  tmin = fmaxf(tmin, fminf(ta, tb));
+  tmax = fminf(tmax, fmaxf(ta, tb));
+}
+
+__device__ __forceinline__ bool box_blocks(float px, float py, float pz, float dx, float dy,
+                                           float dz, const float* b) {
+  float tmin = bits_f(kSegT0Bits), tmax = bits_f(kSegT1Bits);
+  bool miss = false;
+  slab(px, dx, b[0], b[3], tmin, tmax, miss);
+  slab(py, dy, b[1], b[4], tmin, tmax, miss);
+  slab(pz, dz, b[2], b[5], tmin, tmax, miss);
+  return !miss && tmin <= tmax;
+}
+
+__global__ void __launch_bounds__(256) trace_visibility_kernel(
+    const float* __restrict__ lights, int L, const float* __restrict__ spheres, int n_sph,
+    const float* __restrict__ boxes, int n_box, const float* __restrict__ pos, int64_t n,
+    float* __restrict__ vis) {
+  extern __shared__ float s_occ[];
+  float4* s_sph = reinterpret_cast<float4*>(s_occ);
+  float* s_box = s_occ + 4 * n_sph;
+  for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
+    s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
+  for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * L) return;
+  const int64_t p = t / L;
+  const int i = (int)(t - p * L);
+  const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
+  const float4 lt = reinterpret_cast<const float4*>(lights)[i];
+  const float dx = __fsub_rn(lt.x, px), dy = __fsub_rn(lt.y, py), dz = __fsub_rn(lt.z, pz);
+  const float dd = dot3_rn(dx, dy, dz, dx, dy, dz);
+  bool occ = false;
+  for (int k = 0; k < n_sph && !occ; ++k) occ = sphere_blocks(px, py, pz, dx, dy, dz, dd, s_sph[k]);
+  for (int k = 0; k < n_box && !occ; ++k) occ = box_blocks(px, py, pz, dx, dy, dz, s_box + 6 * k);
+  vis[t] = occ ? 0.0f : 1.0f;
+}
+
+// ---- loss and its gradient at the logits ------------------------------------
+// L2: mean (s - y)^2, d/dz = 2 (s - y) s (1 - s) / n.  BCE: mean softplus(z)
+// - y z, d/dz = (s - y) / n.  The gradient is multiplied by the loss scale;
+// the loss value is reduced in double, one partial per block.
+__global__ void __launch_bounds__(256) loss_grad_kernel(const float* __restrict__ logits,
+                                                        const float* __restrict__ target,
+                                                        int64_t count, int loss_kind,
+                                                        float grad_scale,
+                                                        float* __restrict__ dlogits,
+                                                        double* __restrict__ partials,
+                                                        int32_t* status) {
+  __shared__ double s_red[8];
+  double acc = 0.0;
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float z = logits[e], y = target[e];
+    const float s = 1.0f / (1.0f + expf(-z));
+    float g;
+    if (loss_kind == NVC_LOSS_BCE) {
+      acc += (double)(fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))) - y * z);
+      g = s - y;
+    } else {
+      const float r = s - y;
+      acc += (double)r * (double)r;
+      g = 2.0f * r * s * (1.0f - s);
+    }
+    g *= grad_scale;
+    bad = bad || !isfinite(z) || !isfinite(g);
+    dlogits[e] = g;
+  }
+  if (bad) atomicOr(status + kStNonFinite, 1);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_red[w];
+    partials[blockIdx.x] = sum;
+  }
+}
+
+constexpr int kLossBlocks = 256;
+
+// ---- Adam -------------------------------------------------------------------
+// Prologue (one warp): loss = sum of partials / count; decide whether this
+// step applies (all gradients finite); step counter, bias corrections and
+// the scheduled learning rate.
+__global__ void adam_prologue_kernel(const double* __restrict__ partials, int n_partials,
+                                     double inv_count, double* loss_out, int32_t* status,
+                                     AdamScalars* sc, int apply, int schedule, float lr0,
+                                     float lr_end, int ramp, double beta1, double beta2,
+                                     float inv_scale) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n_partials; i += 32) s += partials[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x != 0) return;
+  if (loss_out) *loss_out = s * inv_count;
+  const bool nonfinite = status[kStNonFinite] != 0;
+  status[kStNonFinite] = 0;
+  if (!apply) return;
+  if (nonfinite) {
+    status[kStSkipped] += 1;
+    status[kStFlags] |= kFlagNonFinite;
+    sc->skip = 1;
+    return;
+  }
+  const int t = status[kStStep] + 1;
+  status[kStStep] = t;
+  double lr = lr0;
+  if (schedule == NVC_LR_RAMP) {
+    const int k = t - 1 < ramp ? t - 1 : ramp;
+    lr = (double)lr0 + ((double)lr_end - (double)lr0) * (double)k / (double)ramp;
+  }
+  sc->lr_over_bc1 = (float)(lr / (1.0 - pow(beta1, (double)t)));
+  sc->inv_bc2 = (float)(1.0 / (1.0 - pow(beta2, (double)t)));
+  sc->inv_scale = inv_scale;
+  sc->skip = 0;
+}
+
+// theta -= (lr / bc1) m / (sqrt(v / bc2) + eps), after m, v updates with the
+// unscaled gradient; the gradient buffer is cleared for the next step.
+__global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
+                                                   float* __restrict__ grad,
+                                                   float* __restrict__ m, float* __restrict__ v,
+                                                   int64_t n4, int64_t n, float beta1,
+                                                   float beta2, float eps,
+                                                   const AdamScalars* __restrict__ scp) {
+  const AdamScalars sc = *scp;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto upd = [&](float& th, float g, float& mm, float& vv) {
+    g *= sc.inv_scale;
+    mm = beta1 * mm + (1.0f - beta1) * g;
+    vv = beta2 * vv + (1.0f - beta2) * g * g;
+    th -= sc.lr_over_bc1 * mm / (sqrtf(vv * sc.inv_bc2) + eps);
+  };
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += stride) {
+    float4 g = reinterpret_cast<float4*>(grad)[e];
+    reinterpret_cast<float4*>(grad)[e] = zero;
+    if (sc.skip) continue;
+    float4 th = reinterpret_cast<float4*>(theta)[e];
+    float4 mm = reinterpret_cast<float4*>(m)[e];
+    float4 vv = reinterpret_cast<float4*>(v)[e];
+    upd(th.x, g.x, mm.x, vv.x);
+    upd(th.y, g.y, mm.y, vv.y);
+    upd(th.z, g.z, mm.z, vv.z);
+    upd(th.w, g.w, mm.w, vv.w);
+    reinterpret_cast<float4*>(theta)[e] = th;
+    reinterpret_cast<float4*>(m)[e] = mm;
+    reinterpret_cast<float4*>(v)[e] = vv;
+  }
+  // scalar tail
+  for (int64_t e = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const float g = grad[e];
+    grad[e] = 0.0f;
+    if (sc.skip) continue;
+    upd(theta[e], g, m[e], v[e]);
+  }
+}
+
+// Copy (and unscale) the accumulated gradient out, clearing it.
+__global__ void take_gradient_kernel(float* __restrict__ grad, float* __restrict__ out, int64_t n,
+                                     float inv_scale) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    out[e] = grad[e] * inv_scale;
+    grad[e] = 0.0f;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_training_positions(const nvc_scene* sc, const float* screen_pos,
+                                      int64_t n_screen, int64_t batch, uint64_t seed,
+                                      uint32_t frame, float* pos, cudaStream_t s) {
+  if (batch == 0) return cudaSuccess;
+  const bool have_screen = screen_pos != nullptr && n_screen > 0;
+  const int64_t n_world = batch - (have_screen ? batch / 2 : 0);
+  const float3 lo = make_float3(sc->world_min[0], sc->world_min[1], sc->world_min[2]);
+  const float3 ext = make_float3(sc->world_max[0] - sc->world_min[0],
+                                 sc->world_max[1] - sc->world_min[1],
+                                 sc->world_max[2] - sc->world_min[2]);
+  training_positions_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(
+      lo, ext, screen_pos, have_screen ? n_screen : 0, batch, n_world, (uint32_t)seed,
+      (uint32_t)(seed >> 32), frame, pos);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_visibility(const nvc_scene* sc, const float* pos, int64_t n, float* vis,
+                                    cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t total = n * sc->n_lights;
+  const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  trace_visibility_kernel<<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
+      sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes, pos, n, vis);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_grad(const nvc_handle* h, int64_t n, cudaStream_t s) {
+  const int64_t count = n * h->L;
+  const int top = h->n_layers - 1;
+  const int maxdim = h->width > h->L ? h->width : h->L;
+  float* dtop = h->t_delta + (int64_t)top * h->B * maxdim;
+  const float scale = h->cfg.loss_scale / (float)count;
+  loss_grad_kernel<<<kLossBlocks, 256, 0, s>>>(h->t_logits, h->t_target, count, h->cfg.loss, scale,
+                                               dtop, h->loss_partials, h->status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_t s) {
+  const nvc_config& c = h->cfg;
+  const double inv_count = 1.0 / ((double)h->B * (double)h->L);
+  adam_prologue_kernel<<<1, 32, 0, s>>>(h->loss_partials, kLossBlocks, inv_count, loss_out,
+                                        h->status, h->adam_scalars, apply ? 1 : 0, c.lr_schedule,
+                                        c.lr, c.lr_end, c.lr_ramp_steps, (double)c.beta1,
+                                        (double)c.beta2, 1.0f / c.loss_scale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !apply) return e;
+  const int64_t n4 = h->n_params / 4;
+  const int blocks = h->num_sms * 8;
+  adam_kernel<<<blocks, 256, 0, s>>>(h->params, h->grad, h->adam_m, h->adam_v, n4, h->n_params,
+                                     c.beta1, c.beta2, c.eps, h->adam_scalars);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_gradient(nvc_handle* h, float* grad_out, double* loss_out,
+                                   cudaStream_t s) {
+  cudaError_t e = launch_adam(h, loss_out, false, s);
+  if (e != cudaSuccess) return e;
+  take_gradient_kernel<<<h->num_sms * 4, 256, 0, s>>>(h->grad, grad_out, h->n_params,
+                                                      1.0f / h->cfg.loss_scale);
+  return cudaGetLastError();
+}
+
+}  // namespace nvc

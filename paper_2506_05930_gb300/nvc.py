@@ -1,0 +1,356 @@
+"""Python binding of libnvc: the C entry points under the same names, taking
+torch tensors (argument marshalling only; every step runs in the library's
+CUDA kernels), plus a small ``VisibilityCache`` convenience class.
+
+torch is used for device memory and streams only.  Tensors must be CUDA,
+contiguous and of the stated dtype; the default stream argument is torch's
+current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import NvcConfig, NvcCounters, NvcScene, NvcView, NVCError, check
+
+lib = _lib.load()
+
+NO_TRAINING = -2      # nvc_frame train_view: shade only
+WORLD_ONLY = -1       # nvc_frame train_view: train on world-space positions only
+
+
+# ----------------------------------------------------------------- helpers --
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=torch.float32, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def make_config(cfg=None, **kw) -> NvcConfig:
+    """nvc_config from an object/dict with the fields of the workload sets
+    (``hidden`` is a tuple of equal widths) plus keyword overrides."""
+    src = {}
+    if cfg is not None:
+        src.update(cfg if isinstance(cfg, dict) else
+                   {k: getattr(cfg, k) for k in dir(cfg) if not k.startswith("_")})
+    src.update(kw)
+    hidden = tuple(src.get("hidden", (32, 32)))
+    if len(set(hidden)) != 1:
+        raise ValueError("hidden layers must share one width")
+    c = NvcConfig()
+    c.n_levels = int(src.get("n_levels", 8))
+    c.n_features = int(src.get("n_features", 2))
+    c.log2_table_size = int(src.get("log2_table_size", 14))
+    c.base_resolution = int(src.get("base_resolution", 4))
+    c.growth = float(src.get("growth", 1.5))
+    c.n_hidden = len(hidden)
+    c.hidden_width = int(hidden[0])
+    c.n_outputs = int(src.get("n_outputs", 4))
+    c.leaky_slope = float(src.get("leaky_slope", 0.0))
+    c.precision = _lib.PRECISIONS[src.get("precision", "fp32")]
+    c.train_precision = _lib.PRECISIONS[src.get("train_precision", "fp32")]
+    c.loss = _lib.LOSSES[src.get("loss", "l2")]
+    c.lr_schedule = _lib.LR_SCHEDULES[src.get("lr_schedule", "constant")]
+    c.lr = float(src.get("lr", 1e-2))
+    c.lr_end = float(src.get("lr_end", 1e-3))
+    c.lr_ramp_steps = int(src.get("lr_ramp_steps", 200))
+    c.beta1 = float(src.get("beta1", 0.9))
+    c.beta2 = float(src.get("beta2", 0.99))
+    c.eps = float(src.get("eps", 1e-15))
+    c.loss_scale = float(src.get("loss_scale", 1.0))
+    c.batch_positions = int(src.get("batch_positions", 1024))
+    for d in range(3):
+        c.bounds_min[d] = float(src.get("bounds_min", (0, 0, 0))[d])
+        c.bounds_max[d] = float(src.get("bounds_max", (1, 1, 1))[d])
+    return c
+
+
+class Scene:
+    """Device copies of a scene's lights/occluders and the nvc_scene view."""
+
+    def __init__(self, lights, spheres=None, boxes=None, world_min=(0, 0, 0),
+                 world_max=(1, 1, 1), device="cuda"):
+        def dev(a, cols):
+            t = torch.as_tensor(a if a is not None else torch.zeros((0, cols)),
+                                dtype=torch.float32).reshape(-1, cols)
+            return t.to(device).contiguous()
+        self.lights = dev(lights, 4)
+        self.spheres = dev(spheres, 4)
+        self.boxes = dev(boxes, 6)
+        s = NvcScene()
+        s.lights = self.lights.data_ptr()
+        s.n_lights = self.lights.shape[0]
+        s.spheres = self.spheres.data_ptr() if self.spheres.numel() else None
+        s.n_spheres = self.spheres.shape[0]
+        s.boxes = self.boxes.data_ptr() if self.boxes.numel() else None
+        s.n_boxes = self.boxes.shape[0]
+        for d in range(3):
+            s.world_min[d] = float(world_min[d])
+            s.world_max[d] = float(world_max[d])
+        self.struct = s
+
+    @classmethod
+    def from_synth(cls, sc, device="cuda"):
+        return cls(sc.lights, sc.spheres, sc.boxes, sc.world_min, sc.world_max, device)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+# --------------------------------------------- the C entry points by name --
+
+def nvc_param_count(cfg: NvcConfig) -> int:
+    return int(lib.nvc_param_count(ctypes.byref(cfg)))
+
+
+def nvc_level_resolution(cfg: NvcConfig, level: int) -> int:
+    return int(lib.nvc_level_resolution(ctypes.byref(cfg), level))
+
+
+def nvc_create(cfg: NvcConfig):
+    h = ctypes.c_void_p()
+    check(lib.nvc_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def nvc_destroy(h):
+    lib.nvc_destroy(h)
+
+
+def nvc_last_error(h=None) -> str:
+    return lib.nvc_last_error(h).decode(errors="replace")
+
+
+def nvc_set_state(h, params, adam_m=None, adam_v=None, step=0, stream=None):
+    check(lib.nvc_set_state(h, _ptr(params, name="params"), _ptr(adam_m, name="adam_m"),
+                            _ptr(adam_v, name="adam_v"), int(step), _stream(stream)), h)
+
+
+def nvc_get_state(h, params=None, adam_m=None, adam_v=None, stream=None):
+    check(lib.nvc_get_state(h, _ptr(params), _ptr(adam_m), _ptr(adam_v), _stream(stream)), h)
+
+
+def nvc_set_staging(h, max_pixels: int):
+    check(lib.nvc_set_staging(h, int(max_pixels)), h)
+
+
+def nvc_sync_status(h, stream=None) -> dict:
+    c = NvcCounters()
+    check(lib.nvc_sync_status(h, _stream(stream), ctypes.byref(c)), h)
+    return dict(step=c.step, skipped=c.skipped, error_flags=c.error_flags, frames=c.frames)
+
+
+def nvc_encode(h, pos, feat, stream=None):
+    check(lib.nvc_encode(h, _ptr(pos, name="pos"), pos.shape[0], _ptr(feat, name="feat"),
+                         _stream(stream)), h)
+
+
+def nvc_infer(h, pos, vis, stream=None):
+    check(lib.nvc_infer(h, _ptr(pos, name="pos"), pos.shape[0], _ptr(vis, name="vis"),
+                        _stream(stream)), h)
+
+
+def nvc_light_weights(scene: Scene, pos, nrm, vis, c, w=None, stream=None):
+    check(lib.nvc_light_weights(scene.ref, _ptr(pos), _ptr(nrm), _ptr(vis), pos.shape[0],
+                                _ptr(c), _ptr(w), _stream(stream)))
+
+
+def nvc_wrs_from_weights(w, seed, frame, view=0, pixel_offset=0, idx=None, pdf=None,
+                         wsum=None, stream=None):
+    check(lib.nvc_wrs_from_weights(_ptr(w, name="w"), w.shape[0], w.shape[1], int(seed),
+                                   int(frame), int(view), int(pixel_offset),
+                                   _ptr(idx, torch.int32, "idx"), _ptr(pdf), _ptr(wsum),
+                                   _stream(stream)))
+
+
+def nvc_wrs_sample(h, scene: Scene, pos, nrm, seed, frame, view=0, pixel_offset=0, idx=None,
+                   pdf=None, wsum=None, stream=None):
+    check(lib.nvc_wrs_sample(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0], int(seed),
+                             int(frame), int(view), int(pixel_offset),
+                             _ptr(idx, torch.int32, "idx"), _ptr(pdf), _ptr(wsum),
+                             _stream(stream)), h)
+
+
+def nvc_direct_illum(h, scene: Scene, pos, nrm, radiance, stream=None):
+    check(lib.nvc_direct_illum(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0],
+                               _ptr(radiance), _stream(stream)), h)
+
+
+def nvc_shade(h, scene: Scene, pos, nrm, seed, frame, view=0, pixel_offset=0, idx=None,
+              pdf=None, wsum=None, radiance=None, fused=True, stream=None):
+    check(lib.nvc_shade(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0], int(seed),
+                        int(frame), int(view), int(pixel_offset),
+                        _ptr(idx, torch.int32, "idx"), _ptr(pdf), _ptr(wsum), _ptr(radiance),
+                        1 if fused else 0, _stream(stream)), h)
+
+
+def nvc_trace_visibility(scene: Scene, pos, vis, stream=None):
+    check(lib.nvc_trace_visibility(scene.ref, _ptr(pos), pos.shape[0], _ptr(vis),
+                                   _stream(stream)))
+
+
+def nvc_training_positions(scene: Scene, screen_pos, batch, seed, frame, pos, stream=None):
+    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    check(lib.nvc_training_positions(scene.ref, _ptr(screen_pos), n_screen, int(batch),
+                                     int(seed), int(frame), _ptr(pos), _stream(stream)))
+
+
+def nvc_train_step(h, scene: Scene, screen_pos, seed, frame, loss_out=None, stream=None):
+    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    check(lib.nvc_train_step(h, scene.ref, _ptr(screen_pos), n_screen, int(seed), int(frame),
+                             _ptr(loss_out, torch.float64, "loss_out"), _stream(stream)), h)
+
+
+def nvc_train_gradient(h, scene: Scene, screen_pos, seed, frame, grad, loss_out=None,
+                       stream=None):
+    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    check(lib.nvc_train_gradient(h, scene.ref, _ptr(screen_pos), n_screen, int(seed),
+                                 int(frame), _ptr(grad), _ptr(loss_out, torch.float64),
+                                 _stream(stream)), h)
+
+
+def nvc_mlp_forward(h, pos, logits, stream=None):
+    check(lib.nvc_mlp_forward(h, _ptr(pos), pos.shape[0], _ptr(logits), _stream(stream)), h)
+
+
+def nvc_mlp_backward(h, pos, dlogits, grad, stream=None):
+    check(lib.nvc_mlp_backward(h, _ptr(pos), pos.shape[0], _ptr(dlogits), _ptr(grad),
+                               _stream(stream)), h)
+
+
+@dataclass
+class View:
+    """One view of a frame and its output tensors."""
+    pos: torch.Tensor
+    nrm: torch.Tensor
+    view_id: int = 0
+    idx: Optional[torch.Tensor] = None
+    pdf: Optional[torch.Tensor] = None
+    wsum: Optional[torch.Tensor] = None
+    radiance: Optional[torch.Tensor] = None
+
+    def struct(self) -> NvcView:
+        v = NvcView()
+        v.pos = _ptr(self.pos)
+        v.nrm = _ptr(self.nrm)
+        v.n_pixels = self.pos.shape[0]
+        v.view_id = self.view_id
+        v.idx = _ptr(self.idx, torch.int32, "idx")
+        v.pdf = _ptr(self.pdf)
+        v.wsum = _ptr(self.wsum)
+        v.radiance = _ptr(self.radiance)
+        return v
+
+
+def nvc_frame(h, scene: Scene, views: Sequence[View], train_view, seed, frame, loss_out=None,
+              use_graph=True, stream=None):
+    arr = (NvcView * max(1, len(views)))(*[v.struct() for v in views])
+    check(lib.nvc_frame(h, scene.ref, arr, len(views), WORLD_ONLY if train_view is None else train_view,
+                        int(seed), int(frame), _ptr(loss_out, torch.float64, "loss_out"),
+                        1 if use_graph else 0, _stream(stream)), h)
+
+
+def nvc_set_profiling(h, enable: bool):
+    check(lib.nvc_set_profiling(h, 1 if enable else 0), h)
+
+
+def nvc_stage_times(h):
+    ms = (ctypes.c_double * 4)()
+    n = ctypes.c_int64()
+    check(lib.nvc_stage_times(h, ms, 4, ctypes.byref(n)), h)
+    return list(ms), int(n.value)
+
+
+# ------------------------------------------------------ convenience class --
+
+class VisibilityCache:
+    """Owns one nvc handle; methods allocate outputs with torch."""
+
+    def __init__(self, cfg=None, **kw):
+        self.cfg = make_config(cfg, **kw)
+        self.n_params = nvc_param_count(self.cfg)
+        if self.n_params < 0:
+            raise NVCError(_lib.NVC_ERR_INVALID_ARG, "invalid configuration")
+        self.handle = nvc_create(self.cfg)
+        self.L = self.cfg.n_outputs
+        self.din = self.cfg.n_levels * self.cfg.n_features
+
+    def close(self):
+        if self.handle is not None:
+            nvc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params, m=None, v=None, step=0):
+        p = torch.as_tensor(params, dtype=torch.float32).cuda().contiguous()
+        if p.numel() != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {p.numel()}")
+        mm = None if m is None else torch.as_tensor(m, dtype=torch.float32).cuda().contiguous()
+        vv = None if v is None else torch.as_tensor(v, dtype=torch.float32).cuda().contiguous()
+        nvc_set_state(self.handle, p, mm, vv, step)
+
+    def state(self):
+        p = torch.empty(self.n_params, device="cuda")
+        m = torch.empty_like(p)
+        v = torch.empty_like(p)
+        nvc_get_state(self.handle, p, m, v)
+        return p, m, v
+
+    def encode(self, pos):
+        feat = torch.empty((pos.shape[0], self.din), device="cuda")
+        nvc_encode(self.handle, pos, feat)
+        return feat
+
+    def infer(self, pos):
+        vis = torch.empty((pos.shape[0], self.L), device="cuda")
+        nvc_infer(self.handle, pos, vis)
+        return vis
+
+    def shade(self, scene, pos, nrm, seed=0, frame=0, view=0, pixel_offset=0, fused=True):
+        n = pos.shape[0]
+        out = dict(idx=torch.empty(n, dtype=torch.int32, device="cuda"),
+                   pdf=torch.empty(n, device="cuda"), wsum=torch.empty(n, device="cuda"),
+                   radiance=torch.empty(n, device="cuda"))
+        nvc_shade(self.handle, scene, pos, nrm, seed, frame, view, pixel_offset, fused=fused, **out)
+        return out
+
+    def train_step(self, scene, screen_pos, seed, frame):
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        nvc_train_step(self.handle, scene, screen_pos, seed, frame, loss)
+        return loss
+
+    def train_gradient(self, scene, screen_pos, seed, frame):
+        g = torch.empty(self.n_params, device="cuda")
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        nvc_train_gradient(self.handle, scene, screen_pos, seed, frame, g, loss)
+        return g, loss
+
+    def counters(self):
+        return nvc_sync_status(self.handle)

@@ -1,0 +1,416 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances: float32 paths within 1e-5 absolute visibility of the float64
+oracle; binary decisions (grid cells, shadow rays, training positions, the
+reservoir pick on identical weights) bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import nvc_synth as S
+from oracle import nvc as O
+from helpers import cfg_tiny, cfg_frame, scaled_params, rel_err
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    # a missing library is an error on a GPU machine, not a skip
+    from paper_2506_05930_gb300 import nvc
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    cfg = cfg_tiny()
+    sc = S.scene_unit_cube(seed=0)
+    gb = S.gbuffer_points(0, 64, 64)
+    cache = nvc.VisibilityCache(cfg)
+    p = scaled_params(cfg, seed=0, table_scale=1.0)
+    cache.set_params(p)
+    return cfg, sc, gb, cache, p
+
+
+# ------------------------------------------------------------------ encode --
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 4097])
+def test_encode_matches_oracle(tiny, n):
+    cfg, sc, gb, cache, p = tiny
+    pos = np.random.default_rng(n).uniform(-0.1, 1.1, (n, 3)).astype(np.float32)
+    feat = cache.encode(dev(pos).reshape(n, 3))
+    table, _ = O.split_params(cfg, p)
+    ref = O.encode(cfg, table, pos)
+    got = host(feat)
+    assert got.shape == ref.shape
+    if n:
+        assert np.max(np.abs(got - ref)) < 2e-6
+
+
+def test_encode_grid_vertices_exact():
+    cfg = cfg_tiny(base_resolution=4, growth=2.0, n_levels=4)
+    cache = nvc.VisibilityCache(cfg)
+    p = scaled_params(cfg, seed=3)
+    cache.set_params(p)
+    table, _ = O.split_params(cfg, p)
+    rng = np.random.default_rng(0)
+    for l, n_l in enumerate([4, 8, 16, 32]):
+        k = rng.integers(0, n_l + 1, (300, 3))
+        pos = (k / n_l).astype(np.float32)
+        got = host(cache.encode(dev(pos)))[:, 2 * l:2 * l + 2]
+        rows = O.hash_index(k[:, 0], k[:, 1], k[:, 2], cfg.table_size)
+        assert np.array_equal(got, table[l, rows].astype(np.float32))
+
+
+def test_encode_large_table_1080p_levels():
+    cfg = cfg_frame()
+    cache = nvc.VisibilityCache(cfg)
+    p = scaled_params(cfg, seed=1)
+    cache.set_params(p)
+    pos = np.random.default_rng(2).uniform(0, 10, (5000, 3)).astype(np.float32)
+    table, _ = O.split_params(cfg, p)
+    assert np.max(np.abs(host(cache.encode(dev(pos))) - O.encode(cfg, table, pos))) < 2e-6
+
+
+# ------------------------------------------------------------------- infer --
+
+@pytest.mark.parametrize("n", [1, 127, 128, 4097])
+def test_infer_fp32_matches_oracle(tiny, n):
+    cfg, sc, gb, cache, p = tiny
+    pos = gb.pos[:n]
+    vis = host(cache.infer(dev(pos)))
+    ref = O.infer(cfg, p, pos)
+    assert np.max(np.abs(vis - ref)) <= 1e-5
+    assert np.std(ref) > 1e-3          # the comparison is not trivially flat
+
+
+def test_infer_fp32_1080p_network():
+    cfg = cfg_frame(precision="fp32")
+    cache = nvc.VisibilityCache(cfg)
+    p = scaled_params(cfg, seed=4)
+    cache.set_params(p)
+    pos = np.random.default_rng(3).uniform(0, 10, (3001, 3)).astype(np.float32)
+    vis = host(cache.infer(dev(pos)))
+    ref = O.infer(cfg, p, pos)
+    assert np.max(np.abs(vis - ref)) <= 1e-5
+
+
+# ------------------------------------------------------ training positions --
+
+@pytest.mark.parametrize("screen", [True, False])
+def test_training_positions_bitexact(screen):
+    sc = S.scene_heightfield(seed=1, n_lights=4, n_spheres=2, n_boxes=2)
+    gb = S.gbuffer_points(5, 33, 17, lo=(1, 1, 1), hi=(9, 9, 3))
+    scene = nvc.Scene.from_synth(sc)
+    B = 1001
+    out = torch.empty((B, 3), device="cuda")
+    sp = dev(gb.pos) if screen else None
+    nvc.nvc_training_positions(scene, sp, B, seed=0x1234567890ABCDEF, frame=17, pos=out)
+    ref = O.training_positions(B, sc.world_min, sc.world_max, gb.pos if screen else None,
+                               0x1234567890ABCDEF, 17)
+    assert np.array_equal(host(out), ref)
+
+
+# -------------------------------------------------------------- visibility --
+
+def test_trace_visibility_bitexact():
+    sc = S.scene_heightfield(seed=2, n_lights=32, n_spheres=32, n_boxes=32)
+    rng = np.random.default_rng(4)
+    pos = rng.uniform(0, 10, (3000, 3)).astype(np.float32)
+    # points on occluder surfaces and inside them, and on box faces
+    pos[:32] = sc.spheres[:, :3] + np.array([0, 0, 1], np.float32) * sc.spheres[:, 3:4]
+    pos[32:64] = sc.boxes[:, :3]
+    pos[64:96] = 0.5 * (sc.boxes[:, :3] + sc.boxes[:, 3:])
+    scene = nvc.Scene.from_synth(sc)
+    vis = torch.empty((len(pos), 32), device="cuda")
+    nvc.nvc_trace_visibility(scene, dev(pos), vis)
+    ref = O.visibility(pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    got = host(vis)
+    assert np.array_equal(got, ref)
+    assert 0.05 < got.mean() < 0.95
+
+
+# ------------------------------------------------- light weights and WRS --
+
+def test_light_weights_bitexact(tiny):
+    cfg, sc, gb, cache, p = tiny
+    scene = nvc.Scene.from_synth(sc)
+    n = 4096
+    vis = np.random.default_rng(5).uniform(0, 1, (n, 4)).astype(np.float32)
+    vis[::7] = 0.0
+    c = torch.empty((n, 4), device="cuda")
+    w = torch.empty((n, 4), device="cuda")
+    nvc.nvc_light_weights(scene, dev(gb.pos[:n]), dev(gb.nrm[:n]), dev(vis), c, w)
+    c_ref = O.contributions(gb.pos[:n], gb.nrm[:n], sc.lights, np.float32)
+    assert np.array_equal(host(c), c_ref)
+    assert np.array_equal(host(w), O.light_weights_f32(vis, c_ref))
+    assert (c_ref == 0).mean() > 0.2      # back-facing lights exercised
+
+
+def _weight_rows(rng, n, L):
+    w = (rng.uniform(0, 1, (n, L)) ** 3).astype(np.float32)
+    w *= (10.0 ** rng.uniform(-20, 20, (n, 1))).astype(np.float32)
+    w[rng.uniform(0, 1, (n, L)) < 0.3] = 0.0
+    w[0] = 0.0                                  # all zero
+    w[1] = 0.0
+    w[1, L - 1] = 3.0                           # single nonzero
+    w[2] = np.float32(1e-40)                    # subnormal weights
+    w[3] = np.float32(3e38)                     # near the float32 limit
+    return w
+
+
+@pytest.mark.parametrize("L", [1, 4, 32, 33, 256])
+def test_wrs_from_weights_bitexact(L):
+    rng = np.random.default_rng(L)
+    n = 5000
+    w = _weight_rows(rng, n, L)
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    pdf = torch.empty(n, device="cuda")
+    wsum = torch.empty(n, device="cuda")
+    seed, frame, view, off = 0xABCDEF0123, 9, 2, 1000
+    nvc.nvc_wrs_from_weights(dev(w), seed, frame, view, off, idx, pdf, wsum)
+    r_idx, r_pdf, r_wsum = O.wrs_select(w, off + np.arange(n), seed, frame, view)
+    assert np.array_equal(host(idx), r_idx)
+    ok = np.isfinite(r_wsum) & (r_wsum < 3e38)
+    np.testing.assert_allclose(host(wsum)[ok], r_wsum[ok], rtol=1e-5)
+    np.testing.assert_allclose(host(pdf)[ok], r_pdf[ok], rtol=1e-5, atol=1e-30)
+    assert host(idx)[0] == -1 and host(idx)[1] == L - 1
+
+
+# ------------------------------------------------- full per-pixel path --
+
+def test_shade_unfused_matches_oracle(tiny):
+    cfg, sc, gb, cache, p = tiny
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    out = cache.shade(scene, pos, nrm, seed=7, frame=3, view=1, fused=False)
+    vis_gpu = host(cache.infer(pos))
+    ref = O.shade(cfg, p, gb.pos, gb.nrm, sc.lights, seed=7, frame=3, view=1, vis=vis_gpu)
+    assert np.array_equal(host(out["idx"]), ref["idx"])
+    np.testing.assert_allclose(host(out["pdf"]), ref["pdf"], rtol=1e-5, atol=1e-12)
+    np.testing.assert_allclose(host(out["wsum"]), ref["wsum"], rtol=1e-5)
+    # Neural DI against the oracle's own float64 prediction
+    ref64 = O.shade(cfg, p, gb.pos, gb.nrm, sc.lights, seed=7, frame=3, view=1)
+    c64 = O.contributions(gb.pos, gb.nrm, sc.lights)
+    # float32 error of c_i: n.d cancels at grazing angles, so its absolute
+    # error scales with the normal-incidence value I / (pi d^2), not with c_i
+    d2 = np.sum((sc.lights[None, :, :3].astype(np.float64) - gb.pos[:, None, :]) ** 2, -1)
+    c_scale = (sc.lights[None, :, 3] / (np.pi * d2)).sum(1)
+    bound = 1e-5 * c64.sum(1) + 1e-6 * c_scale
+    err = np.abs(host(out["radiance"]) - ref64["radiance"])
+    worst = np.argmax(err / bound)
+    assert np.all(err <= bound), (worst, err[worst], bound[worst], c64[worst])
+    # the oracle's own pick agrees except where weights are within rounding
+    agree = np.mean(host(out["idx"]) == ref64["idx"])
+    assert agree > 0.999
+
+
+def test_shade_shard_invariance(tiny):
+    cfg, sc, gb, cache, p = tiny
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    full = cache.shade(scene, pos, nrm, seed=1, frame=2, fused=False)
+    a = cache.shade(scene, pos[:1500], nrm[:1500], seed=1, frame=2, pixel_offset=0, fused=False)
+    b = cache.shade(scene, pos[1500:], nrm[1500:], seed=1, frame=2, pixel_offset=1500, fused=False)
+    for k in ("idx", "pdf", "wsum", "radiance"):
+        assert torch.equal(full[k], torch.cat([a[k], b[k]]))
+
+
+def test_wrs_and_di_entry_points_agree_with_shade(tiny):
+    cfg, sc, gb, cache, p = tiny
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    full = cache.shade(scene, pos, nrm, seed=5, frame=1, fused=False)
+    n = pos.shape[0]
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    pdf = torch.empty(n, device="cuda")
+    wsum = torch.empty(n, device="cuda")
+    nvc.nvc_wrs_sample(cache.handle, scene, pos, nrm, 5, 1, 0, 0, idx, pdf, wsum)
+    rad = torch.empty(n, device="cuda")
+    nvc.nvc_direct_illum(cache.handle, scene, pos, nrm, rad)
+    assert torch.equal(idx, full["idx"]) and torch.equal(pdf, full["pdf"])
+    assert torch.equal(rad, full["radiance"])
+
+
+# ---------------------------------------------------------------- training --
+
+def _train_setup(cfg, seed=0):
+    sc = S.scene_unit_cube(seed=0)
+    gb = S.gbuffer_points(0, 64, 64)
+    cache = nvc.VisibilityCache(cfg)
+    p = scaled_params(cfg, seed=seed, table_scale=0.5)
+    cache.set_params(p)
+    return sc, gb, cache, p
+
+
+@pytest.mark.parametrize("loss,slope", [("l2", 0.0), ("bce", 0.01)])
+def test_train_gradient_matches_oracle(loss, slope):
+    cfg = cfg_tiny(loss=loss, leaky_slope=slope)
+    sc, gb, cache, p = _train_setup(cfg)
+    scene = nvc.Scene.from_synth(sc)
+    g, loss_gpu = cache.train_gradient(scene, dev(gb.pos), seed=3, frame=5)
+    pos = O.training_positions(cfg.batch_positions, sc.world_min, sc.world_max, gb.pos, 3, 5)
+    y = O.visibility(pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    loss_ref, g_ref = O.gradients(cfg, p, pos, y)
+    assert abs(host(loss_gpu)[0] - loss_ref) <= 1e-6 * abs(loss_ref)
+    assert rel_err(host(g), g_ref) <= 1e-5
+    n_table = cfg.n_levels * cfg.table_size * cfg.n_features
+    assert rel_err(host(g)[n_table:], g_ref[n_table:]) <= 1e-5
+    assert rel_err(host(g)[:n_table], g_ref[:n_table]) <= 1e-5
+
+
+def test_train_step_one_adam_step_matches_oracle():
+    """Tiny workload: one Adam step (lr 1e-2) on 1024 positions x 4 lights."""
+    cfg = cfg_tiny()
+    sc, gb, cache, p = _train_setup(cfg)
+    scene = nvc.Scene.from_synth(sc)
+    loss = cache.train_step(scene, dev(gb.pos), seed=0, frame=0)
+    st = O.TrainState.fresh(p)
+    loss_ref = O.train_step(cfg, st, sc, gb.pos, seed=0, frame=0)
+    assert abs(host(loss)[0] - loss_ref) <= 1e-6 * loss_ref
+    cnt = cache.counters()
+    assert cnt["step"] == 1 and cnt["skipped"] == 0
+    theta, m, v = (host(t) for t in cache.state())
+    pos = O.training_positions(cfg.batch_positions, sc.world_min, sc.world_max, gb.pos, 0, 0)
+    y = O.visibility(pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    _, g = O.gradients(cfg, p, pos, y)
+    # step 1 of Adam moves every parameter by lr * g / (|g| + eps): its sign
+    # is decided by g, so compare where |g| is well above float32 rounding
+    clear = np.abs(g) > 1e-4 * np.abs(g).max()
+    assert clear.sum() > 1000
+    np.testing.assert_allclose(theta[clear], st.params[clear], atol=2e-6)
+    assert np.all(np.abs(theta - p) <= cfg.lr * (1 + 1e-5) + 1e-7)
+    np.testing.assert_allclose(m[clear], st.m[clear], rtol=1e-4, atol=1e-12)
+
+
+def test_online_training_matches_oracle_for_several_steps():
+    cfg = cfg_tiny(loss="bce", leaky_slope=0.01, batch_positions=512)
+    sc, gb, cache, p = _train_setup(cfg)
+    scene = nvc.Scene.from_synth(sc)
+    st = O.TrainState.fresh(p)
+    losses, losses_ref = [], []
+    for f in range(5):
+        view = S.gbuffer_points(100 + f, 16, 16)
+        losses.append(host(cache.train_step(scene, dev(view.pos), seed=2, frame=f))[0])
+        losses_ref.append(O.train_step(cfg, st, sc, view.pos, seed=2, frame=f))
+    np.testing.assert_allclose(losses, losses_ref, rtol=1e-4)
+    # Adam's early steps move parameters with near-zero gradients by about
+    # lr * sign(g), so later divergence is measured loosely
+    test_pts = S.gbuffer_points(9, 32, 32).pos
+    vis = host(cache.infer(dev(test_pts)))
+    diff = np.abs(vis - O.infer(cfg, st.params, test_pts))
+    assert diff.mean() < 1e-3 and diff.max() < 5e-2
+
+
+def test_nonfinite_gradient_skips_the_step():
+    cfg = cfg_tiny()
+    sc, gb, cache, p = _train_setup(cfg)
+    bad = p.copy()
+    bad[-1] = np.inf                          # an output weight: inf logits
+    cache.set_params(bad, step=7)
+    scene = nvc.Scene.from_synth(sc)
+    cache.train_step(scene, dev(gb.pos), seed=0, frame=0)
+    cnt = cache.counters()
+    assert cnt["step"] == 7 and cnt["skipped"] == 1 and cnt["error_flags"] & 1
+    theta = host(cache.state()[0])
+    assert np.array_equal(theta, bad)
+    cache.set_params(p, step=0)               # recovers
+    cache.train_step(scene, dev(gb.pos), seed=0, frame=0)
+    assert cache.counters()["step"] == 1
+
+
+def test_mlp_forward_backward_adjoint_matches_oracle():
+    cfg = cfg_tiny(leaky_slope=0.01)
+    sc, gb, cache, p = _train_setup(cfg)
+    n = 700
+    pos = gb.pos[:n]
+    logits = torch.empty((n, 4), device="cuda")
+    nvc.nvc_mlp_forward(cache.handle, dev(pos), logits)
+    table, Ws = O.split_params(cfg, p)
+    feat, aux = O.encode(cfg, table, pos, with_aux=True)
+    ref_logits, acts, zs = O.mlp_forward(Ws, feat, cfg.leaky_slope)
+    assert np.max(np.abs(host(logits) - ref_logits)) < 1e-5
+    dl = np.random.default_rng(1).standard_normal((n, 4)).astype(np.float32)
+    grad = torch.empty(cache.n_params, device="cuda")
+    nvc.nvc_mlp_backward(cache.handle, dev(pos), dev(dl), grad)
+    dWs, dfeat = O.mlp_backward(Ws, acts, zs, dl.astype(np.float64), cfg.leaky_slope)
+    g_ref = O.join_params(O.encode_backward(cfg, aux, dfeat), dWs)
+    assert rel_err(host(grad), g_ref) < 1e-5
+
+
+def test_frame_graph_replay_equals_eager():
+    cfg = cfg_tiny()
+    sc, gb, cache_a, p = _train_setup(cfg)
+    cache_b = nvc.VisibilityCache(cfg)
+    cache_b.set_params(p)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    outs = []
+    for cache, graph in ((cache_a, False), (cache_b, True)):
+        n = pos.shape[0]
+        v = nvc.View(pos, nrm, 0, torch.empty(n, dtype=torch.int32, device="cuda"),
+                     torch.empty(n, device="cuda"), torch.empty(n, device="cuda"),
+                     torch.empty(n, device="cuda"))
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        res = []
+        for f in range(3):
+            nvc.nvc_frame(cache.handle, scene, [v], 0, seed=4, frame=f, loss_out=loss,
+                          use_graph=graph)
+            res.append((v.idx.clone(), v.radiance.clone(), loss.clone()))
+        outs.append(res)
+        assert cache.counters()["frames"] == 3
+    for (ia, ra, la), (ib, rb, lb) in zip(*outs):
+        # training uses float atomics, so the two caches can differ in the last bits
+        assert (ia == ib).float().mean() > 0.99
+        assert torch.allclose(ra, rb, rtol=1e-4, atol=1e-6)
+        assert torch.allclose(la, lb, rtol=1e-5)
+
+
+def test_graph_replay_bitwise_with_identical_weights():
+    """Frames without a training step: graph replay and eager shading are
+    bit-identical (no float atomics on the shading path)."""
+    cfg = cfg_tiny()
+    sc, gb, cache, p = _train_setup(cfg)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    n = pos.shape[0]
+    res = []
+    for graph in (False, True, True):
+        cache.set_params(p)
+        v = nvc.View(pos, nrm, 0, torch.empty(n, dtype=torch.int32, device="cuda"),
+                     torch.empty(n, device="cuda"), torch.empty(n, device="cuda"),
+                     torch.empty(n, device="cuda"))
+        nvc.nvc_frame(cache.handle, scene, [v], nvc.NO_TRAINING, seed=4, frame=0,
+                      use_graph=graph)
+        res.append((v.idx.clone(), v.pdf.clone(), v.radiance.clone()))
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert torch.equal(a, b)
+
+
+# --------------------------------------------------------- argument errors --
+
+def test_invalid_arguments_are_rejected(tiny):
+    cfg, sc, gb, cache, p = tiny
+    pos = dev(gb.pos)
+    bad_scene = nvc.Scene(sc.lights[:3], sc.spheres)          # 3 lights != 4 outputs
+    with pytest.raises(nvc.NVCError) as e:
+        cache.shade(bad_scene, pos, dev(gb.nrm))
+    assert e.value.status == 1
+    with pytest.raises(nvc.NVCError) as e:
+        nvc.nvc_wrs_from_weights(torch.zeros((4, 300), device="cuda"), 0, 0)
+    assert e.value.status == 1
+    scene = nvc.Scene.from_synth(sc)
+    with pytest.raises(nvc.NVCError) as e:                    # train_view out of range
+        nvc.nvc_frame(cache.handle, scene, [nvc.View(pos, dev(gb.nrm))], 3, 0, 0)
+    assert e.value.status == 1
+    # a zero-size call is a no-op
+    nvc.nvc_encode(cache.handle, pos[:0], torch.empty((0, 16), device="cuda"))
+    nvc.nvc_infer(cache.handle, pos[:0], torch.empty((0, 4), device="cuda"))

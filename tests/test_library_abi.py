@@ -1,0 +1,88 @@
+"""The C ABI library builds, loads and exports every symbol include/nvc.h
+declares; host-side argument checks answer without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import nvc_synth as S
+from oracle import nvc as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_05930_gb300.build import build
+    build()
+    from paper_2506_05930_gb300 import _lib
+    return _lib.load()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(nvc_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("nvc_encode", "nvc_infer", "nvc_train_step", "nvc_wrs_sample",
+                     "nvc_direct_illum", "nvc_create", "nvc_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2506_05930_gb300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.PROTOTYPES, f"binding lacks a prototype for {name}"
+
+
+def _cfg(name="frame_1080p", **kw):
+    import paper_2506_05930_gb300.nvc as nvc
+    return nvc.make_config(S.config_by_name(name).with_(**kw))
+
+
+def test_param_count_and_level_resolutions_match_the_layout(lib):
+    import paper_2506_05930_gb300.nvc as nvc
+    for name in ("tiny_fp32", "frame_1080p", "multiview", "precision_4k", "paper"):
+        c = S.config_by_name(name)
+        cc = nvc.make_config(c)
+        assert nvc.nvc_param_count(cc) == S.param_count(c)
+        assert [nvc.nvc_level_resolution(cc, l) for l in range(c.n_levels)] == \
+            O.level_resolutions(c.base_resolution, c.growth, c.n_levels)
+    assert nvc.nvc_level_resolution(_cfg(), 99) == -1
+
+
+@pytest.mark.parametrize("field,value", [
+    ("n_levels", 0), ("n_levels", 33), ("n_features", 3), ("log2_table_size", 30),
+    ("hidden_width", 24), ("n_outputs", 257), ("leaky_slope", -0.5), ("loss_scale", 0.0),
+    ("batch_positions", 0), ("growth", 0.5), ("precision", 9), ("beta1", 1.0)])
+def test_invalid_configs_rejected_without_a_gpu(lib, field, value):
+    import paper_2506_05930_gb300.nvc as nvc
+    c = _cfg()
+    setattr(c, field, value)
+    assert nvc.nvc_param_count(c) == -1
+    h = ctypes.c_void_p()
+    assert lib.nvc_create(ctypes.byref(c), ctypes.byref(h)) == 1   # NVC_ERR_INVALID_ARG
+    assert h.value is None
+    assert len(nvc.nvc_last_error(None)) > 0
+
+
+def test_null_arguments_rejected_without_a_gpu(lib):
+    from paper_2506_05930_gb300 import _lib
+    assert lib.nvc_encode(None, None, 10, None, None) == 1
+    assert lib.nvc_wrs_from_weights(None, 10, 4, 0, 0, 0, 0, None, None, None, None) == 1
+    assert lib.nvc_wrs_from_weights(None, 10, 0, 0, 0, 0, 0, None, None, None, None) == 1
+    assert lib.nvc_trace_visibility(None, None, 1, None, None) == 1
+    sc = _lib.NvcScene()
+    assert lib.nvc_trace_visibility(ctypes.byref(sc), None, 1, None, None) == 1
+    # zero-size work is a no-op that touches nothing
+    assert lib.nvc_wrs_from_weights(None, 0, 4, 0, 0, 0, 0, None, None, None, None) == 0
+    lib.nvc_destroy(None)
