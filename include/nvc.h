@@ -225,6 +225,13 @@ nvc_status nvc_shade(nvc_handle* h, const nvc_scene* scene, const float* pos,
                      uint32_t view, int64_t pixel_offset, int32_t* idx, float* pdf,
                      float* wsum, float* radiance, int32_t fused, void* stream);
 
+/* The float32 light weights w (device [n][L]) exactly as the sampler of
+ * this configuration's shading path (nvc_shade with fused = 1 for FP16 /
+ * BF16, fused = 0 for FP32) computes them for these pixels, so that a
+ * caller can re-run the reservoir decision on identical weights. */
+nvc_status nvc_sampler_weights(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                               const float* nrm, int64_t n, float* w, void* stream);
+
 /* ---- training (Section 3.4) -------------------------------------------- */
 
 /* Binary visibility vis (device [n][n_lights], 0 or 1) of every light from

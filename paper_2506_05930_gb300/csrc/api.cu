@@ -510,6 +510,29 @@ nvc_status nvc_direct_illum(nvc_handle* h, const nvc_scene* scene, const float* 
                     h->cfg.precision != NVC_PREC_FP32, (cudaStream_t)stream);
 }
 
+nvc_status nvc_sampler_weights(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                               const float* nrm, int64_t n, float* w, void* stream) {
+  NVC_TRY(shade_checks(h, scene, pos, nrm, n, 0));
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(h, w, "w"));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->cfg.precision != NVC_PREC_FP32) {
+    std::string why;
+    if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
+    NVC_CUDA(h, launch_shade_fused(h, scene, pos, nrm, n, 0, 0, 0, 0, nullptr, nullptr, nullptr,
+                                   nullptr, nullptr, s, w));
+    return NVC_OK;
+  }
+  for (int64_t o = 0; o < n; o += h->stage_pixels) {
+    const int64_t m = n - o < h->stage_pixels ? n - o : h->stage_pixels;
+    NVC_CUDA(h, launch_encode_fwd(h, pos + 3 * o, m, h->s_feat, s));
+    NVC_CUDA(h, launch_mlp_fwd_fp32(h, h->s_feat, m, h->s_vis, true, nullptr, s));
+    NVC_CUDA(h, launch_light_weights(scene, pos + 3 * o, nrm + 3 * o, h->s_vis, m, nullptr,
+                                     w + o * h->L, s));
+  }
+  return NVC_OK;
+}
+
 nvc_status nvc_trace_visibility(const nvc_scene* scene, const float* pos, int64_t n, float* vis,
                                 void* stream) {
   NVC_TRY(check_scene(nullptr, scene, 0));

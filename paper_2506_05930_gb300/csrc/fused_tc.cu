@@ -1,21 +1,667 @@
-// Fused tensor-core shading kernel (placeholder until the tcgen05 path lands).
+// The per-pixel hot path in one kernel: hash-grid encode -> MLP on the
+// 5th-generation tensor cores (tcgen05, accumulators in TMEM) -> sigmoid ->
+// light weights -> weighted reservoir sampling + Neural DI (Sections 3.1 to
+// 3.3 of the paper).
+//
+// Layout.  One CTA = 128 threads = one 128-pixel tile at a time (persistent
+// over tiles); thread t owns pixel row t, which is also TMEM lane t of the
+// M = 128 accumulator, so every thread encodes its own pixel, reads its own
+// row of every layer's output and runs its own pixel's sampler.  Operands
+// live in shared memory in the no-swizzle K-major core-matrix layout (8 rows
+// x 16 bytes per core matrix; the K-adjacent core matrix 128 bytes on, the
+// next 8-row group K*2*8 bytes on).  All layers' weights are loaded once
+// per CTA; the activation tile is rewritten in place between layers.  One
+// elected thread issues K/16 tcgen05.mma (M=128, N=layer width, fp16 or
+// bf16 operands, fp32 accumulate) per layer and commits to an mbarrier.
+// Several CTAs per SM overlap one CTA's gathers with another's MMAs and
+// sampler arithmetic; the TMEM columns per CTA are a power of two and the
+// CTAs per SM are capped so that their columns fit the 512 available.
+//
+// Every wait on the mbarrier is bounded (about one second); a timeout sets
+// an error flag in the handle's status and every thread of the CTA leaves
+// the tile loop together, freeing TMEM on the way out.
 #include "nvc_internal.cuh"
+#include "hashgrid.cuh"
 
 namespace nvc {
 
-size_t mlp_packed_bytes(const nvc_handle*) { return 0; }
+namespace {
 
-cudaError_t launch_pack_mlp(nvc_handle*, cudaStream_t) { return cudaSuccess; }
+constexpr int kTileM = 128;
+constexpr int kMaxLayers = NVC_MAX_HIDDEN_LAYERS + 1;
 
-bool fused_supported(const nvc_handle*, std::string* why) {
-  *why = "fused tensor-core kernel not available";
-  return false;
+struct LayerDesc {
+  int K;           // reduction size (multiple of 16)
+  int N;           // MMA width (multiple of 16)
+  int N_real;      // real output neurons of the layer
+  int K_real;      // real inputs of the layer
+  int w_byte_off;  // offset of the packed matrix in the weight image
+  uint32_t idesc;  // tcgen05 instruction descriptor
+};
+
+struct FusedArgs {
+  const float* pos;
+  const float* nrm;
+  int64_t n;
+  const float* table;
+  EncodeParams ep;
+  int F;
+  const uint4* wimg;
+  int wimg_bytes;
+  int n_layers;
+  LayerDesc layer[kMaxLayers];
+  int kmax;
+  float slope;
+  int L;
+  uint32_t tmem_cols;
+  const float* lights;
+  uint32_t k0, k1, frame, view;
+  int64_t pixel_offset;
+  int32_t* idx;
+  float* pdf;
+  float* wsum;
+  float* radiance;
+  float* vis_out;
+  float* w_out;      // optional: the light weights the sampler uses, [n][L]
+  int32_t* status;
+};
+
+// ---- PTX wrappers -----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-cudaError_t launch_shade_fused(const nvc_handle*, const nvc_scene*, const float*, const float*,
-                               int64_t, uint64_t, uint32_t, uint32_t, int64_t, int32_t*, float*,
-                               float*, float*, float*, cudaStream_t) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of the barrier, for at most ~1 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t holder, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle: start, leading (K-direction)
+// and stride (M/N-direction) byte offsets, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane; the registers are
+// tied to the wait so no use can be scheduled before the load completes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31])::"memory");
+}
+
+// ---- operand packing ------------------------------------------------------
+// Byte offset of element (row, k) of a K-major operand with K columns in the
+// no-swizzle core-matrix layout.
+__host__ __device__ __forceinline__ uint32_t cm_offset(int row, int k, int K, int esize) {
+  return (uint32_t)((row >> 3) * (K * 8 * esize) + (k >> 3) * 128 + (row & 7) * 16 +
+                    (k & 7) * esize);
+}
+
+template <int PREC>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if constexpr (PREC == NVC_PREC_BF16) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+// ---- the sampler's arithmetic ----------------------------------------------
+__device__ __forceinline__ float sigmoid_fast(float z) {
+  return __fdividef(1.0f, 1.0f + __expf(-z));
+}
+
+// Unshadowed contribution of a point light (Lambertian, albedo 1):
+// (I/pi) * (n.d) / (|d| * max(|d|^2, 1e-6)) for n.d > 0, with a hardware
+// reciprocal square root.
+__device__ __forceinline__ float contribution_fast(float px, float py, float pz, float nx,
+                                                   float ny, float nz, float4 l) {
+  const float dx = l.x - px, dy = l.y - py, dz = l.z - pz;
+  const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float ndl = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
+  const float r = rsqrtf(d2);
+  const float inv = d2 >= 1e-6f ? r * r : 1e6f;
+  return ndl > 0.0f ? l.w * ndl * r * inv : 0.0f;
+}
+
+// q = max(1, floor(w * 2^(23 - e))) for w > 0 (e = ilogb(wmax)), from the
+// float bits: w = m * 2^(ew - 150) with m the 24-bit significand, so the
+// product is m >> (E - ew) with E, ew the biased exponents.  Valid for a
+// normal wmax (E >= 1) and any 0 <= w <= wmax.
+__device__ __forceinline__ uint32_t quantize_bits(float w, uint32_t E) {
+  if (!(w > 0.0f)) return 0u;
+  const uint32_t b = __float_as_uint(w);
+  const uint32_t ew = b >> 23;
+  const uint32_t m = (b & 0x7FFFFFu) | (ew ? 0x800000u : 0u);
+  const uint32_t sh = E - (ew ? ew : 1u);
+  const uint32_t q = sh < 24u ? (m >> sh) : 0u;
+  return q ? q : 1u;
+}
+
+__device__ __forceinline__ uint32_t pick_word(uint4 r, int lane) {
+  return lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
+}
+
+// ---- the kernel ----------------------------------------------------------------
+template <int F, int PREC>
+__global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_constant__ FusedArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* s_w = smem;
+  uint8_t* s_a = smem + a.wimg_bytes;
+  float4* s_l = reinterpret_cast<float4*>(s_a + kTileM * a.kmax * 2);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_l + (a.L > 0 ? a.L : 1));
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 1);
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+
+  for (int e = t; e < a.wimg_bytes / 16; e += kTileM)
+    reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
+  if (a.lights) {
+    for (int e = t; e < a.L; e += kTileM) {
+      float4 l = reinterpret_cast<const float4*>(a.lights)[e];
+      l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+      s_l[e] = l;
+    }
+  }
+  const uint32_t bar = smem_u32(s_bar);
+  if (t == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(s_tmem), a.tmem_cols);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t a_base = smem_u32(s_a);
+  const uint32_t w_base = smem_u32(s_w);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const int din = a.ep.n_levels * F;
+  const int K0 = a.layer[0].K;
+  const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+    const int64_t row = tile * kTileM + t;
+    const bool live = row < a.n;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (live) {
+      px = __ldg(a.pos + 3 * row);
+      py = __ldg(a.pos + 3 * row + 1);
+      pz = __ldg(a.pos + 3 * row + 2);
+    }
+    // ---- encode this pixel into the layer-0 A tile ------------------------
+    {
+      const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
+      const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
+      const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
+      constexpr int LPC = F >= 8 ? 1 : 8 / F;   // levels per 8-feature chunk
+      for (int c = 0; c < K0 / 8; ++c) {
+        float f8[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) f8[s] = 0.0f;
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < LPC; ++q) {
+            const int l = (c * 8) / F + q;
+            if (F <= 8 && l * F < din && (l * F) / 8 == c) {
+              Corners cr;
+              level_corners(a.ep, l, x, y, z, cr);
+              const float* tab = a.table + ((int64_t)l << a.ep.log2_table) * F;
+              float acc[F];
+#pragma unroll
+              for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+#pragma unroll
+              for (int d = 0; d < 8; ++d) {
+                const FeatVec<F> v = load_feat<F>(tab + (int64_t)cr.row[d] * F);
+#pragma unroll
+                for (int f = 0; f < F; ++f) acc[f] = fmaf(cr.w[d], v.v[f], acc[f]);
+              }
+#pragma unroll
+              for (int f = 0; f < F; ++f) {
+                const int k = l * F + f - c * 8;
+                if (k >= 0 && k < 8) f8[k] = acc[f];
+              }
+            }
+          }
+        }
+        uint4 pk;
+        pk.x = pack2<PREC>(f8[0], f8[1]);
+        pk.y = pack2<PREC>(f8[2], f8[3]);
+        pk.z = pack2<PREC>(f8[4], f8[5]);
+        pk.w = pack2<PREC>(f8[6], f8[7]);
+        *reinterpret_cast<uint4*>(s_a + cm_offset(t, c * 8, K0, 2)) = pk;
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+
+    // ---- the MLP, layer by layer --------------------------------------------
+    for (int k = 0; k < a.n_layers && !failed; ++k) {
+      const LayerDesc ld = a.layer[k];
+      if (t == 0) {
+        tc_fence_after();
+        const uint32_t sbo = (uint32_t)ld.K * 16u;
+        const uint32_t wb = w_base + (uint32_t)ld.w_byte_off;
+        for (int kk = 0; kk < ld.K / 16; ++kk) {
+          mma_f16(tmem, smem_desc(a_base + kk * 256, 128, sbo), smem_desc(wb + kk * 256, 128, sbo),
+                  ld.idesc, kk > 0 ? 1u : 0u);
+        }
+        mma_commit(bar);
+      }
+      const bool ok = mbar_wait_bounded(bar, phase);
+      phase ^= 1u;
+      tc_fence_after();
+      if (k + 1 < a.n_layers) {
+        // hidden activation -> operand A of the next layer (K = this N)
+        const int Kn = ld.N;
+        for (int c0 = 0; c0 < ld.N; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(t_lane + (uint32_t)c0, r);
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            float h[8];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              const float zz = __uint_as_float(r[g * 8 + s]);
+              h[s] = zz > 0.0f ? zz : a.slope * zz;
+            }
+            uint4 pk;
+            pk.x = pack2<PREC>(h[0], h[1]);
+            pk.y = pack2<PREC>(h[2], h[3]);
+            pk.z = pack2<PREC>(h[4], h[5]);
+            pk.w = pack2<PREC>(h[6], h[7]);
+            if (c0 + g * 8 < Kn)
+              *reinterpret_cast<uint4*>(s_a + cm_offset(t, c0 + g * 8, Kn, 2)) = pk;
+          }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        failed = __syncthreads_or(!ok) != 0;
+        continue;
+      }
+
+      // ---- output layer: sigmoid, light weights, WRS, Neural DI -------------
+      const int L = a.L;
+      if (a.vis_out) {
+        for (int c0 = 0; c0 < L; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(t_lane + (uint32_t)c0, r);
+          if (live) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (c0 + j < L) a.vis_out[row * L + c0 + j] = sigmoid_fast(__uint_as_float(r[j]));
+          }
+        }
+      } else {
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (live) {
+          nx = __ldg(a.nrm + 3 * row);
+          ny = __ldg(a.nrm + 3 * row + 1);
+          nz = __ldg(a.nrm + 3 * row + 2);
+        }
+        float wreg[32];
+        float wmax = 0.0f, sum = 0.0f, di = 0.0f;
+        for (int c0 = 0; c0 < L; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(t_lane + (uint32_t)c0, r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int i = c0 + j;
+            float w = 0.0f;
+            if (i < L) {
+              const float v = sigmoid_fast(__uint_as_float(r[j]));
+              const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
+              w = fmaxf(v, bits_f(kVisClampBits)) * c;
+              if (a.w_out && live) a.w_out[row * L + i] = w;
+              wmax = fmaxf(wmax, w);
+              sum += w;
+              di = fmaf(v, c, di);
+            }
+            wreg[j] = w;
+          }
+        }
+        int sel = -1;
+        float wsel = 0.0f;
+        // tcgen05.ld is warp-collective: the chunk loop runs in every thread,
+        // the per-pixel work only where there is something to pick
+        const bool active = live && wmax > 0.0f;
+        const uint32_t E = __float_as_uint(wmax) >> 23;
+        const int e_sub = (active && E == 0) ? ilogbf(wmax) : 0;
+        const uint32_t pixel = (uint32_t)(a.pixel_offset + row);
+        uint32_t Q = 0;
+        uint4 rr = make_uint4(0, 0, 0, 0);
+        for (int c0 = 0; c0 < L; c0 += 32) {
+          uint32_t r[32];
+          if (L > 32) tmem_ld32(t_lane + (uint32_t)c0, r);
+          if (active) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int i = c0 + j;
+              if (i < L) {
+                float w = wreg[j];
+                if (L > 32) {
+                  const float v = sigmoid_fast(__uint_as_float(r[j]));
+                  w = fmaxf(v, bits_f(kVisClampBits)) *
+                      contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
+                }
+                if ((i & 3) == 0)
+                  rr = philox4x32_10(make_uint4(pixel, a.frame, a.view,
+                                                ((uint32_t)(i >> 2) << 4) | kTagWrs),
+                                     a.k0, a.k1);
+                const uint32_t q = E ? quantize_bits(w, E) : quantize_weight(w, e_sub);
+                Q += q;
+                if (q != 0u && __umulhi(pick_word(rr, i & 3), Q) < q) {
+                  sel = i;
+                  wsel = w;
+                }
+              }
+            }
+          }
+        }
+        if (live) {
+          if (a.idx) a.idx[row] = sel;
+          if (a.pdf) a.pdf[row] = sel >= 0 ? wsel / sum : 0.0f;
+          if (a.wsum) a.wsum[row] = sum;
+          if (a.radiance) a.radiance[row] = di;
+        }
+      }
+      tc_fence_before();
+      failed = __syncthreads_or(!ok) != 0;
+    }
+  }
+  if (failed && t == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
+  __syncthreads();
+  if (failed) mbar_wait_bounded(bar, phase ^ 1u);   // let an MMA in flight land
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, a.tmem_cols);
+  }
+}
+
+// ---- weight packing (fp32 master -> tensor-core operand image) -------------
+struct PackArgs {
+  int n_layers;
+  int K[kMaxLayers], N[kMaxLayers], K_real[kMaxLayers], N_real[kMaxLayers];
+  int64_t w_off[kMaxLayers];     // float offset of W_k in the parameter vector
+  int byte_off[kMaxLayers + 1];  // byte offset of layer k in the image
+  int esize;
+};
+
+template <int PREC>
+__global__ void pack_mlp_kernel(const float* __restrict__ params, PackArgs p, uint8_t* out) {
+  const int total = p.byte_off[p.n_layers] / p.esize;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < p.n_layers && e * p.esize >= p.byte_off[k + 1]) ++k;
+    const int local = e - p.byte_off[k] / p.esize;
+    // invert cm_offset: 64 elements per core matrix, K/8 core matrices per row group
+    const int grp = local >> 6, within = local & 63;
+    const int kg = grp % (p.K[k] / 8), ng = grp / (p.K[k] / 8);
+    const int n = ng * 8 + (within >> 3), kk = kg * 8 + (within & 7);
+    const float v = (n < p.N_real[k] && kk < p.K_real[k])
+                        ? params[p.w_off[k] + (int64_t)n * p.K_real[k] + kk]
+                        : 0.0f;
+    if constexpr (PREC == NVC_PREC_BF16)
+      reinterpret_cast<__nv_bfloat16*>(out + p.byte_off[k])[local] = __float2bfloat16_rn(v);
+    else
+      reinterpret_cast<__half*>(out + p.byte_off[k])[local] = __float2half_rn(v);
+  }
+}
+
+int round16(int x) { return (x + 15) & ~15; }
+
+uint32_t make_idesc(int M, int N, int prec) {
+  const uint32_t ab = prec == NVC_PREC_BF16 ? 1u : 0u;  // kind::f16: 0 = f16, 1 = bf16
+  return (1u << 4)                                       // D = f32
+         | (ab << 7) | (ab << 10)                        // A, B formats; both K-major
+         | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+bool tc_precision(int prec) { return prec == NVC_PREC_FP16 || prec == NVC_PREC_BF16; }
+
+void layer_geometry(const nvc_handle* h, PackArgs& p) {
+  p.n_layers = h->n_layers;
+  p.esize = 2;
+  int off = 0;
+  for (int k = 0; k < h->n_layers; ++k) {
+    p.K_real[k] = h->w_in[k];
+    p.N_real[k] = h->w_out[k];
+    p.K[k] = round16(h->w_in[k]);
+    p.N[k] = round16(h->w_out[k]);
+    p.w_off[k] = h->w_off[k];
+    p.byte_off[k] = off;
+    off += p.K[k] * p.N[k] * p.esize;
+  }
+  p.byte_off[h->n_layers] = off;
+}
+
+uint32_t tmem_cols_for(const PackArgs& p) {
+  int mx = 32;
+  for (int k = 0; k < p.n_layers; ++k) mx = p.N[k] > mx ? p.N[k] : mx;
+  uint32_t c = 32;
+  while ((int)c < mx) c <<= 1;
+  return c;
+}
+
+size_t fused_smem(const nvc_handle* h, const PackArgs& p) {
+  int kmax = 16;
+  for (int k = 0; k < p.n_layers; ++k) kmax = p.K[k] > kmax ? p.K[k] : kmax;
+  return (size_t)p.byte_off[p.n_layers] + (size_t)kTileM * kmax * 2 + 16 * (size_t)h->L + 64;
+}
+
+template <int F, int PREC>
+cudaError_t launch_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cudaStream_t s) {
+  auto kern = fused_shade_kernel<F, PREC>;
+  // cap CTAs per SM so their TMEM columns fit in 512
+  const int max_ctas = (int)(512u / a.tmem_cols);
+  size_t smem = smem_needed;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  for (;;) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileM, smem);
+    if (e != cudaSuccess) return e;
+    if (occ <= max_ctas || smem + 4096 > 227 * 1024) break;
+    smem += 4096;
+  }
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  if (occ > max_ctas) return cudaErrorInvalidConfiguration;
+  const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+  const int64_t cap = (int64_t)occ * num_sms;
+  const int grid = (int)(n_tiles < cap ? n_tiles : cap);
+  kern<<<grid, kTileM, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t mlp_packed_bytes(const nvc_handle* h) {
+  if (!tc_precision(h->cfg.precision)) return 0;
+  PackArgs p{};
+  layer_geometry(h, p);
+  return (size_t)p.byte_off[p.n_layers];
+}
+
+cudaError_t launch_pack_mlp(nvc_handle* h, cudaStream_t s) {
+  if (!h->mlp_packed) return cudaSuccess;
+  PackArgs p{};
+  layer_geometry(h, p);
+  const int total = p.byte_off[p.n_layers] / p.esize;
+  const int blocks = (total + 255) / 256;
+  if (h->cfg.precision == NVC_PREC_BF16)
+    pack_mlp_kernel<NVC_PREC_BF16><<<blocks, 256, 0, s>>>(h->params, p, (uint8_t*)h->mlp_packed);
+  else
+    pack_mlp_kernel<NVC_PREC_FP16><<<blocks, 256, 0, s>>>(h->params, p, (uint8_t*)h->mlp_packed);
+  return cudaGetLastError();
+}
+
+bool fused_supported(const nvc_handle* h, std::string* why) {
+  if (!tc_precision(h->cfg.precision)) {
+    *why = "the fused tensor-core kernel runs in FP16 or BF16 precision";
+    return false;
+  }
+  PackArgs p{};
+  layer_geometry(h, p);
+  for (int k = 0; k < p.n_layers; ++k)
+    if (p.N[k] > 256) {
+      *why = "layer wider than 256";
+      return false;
+    }
+  if (fused_smem(h, p) > 227 * 1024) {
+    *why = "weights and tile exceed shared memory";
+    return false;
+  }
+  return true;
+}
+
+cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const float* pos,
+                               const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
+                               uint32_t view, int64_t pixel_offset, int32_t* idx, float* pdf,
+                               float* wsum, float* radiance, float* vis_out, cudaStream_t s,
+                               float* w_out) {
+  if (n == 0) return cudaSuccess;
+  PackArgs p{};
+  layer_geometry(h, p);
+  FusedArgs a{};
+  a.pos = pos;
+  a.nrm = nrm;
+  a.n = n;
+  a.table = h->params;
+  a.ep = encode_params(h);
+  a.F = h->F;
+  a.wimg = reinterpret_cast<const uint4*>(h->mlp_packed);
+  a.wimg_bytes = p.byte_off[p.n_layers];
+  a.n_layers = h->n_layers;
+  a.kmax = 16;
+  for (int k = 0; k < h->n_layers; ++k) {
+    a.layer[k].K = p.K[k];
+    a.layer[k].N = p.N[k];
+    a.layer[k].N_real = p.N_real[k];
+    a.layer[k].K_real = p.K_real[k];
+    a.layer[k].w_byte_off = p.byte_off[k];
+    a.layer[k].idesc = make_idesc(kTileM, p.N[k], h->cfg.precision);
+    a.kmax = p.K[k] > a.kmax ? p.K[k] : a.kmax;
+  }
+  a.slope = h->cfg.leaky_slope;
+  a.L = h->L;
+  a.tmem_cols = tmem_cols_for(p);
+  a.lights = sc ? sc->lights : nullptr;
+  a.k0 = (uint32_t)seed;
+  a.k1 = (uint32_t)(seed >> 32);
+  a.frame = frame;
+  a.view = view;
+  a.pixel_offset = pixel_offset;
+  a.idx = idx;
+  a.pdf = pdf;
+  a.wsum = wsum;
+  a.radiance = radiance;
+  a.vis_out = vis_out;
+  a.w_out = w_out;
+  a.status = h->status;
+  const size_t smem = fused_smem(h, p);
+  const bool bf16 = h->cfg.precision == NVC_PREC_BF16;
+  switch (h->F) {
+    case 1: return bf16 ? launch_typed<1, NVC_PREC_BF16>(a, smem, h->num_sms, s)
+                        : launch_typed<1, NVC_PREC_FP16>(a, smem, h->num_sms, s);
+    case 2: return bf16 ? launch_typed<2, NVC_PREC_BF16>(a, smem, h->num_sms, s)
+                        : launch_typed<2, NVC_PREC_FP16>(a, smem, h->num_sms, s);
+    case 4: return bf16 ? launch_typed<4, NVC_PREC_BF16>(a, smem, h->num_sms, s)
+                        : launch_typed<4, NVC_PREC_FP16>(a, smem, h->num_sms, s);
+    case 8: return bf16 ? launch_typed<8, NVC_PREC_BF16>(a, smem, h->num_sms, s)
+                        : launch_typed<8, NVC_PREC_FP16>(a, smem, h->num_sms, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace nvc

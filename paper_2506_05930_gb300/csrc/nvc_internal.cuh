@@ -233,7 +233,8 @@ bool fused_supported(const nvc_handle* h, std::string* why);
 cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const float* pos,
                                const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
                                uint32_t view, int64_t pixel_offset, int32_t* idx, float* pdf,
-                               float* wsum, float* radiance, float* vis_out, cudaStream_t s);
+                               float* wsum, float* radiance, float* vis_out, cudaStream_t s,
+                               float* w_out = nullptr);
 size_t mlp_packed_bytes(const nvc_handle* h);
 
 }  // namespace nvc

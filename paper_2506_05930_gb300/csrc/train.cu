@@ -188,11 +188,15 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
   const AdamScalars sc = *scp;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  // approximate sqrt and divide: most table rows have zero gradient, and
+  // 0 / eps would send the correctly rounded divide down its slow path
   auto upd = [&](float& th, float g, float& mm, float& vv) {
     g *= sc.inv_scale;
     mm = beta1 * mm + (1.0f - beta1) * g;
     vv = beta2 * vv + (1.0f - beta2) * g * g;
-    th -= sc.lr_over_bc1 * mm / (sqrtf(vv * sc.inv_bc2) + eps);
+    float s;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(vv * sc.inv_bc2));
+    th -= __fdividef(sc.lr_over_bc1 * mm, s + eps);
   };
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += stride) {
     float4 g = reinterpret_cast<float4*>(grad)[e];

@@ -206,6 +206,11 @@ def nvc_shade(h, scene: Scene, pos, nrm, seed, frame, view=0, pixel_offset=0, id
                         1 if fused else 0, _stream(stream)), h)
 
 
+def nvc_sampler_weights(h, scene: Scene, pos, nrm, w, stream=None):
+    check(lib.nvc_sampler_weights(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0], _ptr(w),
+                                  _stream(stream)), h)
+
+
 def nvc_trace_visibility(scene: Scene, pos, vis, stream=None):
     check(lib.nvc_trace_visibility(scene.ref, _ptr(pos), pos.shape[0], _ptr(vis),
                                    _stream(stream)))

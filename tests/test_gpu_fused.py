@@ -1,0 +1,166 @@
+"""The fused tensor-core kernel (encode + tcgen05 MLP + sampler + Neural
+DI) against the CPU oracle, through the C ABI.
+
+FP16: visibility within 2e-3 of the float64 oracle; the reservoir pick is
+bit-exact on the weights the kernel itself used (read back with
+nvc_sampler_weights); the weights, pdf, sum and Neural DI within tolerances
+derived from the visibility bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import nvc_synth as S
+from oracle import nvc as O
+from helpers import cfg_tiny, cfg_frame, scaled_params
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2506_05930_gb300 import nvc
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def make(cfg, seed=0, table_scale=1.0):
+    cache = nvc.VisibilityCache(cfg)
+    p = scaled_params(cfg, seed=seed, table_scale=table_scale)
+    cache.set_params(p)
+    return cache, p
+
+
+FP16_TOL = 2e-3
+
+
+@pytest.mark.parametrize("n", [1, 127, 129, 1000, 4096])
+def test_fused_infer_fp16_matches_oracle(n):
+    cfg = cfg_tiny(precision="fp16")
+    cache, p = make(cfg)
+    pos = S.gbuffer_points(3, 64, 64).pos[:n]
+    vis = host(cache.infer(dev(pos)))
+    ref = O.infer(cfg, p, pos)
+    assert np.max(np.abs(vis - ref)) <= FP16_TOL
+    assert np.std(ref) > 1e-2
+
+
+@pytest.mark.parametrize("name,L", [("frame_1080p", 32), ("multiview", 128),
+                                    ("precision_4k", 256), ("paper", 32)])
+def test_fused_infer_fp16_network_shapes(name, L):
+    cfg = S.config_by_name(name).with_(precision="fp16", batch_positions=256)
+    assert cfg.n_outputs == L
+    cache, p = make(cfg, seed=2, table_scale=0.5)
+    lo, hi = np.array(cfg.bounds_min), np.array(cfg.bounds_max)
+    pos = np.random.default_rng(1).uniform(lo, hi, (700, 3)).astype(np.float32)
+    vis = host(cache.infer(dev(pos)))
+    ref = O.infer(cfg, p, pos)
+    err = np.abs(vis - ref)
+    assert err.max() <= FP16_TOL, err.max()
+
+
+def test_fused_infer_bf16_error_is_stated():
+    cfg = cfg_frame(precision="bf16", batch_positions=256)
+    cache, p = make(cfg, seed=2, table_scale=0.5)
+    pos = np.random.default_rng(1).uniform(0, 10, (2000, 3)).astype(np.float32)
+    err = np.abs(host(cache.infer(dev(pos))) - O.infer(cfg, p, pos))
+    # bf16 keeps 8 significand bits: about 8x the fp16 error
+    assert err.mean() <= 2e-3 and err.max() <= 2e-2, (err.mean(), err.max())
+
+
+def _shade_case(cfg, sc, gb, seed=0, table_scale=1.0, offset=0):
+    cache, p = make(cfg, seed=seed, table_scale=table_scale)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    out = cache.shade(scene, pos, nrm, seed=11, frame=4, view=2, pixel_offset=offset, fused=True)
+    w = torch.empty((gb.n, cfg.n_outputs), device="cuda")
+    nvc.nvc_sampler_weights(cache.handle, scene, pos, nrm, w)
+    return cache, p, out, host(w)
+
+
+@pytest.mark.parametrize("L", [4, 32, 128, 256])
+def test_fused_shade_pick_bitexact_on_its_weights(L):
+    if L in (4, 128):
+        cfg = (cfg_tiny(precision="fp16") if L == 4 else
+               S.config_by_name("multiview").with_(precision="fp16", batch_positions=256))
+        sc = S.scene_unit_cube(seed=0, n_lights=L)
+        gb = S.gbuffer_points(0, 64, 64)
+    else:
+        base = {32: "frame_1080p", 256: "precision_4k"}[L]
+        cfg = S.config_by_name(base).with_(precision="fp16", batch_positions=256)
+        sc = S.scene_heightfield(seed=5, n_lights=L, n_spheres=4, n_boxes=4)
+        gb = S.gbuffer_heightfield(seed=5, width=61, height=53)
+    cache, p, out, w = _shade_case(cfg, sc, gb, offset=77)
+    idx, pdf, wsum = O.wrs_select(w, 77 + np.arange(gb.n), 11, 4, 2)
+    assert np.array_equal(host(out["idx"]), idx)
+    np.testing.assert_allclose(host(out["wsum"]), wsum, rtol=1e-5, atol=1e-30)
+    np.testing.assert_allclose(host(out["pdf"]), pdf, rtol=1e-5, atol=1e-30)
+    # the weights themselves against the oracle's float64 visibility and contributions
+    v64 = O.infer(cfg, p, gb.pos)
+    c64 = O.contributions(gb.pos, gb.nrm, sc.lights)
+    w64 = np.maximum(v64, 0.001) * c64
+    assert np.all(np.abs(w - w64) <= FP16_TOL * c64 + 1e-5 * w64 + 1e-30)
+    # Neural DI
+    di = host(out["radiance"])
+    ref_di = O.neural_di(v64, c64)
+    assert np.all(np.abs(di - ref_di) <= FP16_TOL * c64.sum(1) + 1e-5 * ref_di + 1e-30)
+
+
+def test_fused_shade_shard_invariance_and_zero_size():
+    cfg = cfg_tiny(precision="fp16")
+    sc = S.scene_unit_cube(seed=0)
+    gb = S.gbuffer_points(0, 64, 64)
+    cache, p = make(cfg)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    full = cache.shade(scene, pos, nrm, seed=1, frame=2, fused=True)
+    a = cache.shade(scene, pos[:1001], nrm[:1001], seed=1, frame=2, fused=True)
+    b = cache.shade(scene, pos[1001:], nrm[1001:], seed=1, frame=2, pixel_offset=1001, fused=True)
+    for k in ("idx", "pdf", "wsum", "radiance"):
+        assert torch.equal(full[k], torch.cat([a[k], b[k]])), k
+    cache.shade(scene, pos[:0], nrm[:0], fused=True)
+
+
+def test_fused_and_separate_paths_agree():
+    cfg = cfg_tiny(precision="fp16")
+    sc = S.scene_unit_cube(seed=0)
+    gb = S.gbuffer_points(0, 64, 64)
+    cache, p = make(cfg)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    f = cache.shade(scene, pos, nrm, seed=3, frame=1, fused=True)
+    u = cache.shade(scene, pos, nrm, seed=3, frame=1, fused=False)
+    assert (host(f["idx"]) == host(u["idx"])).mean() > 0.99
+    np.testing.assert_allclose(host(f["radiance"]), host(u["radiance"]), rtol=5e-3, atol=1e-4)
+
+
+def test_fused_full_1080p_frame_sampled():
+    """The workload the bench times, in the same launch configuration: all
+    2,073,600 pixels in one call; 4096 sampled pixels checked against the
+    oracle one by one."""
+    cfg = cfg_frame()
+    sc = S.scene_heightfield(seed=1, n_lights=32, n_spheres=32, n_boxes=32)
+    gb = S.gbuffer_heightfield(seed=1, width=1920, height=1080)
+    cache, p = make(cfg, seed=0, table_scale=0.3)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    out = cache.shade(scene, pos, nrm, seed=9, frame=500, fused=True)
+    w = torch.empty((gb.n, 32), device="cuda")
+    nvc.nvc_sampler_weights(cache.handle, scene, pos, nrm, w)
+    pick = np.random.default_rng(0).choice(gb.n, 4096, replace=False)
+    w_s = host(w[torch.from_numpy(pick).cuda()])
+    idx, pdf, wsum = O.wrs_select(w_s, pick, 9, 500, 0)
+    assert np.array_equal(host(out["idx"])[pick], idx)
+    v64 = O.infer(cfg, p, gb.pos[pick])
+    vis = host(cache.infer(pos[torch.from_numpy(pick).cuda()]))
+    assert np.max(np.abs(vis - v64)) <= FP16_TOL
+    c64 = O.contributions(gb.pos[pick], gb.nrm[pick], sc.lights)
+    ref_di = O.neural_di(v64, c64)
+    di = host(out["radiance"])[pick]
+    assert np.all(np.abs(di - ref_di) <= FP16_TOL * c64.sum(1) + 1e-5 * ref_di + 1e-30)
+    assert (host(out["idx"]) >= 0).mean() > 0.5
