@@ -44,7 +44,10 @@ MlpDims make_dims(const nvc_handle* h, bool transposed) {
   d.n_layers = h->n_layers;
   d.slope = h->cfg.leaky_slope;
   int off = 0;
-  d.maxdim = h->din;
+  // the shared activation buffers hold the encoded input and hidden layers;
+  // the output layer goes straight to global memory (and, in the backward,
+  // its delta is read from there)
+  d.maxdim = h->din > h->width ? h->din : h->width;
   for (int k = 0; k < h->n_layers; ++k) {
     d.in[k] = h->w_in[k];
     d.out[k] = h->w_out[k];
@@ -53,7 +56,6 @@ MlpDims make_dims(const nvc_handle* h, bool transposed) {
     d.w_off[k] = h->w_off[k];
     d.s_off[k] = off;
     off += transposed ? d.in[k] * d.pad_out[k] : d.out[k] * d.pad_in[k];
-    if (d.out[k] > d.maxdim) d.maxdim = d.out[k];
   }
   d.s_weights = off;
   return d;
@@ -177,11 +179,6 @@ __global__ void __launch_bounds__(kRows) mlp_bwd_kernel(int64_t n, const float* 
     const int64_t row0 = tile * kRows;
     const int rows = (int)(n - row0 < kRows ? n - row0 : kRows);
     const float* dtop = delta + top * delta_layer_stride;
-    for (int e = t; e < kRows * L; e += kRows) {
-      const int r = e / L, j = e - r * L;
-      buf0[j * kStride + r] = r < rows ? dtop[(row0 + r) * L + j] : 0.0f;
-    }
-    __syncthreads();
     float* src = buf0;
     float* dst = buf1;
     const int64_t row = row0 + t;
@@ -189,10 +186,11 @@ __global__ void __launch_bounds__(kRows) mlp_bwd_kernel(int64_t n, const float* 
     for (int k = top; k >= 0; --k) {
       const int in = d.in[k], out = d.out[k], pi = d.pad_in[k];
       const float* wk = sw + d.s_off[k];
+      const float* g_row = dtop + (live ? row : 0) * L;   // top layer: delta from global
       for (int ib = 0; ib < pi; ib += 8) {
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int j = 0; j < out; ++j) {
-          const float g = src[j * kStride + t];
+          const float g = k == top ? (live ? g_row[j] : 0.0f) : src[j * kStride + t];
           const float4 w0 = *reinterpret_cast<const float4*>(wk + j * pi + ib);
           const float4 w1 = *reinterpret_cast<const float4*>(wk + j * pi + ib + 4);
           acc[0] = fmaf(w0.x, g, acc[0]);
