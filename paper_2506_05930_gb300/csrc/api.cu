@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -182,6 +183,31 @@ struct StageScope {
 void count_launches(nvc_handle* h, int n) { h->launches += n; }
 
 }  // namespace
+
+namespace nvc {
+
+int blocks_per_sm(const void* func, int block, size_t dyn_smem) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) return 1;
+  int dev = 0, regs_sm = 65536, smem_sm = 0, thr_sm = 2048, blk_sm = 32, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int warps = (block + 31) / 32;
+  int lim = blk_sm;
+  lim = std::min(lim, thr_sm / (warps * 32));
+  // registers are allocated per warp in units of 256
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+  if (regs_warp > 0) lim = std::min(lim, regs_sm / (regs_warp * warps));
+  const size_t smem = fa.sharedSizeBytes + dyn_smem + (size_t)reserved;
+  if (smem > 0) lim = std::min(lim, (int)((size_t)smem_sm / smem));
+  return lim < 1 ? 1 : lim;
+}
+
+}  // namespace nvc
 
 // ============================================================================
 extern "C" {

@@ -228,8 +228,48 @@ __device__ __forceinline__ uint32_t pick_word(uint4 r, int lane) {
   return lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
 }
 
+// ---- encode of one (pixel, level) ------------------------------------------
+// Same arithmetic as the separate encode kernel (float32 cell, hashed
+// corners, trilinear blend), with the hash's per-axis terms shared between
+// the corners that use them.
+template <int F>
+__device__ __forceinline__ void encode_level(const EncodeParams& ep, const float* __restrict__ table,
+                                             int l, float x, float y, float z, float (&acc)[F]) {
+  const int n = ep.res[l];
+  const float nf = (float)n;
+  int cx = __float2int_rd(__fmul_rn(x, nf)), cy = __float2int_rd(__fmul_rn(y, nf)),
+      cz = __float2int_rd(__fmul_rn(z, nf));
+  cx = min(cx, n - 1);
+  cy = min(cy, n - 1);
+  cz = min(cz, n - 1);
+  const float fx = __fsub_rn(__fmul_rn(x, nf), (float)cx);
+  const float fy = __fsub_rn(__fmul_rn(y, nf), (float)cy);
+  const float fz = __fsub_rn(__fmul_rn(z, nf), (float)cz);
+  const uint32_t mask = (1u << ep.log2_table) - 1u;
+  const uint32_t hx[2] = {(uint32_t)cx, (uint32_t)cx + 1u};
+  const uint32_t hy0 = (uint32_t)cy * kPrime1, hz0 = (uint32_t)cz * kPrime2;
+  const uint32_t hy[2] = {hy0, hy0 + kPrime1};
+  const uint32_t hz[2] = {hz0, hz0 + kPrime2};
+  const float gx[2] = {1.0f - fx, fx}, gy[2] = {1.0f - fy, fy}, gz[2] = {1.0f - fz, fz};
+  const float* tab = table + ((size_t)l << ep.log2_table) * F;
+  uint32_t row[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) row[d] = (hx[d & 1] ^ hy[(d >> 1) & 1] ^ hz[d >> 2]) & mask;
+  FeatVec<F> v[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) v[d] = load_feat<F>(tab + (size_t)row[d] * F);
+#pragma unroll
+  for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const float w = gx[d & 1] * gy[(d >> 1) & 1] * gz[d >> 2];
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = fmaf(w, v[d].v[f], acc[f]);
+  }
+}
+
 // ---- the kernel ----------------------------------------------------------------
-template <int F, int PREC>
+template <int F, int PREC, bool LSMALL>
 __global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* s_w = smem;
@@ -294,18 +334,8 @@ __global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_con
           for (int q = 0; q < LPC; ++q) {
             const int l = (c * 8) / F + q;
             if (F <= 8 && l * F < din && (l * F) / 8 == c) {
-              Corners cr;
-              level_corners(a.ep, l, x, y, z, cr);
-              const float* tab = a.table + ((int64_t)l << a.ep.log2_table) * F;
               float acc[F];
-#pragma unroll
-              for (int f = 0; f < F; ++f) acc[f] = 0.0f;
-#pragma unroll
-              for (int d = 0; d < 8; ++d) {
-                const FeatVec<F> v = load_feat<F>(tab + (int64_t)cr.row[d] * F);
-#pragma unroll
-                for (int f = 0; f < F; ++f) acc[f] = fmaf(cr.w[d], v.v[f], acc[f]);
-              }
+              encode_level<F>(a.ep, a.table, l, x, y, z, acc);
 #pragma unroll
               for (int f = 0; f < F; ++f) {
                 const int k = l * F + f - c * 8;
@@ -354,7 +384,7 @@ __global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_con
 #pragma unroll
             for (int s = 0; s < 8; ++s) {
               const float zz = __uint_as_float(r[g * 8 + s]);
-              h[s] = zz > 0.0f ? zz : a.slope * zz;
+              h[s] = fmaxf(zz, a.slope * zz);   // leaky ReLU, 0 <= slope < 1
             }
             uint4 pk;
             pk.x = pack2<PREC>(h[0], h[1]);
@@ -372,7 +402,7 @@ __global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_con
       }
 
       // ---- output layer: sigmoid, light weights, WRS, Neural DI -------------
-      const int L = a.L;
+      const int L = LSMALL ? (a.L < 32 ? a.L : 32) : a.L;
       if (a.vis_out) {
         for (int c0 = 0; c0 < L; c0 += 32) {
           uint32_t r[32];
@@ -423,14 +453,14 @@ __global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_con
         uint4 rr = make_uint4(0, 0, 0, 0);
         for (int c0 = 0; c0 < L; c0 += 32) {
           uint32_t r[32];
-          if (L > 32) tmem_ld32(t_lane + (uint32_t)c0, r);
+          if (!LSMALL) tmem_ld32(t_lane + (uint32_t)c0, r);
           if (active) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int i = c0 + j;
               if (i < L) {
                 float w = wreg[j];
-                if (L > 32) {
+                if (!LSMALL) {
                   const float v = sigmoid_fast(__uint_as_float(r[j]));
                   w = fmaxf(v, bits_f(kVisClampBits)) *
                       contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
@@ -542,20 +572,17 @@ size_t fused_smem(const nvc_handle* h, const PackArgs& p) {
 
 template <int F, int PREC>
 cudaError_t launch_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cudaStream_t s) {
-  auto kern = fused_shade_kernel<F, PREC>;
+  auto kern = a.L <= 32 ? fused_shade_kernel<F, PREC, true> : fused_shade_kernel<F, PREC, false>;
   // cap CTAs per SM so their TMEM columns fit in 512
   const int max_ctas = (int)(512u / a.tmem_cols);
   size_t smem = smem_needed;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
-  int occ = 0;
-  for (;;) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileM, smem);
-    if (e != cudaSuccess) return e;
-    if (occ <= max_ctas || smem + 4096 > 227 * 1024) break;
+  int occ = blocks_per_sm((const void*)kern, kTileM, smem);
+  while (occ > max_ctas && smem + 4096 <= 227 * 1024) {
     smem += 4096;
+    occ = blocks_per_sm((const void*)kern, kTileM, smem);
   }
-  if (occ < 1) return cudaErrorInvalidConfiguration;
   if (occ > max_ctas) return cudaErrorInvalidConfiguration;
   const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
   const int64_t cap = (int64_t)occ * num_sms;

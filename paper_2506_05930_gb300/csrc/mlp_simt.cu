@@ -278,9 +278,7 @@ __global__ void __launch_bounds__(256) weight_grad_kernel(const float* __restric
 }
 
 int persistent_blocks(const nvc_handle* h, size_t smem, int64_t n_tiles) {
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_fwd_kernel, kRows, smem);
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = blocks_per_sm((const void*)mlp_fwd_kernel, kRows, smem);
   const int64_t cap = (int64_t)per_sm * h->num_sms;
   return (int)(n_tiles < cap ? n_tiles : cap);
 }
@@ -314,9 +312,8 @@ cudaError_t launch_mlp_bwd_fp32(const nvc_handle* h, int64_t n, const float* dlo
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t n_tiles = (n + kRows - 1) / kRows;
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bwd_kernel, kRows, smem);
-  const int64_t cap = (int64_t)(per_sm < 1 ? 1 : per_sm) * h->num_sms;
+  const int per_sm = blocks_per_sm((const void*)mlp_bwd_kernel, kRows, smem);
+  const int64_t cap = (int64_t)per_sm * h->num_sms;
   const int blocks = (int)(n_tiles < cap ? n_tiles : cap);
   const int maxdim = h->width > h->L ? h->width : h->L;
   const int64_t act_stride = (int64_t)h->B * h->width;

@@ -188,6 +188,11 @@ struct nvc_handle {
 
 namespace nvc {
 
+// Resident blocks per SM of `func` with `block` threads and `dyn_smem`
+// dynamic shared memory, from the function's register and shared-memory
+// footprint and the device's per-SM limits.
+int blocks_per_sm(const void* func, int block, size_t dyn_smem);
+
 // ---- launchers (each returns cudaGetLastError() of its launches) ----------
 // encode.cu
 cudaError_t launch_encode_fwd(const nvc_handle* h, const float* pos, int64_t n, float* feat,

@@ -179,6 +179,26 @@ __global__ void adam_prologue_kernel(const double* __restrict__ partials, int n_
 
 // theta -= (lr / bc1) m / (sqrt(v / bc2) + eps), after m, v updates with the
 // unscaled gradient; the gradient buffer is cleared for the next step.
+// HBM-bound: each thread issues all loads of two float4 groups before any
+// arithmetic; m and v stream (evict-first), theta is stored normally so the
+// updated table is still in L2 when the shading kernel gathers from it, and
+// gradient entries already zero (table rows no sample touched) are not
+// rewritten.
+__device__ __forceinline__ void adam_scalar(float& th, float g, float& mm, float& vv,
+                                            const AdamScalars& sc, float beta1, float beta2,
+                                            float eps) {
+  g *= sc.inv_scale;
+  mm = fmaf(beta1, mm, (1.0f - beta1) * g);
+  vv = fmaf(beta2, vv, (1.0f - beta2) * g * g);
+  float s;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(vv * sc.inv_bc2));
+  th -= __fdividef(sc.lr_over_bc1 * mm, s + eps);
+}
+
+__device__ __forceinline__ bool nonzero4(float4 g) {
+  return g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f;
+}
+
 __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
                                                    float* __restrict__ grad,
                                                    float* __restrict__ m, float* __restrict__ v,
@@ -187,38 +207,50 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
                                                    const AdamScalars* __restrict__ scp) {
   const AdamScalars sc = *scp;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float4* g4 = reinterpret_cast<float4*>(grad);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  // approximate sqrt and divide: most table rows have zero gradient, and
-  // 0 / eps would send the correctly rounded divide down its slow path
-  auto upd = [&](float& th, float g, float& mm, float& vv) {
-    g *= sc.inv_scale;
-    mm = beta1 * mm + (1.0f - beta1) * g;
-    vv = beta2 * vv + (1.0f - beta2) * g * g;
-    float s;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(vv * sc.inv_bc2));
-    th -= __fdividef(sc.lr_over_bc1 * mm, s + eps);
-  };
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += stride) {
-    float4 g = reinterpret_cast<float4*>(grad)[e];
-    reinterpret_cast<float4*>(grad)[e] = zero;
-    if (sc.skip) continue;
-    float4 th = reinterpret_cast<float4*>(theta)[e];
-    float4 mm = reinterpret_cast<float4*>(m)[e];
-    float4 vv = reinterpret_cast<float4*>(v)[e];
-    upd(th.x, g.x, mm.x, vv.x);
-    upd(th.y, g.y, mm.y, vv.y);
-    upd(th.z, g.z, mm.z, vv.z);
-    upd(th.w, g.w, mm.w, vv.w);
-    reinterpret_cast<float4*>(theta)[e] = th;
-    reinterpret_cast<float4*>(m)[e] = mm;
-    reinterpret_cast<float4*>(v)[e] = vv;
+  if (sc.skip) {
+    for (int64_t e = t0; e < n4; e += stride)
+      if (nonzero4(g4[e])) g4[e] = zero;
+    for (int64_t e = 4 * n4 + t0; e < n; e += stride) grad[e] = 0.0f;
+    return;
   }
-  // scalar tail
-  for (int64_t e = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+  float4* th4 = reinterpret_cast<float4*>(theta);
+  float4* m4 = reinterpret_cast<float4*>(m);
+  float4* v4 = reinterpret_cast<float4*>(v);
+  for (int64_t e = t0; e < n4; e += 2 * stride) {
+    const int64_t e1 = e + stride;
+    const bool two = e1 < n4;
+    float4 g[2], th[2], mm[2], vv[2];
+    g[0] = __ldcs(g4 + e);
+    th[0] = th4[e];
+    mm[0] = __ldcs(m4 + e);
+    vv[0] = __ldcs(v4 + e);
+    if (two) {
+      g[1] = __ldcs(g4 + e1);
+      th[1] = th4[e1];
+      mm[1] = __ldcs(m4 + e1);
+      vv[1] = __ldcs(v4 + e1);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !two) break;
+      adam_scalar(th[u].x, g[u].x, mm[u].x, vv[u].x, sc, beta1, beta2, eps);
+      adam_scalar(th[u].y, g[u].y, mm[u].y, vv[u].y, sc, beta1, beta2, eps);
+      adam_scalar(th[u].z, g[u].z, mm[u].z, vv[u].z, sc, beta1, beta2, eps);
+      adam_scalar(th[u].w, g[u].w, mm[u].w, vv[u].w, sc, beta1, beta2, eps);
+      const int64_t ee = u == 0 ? e : e1;
+      th4[ee] = th[u];
+      __stcs(m4 + ee, mm[u]);
+      __stcs(v4 + ee, vv[u]);
+      if (nonzero4(g[u])) __stcs(g4 + ee, zero);
+    }
+  }
+  for (int64_t e = 4 * n4 + t0; e < n; e += stride) {
     const float g = grad[e];
     grad[e] = 0.0f;
-    if (sc.skip) continue;
-    upd(theta[e], g, m[e], v[e]);
+    adam_scalar(theta[e], g, m[e], v[e], sc, beta1, beta2, eps);
   }
 }
 
