@@ -304,6 +304,32 @@ nvc_status nvc_frame(nvc_handle* h, const nvc_scene* scene, const nvc_view* view
                      int32_t n_views, int32_t train_view, uint64_t seed, uint32_t frame,
                      double* loss_out, int32_t use_graph, void* stream);
 
+/* ---- inference without allocation ---------------------------------------- */
+
+/* The paper has no counterpart of this entry point.  It exists for callers
+ * that cannot call cudaMalloc: a renderer whose frame loop runs under a
+ * fixed GPU memory budget (cudaMalloc can synchronise the device and stall
+ * a frame), or a plugin inside an application that owns every device
+ * allocation.  Everything else here needs a handle, and nvc_create
+ * allocates.
+ *
+ * Same result as nvc_infer on a float32 handle holding `params`: vis
+ * (device [n][n_outputs]) = sigmoid(MLP(encode(pos))) with the float32
+ * kernels, for pos (device [n][3]) and params (device [nvc_param_count],
+ * 16-byte aligned, the layout of nvc_set_state).  cfg->precision is
+ * ignored.  No memory is allocated: the encoded features go to a fixed
+ * array of 2^21 floats (8 MiB) inside the library, which every GPU that
+ * loads the library holds until the process exits; n * n_levels *
+ * n_features above 2^21 is rejected with NVC_ERR_INVALID_ARG and a message
+ * in nvc_last_error(NULL).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call on a device
+ * uses the same array: calls whose kernels overlap on the GPU (other
+ * streams, other host threads) race on it and must be ordered by the
+ * caller. */
+nvc_status nvc_infer_noalloc(const nvc_config* cfg, const float* params, const float* pos,
+                             int64_t n, float* vis, void* stream);
+
 /* ---- profiling ---------------------------------------------------------- */
 
 /* When enabled, the handle records CUDA events around each stage it

@@ -186,6 +186,8 @@ void count_launches(nvc_handle* h, int n) { h->launches += n; }
 
 namespace nvc {
 
+void record_error(const char* msg) { g_create_error = msg; }
+
 int blocks_per_sm(const void* func, int block, size_t dyn_smem) {
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) return 1;

@@ -188,6 +188,9 @@ struct nvc_handle {
 
 namespace nvc {
 
+// Records the message nvc_last_error(NULL) returns on this thread.
+void record_error(const char* msg);
+
 // Resident blocks per SM of `func` with `block` threads and `dyn_smem`
 // dynamic shared memory, from the function's register and shared-memory
 // footprint and the device's per-SM limits.

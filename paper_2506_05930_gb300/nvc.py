@@ -277,6 +277,15 @@ def nvc_frame(h, scene: Scene, views: Sequence[View], train_view, seed, frame, l
                         1 if use_graph else 0, _stream(stream)), h)
 
 
+def nvc_infer_noalloc(cfg: NvcConfig, params, pos, vis, stream=None):
+    """nvc_infer for callers that cannot allocate GPU memory: parameters come
+    from the caller, the library's fixed scratch array holds the encoded
+    features (at most 2^21 floats per call)."""
+    check(lib.nvc_infer_noalloc(ctypes.byref(cfg), _ptr(params, name="params"),
+                                _ptr(pos, name="pos"), pos.shape[0], _ptr(vis, name="vis"),
+                                _stream(stream)))
+
+
 def nvc_set_profiling(h, enable: bool):
     check(lib.nvc_set_profiling(h, 1 if enable else 0), h)
 
