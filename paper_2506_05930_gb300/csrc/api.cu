@@ -301,6 +301,14 @@ nvc_status nvc_create(const nvc_config* cfg, nvc_handle** out) {
       return cleanup_fail(e, "cudaMalloc");
     cudaMemset(h->mlp_packed, 0, h->mlp_packed_bytes);
   }
+  if (cfg->train_precision == NVC_PREC_FP16) {
+    std::string why;
+    if (!train_tc_supported(h, &why)) {
+      nvc_status st = fail(nullptr, NVC_ERR_UNSUPPORTED, "FP16 training: %s", why.c_str());
+      nvc_destroy(h);
+      return st;
+    }
+  }
   h->stage_pixels = 65536;
   if ((e = dalloc(&h->s_feat, (size_t)h->stage_pixels * h->din)) ||
       (e = dalloc(&h->s_vis, (size_t)h->stage_pixels * h->L)))
@@ -600,6 +608,14 @@ static nvc_status train_forward_backward(nvc_handle* h, const nvc_scene* scene,
     count_launches(h, 2);
   }
   StageScope sc(h, s, 1);
+  if (h->cfg.train_precision == NVC_PREC_FP16) {
+    // encode, forward, loss, backward and the hash scatter in one tensor-core kernel
+    int blocks = 0;
+    NVC_CUDA(h, launch_train_tc(h, B, &blocks, s));
+    h->loss_blocks = blocks;
+    count_launches(h, 1);
+    return NVC_OK;
+  }
   NVC_CUDA(h, launch_encode_fwd(h, h->t_pos, B, h->t_feat, s));
   NVC_CUDA(h, launch_mlp_fwd_fp32(h, h->t_feat, B, h->t_logits, false, h->t_act, s));
   NVC_CUDA(h, launch_loss_grad(h, B, s));

@@ -22,10 +22,13 @@
 // the tile loop together, freeing TMEM on the way out.
 #include "nvc_internal.cuh"
 #include "hashgrid.cuh"
+#include "tc_common.cuh"
 
 namespace nvc {
 
 namespace {
+
+using namespace tc;
 
 constexpr int kTileM = 128;
 constexpr int kMaxLayers = NVC_MAX_HIDDEN_LAYERS + 1;
@@ -66,132 +69,6 @@ struct FusedArgs {
   int32_t* status;
 };
 
-// ---- PTX wrappers -----------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait for phase `parity` of the barrier, for at most ~1 s.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > 1000000000ull) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t holder, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-
-// Shared-memory matrix descriptor, no swizzle: start, leading (K-direction)
-// and stride (M/N-direction) byte offsets, descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= 1ull << 46;
-  return d;
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                        uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-// 32 consecutive fp32 columns of this thread's TMEM lane; the registers are
-// tied to the wait so no use can be scheduled before the load completes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
-                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
-                 "+r"(r[30]), "+r"(r[31])::"memory");
-}
-
-// ---- operand packing ------------------------------------------------------
-// Byte offset of element (row, k) of a K-major operand with K columns in the
-// no-swizzle core-matrix layout.
-__host__ __device__ __forceinline__ uint32_t cm_offset(int row, int k, int K, int esize) {
-  return (uint32_t)((row >> 3) * (K * 8 * esize) + (k >> 3) * 128 + (row & 7) * 16 +
-                    (k & 7) * esize);
-}
-
-template <int PREC>
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
-  if constexpr (PREC == NVC_PREC_BF16) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  } else {
-    __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  }
-}
-
 // ---- the sampler's arithmetic ----------------------------------------------
 __device__ __forceinline__ float sigmoid_fast(float z) {
   return __fdividef(1.0f, 1.0f + __expf(-z));
@@ -226,46 +103,6 @@ __device__ __forceinline__ uint32_t quantize_bits(float w, uint32_t E) {
 
 __device__ __forceinline__ uint32_t pick_word(uint4 r, int lane) {
   return lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
-}
-
-// ---- encode of one (pixel, level) ------------------------------------------
-// Same arithmetic as the separate encode kernel (float32 cell, hashed
-// corners, trilinear blend), with the hash's per-axis terms shared between
-// the corners that use them.
-template <int F>
-__device__ __forceinline__ void encode_level(const EncodeParams& ep, const float* __restrict__ table,
-                                             int l, float x, float y, float z, float (&acc)[F]) {
-  const int n = ep.res[l];
-  const float nf = (float)n;
-  int cx = __float2int_rd(__fmul_rn(x, nf)), cy = __float2int_rd(__fmul_rn(y, nf)),
-      cz = __float2int_rd(__fmul_rn(z, nf));
-  cx = min(cx, n - 1);
-  cy = min(cy, n - 1);
-  cz = min(cz, n - 1);
-  const float fx = __fsub_rn(__fmul_rn(x, nf), (float)cx);
-  const float fy = __fsub_rn(__fmul_rn(y, nf), (float)cy);
-  const float fz = __fsub_rn(__fmul_rn(z, nf), (float)cz);
-  const uint32_t mask = (1u << ep.log2_table) - 1u;
-  const uint32_t hx[2] = {(uint32_t)cx, (uint32_t)cx + 1u};
-  const uint32_t hy0 = (uint32_t)cy * kPrime1, hz0 = (uint32_t)cz * kPrime2;
-  const uint32_t hy[2] = {hy0, hy0 + kPrime1};
-  const uint32_t hz[2] = {hz0, hz0 + kPrime2};
-  const float gx[2] = {1.0f - fx, fx}, gy[2] = {1.0f - fy, fy}, gz[2] = {1.0f - fz, fz};
-  const float* tab = table + ((size_t)l << ep.log2_table) * F;
-  uint32_t row[8];
-#pragma unroll
-  for (int d = 0; d < 8; ++d) row[d] = (hx[d & 1] ^ hy[(d >> 1) & 1] ^ hz[d >> 2]) & mask;
-  FeatVec<F> v[8];
-#pragma unroll
-  for (int d = 0; d < 8; ++d) v[d] = load_feat<F>(tab + (size_t)row[d] * F);
-#pragma unroll
-  for (int f = 0; f < F; ++f) acc[f] = 0.0f;
-#pragma unroll
-  for (int d = 0; d < 8; ++d) {
-    const float w = gx[d & 1] * gy[(d >> 1) & 1] * gz[d >> 2];
-#pragma unroll
-    for (int f = 0; f < F; ++f) acc[f] = fmaf(w, v[d].v[f], acc[f]);
-  }
 }
 
 // ---- the kernel ----------------------------------------------------------------
@@ -594,7 +431,7 @@ cudaError_t launch_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cu
 }  // namespace
 
 size_t mlp_packed_bytes(const nvc_handle* h) {
-  if (!tc_precision(h->cfg.precision)) return 0;
+  if (!tc_precision(h->cfg.precision) && h->cfg.train_precision != NVC_PREC_FP16) return 0;
   PackArgs p{};
   layer_geometry(h, p);
   return (size_t)p.byte_off[p.n_layers];

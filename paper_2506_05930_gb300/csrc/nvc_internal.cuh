@@ -165,6 +165,7 @@ struct nvc_handle {
   float* t_dfeat = nullptr;   // [B][din]
   double* loss_partials = nullptr;
   int n_loss_partials = 0;
+  int loss_blocks = 0;                  // partials written by the last training pass
   int32_t* status = nullptr;            // nvc::kStWords
   nvc::AdamScalars* adam_scalars = nullptr;
 
@@ -230,7 +231,7 @@ cudaError_t launch_training_positions(const nvc_scene* sc, const float* screen_p
                                       uint32_t frame, float* pos, cudaStream_t s);
 cudaError_t launch_trace_visibility(const nvc_scene* sc, const float* pos, int64_t n,
                                     float* vis, cudaStream_t s);
-cudaError_t launch_loss_grad(const nvc_handle* h, int64_t n, cudaStream_t s);
+cudaError_t launch_loss_grad(nvc_handle* h, int64_t n, cudaStream_t s);
 cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_t s);
 cudaError_t launch_finish_gradient(nvc_handle* h, float* grad_out, double* loss_out,
                                    cudaStream_t s);
@@ -244,5 +245,9 @@ cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const f
                                float* wsum, float* radiance, float* vis_out, cudaStream_t s,
                                float* w_out = nullptr);
 size_t mlp_packed_bytes(const nvc_handle* h);
+
+// train_tc.cu
+bool train_tc_supported(const nvc_handle* h, std::string* why);
+cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStream_t s);
 
 }  // namespace nvc

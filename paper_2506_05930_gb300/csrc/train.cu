@@ -292,7 +292,8 @@ cudaError_t launch_trace_visibility(const nvc_scene* sc, const float* pos, int64
   return cudaGetLastError();
 }
 
-cudaError_t launch_loss_grad(const nvc_handle* h, int64_t n, cudaStream_t s) {
+cudaError_t launch_loss_grad(nvc_handle* h, int64_t n, cudaStream_t s) {
+  h->loss_blocks = kLossBlocks;
   const int64_t count = n * h->L;
   const int top = h->n_layers - 1;
   const int maxdim = h->width > h->L ? h->width : h->L;
@@ -306,7 +307,8 @@ cudaError_t launch_loss_grad(const nvc_handle* h, int64_t n, cudaStream_t s) {
 cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_t s) {
   const nvc_config& c = h->cfg;
   const double inv_count = 1.0 / ((double)h->B * (double)h->L);
-  adam_prologue_kernel<<<1, 32, 0, s>>>(h->loss_partials, kLossBlocks, inv_count, loss_out,
+  const int n_partials = h->loss_blocks > 0 ? h->loss_blocks : kLossBlocks;
+  adam_prologue_kernel<<<1, 32, 0, s>>>(h->loss_partials, n_partials, inv_count, loss_out,
                                         h->status, h->adam_scalars, apply ? 1 : 0, c.lr_schedule,
                                         c.lr, c.lr_end, c.lr_ramp_steps, (double)c.beta1,
                                         (double)c.beta2, 1.0f / c.loss_scale);

@@ -414,3 +414,60 @@ def test_invalid_arguments_are_rejected(tiny):
     # a zero-size call is a no-op
     nvc.nvc_encode(cache.handle, pos[:0], torch.empty((0, 16), device="cuda"))
     nvc.nvc_infer(cache.handle, pos[:0], torch.empty((0, 4), device="cuda"))
+
+
+# ------------------------------------------------- FP16 tensor-core training --
+
+@pytest.mark.parametrize("name,loss,batch", [("tiny_fp32", "bce", 1024), ("tiny_fp32", "l2", 1000),
+                                             ("frame_1080p", "bce", 1024)])
+def test_train_gradient_fp16_tensor_cores_matches_oracle(name, loss, batch):
+    """FP16 operands, FP32 accumulation, loss scale 128.  The gradient sits
+    on the fp16 rounding model (features, weights, activations and deltas
+    rounded to fp16, everything else exact) within 5e-4, and is as close to
+    the float64 oracle as that model is (fp16 rounds each operand to 2^-11;
+    through three backward layers with cancelling sums that reaches 1e-2 on
+    the first layer's weights)."""
+    from helpers import fp16_gradient_model
+    cfg = S.config_by_name(name).with_(train_precision="fp16", loss=loss, loss_scale=128.0,
+                                       leaky_slope=0.01, batch_positions=batch)
+    if name == "tiny_fp32":
+        sc = S.scene_unit_cube(seed=0)
+        gb = S.gbuffer_points(0, 64, 64)
+    else:
+        sc = S.scene_heightfield(seed=1, n_lights=32, n_spheres=32, n_boxes=32)
+        gb = S.gbuffer_heightfield(seed=1, width=96, height=54)
+    cache = nvc.VisibilityCache(cfg)
+    p = scaled_params(cfg, seed=2, table_scale=0.5)
+    cache.set_params(p)
+    scene = nvc.Scene.from_synth(sc)
+    g, loss_gpu = cache.train_gradient(scene, dev(gb.pos), seed=5, frame=3)
+    pos = O.training_positions(batch, sc.world_min, sc.world_max, gb.pos, 5, 3)
+    y = O.visibility(pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    loss_ref, g_ref = O.gradients(cfg, p, pos, y)
+    g_model = fp16_gradient_model(cfg, p, pos, y, 128.0)
+    assert abs(host(loss_gpu)[0] - loss_ref) <= 2e-3 * abs(loss_ref)
+    g = host(g)
+    _, _, layers = S.param_layout(cfg)
+    parts = [(0, layers[0][0])] + [(off, off + o * i) for off, o, i in layers]
+    for lo, hi in [(0, len(g))] + parts:
+        assert rel_err(g[lo:hi], g_model[lo:hi]) <= 5e-4, (lo, rel_err(g[lo:hi], g_model[lo:hi]))
+        bound = 1.1 * rel_err(g_model[lo:hi], g_ref[lo:hi]) + 5e-4
+        assert rel_err(g[lo:hi], g_ref[lo:hi]) <= bound
+    assert rel_err(g, g_ref) <= 5e-3
+
+
+def test_online_training_fp16_follows_oracle_and_learns():
+    cfg = cfg_tiny(loss="bce", leaky_slope=0.01, batch_positions=512, train_precision="fp16",
+                   loss_scale=128.0)
+    sc, gb, cache, p = _train_setup(cfg)
+    scene = nvc.Scene.from_synth(sc)
+    st = O.TrainState.fresh(p)
+    losses, losses_ref = [], []
+    for f in range(40):
+        view = S.gbuffer_points(100 + f, 16, 16)
+        losses.append(host(cache.train_step(scene, dev(view.pos), seed=2, frame=f))[0])
+        if f < 5:
+            losses_ref.append(O.train_step(cfg, st, sc, view.pos, seed=2, frame=f))
+    np.testing.assert_allclose(losses[:5], losses_ref, rtol=2e-3)
+    assert cache.counters()["skipped"] == 0
+    assert np.mean(losses[-5:]) < 0.8 * np.mean(losses[:5])
