@@ -59,6 +59,7 @@ struct FusedArgs {
   uint32_t tmem_cols;
   const float* lights;
   uint32_t k0, k1, frame, view;
+  uint2 rkey[10];    // Philox round keys for (k0, k1)
   int64_t pixel_offset;
   int32_t* idx;
   float* pdf;
@@ -82,9 +83,9 @@ __device__ __forceinline__ float contribution_fast(float px, float py, float pz,
   const float dx = l.x - px, dy = l.y - py, dz = l.z - pz;
   const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float ndl = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
-  const float r = rsqrtf(d2);
+  const float r = rsqrtf(fmaxf(d2, 1e-30f));
   const float inv = d2 >= 1e-6f ? r * r : 1e6f;
-  return ndl > 0.0f ? l.w * ndl * r * inv : 0.0f;
+  return fmaxf(l.w * ndl * r * inv, 0.0f);   // n.d <= 0 gives c <= 0 -> 0
 }
 
 // q = max(1, floor(w * 2^(23 - e))) for w > 0 (e = ilogb(wmax)), from the
@@ -101,13 +102,48 @@ __device__ __forceinline__ uint32_t quantize_bits(float w, uint32_t E) {
   return q ? q : 1u;
 }
 
+// Same q as quantize_bits, by one exact multiply: w * 2^(23 - e) is exact
+// whenever the product is a normal float, and truncating a subnormal or
+// zero product gives 0, which the max(1, .) rule then lifts to 1.
+// `scale` = 2^(23 - e), representable for E = biased exponent of wmax >= 23.
+__device__ __forceinline__ uint32_t quantize_scaled(float w, float scale) {
+  const uint32_t q = __float2uint_rz(w * scale);
+  return (w > 0.0f && q == 0u) ? 1u : q;
+}
+
+// Two fp32 pre-activations -> packed 16-bit leaky ReLU (0 <= slope < 1).
+template <int PREC>
+__device__ __forceinline__ uint32_t leaky2(uint32_t za, uint32_t zb, float slope) {
+  if constexpr (PREC == NVC_PREC_BF16) {
+    const __nv_bfloat162 z = __floats2bfloat162_rn(__uint_as_float(za), __uint_as_float(zb));
+    const __nv_bfloat162 h = __hmax2(z, __hmul2(z, __float2bfloat162_rn(slope)));
+    return *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    const __half2 z = __floats2half2_rn(__uint_as_float(za), __uint_as_float(zb));
+    const __half2 h = __hmax2(z, __hmul2(z, __float2half2_rn(slope)));
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+
+// Philox-4x32-10 with the ten round keys (k0 + r W0, k1 + r W1) given: the
+// same function as philox4x32_10, the key schedule done once on the host.
+__device__ __forceinline__ uint4 philox_keyed(uint4 c, const uint2 (&rk)[10]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk[r].x, lo1, hi0 ^ c.w ^ rk[r].y, lo0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint32_t pick_word(uint4 r, int lane) {
   return lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
 }
 
 // ---- the kernel ----------------------------------------------------------------
 template <int F, int PREC, bool LSMALL>
-__global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_constant__ FusedArgs a) {
+__global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* s_w = smem;
   uint8_t* s_a = smem + a.wimg_bytes;
@@ -217,17 +253,12 @@ __global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_con
           tmem_ld32(t_lane + (uint32_t)c0, r);
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
-            float h[8];
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-              const float zz = __uint_as_float(r[g * 8 + s]);
-              h[s] = fmaxf(zz, a.slope * zz);   // leaky ReLU, 0 <= slope < 1
-            }
+            // convert pairs, then leaky ReLU max(z, slope z) in packed 16-bit math
             uint4 pk;
-            pk.x = pack2<PREC>(h[0], h[1]);
-            pk.y = pack2<PREC>(h[2], h[3]);
-            pk.z = pack2<PREC>(h[4], h[5]);
-            pk.w = pack2<PREC>(h[6], h[7]);
+            pk.x = leaky2<PREC>(r[g * 8 + 0], r[g * 8 + 1], a.slope);
+            pk.y = leaky2<PREC>(r[g * 8 + 2], r[g * 8 + 3], a.slope);
+            pk.z = leaky2<PREC>(r[g * 8 + 4], r[g * 8 + 5], a.slope);
+            pk.w = leaky2<PREC>(r[g * 8 + 6], r[g * 8 + 7], a.slope);
             if (c0 + g * 8 < Kn)
               *reinterpret_cast<uint4*>(s_a + cm_offset(t, c0 + g * 8, Kn, 2)) = pk;
           }
@@ -284,7 +315,9 @@ __global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_con
         // the per-pixel work only where there is something to pick
         const bool active = live && wmax > 0.0f;
         const uint32_t E = __float_as_uint(wmax) >> 23;
-        const int e_sub = (active && E == 0) ? ilogbf(wmax) : 0;
+        const bool fast_q = E >= 23u;
+        const float qscale = __uint_as_float((277u - (fast_q ? E : 23u)) << 23);   // 2^(23 - e)
+        const int e_sub = (active && !fast_q) ? ilogbf(wmax) : 0;
         const uint32_t pixel = (uint32_t)(a.pixel_offset + row);
         uint32_t Q = 0;
         uint4 rr = make_uint4(0, 0, 0, 0);
@@ -303,12 +336,13 @@ __global__ void __launch_bounds__(kTileM, 4) fused_shade_kernel(const __grid_con
                       contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
                 }
                 if ((i & 3) == 0)
-                  rr = philox4x32_10(make_uint4(pixel, a.frame, a.view,
-                                                ((uint32_t)(i >> 2) << 4) | kTagWrs),
-                                     a.k0, a.k1);
-                const uint32_t q = E ? quantize_bits(w, E) : quantize_weight(w, e_sub);
+                  rr = philox_keyed(make_uint4(pixel, a.frame, a.view,
+                                               ((uint32_t)(i >> 2) << 4) | kTagWrs),
+                                    a.rkey);
+                const uint32_t q = fast_q ? quantize_scaled(w, qscale) : quantize_weight(w, e_sub);
                 Q += q;
-                if (q != 0u && __umulhi(pick_word(rr, i & 3), Q) < q) {
+                // r*Q < q*2^32  <=>  hi32(r*Q) < q  (Q < 2^32); false for q = 0
+                if (__umulhi(pick_word(rr, i & 3), Q) < q) {
                   sel = i;
                   wsel = w;
                 }
@@ -503,6 +537,8 @@ cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const f
   a.lights = sc ? sc->lights : nullptr;
   a.k0 = (uint32_t)seed;
   a.k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r)
+    a.rkey[r] = make_uint2(a.k0 + (uint32_t)r * kPhiloxW0, a.k1 + (uint32_t)r * kPhiloxW1);
   a.frame = frame;
   a.view = view;
   a.pixel_offset = pixel_offset;
