@@ -232,6 +232,30 @@ nvc_status nvc_shade(nvc_handle* h, const nvc_scene* scene, const float* pos,
 nvc_status nvc_sampler_weights(nvc_handle* h, const nvc_scene* scene, const float* pos,
                                const float* nrm, int64_t n, float* w, void* stream);
 
+/* Variants of the fused shading kernel (nvc_shade with fused = 1):
+ *   0  every warp encodes, multiplies and samples its own 128-pixel tile;
+ *   1  warp-specialised: 4 producer warps encode the next tile while 4
+ *      consumer warps run the MLP and the sampler on the current one;
+ *   2  as 1, with the producers also computing the light contributions;
+ *   3  as 1 with 8 producer warps (two threads per pixel, half the levels
+ *      each);
+ *   4  as 3 with the contributions computed by the producers.
+ * 1-4 need n_outputs <= 32.  All compute the same function. */
+#define NVC_SHADE_VARIANTS 5
+
+/* Times every applicable variant on these pixels (CUDA events on `stream`,
+ * a warm-up then `reps` launches each; synchronises) and keeps the fastest
+ * for this handle.  Outputs as nvc_shade (any may be NULL).  chosen (host,
+ * may be NULL) receives the variant; ms_out (host [NVC_SHADE_VARIANTS], may
+ * be NULL) the mean milliseconds per launch, -1 for a variant not run. */
+nvc_status nvc_autotune_shade(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                              const float* nrm, int64_t n, int32_t* idx, float* pdf,
+                              float* wsum, float* radiance, int32_t reps, int32_t* chosen,
+                              double* ms_out, void* stream);
+
+/* Selects the fused shading kernel variant (0 .. NVC_SHADE_VARIANTS-1). */
+nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant);
+
 /* ---- training (Section 3.4) -------------------------------------------- */
 
 /* Binary visibility vis (device [n][n_lights], 0 or 1) of every light from

@@ -569,6 +569,66 @@ nvc_status nvc_sampler_weights(nvc_handle* h, const nvc_scene* scene, const floa
   return NVC_OK;
 }
 
+nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (variant < 0 || variant >= kShadeVariants)
+    return fail(h, NVC_ERR_INVALID_ARG, "variant out of range");
+  if (variant != kShadeMono && h->L > 32)
+    return fail(h, NVC_ERR_UNSUPPORTED, "warp-specialised variants need n_outputs <= 32");
+  h->shade_variant = variant;
+  return NVC_OK;
+}
+
+nvc_status nvc_autotune_shade(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                              const float* nrm, int64_t n, int32_t* idx, float* pdf,
+                              float* wsum, float* radiance, int32_t reps, int32_t* chosen,
+                              double* ms_out, void* stream) {
+  NVC_TRY(shade_checks(h, scene, pos, nrm, n, 0));
+  if (n == 0 || reps < 1) return fail(h, NVC_ERR_INVALID_ARG, "need n > 0 and reps >= 1");
+  std::string why;
+  if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  NVC_CUDA(h, cudaEventCreate(&e0));
+  NVC_CUDA(h, cudaEventCreate(&e1));
+  const int keep = h->shade_variant;
+  int best = -1;
+  double best_ms = 0.0;
+  for (int v = 0; v < kShadeVariants; ++v) {
+    if (ms_out) ms_out[v] = -1.0;
+    if (v != kShadeMono && h->L > 32) continue;
+    h->shade_variant = v;
+    cudaError_t e = launch_shade_fused(h, scene, pos, nrm, n, 1, 0, 0, 0, idx, pdf, wsum,
+                                       radiance, nullptr, s);
+    if (e != cudaSuccess) continue;   // variant does not fit this configuration
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r)
+      launch_shade_fused(h, scene, pos, nrm, n, 1, (uint32_t)r, 0, 0, idx, pdf, wsum, radiance,
+                         nullptr, s);
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      h->shade_variant = keep;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(h, e, "autotune");
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = (double)ms / reps;
+    if (ms_out) ms_out[v] = per;
+    if (best < 0 || per < best_ms) {
+      best = v;
+      best_ms = per;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->shade_variant = best < 0 ? keep : best;
+  if (chosen) *chosen = h->shade_variant;
+  return NVC_OK;
+}
+
 nvc_status nvc_trace_visibility(const nvc_scene* scene, const float* pos, int64_t n, float* vis,
                                 void* stream) {
   NVC_TRY(check_scene(nullptr, scene, 0));

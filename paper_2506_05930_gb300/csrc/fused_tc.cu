@@ -68,6 +68,8 @@ struct FusedArgs {
   float* vis_out;
   float* w_out;      // optional: the light weights the sampler uses, [n][L]
   int32_t* status;
+  // warp-specialised layout (byte offsets into shared memory)
+  int ws_a0[2], ws_h, ws_c[2], ws_l, ws_bar, ws_cs;
 };
 
 // ---- the sampler's arithmetic ----------------------------------------------
@@ -370,6 +372,295 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
   }
 }
 
+// ---- warp-specialised variant (L <= 32) -----------------------------------
+// 256 threads.  Warps 4-7 produce: for tile i they encode their pixel into
+// the layer-0 operand A0[i % 2] and precompute its 32 light contributions
+// into C[i % 2], then arrive on full[i % 2].  Warps 0-3 consume: wait on
+// full[i % 2], run the MLP (tcgen05, activations through one hidden tile H),
+// the sigmoid and the sampler with the precomputed contributions, write the
+// pixel's outputs and arrive on empty[i % 2] so the producer may refill the
+// buffer.  The producers' gathers thus overlap the consumers' tensor-core
+// and ALU work.  Same arithmetic as fused_shade_kernel.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// bar.sync over the 128 consumer threads (barrier 1) with an OR of `v`.
+__device__ __forceinline__ bool consumers_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+template <int F, int PREC, int PW, bool PRE_C>
+__global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(const __grid_constant__ FusedArgs a) {
+  constexpr int kThreads = kTileM + PW * 32;
+  constexpr int kParts = PW / 4;   // producer threads per pixel
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* s_w = smem;
+  uint8_t* s_h = smem + a.ws_h;
+  float4* s_l = reinterpret_cast<float4*>(smem + a.ws_l);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.ws_bar);   // mma, full0, full1, empty0, empty1
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 5);
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  const int CS = a.ws_cs;
+
+  for (int e = t; e < a.wimg_bytes / 16; e += kThreads)
+    reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
+  if (a.lights) {
+    for (int e = t; e < a.L; e += kThreads) {
+      float4 l = reinterpret_cast<const float4*>(a.lights)[e];
+      l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+      s_l[e] = l;
+    }
+  }
+  const uint32_t bar_mma = smem_u32(s_bar);
+  // full[b] at s_bar + 1 + b, empty[b] at s_bar + 3 + b (8 bytes each)
+  const uint32_t bar_full0 = bar_mma + 8u, bar_empty0 = bar_mma + 24u;
+  if (t == 0) {
+    mbar_init(bar_mma, 1);
+    mbar_init(bar_full0, PW * 32);
+    mbar_init(bar_full0 + 8u, PW * 32);
+    mbar_init(bar_empty0, kTileM);
+    mbar_init(bar_empty0 + 8u, kTileM);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(s_tmem), a.tmem_cols);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const int din = a.ep.n_levels * F;
+  const int K0 = a.layer[0].K;
+  const int L = a.L;
+  const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+  bool failed = false;
+
+  if (warp >= 4) {
+    // ================================ producers ================================
+    const int p = (t - kTileM) & (kTileM - 1);
+    const int part = (t - kTileM) >> 7;
+    int i = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+      const int b = i & 1;
+      if (i >= 2 && !mbar_wait_bounded(bar_empty0 + 8u * b, ((i >> 1) - 1) & 1)) {
+        failed = true;
+        break;
+      }
+      const int64_t row = tile * kTileM + p;
+      const bool live = row < a.n;
+      float px = 0.f, py = 0.f, pz = 0.f;
+      if (live) {
+        px = __ldg(a.pos + 3 * row);
+        py = __ldg(a.pos + 3 * row + 1);
+        pz = __ldg(a.pos + 3 * row + 2);
+      }
+      uint8_t* a0 = smem + (b ? a.ws_a0[1] : a.ws_a0[0]);
+      {
+        const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
+        const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
+        const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
+        constexpr int LPC = F >= 8 ? 1 : 8 / F;
+        for (int c = part; c < K0 / 8; c += kParts) {
+          float f8[8];
+#pragma unroll
+          for (int s = 0; s < 8; ++s) f8[s] = 0.0f;
+          if (live) {
+#pragma unroll
+            for (int q = 0; q < LPC; ++q) {
+              const int l = (c * 8) / F + q;
+              if (l * F < din && (l * F) / 8 == c) {
+                float acc[F];
+                encode_level<F>(a.ep, a.table, l, x, y, z, acc);
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                  const int k = l * F + f - c * 8;
+                  if (k >= 0 && k < 8) f8[k] = acc[f];
+                }
+              }
+            }
+          }
+          uint4 pk;
+          pk.x = pack2<PREC>(f8[0], f8[1]);
+          pk.y = pack2<PREC>(f8[2], f8[3]);
+          pk.z = pack2<PREC>(f8[4], f8[5]);
+          pk.w = pack2<PREC>(f8[6], f8[7]);
+          *reinterpret_cast<uint4*>(a0 + cm_offset(p, c * 8, K0, 2)) = pk;
+        }
+      }
+      if (PRE_C && a.lights) {
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (live) {
+          nx = __ldg(a.nrm + 3 * row);
+          ny = __ldg(a.nrm + 3 * row + 1);
+          nz = __ldg(a.nrm + 3 * row + 2);
+        }
+        float* cr = reinterpret_cast<float*>(smem + (b ? a.ws_c[1] : a.ws_c[0])) + p * CS;
+#pragma unroll 4
+        for (int j = part; j < L; j += kParts)
+          cr[j] = contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
+      }
+      fence_async_smem();
+      mbar_arrive(bar_full0 + 8u * b);
+    }
+  } else {
+    // ================================ consumers ================================
+    const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t w_base = smem_u32(s_w);
+    const uint32_t h_base = smem_u32(s_h);
+    uint32_t mphase = 0;
+    int i = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+      const int b = i & 1;
+      const bool got = mbar_wait_bounded(bar_full0 + 8u * b, (i >> 1) & 1);
+      if (consumers_sync_or(!got)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      const int64_t row = tile * kTileM + t;
+      const bool live = row < a.n;
+      const uint32_t a0_base = smem_u32(smem + (b ? a.ws_a0[1] : a.ws_a0[0]));
+      bool ok = true;
+      for (int k = 0; k < a.n_layers; ++k) {
+        const LayerDesc ld = a.layer[k];
+        if (t == 0) {
+          tc_fence_after();
+          const uint32_t sbo = (uint32_t)ld.K * 16u;
+          const uint32_t ab = k == 0 ? a0_base : h_base;
+          const uint32_t wb = w_base + (uint32_t)ld.w_byte_off;
+          for (int kk = 0; kk < ld.K / 16; ++kk)
+            mma_f16(tmem, smem_desc(ab + kk * 256, 128, sbo), smem_desc(wb + kk * 256, 128, sbo),
+                    ld.idesc, kk > 0 ? 1u : 0u);
+          mma_commit(bar_mma);
+        }
+        ok = mbar_wait_bounded(bar_mma, mphase) && ok;
+        mphase ^= 1u;
+        tc_fence_after();
+        if (k + 1 < a.n_layers) {
+          const int Kn = ld.N;
+          for (int c0 = 0; c0 < ld.N; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(t_lane + (uint32_t)c0, r);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              uint4 pk;
+              pk.x = leaky2<PREC>(r[g * 8 + 0], r[g * 8 + 1], a.slope);
+              pk.y = leaky2<PREC>(r[g * 8 + 2], r[g * 8 + 3], a.slope);
+              pk.z = leaky2<PREC>(r[g * 8 + 4], r[g * 8 + 5], a.slope);
+              pk.w = leaky2<PREC>(r[g * 8 + 6], r[g * 8 + 7], a.slope);
+              if (c0 + g * 8 < Kn)
+                *reinterpret_cast<uint4*>(s_h + cm_offset(t, c0 + g * 8, Kn, 2)) = pk;
+            }
+          }
+          fence_async_smem();
+          tc_fence_before();
+          if (consumers_sync_or(!ok)) {
+            failed = true;
+            break;
+          }
+          continue;
+        }
+        // ---- output layer: sigmoid, weights, WRS, Neural DI --------------------
+        uint32_t r[32];
+        tmem_ld32(t_lane, r);
+        if (a.vis_out) {
+          if (live) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < L) a.vis_out[row * L + j] = sigmoid_fast(__uint_as_float(r[j]));
+          }
+        } else {
+          const float* cr =
+              reinterpret_cast<const float*>(smem + (b ? a.ws_c[1] : a.ws_c[0])) + t * CS;
+          float px = 0.f, py = 0.f, pz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+          if (!PRE_C && live) {
+            px = __ldg(a.pos + 3 * row);
+            py = __ldg(a.pos + 3 * row + 1);
+            pz = __ldg(a.pos + 3 * row + 2);
+            nx = __ldg(a.nrm + 3 * row);
+            ny = __ldg(a.nrm + 3 * row + 1);
+            nz = __ldg(a.nrm + 3 * row + 2);
+          }
+          float wreg[32];
+          float wmax = 0.0f, sum = 0.0f, di = 0.0f;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float w = 0.0f;
+            if (j < L) {
+              const float v = sigmoid_fast(__uint_as_float(r[j]));
+              const float c =
+                  PRE_C ? cr[j] : contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
+              w = fmaxf(v, bits_f(kVisClampBits)) * c;
+              if (a.w_out && live) a.w_out[row * L + j] = w;
+              wmax = fmaxf(wmax, w);
+              sum += w;
+              di = fmaf(v, c, di);
+            }
+            wreg[j] = w;
+          }
+          int sel = -1;
+          float wsel = 0.0f;
+          if (live && wmax > 0.0f) {
+            const uint32_t E = __float_as_uint(wmax) >> 23;
+            const bool fast_q = E >= 23u;
+            const float qscale = __uint_as_float((277u - (fast_q ? E : 23u)) << 23);
+            const int e_sub = fast_q ? 0 : ilogbf(wmax);
+            const uint32_t pixel = (uint32_t)(a.pixel_offset + row);
+            uint32_t Q = 0;
+            uint4 rr = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (j < L) {
+                if ((j & 3) == 0)
+                  rr = philox_keyed(make_uint4(pixel, a.frame, a.view,
+                                               ((uint32_t)(j >> 2) << 4) | kTagWrs),
+                                    a.rkey);
+                const float w = wreg[j];
+                const uint32_t q = fast_q ? quantize_scaled(w, qscale) : quantize_weight(w, e_sub);
+                Q += q;
+                if (__umulhi(pick_word(rr, j & 3), Q) < q) {
+                  sel = j;
+                  wsel = w;
+                }
+              }
+            }
+          }
+          if (live) {
+            if (a.idx) a.idx[row] = sel;
+            if (a.pdf) a.pdf[row] = sel >= 0 ? wsel / sum : 0.0f;
+            if (a.wsum) a.wsum[row] = sum;
+            if (a.radiance) a.radiance[row] = di;
+          }
+        }
+      }
+      if (failed) break;
+      mbar_arrive(bar_empty0 + 8u * b);
+      tc_fence_before();
+      if (consumers_sync_or(!ok)) {
+        failed = true;
+        break;
+      }
+    }
+    if (failed && t == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
+    if (failed) mbar_wait_bounded(bar_mma, mphase ^ 1u);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, a.tmem_cols);
+  }
+}
+
 // ---- weight packing (fp32 master -> tensor-core operand image) -------------
 struct PackArgs {
   int n_layers;
@@ -462,6 +753,52 @@ cudaError_t launch_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cu
   return cudaGetLastError();
 }
 
+// Shared-memory plan of the warp-specialised kernel; returns its size.
+size_t plan_ws(const PackArgs& p, int L, bool pre_c, FusedArgs& a) {
+  int off = p.byte_off[p.n_layers];
+  const int K0 = p.K[0];
+  int Kh = 16;
+  for (int k = 1; k < p.n_layers; ++k) Kh = p.K[k] > Kh ? p.K[k] : Kh;
+  a.ws_a0[0] = off;
+  off += kTileM * K0 * 2;
+  a.ws_a0[1] = off;
+  off += kTileM * K0 * 2;
+  a.ws_h = off;
+  off += kTileM * Kh * 2;
+  a.ws_cs = L | 1;   // odd row stride: conflict-free per-thread rows
+  a.ws_c[0] = off;
+  if (pre_c) off += kTileM * a.ws_cs * 4;
+  a.ws_c[1] = off;
+  if (pre_c) off += kTileM * a.ws_cs * 4;
+  off = (off + 15) & ~15;
+  a.ws_l = off;
+  off += 16 * L;
+  a.ws_bar = off;
+  off += 64;
+  return (size_t)off;
+}
+
+template <int F, int PREC, int PW, bool PRE_C>
+cudaError_t launch_ws_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cudaStream_t s) {
+  auto kern = fused_shade_ws_kernel<F, PREC, PW, PRE_C>;
+  constexpr int kThreads = kTileM + PW * 32;
+  const int max_ctas = (int)(512u / a.tmem_cols);
+  size_t smem = smem_needed;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  int occ = blocks_per_sm((const void*)kern, kThreads, smem);
+  while (occ > max_ctas && smem + 4096 <= 227 * 1024) {
+    smem += 4096;
+    occ = blocks_per_sm((const void*)kern, kThreads, smem);
+  }
+  if (occ > max_ctas) return cudaErrorInvalidConfiguration;
+  const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+  const int64_t cap = (int64_t)occ * num_sms;
+  const int grid = (int)(n_tiles < cap ? n_tiles : cap);
+  kern<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t mlp_packed_bytes(const nvc_handle* h) {
@@ -549,8 +886,28 @@ cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const f
   a.vis_out = vis_out;
   a.w_out = w_out;
   a.status = h->status;
-  const size_t smem = fused_smem(h, p);
   const bool bf16 = h->cfg.precision == NVC_PREC_BF16;
+  const int variant = h->shade_variant;
+  if (h->L <= 32 && variant != kShadeMono) {
+    const bool pre_c = variant == kShadeWs4C || variant == kShadeWs8C;
+    const bool p8 = variant == kShadeWs8 || variant == kShadeWs8C;
+    const size_t smem_ws = plan_ws(p, h->L, pre_c, a);
+    if (smem_ws <= 227 * 1024) {
+#define NVC_WS(FF, PP)                                                                        \
+  if (p8) return pre_c ? launch_ws_typed<FF, PP, 8, true>(a, smem_ws, h->num_sms, s)           \
+                       : launch_ws_typed<FF, PP, 8, false>(a, smem_ws, h->num_sms, s);         \
+  return pre_c ? launch_ws_typed<FF, PP, 4, true>(a, smem_ws, h->num_sms, s)                   \
+               : launch_ws_typed<FF, PP, 4, false>(a, smem_ws, h->num_sms, s);
+      switch (h->F) {
+        case 1: if (bf16) { NVC_WS(1, NVC_PREC_BF16) } else { NVC_WS(1, NVC_PREC_FP16) }
+        case 2: if (bf16) { NVC_WS(2, NVC_PREC_BF16) } else { NVC_WS(2, NVC_PREC_FP16) }
+        case 4: if (bf16) { NVC_WS(4, NVC_PREC_BF16) } else { NVC_WS(4, NVC_PREC_FP16) }
+        case 8: if (bf16) { NVC_WS(8, NVC_PREC_BF16) } else { NVC_WS(8, NVC_PREC_FP16) }
+      }
+#undef NVC_WS
+    }
+  }
+  const size_t smem = fused_smem(h, p);
   switch (h->F) {
     case 1: return bf16 ? launch_typed<1, NVC_PREC_BF16>(a, smem, h->num_sms, s)
                         : launch_typed<1, NVC_PREC_FP16>(a, smem, h->num_sms, s);

@@ -121,6 +121,16 @@ enum StatusWord : int {
 };
 enum : int { kFlagNonFinite = 1, kFlagTimeout = 2 };
 
+// Variants of the fused shading kernel (chosen by nvc_autotune_shade).
+enum ShadeVariant : int {
+  kShadeMono = 0,   // every warp encodes, multiplies and samples its own tile
+  kShadeWs4 = 1,    // 4 producer warps encode, 4 consumer warps run MLP + sampler
+  kShadeWs4C = 2,   // as kShadeWs4, producers also precompute the contributions
+  kShadeWs8 = 3,    // 8 producer warps (two threads per pixel) + 4 consumers
+  kShadeWs8C = 4,   // as kShadeWs8 with precomputed contributions
+  kShadeVariants = 5
+};
+
 // Adam scalars written on the device each step.
 struct AdamScalars {
   float lr_over_bc1;     // lr / (1 - b1^t)
@@ -173,6 +183,9 @@ struct nvc_handle {
   int64_t stage_pixels = 0;
   float* s_feat = nullptr;    // [stage][din]
   float* s_vis = nullptr;     // [stage][L]
+
+  // fused shading kernel variant (nvc::ShadeVariant)
+  int shade_variant = 0;
 
   // frame graph
   cudaStream_t capture_stream = nullptr;

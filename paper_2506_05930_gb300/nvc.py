@@ -211,6 +211,26 @@ def nvc_sampler_weights(h, scene: Scene, pos, nrm, w, stream=None):
                                   _stream(stream)), h)
 
 
+SHADE_VARIANTS = 5
+
+
+def nvc_autotune_shade(h, scene: Scene, pos, nrm, idx=None, pdf=None, wsum=None, radiance=None,
+                       reps=5, stream=None):
+    """Times the fused shading kernel's variants on these pixels and keeps
+    the fastest.  Returns (chosen variant, [ms per launch or -1])."""
+    chosen = ctypes.c_int32()
+    ms = (ctypes.c_double * SHADE_VARIANTS)()
+    check(lib.nvc_autotune_shade(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0],
+                                 _ptr(idx, torch.int32, "idx"), _ptr(pdf), _ptr(wsum),
+                                 _ptr(radiance), int(reps), ctypes.byref(chosen), ms,
+                                 _stream(stream)), h)
+    return int(chosen.value), list(ms)
+
+
+def nvc_set_shade_variant(h, variant: int):
+    check(lib.nvc_set_shade_variant(h, int(variant)), h)
+
+
 def nvc_trace_visibility(scene: Scene, pos, vis, stream=None):
     check(lib.nvc_trace_visibility(scene.ref, _ptr(pos), pos.shape[0], _ptr(vis),
                                    _stream(stream)))

@@ -174,3 +174,32 @@ def test_fused_full_1080p_frame_sampled():
     cs = c_scale(gb.pos[pick], sc.lights).sum(1)
     assert np.all(np.abs(di - ref_di) <= FP16_TOL * c64.sum(1) + 2e-6 * cs + 1e-30)
     assert (host(out["idx"]) >= 0).mean() > 0.5
+
+
+@pytest.mark.parametrize("cfg_name", ["tiny_fp32", "frame_1080p", "paper"])
+def test_every_shade_variant_gives_identical_outputs(cfg_name):
+    """The autotuner's variants differ only in how warps share the work:
+    each one's outputs are bit-identical to the monolithic kernel's."""
+    cfg = S.config_by_name(cfg_name).with_(precision="fp16", batch_positions=256)
+    if cfg_name == "tiny_fp32":
+        sc, gb = S.scene_unit_cube(seed=0), S.gbuffer_points(0, 64, 64)
+    else:
+        sc = S.scene_heightfield(seed=3, n_lights=cfg.n_outputs, n_spheres=8, n_boxes=8)
+        gb = S.gbuffer_heightfield(seed=3, width=130, height=77)
+    cache, p = make(cfg, seed=1, table_scale=0.5)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    ref = None
+    for v in range(nvc.SHADE_VARIANTS):
+        nvc.nvc_set_shade_variant(cache.handle, v)
+        out = cache.shade(scene, pos, nrm, seed=5, frame=2, pixel_offset=9, fused=True)
+        vis = cache.infer(pos)
+        if ref is None:
+            ref = (out, vis)
+            continue
+        for k in ("idx", "pdf", "wsum", "radiance"):
+            assert torch.equal(out[k], ref[0][k]), (v, k)
+        assert torch.equal(vis, ref[1]), v
+    chosen, ms = nvc.nvc_autotune_shade(cache.handle, scene, pos, nrm, reps=2)
+    assert 0 <= chosen < nvc.SHADE_VARIANTS and ms[chosen] > 0
+    assert ms[chosen] == min(m for m in ms if m > 0)
