@@ -785,11 +785,27 @@ static nvc_status frame_body(nvc_handle* h, const nvc_scene* scene, const nvc_vi
                             frame, loss_out, s));
   }
   const bool fused = h->cfg.precision != NVC_PREC_FP32;
-  for (int v = 0; v < n_views; ++v) {
-    const nvc_view& vw = views[v];
-    if (vw.n_pixels == 0) continue;
-    NVC_TRY(shade_impl(h, scene, vw.pos, vw.nrm, vw.n_pixels, seed, frame, vw.view_id, 0, vw.idx,
-                       vw.pdf, vw.wsum, vw.radiance, fused, s));
+  if (fused) {
+    // every view of the frame in one persistent launch
+    std::string why;
+    if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
+    std::vector<FusedView> fv;
+    for (int v = 0; v < n_views; ++v) {
+      const nvc_view& vw = views[v];
+      if (vw.n_pixels == 0) continue;
+      fv.push_back(FusedView{vw.pos, vw.nrm, vw.n_pixels, vw.view_id, 0, vw.idx, vw.pdf, vw.wsum,
+                             vw.radiance, nullptr, nullptr});
+    }
+    StageScope sc(h, s, 3);
+    NVC_CUDA(h, launch_shade_fused_views(h, scene, fv.data(), (int)fv.size(), seed, frame, s));
+    count_launches(h, ((int)fv.size() + 15) / 16);
+  } else {
+    for (int v = 0; v < n_views; ++v) {
+      const nvc_view& vw = views[v];
+      if (vw.n_pixels == 0) continue;
+      NVC_TRY(shade_impl(h, scene, vw.pos, vw.nrm, vw.n_pixels, seed, frame, vw.view_id, 0,
+                         vw.idx, vw.pdf, vw.wsum, vw.radiance, 0, s));
+    }
   }
   bump_frames_kernel<<<1, 1, 0, s>>>(h->status);
   NVC_CUDA(h, cudaGetLastError());

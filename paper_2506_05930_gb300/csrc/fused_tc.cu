@@ -42,10 +42,28 @@ struct LayerDesc {
   uint32_t idesc;  // tcgen05 instruction descriptor
 };
 
-struct FusedArgs {
+constexpr int kMaxViews = 16;
+
+// One view of a launch: its pixels, outputs and first tile.
+struct ViewDesc {
   const float* pos;
   const float* nrm;
   int64_t n;
+  int64_t tile_start;   // tiles of earlier views
+  int64_t pixel_offset;
+  uint32_t view;
+  int32_t* idx;
+  float* pdf;
+  float* wsum;
+  float* radiance;
+  float* vis_out;
+  float* w_out;
+};
+
+struct FusedArgs {
+  int n_views;
+  int64_t n_tiles;
+  ViewDesc v[kMaxViews];
   const float* table;
   EncodeParams ep;
   int F;
@@ -58,15 +76,8 @@ struct FusedArgs {
   int L;
   uint32_t tmem_cols;
   const float* lights;
-  uint32_t k0, k1, frame, view;
+  uint32_t k0, k1, frame;
   uint2 rkey[10];    // Philox round keys for (k0, k1)
-  int64_t pixel_offset;
-  int32_t* idx;
-  float* pdf;
-  float* wsum;
-  float* radiance;
-  float* vis_out;
-  float* w_out;      // optional: the light weights the sampler uses, [n][L]
   int32_t* status;
   // warp-specialised layout (byte offsets into shared memory)
   int ws_a0[2], ws_h, ws_c[2], ws_l, ws_bar, ws_cs;
@@ -143,6 +154,13 @@ __device__ __forceinline__ uint32_t pick_word(uint4 r, int lane) {
   return lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
 }
 
+// View that tile `tile` belongs to (views are few and tiles sorted by view).
+__device__ __forceinline__ int view_of(const FusedArgs& a, int64_t tile) {
+  int v = 0;
+  while (v + 1 < a.n_views && tile >= a.v[v + 1].tile_start) ++v;
+  return v;
+}
+
 // ---- the kernel ----------------------------------------------------------------
 template <int F, int PREC, bool LSMALL>
 __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_constant__ FusedArgs a) {
@@ -183,16 +201,17 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
 
   const int din = a.ep.n_levels * F;
   const int K0 = a.layer[0].K;
-  const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+  const int64_t n_tiles = a.n_tiles;
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
-    const int64_t row = tile * kTileM + t;
-    const bool live = row < a.n;
+    const ViewDesc& V = a.v[view_of(a, tile)];
+    const int64_t row = (tile - V.tile_start) * kTileM + t;
+    const bool live = row < V.n;
     float px = 0.f, py = 0.f, pz = 0.f;
     if (live) {
-      px = __ldg(a.pos + 3 * row);
-      py = __ldg(a.pos + 3 * row + 1);
-      pz = __ldg(a.pos + 3 * row + 2);
+      px = __ldg(V.pos + 3 * row);
+      py = __ldg(V.pos + 3 * row + 1);
+      pz = __ldg(V.pos + 3 * row + 2);
     }
     // ---- encode this pixel into the layer-0 A tile ------------------------
     {
@@ -273,22 +292,22 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
 
       // ---- output layer: sigmoid, light weights, WRS, Neural DI -------------
       const int L = LSMALL ? (a.L < 32 ? a.L : 32) : a.L;
-      if (a.vis_out) {
+      if (V.vis_out) {
         for (int c0 = 0; c0 < L; c0 += 32) {
           uint32_t r[32];
           tmem_ld32(t_lane + (uint32_t)c0, r);
           if (live) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              if (c0 + j < L) a.vis_out[row * L + c0 + j] = sigmoid_fast(__uint_as_float(r[j]));
+              if (c0 + j < L) V.vis_out[row * L + c0 + j] = sigmoid_fast(__uint_as_float(r[j]));
           }
         }
       } else {
         float nx = 0.f, ny = 0.f, nz = 0.f;
         if (live) {
-          nx = __ldg(a.nrm + 3 * row);
-          ny = __ldg(a.nrm + 3 * row + 1);
-          nz = __ldg(a.nrm + 3 * row + 2);
+          nx = __ldg(V.nrm + 3 * row);
+          ny = __ldg(V.nrm + 3 * row + 1);
+          nz = __ldg(V.nrm + 3 * row + 2);
         }
         float wreg[32];
         float wmax = 0.0f, sum = 0.0f, di = 0.0f;
@@ -303,7 +322,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
               const float v = sigmoid_fast(__uint_as_float(r[j]));
               const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
               w = fmaxf(v, bits_f(kVisClampBits)) * c;
-              if (a.w_out && live) a.w_out[row * L + i] = w;
+              if (V.w_out && live) V.w_out[row * L + i] = w;
               wmax = fmaxf(wmax, w);
               sum += w;
               di = fmaf(v, c, di);
@@ -320,7 +339,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
         const bool fast_q = E >= 23u;
         const float qscale = __uint_as_float((277u - (fast_q ? E : 23u)) << 23);   // 2^(23 - e)
         const int e_sub = (active && !fast_q) ? ilogbf(wmax) : 0;
-        const uint32_t pixel = (uint32_t)(a.pixel_offset + row);
+        const uint32_t pixel = (uint32_t)(V.pixel_offset + row);
         uint32_t Q = 0;
         uint4 rr = make_uint4(0, 0, 0, 0);
         for (int c0 = 0; c0 < L; c0 += 32) {
@@ -338,7 +357,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
                       contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
                 }
                 if ((i & 3) == 0)
-                  rr = philox_keyed(make_uint4(pixel, a.frame, a.view,
+                  rr = philox_keyed(make_uint4(pixel, a.frame, V.view,
                                                ((uint32_t)(i >> 2) << 4) | kTagWrs),
                                     a.rkey);
                 const uint32_t q = fast_q ? quantize_scaled(w, qscale) : quantize_weight(w, e_sub);
@@ -353,10 +372,10 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
           }
         }
         if (live) {
-          if (a.idx) a.idx[row] = sel;
-          if (a.pdf) a.pdf[row] = sel >= 0 ? wsel / sum : 0.0f;
-          if (a.wsum) a.wsum[row] = sum;
-          if (a.radiance) a.radiance[row] = di;
+          if (V.idx) V.idx[row] = sel;
+          if (V.pdf) V.pdf[row] = sel >= 0 ? wsel / sum : 0.0f;
+          if (V.wsum) V.wsum[row] = sum;
+          if (V.radiance) V.radiance[row] = di;
         }
       }
       tc_fence_before();
@@ -442,7 +461,7 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
   const int din = a.ep.n_levels * F;
   const int K0 = a.layer[0].K;
   const int L = a.L;
-  const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+  const int64_t n_tiles = a.n_tiles;
   bool failed = false;
 
   if (warp >= 4) {
@@ -456,13 +475,14 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
         failed = true;
         break;
       }
-      const int64_t row = tile * kTileM + p;
-      const bool live = row < a.n;
+      const ViewDesc& V = a.v[view_of(a, tile)];
+      const int64_t row = (tile - V.tile_start) * kTileM + p;
+      const bool live = row < V.n;
       float px = 0.f, py = 0.f, pz = 0.f;
       if (live) {
-        px = __ldg(a.pos + 3 * row);
-        py = __ldg(a.pos + 3 * row + 1);
-        pz = __ldg(a.pos + 3 * row + 2);
+        px = __ldg(V.pos + 3 * row);
+        py = __ldg(V.pos + 3 * row + 1);
+        pz = __ldg(V.pos + 3 * row + 2);
       }
       uint8_t* a0 = smem + (b ? a.ws_a0[1] : a.ws_a0[0]);
       {
@@ -500,9 +520,9 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
       if (PRE_C && a.lights) {
         float nx = 0.f, ny = 0.f, nz = 0.f;
         if (live) {
-          nx = __ldg(a.nrm + 3 * row);
-          ny = __ldg(a.nrm + 3 * row + 1);
-          nz = __ldg(a.nrm + 3 * row + 2);
+          nx = __ldg(V.nrm + 3 * row);
+          ny = __ldg(V.nrm + 3 * row + 1);
+          nz = __ldg(V.nrm + 3 * row + 2);
         }
         float* cr = reinterpret_cast<float*>(smem + (b ? a.ws_c[1] : a.ws_c[0])) + p * CS;
 #pragma unroll 4
@@ -527,8 +547,9 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
         break;
       }
       tc_fence_after();
-      const int64_t row = tile * kTileM + t;
-      const bool live = row < a.n;
+      const ViewDesc& V = a.v[view_of(a, tile)];
+      const int64_t row = (tile - V.tile_start) * kTileM + t;
+      const bool live = row < V.n;
       const uint32_t a0_base = smem_u32(smem + (b ? a.ws_a0[1] : a.ws_a0[0]));
       bool ok = true;
       for (int k = 0; k < a.n_layers; ++k) {
@@ -573,23 +594,23 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
         // ---- output layer: sigmoid, weights, WRS, Neural DI --------------------
         uint32_t r[32];
         tmem_ld32(t_lane, r);
-        if (a.vis_out) {
+        if (V.vis_out) {
           if (live) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              if (j < L) a.vis_out[row * L + j] = sigmoid_fast(__uint_as_float(r[j]));
+              if (j < L) V.vis_out[row * L + j] = sigmoid_fast(__uint_as_float(r[j]));
           }
         } else {
           const float* cr =
               reinterpret_cast<const float*>(smem + (b ? a.ws_c[1] : a.ws_c[0])) + t * CS;
           float px = 0.f, py = 0.f, pz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
           if (!PRE_C && live) {
-            px = __ldg(a.pos + 3 * row);
-            py = __ldg(a.pos + 3 * row + 1);
-            pz = __ldg(a.pos + 3 * row + 2);
-            nx = __ldg(a.nrm + 3 * row);
-            ny = __ldg(a.nrm + 3 * row + 1);
-            nz = __ldg(a.nrm + 3 * row + 2);
+            px = __ldg(V.pos + 3 * row);
+            py = __ldg(V.pos + 3 * row + 1);
+            pz = __ldg(V.pos + 3 * row + 2);
+            nx = __ldg(V.nrm + 3 * row);
+            ny = __ldg(V.nrm + 3 * row + 1);
+            nz = __ldg(V.nrm + 3 * row + 2);
           }
           float wreg[32];
           float wmax = 0.0f, sum = 0.0f, di = 0.0f;
@@ -601,7 +622,7 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
               const float c =
                   PRE_C ? cr[j] : contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
               w = fmaxf(v, bits_f(kVisClampBits)) * c;
-              if (a.w_out && live) a.w_out[row * L + j] = w;
+              if (V.w_out && live) V.w_out[row * L + j] = w;
               wmax = fmaxf(wmax, w);
               sum += w;
               di = fmaf(v, c, di);
@@ -615,14 +636,14 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
             const bool fast_q = E >= 23u;
             const float qscale = __uint_as_float((277u - (fast_q ? E : 23u)) << 23);
             const int e_sub = fast_q ? 0 : ilogbf(wmax);
-            const uint32_t pixel = (uint32_t)(a.pixel_offset + row);
+            const uint32_t pixel = (uint32_t)(V.pixel_offset + row);
             uint32_t Q = 0;
             uint4 rr = make_uint4(0, 0, 0, 0);
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               if (j < L) {
                 if ((j & 3) == 0)
-                  rr = philox_keyed(make_uint4(pixel, a.frame, a.view,
+                  rr = philox_keyed(make_uint4(pixel, a.frame, V.view,
                                                ((uint32_t)(j >> 2) << 4) | kTagWrs),
                                     a.rkey);
                 const float w = wreg[j];
@@ -636,10 +657,10 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
             }
           }
           if (live) {
-            if (a.idx) a.idx[row] = sel;
-            if (a.pdf) a.pdf[row] = sel >= 0 ? wsel / sum : 0.0f;
-            if (a.wsum) a.wsum[row] = sum;
-            if (a.radiance) a.radiance[row] = di;
+            if (V.idx) V.idx[row] = sel;
+            if (V.pdf) V.pdf[row] = sel >= 0 ? wsel / sum : 0.0f;
+            if (V.wsum) V.wsum[row] = sum;
+            if (V.radiance) V.radiance[row] = di;
           }
         }
       }
@@ -746,7 +767,7 @@ cudaError_t launch_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cu
     occ = blocks_per_sm((const void*)kern, kTileM, smem);
   }
   if (occ > max_ctas) return cudaErrorInvalidConfiguration;
-  const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+  const int64_t n_tiles = a.n_tiles;
   const int64_t cap = (int64_t)occ * num_sms;
   const int grid = (int)(n_tiles < cap ? n_tiles : cap);
   kern<<<grid, kTileM, smem, s>>>(a);
@@ -792,7 +813,7 @@ cudaError_t launch_ws_typed(const FusedArgs& a, size_t smem_needed, int num_sms,
     occ = blocks_per_sm((const void*)kern, kThreads, smem);
   }
   if (occ > max_ctas) return cudaErrorInvalidConfiguration;
-  const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
+  const int64_t n_tiles = a.n_tiles;
   const int64_t cap = (int64_t)occ * num_sms;
   const int grid = (int)(n_tiles < cap ? n_tiles : cap);
   kern<<<grid, kThreads, smem, s>>>(a);
@@ -840,18 +861,39 @@ bool fused_supported(const nvc_handle* h, std::string* why) {
   return true;
 }
 
-cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const float* pos,
-                               const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
-                               uint32_t view, int64_t pixel_offset, int32_t* idx, float* pdf,
-                               float* wsum, float* radiance, float* vis_out, cudaStream_t s,
-                               float* w_out) {
-  if (n == 0) return cudaSuccess;
+cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
+                                     const FusedView* views, int n_views, uint64_t seed,
+                                     uint32_t frame, cudaStream_t s) {
+  // views beyond one launch's table go to further launches
+  if (n_views > kMaxViews) {
+    cudaError_t e = launch_shade_fused_views(h, sc, views, kMaxViews, seed, frame, s);
+    if (e != cudaSuccess) return e;
+    return launch_shade_fused_views(h, sc, views + kMaxViews, n_views - kMaxViews, seed, frame, s);
+  }
   PackArgs p{};
   layer_geometry(h, p);
   FusedArgs a{};
-  a.pos = pos;
-  a.nrm = nrm;
-  a.n = n;
+  int64_t tiles = 0;
+  for (int i = 0; i < n_views; ++i) {
+    const FusedView& fv = views[i];
+    if (fv.n <= 0) continue;
+    ViewDesc& V = a.v[a.n_views++];
+    V.pos = fv.pos;
+    V.nrm = fv.nrm;
+    V.n = fv.n;
+    V.tile_start = tiles;
+    V.pixel_offset = fv.pixel_offset;
+    V.view = fv.view;
+    V.idx = fv.idx;
+    V.pdf = fv.pdf;
+    V.wsum = fv.wsum;
+    V.radiance = fv.radiance;
+    V.vis_out = fv.vis_out;
+    V.w_out = fv.w_out;
+    tiles += (fv.n + kTileM - 1) / kTileM;
+  }
+  if (tiles == 0) return cudaSuccess;
+  a.n_tiles = tiles;
   a.table = h->params;
   a.ep = encode_params(h);
   a.F = h->F;
@@ -877,14 +919,6 @@ cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const f
   for (int r = 0; r < 10; ++r)
     a.rkey[r] = make_uint2(a.k0 + (uint32_t)r * kPhiloxW0, a.k1 + (uint32_t)r * kPhiloxW1);
   a.frame = frame;
-  a.view = view;
-  a.pixel_offset = pixel_offset;
-  a.idx = idx;
-  a.pdf = pdf;
-  a.wsum = wsum;
-  a.radiance = radiance;
-  a.vis_out = vis_out;
-  a.w_out = w_out;
   a.status = h->status;
   const bool bf16 = h->cfg.precision == NVC_PREC_BF16;
   const int variant = h->shade_variant;
@@ -919,6 +953,16 @@ cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const f
                         : launch_typed<8, NVC_PREC_FP16>(a, smem, h->num_sms, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const float* pos,
+                               const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
+                               uint32_t view, int64_t pixel_offset, int32_t* idx, float* pdf,
+                               float* wsum, float* radiance, float* vis_out, cudaStream_t s,
+                               float* w_out) {
+  if (n == 0) return cudaSuccess;
+  FusedView v{pos, nrm, n, view, pixel_offset, idx, pdf, wsum, radiance, vis_out, w_out};
+  return launch_shade_fused_views(h, sc, &v, 1, seed, frame, s);
 }
 
 }  // namespace nvc

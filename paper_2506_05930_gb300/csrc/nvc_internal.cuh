@@ -258,6 +258,23 @@ cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const f
                                float* wsum, float* radiance, float* vis_out, cudaStream_t s,
                                float* w_out = nullptr);
 size_t mlp_packed_bytes(const nvc_handle* h);
+// One view of a multi-view fused launch.
+struct FusedView {
+  const float* pos;
+  const float* nrm;
+  int64_t n;
+  uint32_t view;
+  int64_t pixel_offset;
+  int32_t* idx;
+  float* pdf;
+  float* wsum;
+  float* radiance;
+  float* vis_out;
+  float* w_out;
+};
+cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
+                                     const FusedView* views, int n_views, uint64_t seed,
+                                     uint32_t frame, cudaStream_t s);
 
 // train_tc.cu
 bool train_tc_supported(const nvc_handle* h, std::string* why);

@@ -203,3 +203,67 @@ def test_every_shade_variant_gives_identical_outputs(cfg_name):
     chosen, ms = nvc.nvc_autotune_shade(cache.handle, scene, pos, nrm, reps=2)
     assert 0 <= chosen < nvc.SHADE_VARIANTS and ms[chosen] > 0
     assert ms[chosen] == min(m for m in ms if m > 0)
+
+
+def _views(gbs):
+    out = []
+    for v, gb in enumerate(gbs):
+        n = gb.n
+        out.append(nvc.View(dev(gb.pos), dev(gb.nrm), v,
+                            torch.empty(n, dtype=torch.int32, device="cuda"),
+                            torch.empty(n, device="cuda"), torch.empty(n, device="cuda"),
+                            torch.empty(n, device="cuda")))
+    return out
+
+
+def test_multiview_frame_is_one_launch_equal_to_per_view_launches():
+    """Views of uneven resolution shaded by one persistent launch give the
+    same bits as one launch per view (the tile -> view table only changes
+    which CTA takes which tile)."""
+    cfg = S.config_by_name("multiview").with_(batch_positions=256)
+    sc = S.scene_unit_cube(seed=0, n_lights=128)
+    gbs = S.multiview_gbuffers(seed=3, sizes=((160, 90), (192, 108), (256, 144), (384, 216)))
+    cache, p = make(cfg, seed=1, table_scale=0.5)
+    scene = nvc.Scene.from_synth(sc)
+    views = _views(gbs)
+    nvc.nvc_stage_times(cache.handle)
+    nvc.nvc_frame(cache.handle, scene, views, nvc.NO_TRAINING, seed=7, frame=3, use_graph=False)
+    _, launches = nvc.nvc_stage_times(cache.handle)
+    assert launches == 2          # all four views in one shading launch + the frame counter
+    for v, gb in zip(views, gbs):
+        ref = cache.shade(scene, v.pos, v.nrm, seed=7, frame=3, view=v.view_id, fused=True)
+        for k in ("idx", "pdf", "wsum", "radiance"):
+            assert torch.equal(getattr(v, k), ref[k]), (v.view_id, k)
+
+
+def test_multiview_full_workload_in_one_graph_launch_sampled():
+    """The batched multi-view workload: 1280x720, 1920x1080, 2560x1440 and
+    3840x2160 (14,976,000 pixels) with 128 lights, trained and shaded as
+    one graph-replayed frame; 2048 pixels per view checked against the
+    oracle."""
+    cfg = S.config_by_name("multiview")
+    sc = S.scene_unit_cube(seed=0, n_lights=128)
+    gbs = S.multiview_gbuffers(seed=0)
+    assert sum(g.n for g in gbs) == 14_976_000
+    cache, p = make(cfg, seed=2, table_scale=0.5)
+    scene = nvc.Scene.from_synth(sc)
+    views = _views(gbs)
+    nvc.nvc_frame(cache.handle, scene, views, nvc.NO_TRAINING, seed=1, frame=0, use_graph=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    for v, gb in zip(views, gbs):
+        pick = rng.choice(gb.n, 2048, replace=False)
+        pt = torch.from_numpy(pick).cuda()
+        w = torch.empty((2048, 128), device="cuda")
+        nvc.nvc_sampler_weights(cache.handle, scene, v.pos[pt].contiguous(), v.nrm[pt].contiguous(), w)
+        idx, pdf, wsum = O.wrs_select(host(w), pick, 1, 0, v.view_id)
+        assert np.array_equal(host(v.idx)[pick], idx)
+        v64 = O.infer(cfg, p, gb.pos[pick])
+        c64 = O.contributions(gb.pos[pick], gb.nrm[pick], sc.lights)
+        ref_di = O.neural_di(v64, c64)
+        cs = c_scale(gb.pos[pick], sc.lights).sum(1)
+        assert np.all(np.abs(host(v.radiance)[pick] - ref_di) <= FP16_TOL * c64.sum(1) + 2e-6 * cs)
+    # and a training frame over the same views runs and counts
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    nvc.nvc_frame(cache.handle, scene, views, 1, seed=1, frame=1, loss_out=loss, use_graph=True)
+    assert cache.counters()["step"] == 1 and np.isfinite(host(loss)[0])
