@@ -103,6 +103,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------- multi-rank logic --
+
+def rank_stream(rank: int):
+    """Seed and view id of a rank: every rank renders and trains its own
+    view (weak scaling), so their random streams must differ."""
+    return 1234 + rank, rank
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's time (a no-op on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, pixels_per_rank: int, ms_per_frame: float) -> float:
+    """Whole-job Mpixels/s: all ranks' pixels over the slowest rank's frame time."""
+    return world * pixels_per_rank / (ms_per_frame * 1e-3) / 1e6
+
+
 # --------------------------------------------------------------- workload --
 
 _WORKLOAD_CACHE = {}
@@ -164,7 +188,7 @@ def run_ours(args):
     fused = cfg.precision != "fp32"
     if not fused:
         nvc.nvc_set_staging(cache.handle, P)
-    view = nvc.View(pos, nrm, rank, torch.empty(P, dtype=torch.int32, device="cuda"),
+    view = nvc.View(pos, nrm, view_id, torch.empty(P, dtype=torch.int32, device="cuda"),
                     torch.empty(P, device="cuda"), torch.empty(P, device="cuda"),
                     torch.empty(P, device="cuda"))
     tune = None
@@ -174,7 +198,7 @@ def run_ours(args):
                                             view.wsum, view.radiance, reps=5)
         tune = {"chosen_variant": chosen, "variant_ms": [round(m, 4) for m in ms]}
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
-    seed = 1234 + rank
+    seed, view_id = rank_stream(rank)
     use_graph = not args.no_graph
     # pretraining (untimed): 500 frames of online training on this view
     for f in range(args.pretrain):
@@ -205,12 +229,9 @@ def run_ours(args):
     ms_total = t0.elapsed_time(t1)
     clk = clocks.stop() if clocks else None
     _, launches = nvc.nvc_stage_times(cache.handle)
-    if world > 1:
-        tt = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(ms_total, "cuda")
     ms_frame = ms_total / args.steps
-    value = world * P / (ms_frame * 1e-3) / 1e6
+    value = job_throughput(world, P, ms_frame)
 
     # per-stage attribution with CUDA events around each stage (eager frames)
     nvc.nvc_set_profiling(cache.handle, True)
@@ -258,10 +279,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e_ms = e0.elapsed_time(e1) / e_steps
-    if world > 1:
-        tt = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_ms = float(tt.item())
+    e_ms = max_over_ranks(e_ms, "cuda")
 
     # the plain float32 separate-kernel path, same frame (the baseline to beat)
     base = None
@@ -326,7 +344,7 @@ def run_ours(args):
                       "adam": stage_ms[2], "shade": stage_ms[3], "eager_frame": eager_ms},
         "infer_mpixels_s": P / shade_s / 1e6 if shade_s > 0 else None,
         "train_ms": stage_ms[0] + stage_ms[1] + stage_ms[2],
-        "e2e": {"value": world * P / (e_ms * 1e-3) / 1e6, "unit": "Mpixels/s",
+        "e2e": {"value": job_throughput(world, P, e_ms), "unit": "Mpixels/s",
                 "ms_per_step": e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "autotune": tune,
