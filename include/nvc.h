@@ -232,6 +232,13 @@ nvc_status nvc_shade(nvc_handle* h, const nvc_scene* scene, const float* pos,
 nvc_status nvc_sampler_weights(nvc_handle* h, const nvc_scene* scene, const float* pos,
                                const float* nrm, int64_t n, float* w, void* stream);
 
+/* Activation scales of the FP8 (E4M3) path: runs the float32 network on
+ * pos (device [n][3], 1 <= n <= batch_positions) and sets each layer
+ * input's per-tensor scale to 448 / max |value| (the weights' scales are
+ * set the same way from the weights whenever they change).  Required once
+ * before FP8 inference; asynchronous. */
+nvc_status nvc_calibrate(nvc_handle* h, const float* pos, int64_t n, void* stream);
+
 /* Variants of the fused shading kernel (nvc_shade with fused = 1):
  *   0  every warp encodes, multiplies and samples its own 128-pixel tile;
  *   1  warp-specialised: 4 producer warps encode the next tile while 4
@@ -240,7 +247,7 @@ nvc_status nvc_sampler_weights(nvc_handle* h, const nvc_scene* scene, const floa
  *   3  as 1 with 8 producer warps (two threads per pixel, half the levels
  *      each);
  *   4  as 3 with the contributions computed by the producers.
- * 1-4 need n_outputs <= 32.  All compute the same function. */
+ * 1-4 need n_outputs <= 32 and FP16/BF16.  All compute the same function. */
 #define NVC_SHADE_VARIANTS 5
 
 /* Times every applicable variant on these pixels (CUDA events on `stream`,

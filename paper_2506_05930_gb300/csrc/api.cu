@@ -30,6 +30,7 @@ nvc_status fail(nvc_handle* h, nvc_status st, const char* fmt, ...) {
 }
 
 nvc_status cuda_fail(nvc_handle* h, cudaError_t e, const char* what) {
+  cudaGetLastError();   // the error is reported here; do not leave it for the next call
   return fail(h, NVC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -295,6 +296,13 @@ nvc_status nvc_create(const nvc_config* cfg, nvc_handle** out) {
       (e = dalloc(&h->status, kStWords)) || (e = dalloc(&h->adam_scalars, 1)))
     return cleanup_fail(e, "cudaMalloc");
   h->n_loss_partials = 256;
+  {
+    float ones[2 * (NVC_MAX_HIDDEN_LAYERS + 1)];
+    for (float& o : ones) o = 1.0f;
+    if ((e = dalloc(&h->fp8_scales, 2 * (NVC_MAX_HIDDEN_LAYERS + 1))) ||
+        (e = cudaMemcpy(h->fp8_scales, ones, sizeof(ones), cudaMemcpyHostToDevice)))
+      return cleanup_fail(e, "cudaMalloc");
+  }
   h->mlp_packed_bytes = mlp_packed_bytes(h);
   if (h->mlp_packed_bytes) {
     if ((e = cudaMalloc(&h->mlp_packed, h->mlp_packed_bytes)) != cudaSuccess)
@@ -303,6 +311,13 @@ nvc_status nvc_create(const nvc_config* cfg, nvc_handle** out) {
   }
   if (cfg->train_precision == NVC_PREC_FP16) {
     std::string why;
+    if (cfg->precision == NVC_PREC_FP8) {
+      nvc_status st = fail(nullptr, NVC_ERR_UNSUPPORTED,
+                           "FP16 training shares the 16-bit weight image: with FP8 inference "
+                           "train in FP32");
+      nvc_destroy(h);
+      return st;
+    }
     if (!train_tc_supported(h, &why)) {
       nvc_status st = fail(nullptr, NVC_ERR_UNSUPPORTED, "FP16 training: %s", why.c_str());
       nvc_destroy(h);
@@ -340,6 +355,7 @@ void nvc_destroy(nvc_handle* h) {
   cudaFree(h->loss_partials);
   cudaFree(h->status);
   cudaFree(h->adam_scalars);
+  cudaFree(h->fp8_scales);
   cudaFree(h->s_feat);
   cudaFree(h->s_vis);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
@@ -569,12 +585,48 @@ nvc_status nvc_sampler_weights(nvc_handle* h, const nvc_scene* scene, const floa
   return NVC_OK;
 }
 
+// max |x| over each of the layer inputs of a calibration batch -> E4M3 scale
+__global__ void activation_scales_kernel(const float* __restrict__ feat, int64_t feat_n,
+                                         const float* __restrict__ act, int64_t act_stride,
+                                         int64_t act_n, float* scales) {
+  const int k = blockIdx.x;
+  const float* x = k == 0 ? feat : act + (int64_t)(k - 1) * act_stride;
+  const int64_t n = k == 0 ? feat_n : act_n;
+  __shared__ float s_max[32];
+  float m = 0.0f;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) m = fmaxf(m, fabsf(x[e]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_max[w]);
+    m = fmaxf(m, s_max[0]);
+    scales[k] = m > 0.0f ? 448.0f / m : 1.0f;
+  }
+}
+
+nvc_status nvc_calibrate(nvc_handle* h, const float* pos, int64_t n, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 1 || n > h->B) return fail(h, NVC_ERR_INVALID_ARG, "n must be in [1, batch_positions]");
+  NVC_TRY(check_ptr(h, pos, "pos"));
+  cudaStream_t s = (cudaStream_t)stream;
+  NVC_CUDA(h, launch_encode_fwd(h, pos, n, h->t_feat, s));
+  NVC_CUDA(h, launch_mlp_fwd_fp32(h, h->t_feat, n, h->t_logits, false, h->t_act, s));
+  activation_scales_kernel<<<h->n_layers, 256, 0, s>>>(h->t_feat, n * h->din, h->t_act,
+                                                        (int64_t)h->B * h->width,
+                                                        n * h->width, h->fp8_scales);
+  NVC_CUDA(h, cudaGetLastError());
+  h->fp8_calibrated = true;
+  return NVC_OK;
+}
+
 nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant) {
   if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
   if (variant < 0 || variant >= kShadeVariants)
     return fail(h, NVC_ERR_INVALID_ARG, "variant out of range");
-  if (variant != kShadeMono && h->L > 32)
-    return fail(h, NVC_ERR_UNSUPPORTED, "warp-specialised variants need n_outputs <= 32");
+  if (variant != kShadeMono && (h->L > 32 || h->cfg.precision == NVC_PREC_FP8))
+    return fail(h, NVC_ERR_UNSUPPORTED,
+                "warp-specialised variants need n_outputs <= 32 and 16-bit operands");
   h->shade_variant = variant;
   return NVC_OK;
 }
@@ -596,7 +648,7 @@ nvc_status nvc_autotune_shade(nvc_handle* h, const nvc_scene* scene, const float
   double best_ms = 0.0;
   for (int v = 0; v < kShadeVariants; ++v) {
     if (ms_out) ms_out[v] = -1.0;
-    if (v != kShadeMono && h->L > 32) continue;
+    if (v != kShadeMono && (h->L > 32 || h->cfg.precision == NVC_PREC_FP8)) continue;
     h->shade_variant = v;
     cudaError_t e = launch_shade_fused(h, scene, pos, nrm, n, 1, 0, 0, 0, idx, pdf, wsum,
                                        radiance, nullptr, s);

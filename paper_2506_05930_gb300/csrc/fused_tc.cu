@@ -79,8 +79,11 @@ struct FusedArgs {
   uint32_t k0, k1, frame;
   uint2 rkey[10];    // Philox round keys for (k0, k1)
   int32_t* status;
+  const float* fp8_scales;   // [0, kMaxLayers): activation scales, [kMaxLayers, 2 kMaxLayers): weight scales
   // warp-specialised layout (byte offsets into shared memory)
   int ws_a0[2], ws_h, ws_c[2], ws_l, ws_bar, ws_cs;
+  // monolithic layout: activation tile, light table, mbarrier + TMEM word
+  int mono_a, mono_l, mono_bar;
 };
 
 // ---- the sampler's arithmetic ----------------------------------------------
@@ -124,10 +127,33 @@ __device__ __forceinline__ uint32_t quantize_scaled(float w, float scale) {
   return (w > 0.0f && q == 0u) ? 1u : q;
 }
 
+// One 16-byte core-matrix row of an operand: 8 fp16/bf16 or 16 E4M3 values
+// (the latter multiplied by the tensor's scale first).
+template <int PREC, int CH>
+__device__ __forceinline__ uint4 pack_chunk(const float (&v)[CH], float scale) {
+  uint4 pk;
+  if constexpr (PREC == NVC_PREC_FP8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      w[q] = pack_e4m3x2(v[4 * q] * scale, v[4 * q + 1] * scale) |
+             (pack_e4m3x2(v[4 * q + 2] * scale, v[4 * q + 3] * scale) << 16);
+    pk = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    pk.x = pack2<PREC>(v[0], v[1]);
+    pk.y = pack2<PREC>(v[2], v[3]);
+    pk.z = pack2<PREC>(v[4], v[5]);
+    pk.w = pack2<PREC>(v[6], v[7]);
+  }
+  return pk;
+}
+
 // Two fp32 pre-activations -> packed 16-bit leaky ReLU (0 <= slope < 1).
 template <int PREC>
 __device__ __forceinline__ uint32_t leaky2(uint32_t za, uint32_t zb, float slope) {
-  if constexpr (PREC == NVC_PREC_BF16) {
+  if constexpr (PREC == NVC_PREC_FP8) {
+    return 0u;   // the E4M3 path converts in fp32 (see the hidden-layer store)
+  } else if constexpr (PREC == NVC_PREC_BF16) {
     const __nv_bfloat162 z = __floats2bfloat162_rn(__uint_as_float(za), __uint_as_float(zb));
     const __nv_bfloat162 h = __hmax2(z, __hmul2(z, __float2bfloat162_rn(slope)));
     return *reinterpret_cast<const uint32_t*>(&h);
@@ -165,10 +191,11 @@ __device__ __forceinline__ int view_of(const FusedArgs& a, int64_t tile) {
 template <int F, int PREC, bool LSMALL>
 __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
+  // offsets computed by the host (fused_smem), which sized the allocation
   uint8_t* s_w = smem;
-  uint8_t* s_a = smem + a.wimg_bytes;
-  float4* s_l = reinterpret_cast<float4*>(s_a + kTileM * a.kmax * 2);
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_l + (a.L > 0 ? a.L : 1));
+  uint8_t* s_a = smem + a.mono_a;
+  float4* s_l = reinterpret_cast<float4*>(smem + a.mono_l);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.mono_bar);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 1);
   const int t = threadIdx.x;
   const int warp = t >> 5;
@@ -199,6 +226,23 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
   uint32_t phase = 0;
   bool failed = false;
 
+  constexpr bool kF8 = PREC == NVC_PREC_FP8;
+  constexpr int CH = kF8 ? 16 : 8;     // operand elements per 16-byte core-matrix row
+  constexpr int ES = kF8 ? 1 : 2;      // bytes per operand element
+  constexpr int KS = kF8 ? 32 : 16;    // K per MMA instruction
+  // E4M3: layer k's accumulator times s_mult[k] is the next layer's scaled
+  // input (or, for the last layer, the logit)
+  __shared__ float s_mult[kMaxLayers];
+  float s_in0 = 1.0f;
+  if constexpr (kF8) {
+    const float* sa = a.fp8_scales;
+    const float* sw = a.fp8_scales + kMaxLayers;
+    s_in0 = sa[0];
+    if (t < a.n_layers)
+      s_mult[t] = (t + 1 < a.n_layers ? sa[t + 1] : 1.0f) / (sa[t] * sw[t]);
+    __syncthreads();
+  }
+
   const int din = a.ep.n_levels * F;
   const int K0 = a.layer[0].K;
   const int64_t n_tiles = a.n_tiles;
@@ -218,32 +262,28 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
       const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
       const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
       const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
-      constexpr int LPC = F >= 8 ? 1 : 8 / F;   // levels per 8-feature chunk
-      for (int c = 0; c < K0 / 8; ++c) {
-        float f8[8];
+      constexpr int LPC = F >= CH ? 1 : CH / F;   // levels per chunk
+      for (int c = 0; c < K0 / CH; ++c) {
+        float fv[CH];
 #pragma unroll
-        for (int s = 0; s < 8; ++s) f8[s] = 0.0f;
+        for (int s = 0; s < CH; ++s) fv[s] = 0.0f;
         if (live) {
 #pragma unroll
           for (int q = 0; q < LPC; ++q) {
-            const int l = (c * 8) / F + q;
-            if (F <= 8 && l * F < din && (l * F) / 8 == c) {
+            const int l = (c * CH) / F + q;
+            if (l * F < din && (l * F) / CH == c) {
               float acc[F];
               encode_level<F>(a.ep, a.table, l, x, y, z, acc);
 #pragma unroll
               for (int f = 0; f < F; ++f) {
-                const int k = l * F + f - c * 8;
-                if (k >= 0 && k < 8) f8[k] = acc[f];
+                const int k = l * F + f - c * CH;
+                if (k >= 0 && k < CH) fv[k] = acc[f];
               }
             }
           }
         }
-        uint4 pk;
-        pk.x = pack2<PREC>(f8[0], f8[1]);
-        pk.y = pack2<PREC>(f8[2], f8[3]);
-        pk.z = pack2<PREC>(f8[4], f8[5]);
-        pk.w = pack2<PREC>(f8[6], f8[7]);
-        *reinterpret_cast<uint4*>(s_a + cm_offset(t, c * 8, K0, 2)) = pk;
+        *reinterpret_cast<uint4*>(s_a + cm_offset(t, c * CH, K0, ES)) =
+            pack_chunk<PREC, CH>(fv, s_in0);
       }
     }
     fence_async_smem();
@@ -255,11 +295,15 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
       const LayerDesc ld = a.layer[k];
       if (t == 0) {
         tc_fence_after();
-        const uint32_t sbo = (uint32_t)ld.K * 16u;
+        const uint32_t sbo = (uint32_t)ld.K * 8u * ES;
         const uint32_t wb = w_base + (uint32_t)ld.w_byte_off;
-        for (int kk = 0; kk < ld.K / 16; ++kk) {
-          mma_f16(tmem, smem_desc(a_base + kk * 256, 128, sbo), smem_desc(wb + kk * 256, 128, sbo),
-                  ld.idesc, kk > 0 ? 1u : 0u);
+        for (int kk = 0; kk < ld.K / KS; ++kk) {
+          if constexpr (kF8)
+            mma_f8(tmem, smem_desc(a_base + kk * 256, 128, sbo),
+                   smem_desc(wb + kk * 256, 128, sbo), ld.idesc, kk > 0 ? 1u : 0u);
+          else
+            mma_f16(tmem, smem_desc(a_base + kk * 256, 128, sbo),
+                    smem_desc(wb + kk * 256, 128, sbo), ld.idesc, kk > 0 ? 1u : 0u);
         }
         mma_commit(bar);
       }
@@ -272,16 +316,33 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
         for (int c0 = 0; c0 < ld.N; c0 += 32) {
           uint32_t r[32];
           tmem_ld32(t_lane + (uint32_t)c0, r);
+          if constexpr (kF8) {
+            // leaky ReLU is positively homogeneous: leaky(m z) = m leaky(z)
+            const float m = s_mult[k];
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            // convert pairs, then leaky ReLU max(z, slope z) in packed 16-bit math
-            uint4 pk;
-            pk.x = leaky2<PREC>(r[g * 8 + 0], r[g * 8 + 1], a.slope);
-            pk.y = leaky2<PREC>(r[g * 8 + 2], r[g * 8 + 3], a.slope);
-            pk.z = leaky2<PREC>(r[g * 8 + 4], r[g * 8 + 5], a.slope);
-            pk.w = leaky2<PREC>(r[g * 8 + 6], r[g * 8 + 7], a.slope);
-            if (c0 + g * 8 < Kn)
-              *reinterpret_cast<uint4*>(s_a + cm_offset(t, c0 + g * 8, Kn, 2)) = pk;
+            for (int g = 0; g < 2; ++g) {
+              float v[16];
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                const float zz = __uint_as_float(r[g * 16 + q]) * m;
+                v[q] = fmaxf(zz, a.slope * zz);
+              }
+              if (c0 + g * 16 < Kn)
+                *reinterpret_cast<uint4*>(s_a + cm_offset(t, c0 + g * 16, Kn, 1)) =
+                    pack_chunk<PREC, 16>(v, 1.0f);
+            }
+          } else {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              // convert pairs, then leaky ReLU max(z, slope z) in packed 16-bit math
+              uint4 pk;
+              pk.x = leaky2<PREC>(r[g * 8 + 0], r[g * 8 + 1], a.slope);
+              pk.y = leaky2<PREC>(r[g * 8 + 2], r[g * 8 + 3], a.slope);
+              pk.z = leaky2<PREC>(r[g * 8 + 4], r[g * 8 + 5], a.slope);
+              pk.w = leaky2<PREC>(r[g * 8 + 6], r[g * 8 + 7], a.slope);
+              if (c0 + g * 8 < Kn)
+                *reinterpret_cast<uint4*>(s_a + cm_offset(t, c0 + g * 8, Kn, 2)) = pk;
+            }
           }
         }
         fence_async_smem();
@@ -292,6 +353,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
 
       // ---- output layer: sigmoid, light weights, WRS, Neural DI -------------
       const int L = LSMALL ? (a.L < 32 ? a.L : 32) : a.L;
+      const float outmul = kF8 ? s_mult[a.n_layers - 1] : 1.0f;
       if (V.vis_out) {
         for (int c0 = 0; c0 < L; c0 += 32) {
           uint32_t r[32];
@@ -299,7 +361,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
           if (live) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              if (c0 + j < L) V.vis_out[row * L + c0 + j] = sigmoid_fast(__uint_as_float(r[j]));
+              if (c0 + j < L) V.vis_out[row * L + c0 + j] = sigmoid_fast(__uint_as_float(r[j]) * outmul);
           }
         }
       } else {
@@ -319,7 +381,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
             const int i = c0 + j;
             float w = 0.0f;
             if (i < L) {
-              const float v = sigmoid_fast(__uint_as_float(r[j]));
+              const float v = sigmoid_fast(__uint_as_float(r[j]) * outmul);
               const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
               w = fmaxf(v, bits_f(kVisClampBits)) * c;
               if (V.w_out && live) V.w_out[row * L + i] = w;
@@ -352,7 +414,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
               if (i < L) {
                 float w = wreg[j];
                 if (!LSMALL) {
-                  const float v = sigmoid_fast(__uint_as_float(r[j]));
+                  const float v = sigmoid_fast(__uint_as_float(r[j]) * outmul);
                   w = fmaxf(v, bits_f(kVisClampBits)) *
                       contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
                 }
@@ -712,25 +774,63 @@ __global__ void pack_mlp_kernel(const float* __restrict__ params, PackArgs p, ui
   }
 }
 
+// E4M3 weight image: one block per layer finds max |W_k|, sets the layer's
+// scale 448 / max (1 when the layer is zero), then writes round(W_k * scale).
+__global__ void pack_mlp_fp8_kernel(const float* __restrict__ params, PackArgs p, uint8_t* out,
+                                    float* w_scales) {
+  const int k = blockIdx.x;
+  __shared__ float s_max[32];
+  const int nr = p.N_real[k], kr = p.K_real[k];
+  const float* W = params + p.w_off[k];
+  float m = 0.0f;
+  for (int e = threadIdx.x; e < nr * kr; e += blockDim.x) m = fmaxf(m, fabsf(W[e]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (int)(blockDim.x >> 5) ? s_max[threadIdx.x] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) s_max[0] = m;
+  }
+  __syncthreads();
+  const float scale = s_max[0] > 0.0f ? 448.0f / s_max[0] : 1.0f;
+  if (threadIdx.x == 0) w_scales[k] = scale;
+  const int K = p.K[k], total = p.N[k] * K;
+  uint8_t* dst = out + p.byte_off[k];
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    // invert cm_offset for 1-byte elements: 128 elements per core matrix
+    const int grp = e >> 7, within = e & 127;
+    const int kg = grp % (K / 16), ng = grp / (K / 16);
+    const int n = ng * 8 + (within >> 4), kk = kg * 16 + (within & 15);
+    const float v = (n < nr && kk < kr) ? W[(int64_t)n * kr + kk] * scale : 0.0f;
+    dst[e] = (uint8_t)(pack_e4m3x2(v, 0.0f) & 0xFFu);
+  }
+}
+
 int round16(int x) { return (x + 15) & ~15; }
+int round32(int x) { return (x + 31) & ~31; }
 
 uint32_t make_idesc(int M, int N, int prec) {
-  const uint32_t ab = prec == NVC_PREC_BF16 ? 1u : 0u;  // kind::f16: 0 = f16, 1 = bf16
+  // kind::f16: 0 = f16, 1 = bf16; kind::f8f6f4: 0 = E4M3
+  const uint32_t ab = prec == NVC_PREC_BF16 ? 1u : 0u;
   return (1u << 4)                                       // D = f32
          | (ab << 7) | (ab << 10)                        // A, B formats; both K-major
          | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-bool tc_precision(int prec) { return prec == NVC_PREC_FP16 || prec == NVC_PREC_BF16; }
+bool tc_precision(int prec) {
+  return prec == NVC_PREC_FP16 || prec == NVC_PREC_BF16 || prec == NVC_PREC_FP8;
+}
 
 void layer_geometry(const nvc_handle* h, PackArgs& p) {
   p.n_layers = h->n_layers;
-  p.esize = 2;
+  const bool f8 = h->cfg.precision == NVC_PREC_FP8;
+  p.esize = f8 ? 1 : 2;
   int off = 0;
   for (int k = 0; k < h->n_layers; ++k) {
     p.K_real[k] = h->w_in[k];
     p.N_real[k] = h->w_out[k];
-    p.K[k] = round16(h->w_in[k]);
+    p.K[k] = f8 ? round32(h->w_in[k]) : round16(h->w_in[k]);
     p.N[k] = round16(h->w_out[k]);
     p.w_off[k] = h->w_off[k];
     p.byte_off[k] = off;
@@ -747,10 +847,26 @@ uint32_t tmem_cols_for(const PackArgs& p) {
   return c;
 }
 
-size_t fused_smem(const nvc_handle* h, const PackArgs& p) {
+// Shared-memory plan of the monolithic kernel: weight image, one activation
+// tile (128 rows x the widest K, p.esize bytes each), light table, then the
+// mbarrier and TMEM address word.  Fills the offsets when `a` is given.
+size_t fused_smem(const nvc_handle* h, const PackArgs& p, FusedArgs* a = nullptr) {
   int kmax = 16;
   for (int k = 0; k < p.n_layers; ++k) kmax = p.K[k] > kmax ? p.K[k] : kmax;
-  return (size_t)p.byte_off[p.n_layers] + (size_t)kTileM * kmax * 2 + 16 * (size_t)h->L + 64;
+  size_t off = (size_t)p.byte_off[p.n_layers];
+  const size_t a_off = off;
+  off += (size_t)kTileM * kmax * p.esize;
+  off = (off + 15) & ~(size_t)15;
+  const size_t l_off = off;
+  off += 16 * (size_t)(h->L > 0 ? h->L : 1);
+  const size_t bar_off = off;
+  off += 64;
+  if (a) {
+    a->mono_a = (int)a_off;
+    a->mono_l = (int)l_off;
+    a->mono_bar = (int)bar_off;
+  }
+  return off;
 }
 
 template <int F, int PREC>
@@ -759,10 +875,14 @@ cudaError_t launch_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cu
   // cap CTAs per SM so their TMEM columns fit in 512
   const int max_ctas = (int)(512u / a.tmem_cols);
   size_t smem = smem_needed;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)kern);
+  if (e != cudaSuccess) return e;
+  const size_t dyn_max = 227 * 1024 - fa.sharedSizeBytes;   // static + dynamic <= 227 KB
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
   if (e != cudaSuccess) return e;
   int occ = blocks_per_sm((const void*)kern, kTileM, smem);
-  while (occ > max_ctas && smem + 4096 <= 227 * 1024) {
+  while (occ > max_ctas && smem + 4096 <= dyn_max) {
     smem += 4096;
     occ = blocks_per_sm((const void*)kern, kTileM, smem);
   }
@@ -805,10 +925,14 @@ cudaError_t launch_ws_typed(const FusedArgs& a, size_t smem_needed, int num_sms,
   constexpr int kThreads = kTileM + PW * 32;
   const int max_ctas = (int)(512u / a.tmem_cols);
   size_t smem = smem_needed;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)kern);
+  if (e != cudaSuccess) return e;
+  const size_t dyn_max = 227 * 1024 - fa.sharedSizeBytes;   // static + dynamic <= 227 KB
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
   if (e != cudaSuccess) return e;
   int occ = blocks_per_sm((const void*)kern, kThreads, smem);
-  while (occ > max_ctas && smem + 4096 <= 227 * 1024) {
+  while (occ > max_ctas && smem + 4096 <= dyn_max) {
     smem += 4096;
     occ = blocks_per_sm((const void*)kern, kThreads, smem);
   }
@@ -835,7 +959,10 @@ cudaError_t launch_pack_mlp(nvc_handle* h, cudaStream_t s) {
   layer_geometry(h, p);
   const int total = p.byte_off[p.n_layers] / p.esize;
   const int blocks = (total + 255) / 256;
-  if (h->cfg.precision == NVC_PREC_BF16)
+  if (h->cfg.precision == NVC_PREC_FP8)
+    pack_mlp_fp8_kernel<<<p.n_layers, 256, 0, s>>>(h->params, p, (uint8_t*)h->mlp_packed,
+                                                    h->fp8_scales + kMaxLayers);
+  else if (h->cfg.precision == NVC_PREC_BF16)
     pack_mlp_kernel<NVC_PREC_BF16><<<blocks, 256, 0, s>>>(h->params, p, (uint8_t*)h->mlp_packed);
   else
     pack_mlp_kernel<NVC_PREC_FP16><<<blocks, 256, 0, s>>>(h->params, p, (uint8_t*)h->mlp_packed);
@@ -844,7 +971,11 @@ cudaError_t launch_pack_mlp(nvc_handle* h, cudaStream_t s) {
 
 bool fused_supported(const nvc_handle* h, std::string* why) {
   if (!tc_precision(h->cfg.precision)) {
-    *why = "the fused tensor-core kernel runs in FP16 or BF16 precision";
+    *why = "the fused tensor-core kernel runs in FP16, BF16 or FP8 precision";
+    return false;
+  }
+  if (h->cfg.precision == NVC_PREC_FP8 && !h->fp8_calibrated) {
+    *why = "FP8 needs activation scales: call nvc_calibrate first";
     return false;
   }
   PackArgs p{};
@@ -920,6 +1051,17 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
     a.rkey[r] = make_uint2(a.k0 + (uint32_t)r * kPhiloxW0, a.k1 + (uint32_t)r * kPhiloxW1);
   a.frame = frame;
   a.status = h->status;
+  a.fp8_scales = h->fp8_scales;
+  if (h->cfg.precision == NVC_PREC_FP8) {
+    const size_t smem8 = fused_smem(h, p, &a);
+    switch (h->F) {
+      case 1: return launch_typed<1, NVC_PREC_FP8>(a, smem8, h->num_sms, s);
+      case 2: return launch_typed<2, NVC_PREC_FP8>(a, smem8, h->num_sms, s);
+      case 4: return launch_typed<4, NVC_PREC_FP8>(a, smem8, h->num_sms, s);
+      case 8: return launch_typed<8, NVC_PREC_FP8>(a, smem8, h->num_sms, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   const bool bf16 = h->cfg.precision == NVC_PREC_BF16;
   const int variant = h->shade_variant;
   if (h->L <= 32 && variant != kShadeMono) {
@@ -941,7 +1083,7 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
 #undef NVC_WS
     }
   }
-  const size_t smem = fused_smem(h, p);
+  const size_t smem = fused_smem(h, p, &a);
   switch (h->F) {
     case 1: return bf16 ? launch_typed<1, NVC_PREC_BF16>(a, smem, h->num_sms, s)
                         : launch_typed<1, NVC_PREC_FP16>(a, smem, h->num_sms, s);

@@ -186,6 +186,10 @@ struct nvc_handle {
 
   // fused shading kernel variant (nvc::ShadeVariant)
   int shade_variant = 0;
+  // E4M3 per-tensor scales: [0, 9) activations (set by nvc_calibrate),
+  // [9, 18) weights (set by the weight packing)
+  float* fp8_scales = nullptr;
+  bool fp8_calibrated = false;
 
   // frame graph
   cudaStream_t capture_stream = nullptr;

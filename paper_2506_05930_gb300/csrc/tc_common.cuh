@@ -3,6 +3,8 @@
 // encode shared by the tensor-core kernels.
 #pragma once
 
+#include <cuda_fp8.h>
+
 #include "nvc_internal.cuh"
 #include "hashgrid.cuh"
 
@@ -88,6 +90,22 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       : "memory");
 }
 
+// E4M3 x E4M3 -> fp32 (kind::f8f6f4): K = 32 per instruction.
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Two floats -> two saturating round-to-nearest E4M3 bytes (low = a).
+__device__ __forceinline__ uint32_t pack_e4m3x2(float a, float b) {
+  return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -120,8 +138,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 // Byte offset of element (row, k) of a K-major operand with K columns in the
 // no-swizzle core-matrix layout.
 __host__ __device__ __forceinline__ uint32_t cm_offset(int row, int k, int K, int esize) {
-  return (uint32_t)((row >> 3) * (K * 8 * esize) + (k >> 3) * 128 + (row & 7) * 16 +
-                    (k & 7) * esize);
+  // a core-matrix row is 16 bytes: 16 / esize elements of K
+  const int cpr = 16 / esize;
+  return (uint32_t)((row >> 3) * (K * 8 * esize) + (k / cpr) * 128 + (row & 7) * 16 +
+                    (k % cpr) * esize);
 }
 
 template <int PREC>

@@ -227,6 +227,11 @@ def nvc_autotune_shade(h, scene: Scene, pos, nrm, idx=None, pdf=None, wsum=None,
     return int(chosen.value), list(ms)
 
 
+def nvc_calibrate(h, pos, stream=None):
+    """Per-tensor E4M3 activation scales from a float32 pass over pos."""
+    check(lib.nvc_calibrate(h, _ptr(pos, name="pos"), pos.shape[0], _stream(stream)), h)
+
+
 def nvc_set_shade_variant(h, variant: int):
     check(lib.nvc_set_shade_variant(h, int(variant)), h)
 

@@ -1,0 +1,87 @@
+"""Precision sweep of the inference path: FP32 (CUDA cores) and FP16, BF16,
+FP8-E4M3 (tensor cores, FP32 accumulation, per-tensor scales for E4M3) on
+the 4K workload: 3840x2160 pixels, 256 lights, a 2^21-entry table.  For each
+precision: visibility error against the float64 oracle on a seeded
+65,536-pixel subset, WRS light-index agreement with the FP32 path on every
+pixel (same random streams), and the Neural-DI relative error."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import nvc_synth as S
+from oracle import nvc as O
+from helpers import scaled_params
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2506_05930_gb300 import nvc
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+# per precision: (max |vis - oracle|, mean |vis - oracle|, min index agreement, mean DI rel. error)
+BOUNDS = {"fp32": (1e-5, 1e-6, 1.0, 1e-5), "fp16": (2e-3, 2e-4, 0.99, 1e-3),
+          "bf16": (2e-2, 2e-3, 0.95, 5e-3), "fp8": (0.2, 2e-2, 0.7, 5e-2)}
+
+
+def test_fp8_small_network_close_to_oracle():
+    cfg = S.config_by_name("tiny_fp32").with_(precision="fp8", batch_positions=2048)
+    cache = nvc.VisibilityCache(cfg)
+    p = scaled_params(cfg, seed=3, table_scale=0.5)
+    cache.set_params(p)
+    gb = S.gbuffer_points(4, 64, 64)
+    pos = torch.from_numpy(gb.pos).cuda()
+    with pytest.raises(nvc.NVCError):
+        cache.infer(pos)                      # scales not calibrated yet
+    nvc.nvc_calibrate(cache.handle, pos[:2048])
+    err = np.abs(host(cache.infer(pos)) - O.infer(cfg, p, gb.pos))
+    assert err.mean() < 2e-2 and err.max() < 0.2, (err.mean(), err.max())
+
+
+def test_precision_sweep_4k_256_lights():
+    base = S.config_by_name("precision_4k").with_(train_precision="fp32")
+    sc = S.scene_heightfield(seed=5, n_lights=256, n_spheres=128, n_boxes=128)
+    gb = S.gbuffer_heightfield(seed=5, width=3840, height=2160)
+    scene = nvc.Scene.from_synth(sc)
+    pos = torch.from_numpy(gb.pos).cuda()
+    nrm = torch.from_numpy(gb.nrm).cuda()
+    p = scaled_params(base, seed=6, table_scale=0.5)
+    pick = np.sort(np.random.default_rng(7).choice(gb.n, 65536, replace=False))
+    v64 = O.infer(base, p, gb.pos[pick])
+    di64 = O.neural_di(v64, O.contributions(gb.pos[pick], gb.nrm[pick], sc.lights))
+    lit = di64 > 1e-3 * di64.max()
+    pt = torch.from_numpy(pick).cuda()
+    results, ref_idx = {}, None
+    for prec in ("fp32", "fp16", "bf16", "fp8"):
+        cfg = base.with_(precision=prec)
+        cache = nvc.VisibilityCache(cfg)
+        cache.set_params(p)
+        if prec == "fp8":
+            nvc.nvc_calibrate(cache.handle, pos[torch.randperm(gb.n, device="cuda")[:8192]])
+        out = cache.shade(scene, pos, nrm, seed=3, frame=0, fused=prec != "fp32")
+        vis = host(cache.infer(pos[pt].contiguous()))
+        idx = host(out["idx"])
+        if ref_idx is None:
+            ref_idx = idx
+        err = np.abs(vis - v64)
+        di = host(out["radiance"])[pick]
+        results[prec] = {
+            "vis_max_abs_err": float(err.max()), "vis_mae": float(err.mean()),
+            "wrs_index_agreement_vs_fp32": float(np.mean(idx == ref_idx)),
+            "neural_di_rel_err": float(np.mean(np.abs(di[lit] - di64[lit]) / di64[lit]))}
+        cache.close()
+        del out
+        torch.cuda.empty_cache()
+    print("precision sweep:", json.dumps(results))
+    for prec, r in results.items():
+        mx, mae, agree, dierr = BOUNDS[prec]
+        assert r["vis_max_abs_err"] <= mx, (prec, r)
+        assert r["vis_mae"] <= mae, (prec, r)
+        assert r["wrs_index_agreement_vs_fp32"] >= agree, (prec, r)
+        assert r["neural_di_rel_err"] <= dierr, (prec, r)

@@ -501,3 +501,22 @@ def test_oracle_training_converges_to_brute_force_visibility_and_gains():
     _, var_cache = O.estimator_moments(Vt, c, O.selection_law(O.light_weights_f32(vis, c)))
     _, var_none = O.estimator_moments(Vt, c, O.selection_law(O.light_weights_f32(np.ones_like(vis), c)))
     assert var_cache.mean() < 0.8 * var_none.mean()
+
+
+# -------------------------------------------------------------------- fp8 --
+
+def test_e4m3_rounding_matches_torch_float8():
+    """The oracle's E4M3 rounding against torch's float8_e4m3fn conversion
+    (a library implementation of the same OCP format)."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8")
+    from oracle import fp8
+    rng = np.random.default_rng(12)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.uniform(-4, 3, 20000),
+                        [0.0, 448.0, -448.0, 2.0 ** -9, 2.0 ** -10, 1.0625, 1.1875, 240.0, 232.0]])
+    x = x[np.abs(x) <= 448.0].astype(np.float32)
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(fp8.round_e4m3(x), want)
+    # saturation above the largest finite value
+    assert fp8.round_e4m3(np.array([1e4, -600.0])).tolist() == [448.0, -448.0]
