@@ -362,7 +362,9 @@ def visibility(pos, lights, spheres, boxes, dtype=np.float64) -> np.ndarray:
     [1e-4, 1 - 1e-4], meets no occluder: a sphere blocks it when the
     segment's closest point lies strictly inside (|c - q|^2 < r^2); a box
     blocks it when the segment overlaps the closed box (slab test).  The
-    arithmetic runs in ``dtype`` with float32 giving the kernel's decision.
+    arithmetic runs in ``dtype`` with float32 giving the kernel's decision;
+    the reciprocals 1/|d|^2 and 1/d_a are formed once per (position, light)
+    and multiply the per-occluder numerators.
     """
     t = np.dtype(dtype).type
     X = np.asarray(pos, t)[:, None, :]
@@ -371,11 +373,13 @@ def visibility(pos, lights, spheres, boxes, dtype=np.float64) -> np.ndarray:
     dd = _dot3(D, D)
     occ = np.zeros(dd.shape, bool)
     t0, t1 = t(SEG_T0), t(SEG_T1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv_dd = np.where(dd > 0, t(1) / np.where(dd > 0, dd, t(1)), t(0))
+        inv_d = np.where(D != 0, t(1) / np.where(D != 0, D, t(1)), t(0))
     for s in np.asarray(spheres, t).reshape(-1, 4):
         C, r = s[:3], s[3]
         O = C - X
-        with np.errstate(divide="ignore", invalid="ignore"):
-            tc = np.where(dd > 0, _dot3(O, D) / np.where(dd > 0, dd, t(1)), t0)
+        tc = _dot3(O, D) * inv_dd         # dd = 0: the segment is a point, t -> t0
         tc = np.minimum(np.maximum(tc, t0), t1)
         Q = X + tc[..., None] * D
         E = C - Q
@@ -390,9 +394,8 @@ def visibility(pos, lights, spheres, boxes, dtype=np.float64) -> np.ndarray:
             da = D[..., a]
             par = da == 0
             miss |= par & ((xa < lo[a]) | (xa > hi[a]))
-            with np.errstate(divide="ignore", invalid="ignore"):
-                ta = (lo[a] - xa) / np.where(par, t(1), da)
-                tb = (hi[a] - xa) / np.where(par, t(1), da)
+            ta = (lo[a] - xa) * inv_d[..., a]
+            tb = (hi[a] - xa) * inv_d[..., a]
             tn = np.where(par, t0, np.minimum(ta, tb))
             tf = np.where(par, t1, np.maximum(ta, tb))
             tmin = np.maximum(tmin, tn)

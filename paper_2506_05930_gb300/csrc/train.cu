@@ -37,12 +37,15 @@ __global__ void training_positions_kernel(float3 lo, float3 ext, const float* __
 // ---- shadow rays ------------------------------------------------------------
 // One thread per (position, light); occluders staged in shared memory.  The
 // arithmetic is correctly rounded float32 in a fixed order, so the binary
-// decision is reproducible operation by operation.
+// decision is reproducible operation by operation.  The divisions are
+// taken once per (position, light): 1/|d|^2 for the spheres' closest-point
+// parameter and 1/d per axis for the boxes' slabs; each occluder then
+// costs multiplications only.
 __device__ __forceinline__ bool sphere_blocks(float px, float py, float pz, float dx, float dy,
-                                              float dz, float dd, float4 s) {
+                                              float dz, float inv_dd, float4 s) {
   const float t0 = bits_f(kSegT0Bits), t1 = bits_f(kSegT1Bits);
   const float ox = __fsub_rn(s.x, px), oy = __fsub_rn(s.y, py), oz = __fsub_rn(s.z, pz);
-  float tc = dd > 0.0f ? __fdiv_rn(dot3_rn(ox, oy, oz, dx, dy, dz), dd) : t0;
+  float tc = __fmul_rn(dot3_rn(ox, oy, oz, dx, dy, dz), inv_dd);
   tc = fminf(fmaxf(tc, t0), t1);
   const float ex = __fsub_rn(s.x, __fadd_rn(px, __fmul_rn(tc, dx)));
   const float ey = __fsub_rn(s.y, __fadd_rn(py, __fmul_rn(tc, dy)));
@@ -50,25 +53,26 @@ __device__ __forceinline__ bool sphere_blocks(float px, float py, float pz, floa
   return dot3_rn(ex, ey, ez, ex, ey, ez) < __fmul_rn(s.w, s.w);
 }
 
-__device__ __forceinline__ void slab(float xa, float da, float lo, float hi, float& tmin,
-                                     float& tmax, bool& miss) {
+__device__ __forceinline__ void slab(float xa, float da, float inv_da, float lo, float hi,
+                                     float& tmin, float& tmax, bool& miss) {
   if (da == 0.0f) {
     miss = miss || xa < lo || xa > hi;
     return;
   }
-  const float ta = __fdiv_rn(__fsub_rn(lo, xa), da);
-  const float tb = __fdiv_rn(__fsub_rn(hi, xa), da);
+  const float ta = __fmul_rn(__fsub_rn(lo, xa), inv_da);
+  const float tb = __fmul_rn(__fsub_rn(hi, xa), inv_da);
   tmin = fmaxf(tmin, fminf(ta, tb));
   tmax = fminf(tmax, fmaxf(ta, tb));
 }
 
 __device__ __forceinline__ bool box_blocks(float px, float py, float pz, float dx, float dy,
-                                           float dz, const float* b) {
+                                           float dz, float ix, float iy, float iz,
+                                           const float* b) {
   float tmin = bits_f(kSegT0Bits), tmax = bits_f(kSegT1Bits);
   bool miss = false;
-  slab(px, dx, b[0], b[3], tmin, tmax, miss);
-  slab(py, dy, b[1], b[4], tmin, tmax, miss);
-  slab(pz, dz, b[2], b[5], tmin, tmax, miss);
+  slab(px, dx, ix, b[0], b[3], tmin, tmax, miss);
+  slab(py, dy, iy, b[1], b[4], tmin, tmax, miss);
+  slab(pz, dz, iz, b[2], b[5], tmin, tmax, miss);
   return !miss && tmin <= tmax;
 }
 
@@ -91,9 +95,16 @@ __global__ void __launch_bounds__(256) trace_visibility_kernel(
   const float4 lt = reinterpret_cast<const float4*>(lights)[i];
   const float dx = __fsub_rn(lt.x, px), dy = __fsub_rn(lt.y, py), dz = __fsub_rn(lt.z, pz);
   const float dd = dot3_rn(dx, dy, dz, dx, dy, dz);
+  // a zero-length segment (light on the point): t stays at t0
+  const float inv_dd = dd > 0.0f ? __fdiv_rn(1.0f, dd) : 0.0f;
+  const float ix = dx != 0.0f ? __fdiv_rn(1.0f, dx) : 0.0f;
+  const float iy = dy != 0.0f ? __fdiv_rn(1.0f, dy) : 0.0f;
+  const float iz = dz != 0.0f ? __fdiv_rn(1.0f, dz) : 0.0f;
   bool occ = false;
-  for (int k = 0; k < n_sph && !occ; ++k) occ = sphere_blocks(px, py, pz, dx, dy, dz, dd, s_sph[k]);
-  for (int k = 0; k < n_box && !occ; ++k) occ = box_blocks(px, py, pz, dx, dy, dz, s_box + 6 * k);
+  for (int k = 0; k < n_sph && !occ; ++k)
+    occ = sphere_blocks(px, py, pz, dx, dy, dz, inv_dd, s_sph[k]);
+  for (int k = 0; k < n_box && !occ; ++k)
+    occ = box_blocks(px, py, pz, dx, dy, dz, ix, iy, iz, s_box + 6 * k);
   vis[t] = occ ? 0.0f : 1.0f;
 }
 
