@@ -153,6 +153,20 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(const float* __restrict_
 constexpr int kLossBlocks = 256;
 
 // ---- Adam -------------------------------------------------------------------
+// b^t by repeated squaring: at most 2 log2(t) double multiplications, each
+// correctly rounded, so a relative error of a few ulps of a double -- far
+// below the float32 the results are stored in.  (A library pow in double is
+// several microseconds of dependent FP64 work on this part.)
+__device__ __forceinline__ double pow_int(double b, int t) {
+  double r = 1.0;
+  while (t > 0) {
+    if (t & 1) r *= b;
+    b *= b;
+    t >>= 1;
+  }
+  return r;
+}
+
 // Prologue (one warp): loss = sum of partials / count; decide whether this
 // step applies (all gradients finite); step counter, bias corrections and
 // the scheduled learning rate.
@@ -182,8 +196,8 @@ __global__ void adam_prologue_kernel(const double* __restrict__ partials, int n_
     const int k = t - 1 < ramp ? t - 1 : ramp;
     lr = (double)lr0 + ((double)lr_end - (double)lr0) * (double)k / (double)ramp;
   }
-  sc->lr_over_bc1 = (float)(lr / (1.0 - pow(beta1, (double)t)));
-  sc->inv_bc2 = (float)(1.0 / (1.0 - pow(beta2, (double)t)));
+  sc->lr_over_bc1 = (float)(lr / (1.0 - pow_int(beta1, t)));
+  sc->inv_bc2 = (float)(1.0 / (1.0 - pow_int(beta2, t)));
   sc->inv_scale = inv_scale;
   sc->skip = 0;
 }

@@ -3,7 +3,8 @@
 // TMEM, static loss scaling).
 //
 // One CTA takes 128 training positions at a time (persistent over tiles);
-// thread t owns sample row t = TMEM lane t.
+// its four warpgroups share each sample row (= TMEM lane) by levels and by
+// 16-column chunks.
 //   forward:  encode -> act_0; z_k = act_k W_k^T (tcgen05, M=128) ->
 //             act_{k+1} = leaky_relu(z_k) kept in shared memory (fp16);
 //   loss:     logits from TMEM, targets from memory; delta_out =
@@ -83,13 +84,13 @@ __device__ __forceinline__ void unpack2(uint32_t u, float& a, float& b) {
   }
 }
 
-// Store 32 fp32 values (columns c0..c0+31 of this thread's row) as fp16 into
-// a K-major tile with row length K, zero where the column is >= valid.
+// Store 16 fp32 values (columns c0..c0+15 of row `row`) as 16-bit values
+// into a K-major tile with row length K, zero where the column is >= valid.
 template <int PREC>
-__device__ __forceinline__ void store_row32(uint8_t* tile, int row, int c0, int K, int valid,
-                                            const float (&v)[32]) {
+__device__ __forceinline__ void store_row16(uint8_t* tile, int row, int c0, int K, int valid,
+                                            const float (&v)[16]) {
 #pragma unroll
-  for (int g = 0; g < 4; ++g) {
+  for (int g = 0; g < 2; ++g) {
     const int c = c0 + g * 8;
     if (c < K) {
       float h[8];
@@ -105,19 +106,30 @@ __device__ __forceinline__ void store_row32(uint8_t* tile, int row, int c0, int 
   }
 }
 
-template <int F, int PREC>
-__global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_constant__ TrainTcArgs a) {
+// kGroups warpgroups per CTA.  Thread t serves sample row t % 128 (its TMEM
+// lane: warp w reads lanes 32 (w % 4) .. +31) and warpgroup t / 128 takes
+// every kGroups-th share of the row's work -- the encode's 8-feature chunks,
+// the hash-table scatter's levels and the epilogues' 16-column TMEM chunks --
+// so a sample's gathers, atomics and conversions run kGroups ways in
+// parallel instead of one after another in a single thread.
+constexpr int kGroups = 4;
+
+template <int F, int PREC, int NG>
+__global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_constant__ TrainTcArgs a) {
+  constexpr int kThreads = kTileM * NG;
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ double s_red[4];
+  __shared__ double s_red[kThreads / 32];
   uint8_t* s_w = smem;
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.bar_off);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 1);
   const int t = threadIdx.x;
   const int warp = t >> 5;
+  const int rw = t & (kTileM - 1);   // sample row within the tile = TMEM lane
+  const int wg = t / kTileM;         // this thread's share of the row's work
 
-  for (int e = t; e < a.wimg_bytes / 16; e += kTileM)
+  for (int e = t; e < a.wimg_bytes / 16; e += kThreads)
     reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
-  for (int e = t; e < kGuardBytes / 16; e += kTileM)
+  for (int e = t; e < kGuardBytes / 16; e += kThreads)
     reinterpret_cast<uint4*>(smem + a.guard_off)[e] = make_uint4(0, 0, 0, 0);
   const uint32_t bar = smem_u32(s_bar);
   if (t == 0) {
@@ -130,20 +142,19 @@ __global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_consta
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
-  const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t t_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t s_base = smem_u32(smem);
   uint32_t phase = 0;
   bool failed = false;
   bool bad = false;
   double loss_acc = 0.0;
   int tiles_done = 0;
-
   const int last = a.n_layers - 1;
   const int din = a.ep.n_levels * F;
   const int64_t n_tiles = (a.n + kTileM - 1) / kTileM;
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
-    const int64_t row = tile * kTileM + t;
+    const int64_t row = tile * kTileM + rw;
     const bool live = row < a.n;
     float x = 0.f, y = 0.f, z = 0.f;
     if (live) {
@@ -151,27 +162,24 @@ __global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_consta
       y = normalise(__ldg(a.pos + 3 * row + 1), a.ep.lo[1], a.ep.ext[1]);
       z = normalise(__ldg(a.pos + 3 * row + 2), a.ep.lo[2], a.ep.ext[2]);
     }
-    // ---- encode into act_0 ------------------------------------------------
+    // ---- encode into act_0 (this warpgroup's 8-feature chunks) ------------
     {
       uint8_t* act0 = smem + a.act_off[0];
       const int K0 = a.K[0];
       constexpr int LPC = F >= 8 ? 1 : 8 / F;
-      for (int c = 0; c < K0 / 8; ++c) {
+      for (int c = wg; c < K0 / 8; c += NG) {
         float f8[8];
 #pragma unroll
         for (int s = 0; s < 8; ++s) f8[s] = 0.0f;
         if (live) {
 #pragma unroll
           for (int q = 0; q < LPC; ++q) {
-            const int l = (c * 8) / F + q;
-            if (l * F < din && (l * F) / 8 == c) {
+            const int l = c * LPC + q;   // F divides 8: chunk c holds levels c LPC ..
+            if (l * F < din) {
               float acc[F];
               encode_level<F>(a.ep, a.table, l, x, y, z, acc);
 #pragma unroll
-              for (int f = 0; f < F; ++f) {
-                const int k = l * F + f - c * 8;
-                if (k >= 0 && k < 8) f8[k] = acc[f];
-              }
+              for (int f = 0; f < F; ++f) f8[q * F + f] = acc[f];
             }
           }
         }
@@ -180,7 +188,7 @@ __global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_consta
         pk.y = pack2<PREC>(f8[2], f8[3]);
         pk.z = pack2<PREC>(f8[4], f8[5]);
         pk.w = pack2<PREC>(f8[6], f8[7]);
-        *reinterpret_cast<uint4*>(act0 + cm_offset(t, c * 8, K0, 2)) = pk;
+        *reinterpret_cast<uint4*>(act0 + cm_offset(rw, c * 8, K0, 2)) = pk;
       }
     }
     fence_async_smem();
@@ -204,27 +212,27 @@ __global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_consta
       tc_fence_after();
       if (k < last) {
         uint8_t* nxt = smem + a.act_off[k + 1];
-        for (int c0 = 0; c0 < N; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(t_lane + (uint32_t)c0, r);
-          float v[32];
+        for (int c0 = wg * 16; c0 < N; c0 += 16 * NG) {
+          uint32_t r[16];
+          tmem_ld16(t_lane + (uint32_t)c0, r);
+          float v[16];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < 16; ++j) {
             const float zz = __uint_as_float(r[j]);
             v[j] = live ? fmaxf(zz, a.slope * zz) : 0.0f;
           }
-          store_row32<PREC>(nxt, t, c0, N, a.N_real[k], v);
+          store_row16<PREC>(nxt, rw, c0, N, a.N_real[k], v);
         }
       } else {
         // loss and the scaled gradient at the logits
         uint8_t* dt = smem + a.d_off[cur];
         const float* yrow = a.target + (live ? row : 0) * a.L;
-        for (int c0 = 0; c0 < N; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(t_lane + (uint32_t)c0, r);
-          float v[32];
+        for (int c0 = wg * 16; c0 < N; c0 += 16 * NG) {
+          uint32_t r[16];
+          tmem_ld16(t_lane + (uint32_t)c0, r);
+          float v[16];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < 16; ++j) {
             const int i = c0 + j;
             float g = 0.0f;
             if (live && i < a.L) {
@@ -244,7 +252,7 @@ __global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_consta
             }
             v[j] = g;
           }
-          store_row32<PREC>(dt, t, c0, N, a.L, v);
+          store_row16<PREC>(dt, rw, c0, N, a.L, v);
         }
       }
       fence_async_smem();
@@ -279,15 +287,15 @@ __global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_consta
         // delta_{k-1} = g * act'(z_{k-1}); act_k holds leaky_relu(z_{k-1})
         uint8_t* dn = smem + a.d_off[cur ^ 1];
         const uint8_t* act = smem + a.act_off[k];
-        for (int c0 = 0; c0 < K; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(t_lane + (uint32_t)c0, r);
-          float v[32];
+        for (int c0 = wg * 16; c0 < K; c0 += 16 * NG) {
+          uint32_t r[16];
+          tmem_ld16(t_lane + (uint32_t)c0, r);
+          float v[16];
 #pragma unroll
-          for (int g8 = 0; g8 < 4; ++g8) {
+          for (int g8 = 0; g8 < 2; ++g8) {
             const int c = c0 + g8 * 8;
             uint4 av = make_uint4(0, 0, 0, 0);
-            if (c < K) av = *reinterpret_cast<const uint4*>(act + cm_offset(t, c, K, 2));
+            if (c < K) av = *reinterpret_cast<const uint4*>(act + cm_offset(rw, c, K, 2));
             float h[8];
             unpack2<PREC>(av.x, h[0], h[1]);
             unpack2<PREC>(av.y, h[2], h[3]);
@@ -299,21 +307,25 @@ __global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_consta
               v[g8 * 8 + s] = live ? (h[s] > 0.0f ? g : a.slope * g) : 0.0f;
             }
           }
-          store_row32<PREC>(dn, t, c0, K, a.K_real[k], v);
+          store_row16<PREC>(dn, rw, c0, K, a.K_real[k], v);
         }
       } else {
-        // feature gradient -> hash-table gradient (adjoint of the encoding)
-        float dfeat[NVC_MAX_FEATURES * 4];
-        for (int c0 = 0; c0 < K; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(t_lane + (uint32_t)c0, r);
+        // feature gradient -> hash-table gradient (adjoint of the encoding);
+        // level l is scattered by warpgroup l % NG.  F divides 16, so no
+        // level straddles two 16-column chunks.
+        float dfeat[NVC_MAX_FEATURES];
+        for (int c0 = 0; c0 < K; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(t_lane + (uint32_t)c0, r);
           if (live) {
-            for (int l = c0 / F; l < din / F && l * F < c0 + 32; ++l) {
+#pragma unroll
+            for (int q = 0; q < 16 / F; ++q) {
+              const int l = c0 / F + q;
+              if (l >= din / F || l % NG != wg) continue;
               bool any = false;
 #pragma unroll
               for (int f = 0; f < F; ++f) {
-                const int col = l * F + f - c0;
-                dfeat[f] = (col >= 0 && col < 32 ? __uint_as_float(r[col]) : 0.0f) * a.inv_count;
+                dfeat[f] = __uint_as_float(r[q * F + f]) * a.inv_count;
                 any = any || dfeat[f] != 0.0f;
                 bad = bad || !isfinite(dfeat[f]);
               }
@@ -349,14 +361,14 @@ __global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_consta
     tc_fence_after();
     for (int k = 0; k <= last; ++k) {
       const int out = a.N_real[k], in = a.K_real[k];
-      const int j = t;   // TMEM lane = output row j of dW_k
-      for (int c0 = 0; c0 < a.K[k]; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(t_lane + a.dw_col[k] + (uint32_t)c0, r);
+      const int j = rw;   // TMEM lane = output row j of dW_k
+      for (int c0 = wg * 16; c0 < a.K[k]; c0 += 16 * NG) {
+        uint32_t r[16];
+        tmem_ld16(t_lane + a.dw_col[k] + (uint32_t)c0, r);
         if (j < out) {
           float* dst = a.grad + a.w_off[k] + (int64_t)j * in;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
+          for (int q = 0; q < 16; ++q) {
             const int i = c0 + q;
             if (i < in) {
               const float v = __uint_as_float(r[q]) * a.inv_count;
@@ -374,7 +386,9 @@ __global__ void __launch_bounds__(kTileM, 1) train_tc_kernel(const __grid_consta
   if ((t & 31) == 0) s_red[warp] = lsum;
   const bool any_bad = __syncthreads_or(bad) != 0;
   if (t == 0) {
-    a.partials[blockIdx.x] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
+    double p = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) p += s_red[w];
+    a.partials[blockIdx.x] = p;
     if (any_bad) atomicOr(a.status + kStNonFinite, 1);
     if (failed) atomicOr(a.status + kStFlags, kFlagTimeout);
   }
@@ -502,10 +516,10 @@ cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStre
     switch (h->F) {
 #define NVC_TRAIN_CASE(FF)                                                                      \
   case FF:                                                                                      \
-    e = cudaFuncSetAttribute(train_tc_kernel<FF, NVC_PREC_BF16>,                                \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+    e = cudaFuncSetAttribute(train_tc_kernel<FF, NVC_PREC_BF16, kGroups>,                           \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
     if (e != cudaSuccess) return e;                                                             \
-    train_tc_kernel<FF, NVC_PREC_BF16><<<grid, kTileM, smem, s>>>(a);                           \
+    train_tc_kernel<FF, NVC_PREC_BF16, kGroups><<<grid, kTileM * kGroups, smem, s>>>(a);            \
     return cudaGetLastError();
       NVC_TRAIN_CASE(1) NVC_TRAIN_CASE(2) NVC_TRAIN_CASE(4) NVC_TRAIN_CASE(8)
 #undef NVC_TRAIN_CASE
@@ -514,10 +528,10 @@ cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStre
     switch (h->F) {
 #define NVC_TRAIN_CASE(FF)                                                                      \
   case FF:                                                                                      \
-    e = cudaFuncSetAttribute(train_tc_kernel<FF, NVC_PREC_FP16>,                                \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+    e = cudaFuncSetAttribute(train_tc_kernel<FF, NVC_PREC_FP16, kGroups>,                           \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
     if (e != cudaSuccess) return e;                                                             \
-    train_tc_kernel<FF, NVC_PREC_FP16><<<grid, kTileM, smem, s>>>(a);                           \
+    train_tc_kernel<FF, NVC_PREC_FP16, kGroups><<<grid, kTileM * kGroups, smem, s>>>(a);            \
     return cudaGetLastError();
       NVC_TRAIN_CASE(1) NVC_TRAIN_CASE(2) NVC_TRAIN_CASE(4) NVC_TRAIN_CASE(8)
 #undef NVC_TRAIN_CASE
