@@ -145,6 +145,17 @@ def workload(precision=None):
     return cfg, sc, gb
 
 
+def workload_config(world, pixels_per_gpu, positions_per_frame):
+    """The bench line's `config`, the same for both arms."""
+    return {"workload": "frame_1080p: 1920x1080 heightfield+boxes view, 32 point lights, "
+                        "32 spheres + 32 boxes; hash grid 16 levels x 2 features x 2^19, "
+                        "MLP 32-64-64-64-32; training 8192 positions x 32 lights per frame",
+            "global_batch": world * pixels_per_gpu, "pixels_per_gpu": pixels_per_gpu,
+            "train_positions_per_frame": positions_per_frame, "parallelism": f"replica{world}",
+            "l2": "no flush: per-frame working set (G-buffer 50 MB, table+Adam state 270 MB) "
+                  "exceeds L2"}
+
+
 # Algorithmic work of one pixel, counted from the method's definition (each
 # arithmetic operation once, a fused multiply-add as one):
 #   normalise: 3 x (sub, div, two clamps)                                12
@@ -365,14 +376,8 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_frame,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": cfg.precision, "data": "synthetic",
-        "config": {"workload": "frame_1080p: 1920x1080 heightfield+boxes view, 32 point lights, "
-                               "32 spheres + 32 boxes; hash grid 16 levels x 2 features x 2^19, "
-                               "MLP 32-64-64-64-32; training 8192 positions x 32 lights per frame",
-                   "global_batch": world * P, "pixels_per_gpu": P,
-                   "train_positions_per_frame": cfg.batch_positions, "parallelism": f"replica{world}",
-                   "graph": use_graph,
-                   "l2": "no flush: per-frame working set (G-buffer 50 MB, table+Adam state 270 MB) "
-                         "exceeds L2"},
+        "config": workload_config(world, P, cfg.batch_positions),
+        "cuda_graph": use_graph,
         "roofline": roof,
         "roofline_other": [v for v in (shade_view, adam_view, tensor_view) if v is not roof],
         "stages_ms": {"train_data": stage_ms[0], "train_fwd_bwd": stage_ms[1],
@@ -443,6 +448,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    cfg, _, _ = workload()
     for _ in range(args.warmup):
         oracle_frame_sample(n_pixels=4096, n_positions=256)
     frames, walls = [], []
@@ -458,7 +464,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame_s * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": "frame_1080p (CPU float64 oracle, extrapolated from a sample)"},
+        "config": workload_config(world, P, cfg.batch_positions),
         "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
                          "sample": "per step 4,096 pixels shaded, training forward/backward on "
                                    "256 positions, one dense Adam update; extrapolated to the "
