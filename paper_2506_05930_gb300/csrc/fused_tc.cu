@@ -104,24 +104,25 @@ __device__ __forceinline__ float contribution_fast(float px, float py, float pz,
   return fmaxf(l.w * ndl * r * inv, 0.0f);   // n.d <= 0 gives c <= 0 -> 0
 }
 
-// q = max(1, floor(w * 2^(23 - e))) for w > 0 (e = ilogb(wmax)), from the
-// float bits: w = m * 2^(ew - 150) with m the 24-bit significand, so the
-// product is m >> (E - ew) with E, ew the biased exponents.  Valid for a
-// normal wmax (E >= 1) and any 0 <= w <= wmax.
-__device__ __forceinline__ uint32_t quantize_bits(float w, uint32_t E) {
-  if (!(w > 0.0f)) return 0u;
-  const uint32_t b = __float_as_uint(w);
-  const uint32_t ew = b >> 23;
-  const uint32_t m = (b & 0x7FFFFFu) | (ew ? 0x800000u : 0u);
-  const uint32_t sh = E - (ew ? ew : 1u);
-  const uint32_t q = sh < 24u ? (m >> sh) : 0u;
-  return q ? q : 1u;
+// Per-pixel scales for q = max(1, floor(w 2^(23 - e))), e = ilogb(wmax), by
+// exact multiplications only: when wmax < 2^-104 the weights are first
+// multiplied by 2^64 (a power of two, so exact, and every w <= wmax stays
+// far from overflow); then e' = ilogb(wmax 2^64) = e + 64 and
+// w 2^64 2^(23 - e') = w 2^(23 - e), with 2^(23 - e') a normal float.
+struct QuantScale {
+  float pre, scale;
+};
+__device__ __forceinline__ QuantScale quant_scale(float wmax) {
+  const bool tiny = (__float_as_uint(wmax) >> 23) < 23u;
+  const float pre = tiny ? 0x1p64f : 1.0f;
+  const uint32_t E = max(__float_as_uint(__fmul_rn(wmax, pre)) >> 23, 23u);
+  return {pre, __uint_as_float((277u - E) << 23)};   // 2^(150 - E) = 2^(23 - e')
 }
 
-// Same q as quantize_bits, by one exact multiply: w * 2^(23 - e) is exact
-// whenever the product is a normal float, and truncating a subnormal or
-// zero product gives 0, which the max(1, .) rule then lifts to 1.
-// `scale` = 2^(23 - e), representable for E = biased exponent of wmax >= 23.
+// q = max(1, floor(w * scale)) for w > 0, else 0, with scale = 2^(23 - e)
+// from quant_scale (w already multiplied by its `pre`): the product is exact
+// whenever it is a normal float, and truncating a subnormal or zero product
+// gives 0, which the max(1, .) rule then lifts to 1.
 __device__ __forceinline__ uint32_t quantize_scaled(float w, float scale) {
   const uint32_t q = __float2uint_rz(w * scale);
   return (w > 0.0f && q == 0u) ? 1u : q;
@@ -270,15 +271,12 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
         if (live) {
 #pragma unroll
           for (int q = 0; q < LPC; ++q) {
-            const int l = (c * CH) / F + q;
-            if (l * F < din && (l * F) / CH == c) {
+            const int l = c * LPC + q;   // F divides CH: chunk c holds levels c LPC ..
+            if (l * F < din) {
               float acc[F];
               encode_level<F>(a.ep, a.table, l, x, y, z, acc);
 #pragma unroll
-              for (int f = 0; f < F; ++f) {
-                const int k = l * F + f - c * CH;
-                if (k >= 0 && k < CH) fv[k] = acc[f];
-              }
+              for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
             }
           }
         }
@@ -384,12 +382,16 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
               const float v = sigmoid_fast(__uint_as_float(r[j]) * outmul);
               const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
               w = fmaxf(v, bits_f(kVisClampBits)) * c;
-              if (V.w_out && live) V.w_out[row * L + i] = w;
               wmax = fmaxf(wmax, w);
               sum += w;
               di = fmaf(v, c, di);
             }
             wreg[j] = w;
+          }
+          if (V.w_out != nullptr && live) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (c0 + j < L) V.w_out[row * L + c0 + j] = wreg[j];
           }
         }
         int sel = -1;
@@ -397,10 +399,14 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
         // tcgen05.ld is warp-collective: the chunk loop runs in every thread,
         // the per-pixel work only where there is something to pick
         const bool active = live && wmax > 0.0f;
-        const uint32_t E = __float_as_uint(wmax) >> 23;
-        const bool fast_q = E >= 23u;
-        const float qscale = __uint_as_float((277u - (fast_q ? E : 23u)) << 23);   // 2^(23 - e)
-        const int e_sub = (active && !fast_q) ? ilogbf(wmax) : 0;
+        const QuantScale qs = quant_scale(wmax);
+        // the pick runs on pre-scaled weights; pdf = (pre w_sel) / (pre sum)
+        // is the same correctly rounded quotient (pre is a power of two)
+        const float sum_q = __fmul_rn(sum, qs.pre);
+        if (LSMALL && active && qs.pre != 1.0f) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) wreg[j] = __fmul_rn(wreg[j], qs.pre);
+        }
         const uint32_t pixel = (uint32_t)(V.pixel_offset + row);
         uint32_t Q = 0;
         uint4 rr = make_uint4(0, 0, 0, 0);
@@ -415,14 +421,15 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
                 float w = wreg[j];
                 if (!LSMALL) {
                   const float v = sigmoid_fast(__uint_as_float(r[j]) * outmul);
-                  w = fmaxf(v, bits_f(kVisClampBits)) *
-                      contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
+                  w = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)) *
+                                    contribution_fast(px, py, pz, nx, ny, nz, s_l[i]),
+                                qs.pre);
                 }
                 if ((i & 3) == 0)
                   rr = philox_keyed(make_uint4(pixel, a.frame, V.view,
                                                ((uint32_t)(i >> 2) << 4) | kTagWrs),
                                     a.rkey);
-                const uint32_t q = fast_q ? quantize_scaled(w, qscale) : quantize_weight(w, e_sub);
+                const uint32_t q = quantize_scaled(w, qs.scale);
                 Q += q;
                 // r*Q < q*2^32  <=>  hi32(r*Q) < q  (Q < 2^32); false for q = 0
                 if (__umulhi(pick_word(rr, i & 3), Q) < q) {
@@ -435,7 +442,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
         }
         if (live) {
           if (V.idx) V.idx[row] = sel;
-          if (V.pdf) V.pdf[row] = sel >= 0 ? wsel / sum : 0.0f;
+          if (V.pdf) V.pdf[row] = sel >= 0 ? wsel / sum_q : 0.0f;
           if (V.wsum) V.wsum[row] = sum;
           if (V.radiance) V.radiance[row] = di;
         }
@@ -559,15 +566,12 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
           if (live) {
 #pragma unroll
             for (int q = 0; q < LPC; ++q) {
-              const int l = (c * 8) / F + q;
-              if (l * F < din && (l * F) / 8 == c) {
+              const int l = c * LPC + q;   // F divides 8: chunk c holds levels c LPC ..
+              if (l * F < din) {
                 float acc[F];
                 encode_level<F>(a.ep, a.table, l, x, y, z, acc);
 #pragma unroll
-                for (int f = 0; f < F; ++f) {
-                  const int k = l * F + f - c * 8;
-                  if (k >= 0 && k < 8) f8[k] = acc[f];
-                }
+                for (int f = 0; f < F; ++f) f8[q * F + f] = acc[f];
               }
             }
           }
@@ -684,20 +688,26 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
               const float c =
                   PRE_C ? cr[j] : contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
               w = fmaxf(v, bits_f(kVisClampBits)) * c;
-              if (V.w_out && live) V.w_out[row * L + j] = w;
               wmax = fmaxf(wmax, w);
               sum += w;
               di = fmaf(v, c, di);
             }
             wreg[j] = w;
           }
+          if (V.w_out != nullptr && live) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < L) V.w_out[row * L + j] = wreg[j];
+          }
           int sel = -1;
           float wsel = 0.0f;
+          const QuantScale qs = quant_scale(wmax);
+          const float sum_q = __fmul_rn(sum, qs.pre);
           if (live && wmax > 0.0f) {
-            const uint32_t E = __float_as_uint(wmax) >> 23;
-            const bool fast_q = E >= 23u;
-            const float qscale = __uint_as_float((277u - (fast_q ? E : 23u)) << 23);
-            const int e_sub = fast_q ? 0 : ilogbf(wmax);
+            if (qs.pre != 1.0f) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) wreg[j] = __fmul_rn(wreg[j], qs.pre);
+            }
             const uint32_t pixel = (uint32_t)(V.pixel_offset + row);
             uint32_t Q = 0;
             uint4 rr = make_uint4(0, 0, 0, 0);
@@ -709,7 +719,7 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
                                                ((uint32_t)(j >> 2) << 4) | kTagWrs),
                                     a.rkey);
                 const float w = wreg[j];
-                const uint32_t q = fast_q ? quantize_scaled(w, qscale) : quantize_weight(w, e_sub);
+                const uint32_t q = quantize_scaled(w, qs.scale);
                 Q += q;
                 if (__umulhi(pick_word(rr, j & 3), Q) < q) {
                   sel = j;
@@ -720,7 +730,7 @@ __global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(con
           }
           if (live) {
             if (V.idx) V.idx[row] = sel;
-            if (V.pdf) V.pdf[row] = sel >= 0 ? wsel / sum : 0.0f;
+            if (V.pdf) V.pdf[row] = sel >= 0 ? wsel / sum_q : 0.0f;
             if (V.wsum) V.wsum[row] = sum;
             if (V.radiance) V.radiance[row] = di;
           }

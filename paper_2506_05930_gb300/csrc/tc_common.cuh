@@ -189,15 +189,17 @@ __device__ __forceinline__ void encode_level(const EncodeParams& ep, const float
   const float fy = __fsub_rn(__fmul_rn(y, nf), (float)cy);
   const float fz = __fsub_rn(__fmul_rn(z, nf), (float)cz);
   const uint32_t mask = (1u << ep.log2_table) - 1u;
-  const uint32_t hx[2] = {(uint32_t)cx, (uint32_t)cx + 1u};
+  // (a ^ b ^ c) & m = (a & m) ^ (b & m) ^ (c & m): masking the six axis
+  // terms leaves one three-input XOR per corner
+  const uint32_t hx[2] = {(uint32_t)cx & mask, ((uint32_t)cx + 1u) & mask};
   const uint32_t hy0 = (uint32_t)cy * kPrime1, hz0 = (uint32_t)cz * kPrime2;
-  const uint32_t hy[2] = {hy0, hy0 + kPrime1};
-  const uint32_t hz[2] = {hz0, hz0 + kPrime2};
+  const uint32_t hy[2] = {hy0 & mask, (hy0 + kPrime1) & mask};
+  const uint32_t hz[2] = {hz0 & mask, (hz0 + kPrime2) & mask};
   const float gx[2] = {1.0f - fx, fx}, gy[2] = {1.0f - fy, fy}, gz[2] = {1.0f - fz, fz};
   const float* tab = table + ((size_t)l << ep.log2_table) * F;
   uint32_t row[8];
 #pragma unroll
-  for (int d = 0; d < 8; ++d) row[d] = (hx[d & 1] ^ hy[(d >> 1) & 1] ^ hz[d >> 2]) & mask;
+  for (int d = 0; d < 8; ++d) row[d] = hx[d & 1] ^ hy[(d >> 1) & 1] ^ hz[d >> 2];
   FeatVec<F> v[8];
 #pragma unroll
   for (int d = 0; d < 8; ++d) v[d] = load_feat<F>(tab + (size_t)row[d] * F);
