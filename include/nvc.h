@@ -246,9 +246,16 @@ nvc_status nvc_calibrate(nvc_handle* h, const float* pos, int64_t n, void* strea
  *   2  as 1, with the producers also computing the light contributions;
  *   3  as 1 with 8 producer warps (two threads per pixel, half the levels
  *      each);
- *   4  as 3 with the contributions computed by the producers.
- * 1-4 need n_outputs <= 32 and FP16/BF16.  All compute the same function. */
-#define NVC_SHADE_VARIANTS 5
+ *   4  as 3 with the contributions computed by the producers;
+ *   5  two threads per pixel (256-thread CTAs): the halves split the
+ *      encode's levels, the hidden layers' columns and the lights, and meet
+ *      in shared memory for the weight maximum, sums and the pick.
+ * 1-4 need n_outputs <= 32; 1-5 need FP16/BF16.  All make the same picks
+ * from the same float32 weights; 0-4 give bit-identical outputs, 5 sums
+ * w and the Neural DI terms over lights [0, H) and [H, L) separately
+ * (H = ceil(ceil(L / 2) / 16) * 16), which can change the last bits of
+ * wsum, pdf and radiance. */
+#define NVC_SHADE_VARIANTS 6
 
 /* Times every applicable variant on these pixels (CUDA events on `stream`,
  * a warm-up then `reps` launches each; synchronises) and keeps the fastest

@@ -624,9 +624,10 @@ nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant) {
   if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
   if (variant < 0 || variant >= kShadeVariants)
     return fail(h, NVC_ERR_INVALID_ARG, "variant out of range");
-  if (variant != kShadeMono && (h->L > 32 || h->cfg.precision == NVC_PREC_FP8))
-    return fail(h, NVC_ERR_UNSUPPORTED,
-                "warp-specialised variants need n_outputs <= 32 and 16-bit operands");
+  if (variant != kShadeMono && h->cfg.precision == NVC_PREC_FP8)
+    return fail(h, NVC_ERR_UNSUPPORTED, "E4M3 operands run the monolithic variant only");
+  if (variant != kShadeMono && variant != kShadePair && h->L > 32)
+    return fail(h, NVC_ERR_UNSUPPORTED, "warp-specialised variants need n_outputs <= 32");
   h->shade_variant = variant;
   return NVC_OK;
 }
@@ -648,7 +649,8 @@ nvc_status nvc_autotune_shade(nvc_handle* h, const nvc_scene* scene, const float
   double best_ms = 0.0;
   for (int v = 0; v < kShadeVariants; ++v) {
     if (ms_out) ms_out[v] = -1.0;
-    if (v != kShadeMono && (h->L > 32 || h->cfg.precision == NVC_PREC_FP8)) continue;
+    if (v != kShadeMono && h->cfg.precision == NVC_PREC_FP8) continue;
+    if (v != kShadeMono && v != kShadePair && h->L > 32) continue;
     h->shade_variant = v;
     cudaError_t e = launch_shade_fused(h, scene, pos, nrm, n, 1, 0, 0, 0, idx, pdf, wsum,
                                        radiance, nullptr, s);

@@ -84,9 +84,14 @@ struct FusedArgs {
   int ws_a0[2], ws_h, ws_c[2], ws_l, ws_bar, ws_cs;
   // monolithic layout: activation tile, light table, mbarrier + TMEM word
   int mono_a, mono_l, mono_bar;
+  int pair_x;   // two-threads-per-pixel kernel: the halves' exchange area
 };
 
 // ---- the sampler's arithmetic ----------------------------------------------
+// The two-threads-per-pixel kernel gives lights [0, H) to one thread and
+// [H, L) to the other, H = ceil(L / 2) rounded up to a multiple of 16.
+__host__ __device__ __forceinline__ int split_h(int L) { return ((((L + 1) >> 1) + 15) >> 4) << 4; }
+
 __device__ __forceinline__ float sigmoid_fast(float z) {
   return __fdividef(1.0f, 1.0f + __expf(-z));
 }
@@ -454,6 +459,304 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
   if (failed && t == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
   __syncthreads();
   if (failed) mbar_wait_bounded(bar, phase ^ 1u);   // let an MMA in flight land
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, a.tmem_cols);
+  }
+}
+
+// ---- two threads per pixel (256 threads, 128-pixel tiles) -------------------
+// Thread t serves pixel row t % 128 (TMEM lane; warps w and w + 4 read the
+// same 32 lanes) and half h = t / 128 of that pixel's work: every other
+// 8-feature chunk of the encode, every other 32-column chunk of each hidden
+// epilogue, and lights [0, H) or [H, L) of the sampler (H = the half of L
+// rounded up to 16).  The halves meet in shared memory three times per
+// tile, each time behind a 64-thread named barrier of the warp pair:
+//   1. max w, sum w and Neural DI of each half -> both halves;
+//   2. Q_A, the first half's integer weight total -> the second half, whose
+//      prefix sums start there (so every Q_i is the one-thread value);
+//   3. the second half's pick, which wins when there is one (it is the
+//      later light) -> the first half, which writes the pixel's outputs.
+// Sum w and Neural DI are the first half's sum plus the second half's, so
+// they can differ from the other variants' one-pass sums in the last bits;
+// the picks are the same integers from the same float32 weights.
+// (constant barrier ids, so the CTA holds five hardware barriers, not 16)
+__device__ __forceinline__ void pair_sync(int warp) {
+  switch (warp & 3) {
+    case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+  }
+}
+
+template <int F, int PREC, bool HSMALL>
+__global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const __grid_constant__ FusedArgs a) {
+  constexpr int kThreads = 2 * kTileM;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* s_w = smem;
+  uint8_t* s_a = smem + a.mono_a;
+  float4* s_l = reinterpret_cast<float4*>(smem + a.mono_l);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.mono_bar);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 1);
+  float4* s_x = reinterpret_cast<float4*>(smem + a.pair_x);          // [2][128] partials
+  uint32_t* s_q = reinterpret_cast<uint32_t*>(s_x + 2 * kTileM);     // [128] Q_A
+  int2* s_s = reinterpret_cast<int2*>(s_q + kTileM);                 // [128] (sel, w_sel bits) of half 1
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  const int rw = t & (kTileM - 1);
+  const int half = t >> 7;
+
+  for (int e = t; e < a.wimg_bytes / 16; e += kThreads)
+    reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
+  if (a.lights) {
+    for (int e = t; e < a.L; e += kThreads) {
+      float4 l = reinterpret_cast<const float4*>(a.lights)[e];
+      l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+      s_l[e] = l;
+    }
+  }
+  const uint32_t bar = smem_u32(s_bar);
+  if (t == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(s_tmem), a.tmem_cols);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t t_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t a_base = smem_u32(s_a);
+  const uint32_t w_base = smem_u32(s_w);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  constexpr int CH = 8;    // 16-bit operands: 8 per 16-byte core-matrix row
+  constexpr int KS = 16;
+  const int din = a.ep.n_levels * F;
+  const int K0 = a.layer[0].K;
+  const int64_t n_tiles = a.n_tiles;
+  const int L = a.L;
+  const int H = split_h(L);   // first half: lights [0, H)
+  const int lo = half ? H : 0;
+  const int hi = half ? L : (H < L ? H : L);
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+    const ViewDesc& V = a.v[view_of(a, tile)];
+    const int64_t row = (tile - V.tile_start) * kTileM + rw;
+    const bool live = row < V.n;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (live) {
+      px = __ldg(V.pos + 3 * row);
+      py = __ldg(V.pos + 3 * row + 1);
+      pz = __ldg(V.pos + 3 * row + 2);
+    }
+    // ---- encode: this half's 8-feature chunks of the layer-0 A tile -------
+    {
+      const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
+      const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
+      const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
+      constexpr int LPC = F >= CH ? 1 : CH / F;
+      for (int c = half; c < K0 / CH; c += 2) {
+        float fv[CH];
+#pragma unroll
+        for (int s = 0; s < CH; ++s) fv[s] = 0.0f;
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < LPC; ++q) {
+            const int l = c * LPC + q;
+            if (l * F < din) {
+              float acc[F];
+              encode_level<F>(a.ep, a.table, l, x, y, z, acc);
+#pragma unroll
+              for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
+            }
+          }
+        }
+        *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, 2)) = pack_chunk<PREC, CH>(fv, 1.0f);
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+
+    // ---- the MLP -------------------------------------------------------------
+    for (int k = 0; k < a.n_layers && !failed; ++k) {
+      const LayerDesc ld = a.layer[k];
+      if (t == 0) {
+        tc_fence_after();
+        const uint32_t sbo = (uint32_t)ld.K * 16u;
+        const uint32_t wb = w_base + (uint32_t)ld.w_byte_off;
+        for (int kk = 0; kk < ld.K / KS; ++kk)
+          mma_f16(tmem, smem_desc(a_base + kk * 256, 128, sbo), smem_desc(wb + kk * 256, 128, sbo),
+                  ld.idesc, kk > 0 ? 1u : 0u);
+        mma_commit(bar);
+      }
+      const bool ok = mbar_wait_bounded(bar, phase);
+      phase ^= 1u;
+      tc_fence_after();
+      if (k + 1 < a.n_layers) {
+        const int Kn = ld.N;
+        for (int c0 = half * 32; c0 < ld.N; c0 += 64) {
+          uint32_t r[32];
+          tmem_ld32(t_lane + (uint32_t)c0, r);
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            uint4 pk;
+            pk.x = leaky2<PREC>(r[g * 8 + 0], r[g * 8 + 1], a.slope);
+            pk.y = leaky2<PREC>(r[g * 8 + 2], r[g * 8 + 3], a.slope);
+            pk.z = leaky2<PREC>(r[g * 8 + 4], r[g * 8 + 5], a.slope);
+            pk.w = leaky2<PREC>(r[g * 8 + 6], r[g * 8 + 7], a.slope);
+            if (c0 + g * 8 < Kn) *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c0 + g * 8, Kn, 2)) = pk;
+          }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        failed = __syncthreads_or(!ok) != 0;
+        continue;
+      }
+
+      // ---- output layer: this half's lights -----------------------------------
+      if (V.vis_out) {
+        for (int c0 = lo; c0 < hi; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(t_lane + (uint32_t)c0, r);
+          if (live) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < hi) V.vis_out[row * L + c0 + j] = sigmoid_fast(__uint_as_float(r[j]));
+          }
+        }
+      } else {
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (live) {
+          nx = __ldg(V.nrm + 3 * row);
+          ny = __ldg(V.nrm + 3 * row + 1);
+          nz = __ldg(V.nrm + 3 * row + 2);
+        }
+        float wreg[16];
+        float wmax = 0.0f, sum = 0.0f, di = 0.0f;
+        for (int c0 = lo; c0 < hi; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(t_lane + (uint32_t)c0, r);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int i = c0 + j;
+            float w = 0.0f;
+            if (i < hi) {
+              const float v = sigmoid_fast(__uint_as_float(r[j]));
+              const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
+              w = fmaxf(v, bits_f(kVisClampBits)) * c;
+              wmax = fmaxf(wmax, w);
+              sum += w;
+              di = fmaf(v, c, di);
+            }
+            wreg[j] = w;
+          }
+          if (V.w_out != nullptr && live) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < hi) V.w_out[row * L + c0 + j] = wreg[j];
+          }
+        }
+        // exchange 1: the other half's max, sum and DI
+        s_x[half * kTileM + rw] = make_float4(wmax, sum, di, 0.0f);
+        pair_sync(warp);
+        const float4 o = s_x[(half ^ 1) * kTileM + rw];
+        wmax = fmaxf(wmax, o.x);
+        const float sumA = half ? o.y : sum, sumB = half ? sum : o.y;
+        const float diA = half ? o.z : di, diB = half ? di : o.z;
+        sum = sumA + sumB;
+        di = diA + diB;
+        const bool active = live && wmax > 0.0f;
+        const QuantScale qs = quant_scale(wmax);
+        const float sum_q = __fmul_rn(sum, qs.pre);
+        if (HSMALL && active && qs.pre != 1.0f) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) wreg[j] = __fmul_rn(wreg[j], qs.pre);
+        }
+        // this half's integer weight total (exchange 2 hands Q_A to half 1)
+        uint32_t Q = 0;
+        if (half == 0) {
+          uint32_t QA = 0;
+          for (int c0 = lo; c0 < hi; c0 += 16) {
+            uint32_t r[16];
+            if (!HSMALL) tmem_ld16(t_lane + (uint32_t)c0, r);
+            if (active) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int i = c0 + j;
+                if (i < hi) {
+                  float w = wreg[j];
+                  if (!HSMALL)
+                    w = __fmul_rn(fmaxf(sigmoid_fast(__uint_as_float(r[j])), bits_f(kVisClampBits)) *
+                                      contribution_fast(px, py, pz, nx, ny, nz, s_l[i]),
+                                  qs.pre);
+                  QA += quantize_scaled(w, qs.scale);
+                }
+              }
+            }
+          }
+          s_q[rw] = QA;
+        }
+        pair_sync(warp);
+        if (half == 1) Q = s_q[rw];
+        // the pick over this half's lights, prefix sums continuing from Q
+        int sel = -1;
+        float wsel = 0.0f;
+        const uint32_t pixel = (uint32_t)(V.pixel_offset + row);
+        uint4 rr = make_uint4(0, 0, 0, 0);
+        for (int c0 = lo; c0 < hi; c0 += 16) {
+          uint32_t r[16];
+          if (!HSMALL) tmem_ld16(t_lane + (uint32_t)c0, r);
+          if (active) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int i = c0 + j;
+              if (i < hi) {
+                float w = wreg[j];
+                if (!HSMALL)
+                  w = __fmul_rn(fmaxf(sigmoid_fast(__uint_as_float(r[j])), bits_f(kVisClampBits)) *
+                                    contribution_fast(px, py, pz, nx, ny, nz, s_l[i]),
+                                qs.pre);
+                if ((i & 3) == 0)
+                  rr = philox_keyed(make_uint4(pixel, a.frame, V.view,
+                                               ((uint32_t)(i >> 2) << 4) | kTagWrs),
+                                    a.rkey);
+                const uint32_t q = quantize_scaled(w, qs.scale);
+                Q += q;
+                if (__umulhi(pick_word(rr, i & 3), Q) < q) {
+                  sel = i;
+                  wsel = w;
+                }
+              }
+            }
+          }
+        }
+        // exchange 3: the second half's pick is the later light
+        if (half == 1) s_s[rw] = make_int2(sel, __float_as_int(wsel));
+        pair_sync(warp);
+        if (half == 0 && live) {
+          const int2 b = s_s[rw];
+          if (b.x >= 0) {
+            sel = b.x;
+            wsel = __int_as_float(b.y);
+          }
+          if (V.idx) V.idx[row] = sel;
+          if (V.pdf) V.pdf[row] = sel >= 0 ? wsel / sum_q : 0.0f;
+          if (V.wsum) V.wsum[row] = sum;
+          if (V.radiance) V.radiance[row] = di;
+        }
+      }
+      tc_fence_before();
+      failed = __syncthreads_or(!ok) != 0;
+    }
+  }
+  if (failed && t == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
+  __syncthreads();
+  if (failed) mbar_wait_bounded(bar, phase ^ 1u);
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, a.tmem_cols);
@@ -879,6 +1182,40 @@ size_t fused_smem(const nvc_handle* h, const PackArgs& p, FusedArgs* a = nullptr
   return off;
 }
 
+// The monolithic plan followed by the exchange area of the two-threads-per-
+// pixel kernel: partials [2][128] float4, Q_A [128] uint32, pick [128] int2.
+size_t pair_smem(const nvc_handle* h, const PackArgs& p, FusedArgs* a = nullptr) {
+  size_t off = fused_smem(h, p, a);
+  off = (off + 15) & ~(size_t)15;
+  if (a) a->pair_x = (int)off;
+  return off + 2 * kTileM * 16 + kTileM * 4 + kTileM * 8;
+}
+
+template <int F, int PREC>
+cudaError_t launch_pair_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cudaStream_t s) {
+  const int H = split_h(a.L);
+  auto kern = H <= 16 ? fused_shade_pair_kernel<F, PREC, true> : fused_shade_pair_kernel<F, PREC, false>;
+  const int max_ctas = (int)(512u / a.tmem_cols);
+  size_t smem = smem_needed;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)kern);
+  if (e != cudaSuccess) return e;
+  const size_t dyn_max = 227 * 1024 - fa.sharedSizeBytes;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+  if (e != cudaSuccess) return e;
+  int occ = blocks_per_sm((const void*)kern, 2 * kTileM, smem);
+  while (occ > max_ctas && smem + 4096 <= dyn_max) {
+    smem += 4096;
+    occ = blocks_per_sm((const void*)kern, 2 * kTileM, smem);
+  }
+  if (occ > max_ctas) return cudaErrorInvalidConfiguration;
+  const int64_t n_tiles = a.n_tiles;
+  const int64_t cap = (int64_t)occ * num_sms;
+  const int grid = (int)(n_tiles < cap ? n_tiles : cap);
+  kern<<<grid, 2 * kTileM, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int F, int PREC>
 cudaError_t launch_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cudaStream_t s) {
   auto kern = a.L <= 32 ? fused_shade_kernel<F, PREC, true> : fused_shade_kernel<F, PREC, false>;
@@ -1074,6 +1411,20 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
   }
   const bool bf16 = h->cfg.precision == NVC_PREC_BF16;
   const int variant = h->shade_variant;
+  if (variant == kShadePair) {
+    const size_t smem_p = pair_smem(h, p, &a);
+    switch (h->F) {
+      case 1: return bf16 ? launch_pair_typed<1, NVC_PREC_BF16>(a, smem_p, h->num_sms, s)
+                          : launch_pair_typed<1, NVC_PREC_FP16>(a, smem_p, h->num_sms, s);
+      case 2: return bf16 ? launch_pair_typed<2, NVC_PREC_BF16>(a, smem_p, h->num_sms, s)
+                          : launch_pair_typed<2, NVC_PREC_FP16>(a, smem_p, h->num_sms, s);
+      case 4: return bf16 ? launch_pair_typed<4, NVC_PREC_BF16>(a, smem_p, h->num_sms, s)
+                          : launch_pair_typed<4, NVC_PREC_FP16>(a, smem_p, h->num_sms, s);
+      case 8: return bf16 ? launch_pair_typed<8, NVC_PREC_BF16>(a, smem_p, h->num_sms, s)
+                          : launch_pair_typed<8, NVC_PREC_FP16>(a, smem_p, h->num_sms, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   if (h->L <= 32 && variant != kShadeMono) {
     const bool pre_c = variant == kShadeWs4C || variant == kShadeWs8C;
     const bool p8 = variant == kShadeWs8 || variant == kShadeWs8C;

@@ -128,7 +128,8 @@ enum ShadeVariant : int {
   kShadeWs4C = 2,   // as kShadeWs4, producers also precompute the contributions
   kShadeWs8 = 3,    // 8 producer warps (two threads per pixel) + 4 consumers
   kShadeWs8C = 4,   // as kShadeWs8 with precomputed contributions
-  kShadeVariants = 5
+  kShadePair = 5,   // two threads per pixel: levels, columns and lights split in halves
+  kShadeVariants = 6
 };
 
 // Adam scalars written on the device each step.

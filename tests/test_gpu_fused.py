@@ -176,10 +176,26 @@ def test_fused_full_1080p_frame_sampled():
     assert (host(out["idx"]) >= 0).mean() > 0.5
 
 
+PAIR_VARIANT = 5   # two threads per pixel: sums taken as two half-sums
+
+
+def _assert_resummed(a, b, L):
+    """a, b: the same sums of L non-negative float32 terms in two orders.
+    Each order is within (L - 1) u of the exact sum (u = 2^-24), so they
+    differ by at most 2 (L - 1) u relative; pdf = w / sum adds one more
+    rounding."""
+    a = a.double().cpu().numpy()
+    b = b.double().cpu().numpy()
+    tol = (2 * (L - 1) + 2) * 2.0 ** -24
+    assert np.all(np.abs(a - b) <= tol * np.abs(b) + 1e-37), np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-37))
+
+
 @pytest.mark.parametrize("cfg_name", ["tiny_fp32", "frame_1080p", "paper"])
 def test_every_shade_variant_gives_identical_outputs(cfg_name):
     """The autotuner's variants differ only in how warps share the work:
-    each one's outputs are bit-identical to the monolithic kernel's."""
+    each one's picks and visibilities are bit-identical to the monolithic
+    kernel's, and so are its sums, except for the two-threads-per-pixel
+    variant, which adds two half-sums."""
     cfg = S.config_by_name(cfg_name).with_(precision="fp16", batch_positions=256)
     if cfg_name == "tiny_fp32":
         sc, gb = S.scene_unit_cube(seed=0), S.gbuffer_points(0, 64, 64)
@@ -197,12 +213,44 @@ def test_every_shade_variant_gives_identical_outputs(cfg_name):
         if ref is None:
             ref = (out, vis)
             continue
-        for k in ("idx", "pdf", "wsum", "radiance"):
-            assert torch.equal(out[k], ref[0][k]), (v, k)
+        assert torch.equal(out["idx"], ref[0]["idx"]), v
         assert torch.equal(vis, ref[1]), v
+        for k in ("pdf", "wsum", "radiance"):
+            if v == PAIR_VARIANT:
+                _assert_resummed(out[k], ref[0][k], cfg.n_outputs)
+            else:
+                assert torch.equal(out[k], ref[0][k]), (v, k)
     chosen, ms = nvc.nvc_autotune_shade(cache.handle, scene, pos, nrm, reps=2)
     assert 0 <= chosen < nvc.SHADE_VARIANTS and ms[chosen] > 0
     assert ms[chosen] == min(m for m in ms if m > 0)
+
+
+@pytest.mark.parametrize("L", [4, 48, 128, 256])
+def test_two_threads_per_pixel_variant_across_light_counts(L):
+    """Variant 5 splits the lights at H = ceil(L/2) rounded up to 16: for
+    L = 4 the second thread has no lights, for 48 the first has two 16-light
+    chunks, 128 and 256 take the recomputing path (256 TMEM columns).  Its
+    picks equal the monolithic kernel's, its sums agree to rounding, and the
+    picks are the oracle's on the kernel's own weights."""
+    cfg = S.config_by_name("frame_1080p").with_(n_outputs=L, precision="fp16", batch_positions=256)
+    sc = S.scene_heightfield(seed=4, n_lights=L, n_spheres=8, n_boxes=8)
+    gb = S.gbuffer_heightfield(seed=4, width=97, height=61)
+    cache, p = make(cfg, seed=2, table_scale=0.5)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    outs = []
+    for v in (0, PAIR_VARIANT):
+        nvc.nvc_set_shade_variant(cache.handle, v)
+        outs.append(cache.shade(scene, pos, nrm, seed=3, frame=1, pixel_offset=5, fused=True))
+    ref, out = outs
+    assert torch.equal(out["idx"], ref["idx"])
+    assert (host(out["idx"]) >= 0).mean() > 0.5
+    for k in ("pdf", "wsum", "radiance"):
+        _assert_resummed(out[k], ref[k], L)
+    w = torch.empty((gb.n, L), device="cuda")
+    nvc.nvc_sampler_weights(cache.handle, scene, pos, nrm, w)
+    idx, _, _ = O.wrs_select(host(w), 5 + np.arange(gb.n), 3, 1, 0)
+    assert np.array_equal(host(out["idx"]), idx)
 
 
 def _views(gbs):
