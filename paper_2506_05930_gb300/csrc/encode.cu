@@ -80,12 +80,31 @@ __global__ void __launch_bounds__(256) encode_bwd_kernel(const float* __restrict
   Corners cr;
   level_corners(ep, l, x, y, z, cr);
   float* tab = grad + ((int64_t)l << ep.log2_table) * F;
+  if constexpr (F == 2) {
+    // The x-corners d, d + 1 of each (y, z) pair: when their rows are the two
+    // rows of one aligned 16-byte pair -- always for an even cell x, as the
+    // x prime is 1 and so hash(x + 1) = hash(x) ^ 1 -- one 16-byte atomic
+    // adds both; otherwise two 8-byte atomics.
+#pragma unroll
+    for (int d = 0; d < 8; d += 2) {
+      const uint32_t r0 = cr.row[d], r1 = cr.row[d + 1];
+      const float2 g0 = make_float2(cr.w[d] * g[0], cr.w[d] * g[1]);
+      const float2 g1 = make_float2(cr.w[d + 1] * g[0], cr.w[d + 1] * g[1]);
+      if ((r0 ^ r1) == 1u) {
+        const float4 v = (r0 & 1u) ? make_float4(g1.x, g1.y, g0.x, g0.y)
+                                   : make_float4(g0.x, g0.y, g1.x, g1.y);
+        atomicAdd(reinterpret_cast<float4*>(tab + (int64_t)(r0 & ~1u) * 2), v);
+      } else {
+        atomicAdd(reinterpret_cast<float2*>(tab + (int64_t)r0 * 2), g0);
+        atomicAdd(reinterpret_cast<float2*>(tab + (int64_t)r1 * 2), g1);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int d = 0; d < 8; ++d) {
     float* dst = tab + (int64_t)cr.row[d] * F;
-    if constexpr (F == 2) {
-      atomicAdd(reinterpret_cast<float2*>(dst), make_float2(cr.w[d] * g[0], cr.w[d] * g[1]));
-    } else if constexpr (F % 4 == 0) {
+    if constexpr (F % 4 == 0) {
 #pragma unroll
       for (int k = 0; k < F; k += 4)
         atomicAdd(reinterpret_cast<float4*>(dst + k),

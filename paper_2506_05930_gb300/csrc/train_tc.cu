@@ -333,13 +333,28 @@ __global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_c
               Corners cr;
               level_corners(a.ep, l, x, y, z, cr);
               float* gt = a.grad + ((int64_t)l << a.ep.log2_table) * F;
+              if constexpr (F == 2) {
+                // x-corners d, d + 1 whose rows form one aligned 16-byte pair
+                // (always for an even cell x: hash(x + 1) = hash(x) ^ 1) go out
+                // as one 16-byte atomic
 #pragma unroll
-              for (int d = 0; d < 8; ++d) {
-                float* dst = gt + (int64_t)cr.row[d] * F;
-                if constexpr (F == 2) {
-                  atomicAdd(reinterpret_cast<float2*>(dst),
-                            make_float2(cr.w[d] * dfeat[0], cr.w[d] * dfeat[1]));
-                } else {
+                for (int d = 0; d < 8; d += 2) {
+                  const uint32_t r0 = cr.row[d], r1 = cr.row[d + 1];
+                  const float2 g0 = make_float2(cr.w[d] * dfeat[0], cr.w[d] * dfeat[1]);
+                  const float2 g1 = make_float2(cr.w[d + 1] * dfeat[0], cr.w[d + 1] * dfeat[1]);
+                  if ((r0 ^ r1) == 1u) {
+                    const float4 v = (r0 & 1u) ? make_float4(g1.x, g1.y, g0.x, g0.y)
+                                               : make_float4(g0.x, g0.y, g1.x, g1.y);
+                    atomicAdd(reinterpret_cast<float4*>(gt + (int64_t)(r0 & ~1u) * 2), v);
+                  } else {
+                    atomicAdd(reinterpret_cast<float2*>(gt + (int64_t)r0 * 2), g0);
+                    atomicAdd(reinterpret_cast<float2*>(gt + (int64_t)r1 * 2), g1);
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                  float* dst = gt + (int64_t)cr.row[d] * F;
 #pragma unroll
                   for (int f = 0; f < F; ++f) atomicAdd(dst + f, cr.w[d] * dfeat[f]);
                 }
@@ -367,14 +382,23 @@ __global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_c
         tmem_ld16(t_lane + a.dw_col[k] + (uint32_t)c0, r);
         if (j < out) {
           float* dst = a.grad + a.w_off[k] + (int64_t)j * in;
+          float v[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
-            const int i = c0 + q;
-            if (i < in) {
-              const float v = __uint_as_float(r[q]) * a.inv_count;
-              bad = bad || !isfinite(v);
-              atomicAdd(dst + i, v);
-            }
+            v[q] = __uint_as_float(r[q]) * a.inv_count;
+            bad = bad || (c0 + q < in && !isfinite(v[q]));
+          }
+          if ((in & 3) == 0 && ((a.w_off[k] & 3) == 0)) {
+            // 16-byte aligned rows: four 16-byte atomics instead of 16 scalar
+#pragma unroll
+            for (int q = 0; q < 16; q += 4)
+              if (c0 + q < in)
+                atomicAdd(reinterpret_cast<float4*>(dst + c0 + q),
+                          make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]));
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (c0 + q < in) atomicAdd(dst + c0 + q, v[q]);
           }
         }
       }
