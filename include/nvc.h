@@ -342,6 +342,28 @@ nvc_status nvc_frame(nvc_handle* h, const nvc_scene* scene, const nvc_view* view
                      int32_t n_views, int32_t train_view, uint64_t seed, uint32_t frame,
                      double* loss_out, int32_t use_graph, void* stream);
 
+/* One frame from and to host memory: as nvc_frame, with every view's pos,
+ * nrm, idx, pdf, wsum and radiance pointing to host memory (page-locked,
+ * e.g. cudaHostAlloc; outputs may be NULL).  No counterpart in the paper:
+ * it is the upload / read-back a renderer wraps around Section 4's passes.
+ *
+ * Asynchronous and pipelined: the library stages the G-buffers in one of two
+ * device slots (alternating per call; grown with cudaMalloc when a frame has
+ * more pixels than any before), uploads on its own copy stream, runs the
+ * frame on `stream` once the upload is done, and reads the outputs back on a
+ * second copy stream once the frame is done.  So frame f's compute overlaps
+ * frame f + 1's upload and frame f - 1's read-back.  The host inputs must
+ * stay unchanged, and the host outputs unread, until the frame's read-back
+ * has completed: nvc_host_frames_wait orders `stream` after every read-back
+ * issued so far.  Errors as nvc_frame. */
+nvc_status nvc_frame_host(nvc_handle* h, const nvc_scene* scene, const nvc_view* host_views,
+                          int32_t n_views, int32_t train_view, uint64_t seed, uint32_t frame,
+                          double* loss_out, int32_t use_graph, void* stream);
+
+/* Makes `stream` wait for every read-back nvc_frame_host has issued
+ * (asynchronous: synchronise `stream` to wait on the host). */
+nvc_status nvc_host_frames_wait(nvc_handle* h, void* stream);
+
 /* ---- inference without allocation ---------------------------------------- */
 
 /* The paper has no counterpart of this entry point.  It exists for callers

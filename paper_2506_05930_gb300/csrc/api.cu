@@ -361,6 +361,17 @@ void nvc_destroy(nvc_handle* h) {
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  for (auto& sl : h->host_slot) {
+    cudaFree(sl.pos);
+    cudaFree(sl.nrm);
+    cudaFree(sl.idx);
+    cudaFree(sl.out);
+    if (sl.up) cudaEventDestroy(sl.up);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.down) cudaEventDestroy(sl.down);
+  }
+  if (h->up_stream) cudaStreamDestroy(h->up_stream);
+  if (h->down_stream) cudaStreamDestroy(h->down_stream);
   for (size_t i = 0; i < g_prof.size(); ++i)
     if (g_prof[i]->h == h) {
       for (cudaEvent_t ev : g_prof[i]->ev.pool) cudaEventDestroy(ev);
@@ -913,6 +924,121 @@ nvc_status nvc_frame(nvc_handle* h, const nvc_scene* scene, const nvc_view* view
   if (h->graph) cudaGraphDestroy(h->graph);
   h->graph = g;
   NVC_CUDA(h, cudaGraphLaunch(h->graph_exec, s));
+  return NVC_OK;
+}
+
+// Copy streams, events and two device slots of at least `total` pixels for
+// nvc_frame_host.  A slot that must grow is first waited for (its frame and
+// read-back), then reallocated.
+static cudaError_t host_staging(nvc_handle* h, int64_t total) {
+  cudaError_t e;
+  if (!h->up_stream) {
+    if ((e = cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaStreamCreateWithFlags(&h->down_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    for (auto& sl : h->host_slot) {
+      if ((e = cudaEventCreateWithFlags(&sl.up, cudaEventDisableTiming)) != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&sl.down, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+  }
+  for (auto& sl : h->host_slot) {
+    if (sl.cap >= total) continue;
+    if ((e = cudaEventSynchronize(sl.done)) != cudaSuccess) return e;
+    if ((e = cudaEventSynchronize(sl.down)) != cudaSuccess) return e;
+    cudaFree(sl.pos);
+    cudaFree(sl.nrm);
+    cudaFree(sl.idx);
+    cudaFree(sl.out);
+    sl.pos = sl.nrm = sl.out = nullptr;
+    sl.idx = nullptr;
+    sl.cap = 0;
+    const int64_t cap = total > 128 ? total : 128;
+    if ((e = cudaMalloc(&sl.pos, sizeof(float) * 3 * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&sl.nrm, sizeof(float) * 3 * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&sl.idx, sizeof(int32_t) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&sl.out, sizeof(float) * 3 * cap)) != cudaSuccess) return e;
+    sl.cap = cap;
+  }
+  return cudaSuccess;
+}
+
+nvc_status nvc_frame_host(nvc_handle* h, const nvc_scene* scene, const nvc_view* host_views,
+                          int32_t n_views, int32_t train_view, uint64_t seed, uint32_t frame,
+                          double* loss_out, int32_t use_graph, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_views < 0 || (n_views > 0 && !host_views)) return fail(h, NVC_ERR_INVALID_ARG, "bad views");
+  int64_t total = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const nvc_view& hv = host_views[v];
+    if (hv.n_pixels < 0 || hv.n_pixels > ((int64_t)1 << 32))
+      return fail(h, NVC_ERR_INVALID_ARG, "view %d: n_pixels out of range", v);
+    if (hv.n_pixels > 0 && (!hv.pos || !hv.nrm))
+      return fail(h, NVC_ERR_INVALID_ARG, "view %d: pos or nrm is NULL", v);
+    total += hv.n_pixels;
+  }
+  NVC_CUDA(h, host_staging(h, total));
+  const int b = h->host_next;
+  nvc_handle::HostSlot& sl = h->host_slot[b];
+  cudaStream_t s = (cudaStream_t)stream;
+  // upload into slot b once the frame that last read it is done
+  NVC_CUDA(h, cudaStreamWaitEvent(h->up_stream, sl.done, 0));
+  std::vector<nvc_view> dv(n_views > 0 ? n_views : 1);
+  int64_t off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const nvc_view& hv = host_views[v];
+    nvc_view& d = dv[v];
+    const int64_t n = hv.n_pixels;
+    d = hv;
+    d.pos = sl.pos + 3 * off;
+    d.nrm = sl.nrm + 3 * off;
+    d.idx = hv.idx ? sl.idx + off : nullptr;
+    d.pdf = hv.pdf ? sl.out + off : nullptr;
+    d.wsum = hv.wsum ? sl.out + sl.cap + off : nullptr;
+    d.radiance = hv.radiance ? sl.out + 2 * sl.cap + off : nullptr;
+    if (n > 0) {
+      NVC_CUDA(h, cudaMemcpyAsync((void*)d.pos, hv.pos, sizeof(float) * 3 * n,
+                                  cudaMemcpyHostToDevice, h->up_stream));
+      NVC_CUDA(h, cudaMemcpyAsync((void*)d.nrm, hv.nrm, sizeof(float) * 3 * n,
+                                  cudaMemcpyHostToDevice, h->up_stream));
+    }
+    off += n;
+  }
+  NVC_CUDA(h, cudaEventRecord(sl.up, h->up_stream));
+  // the frame: after the upload, and after this slot's previous read-back
+  NVC_CUDA(h, cudaStreamWaitEvent(s, sl.up, 0));
+  NVC_CUDA(h, cudaStreamWaitEvent(s, sl.down, 0));
+  NVC_TRY(nvc_frame(h, scene, dv.data(), n_views, train_view, seed, frame, loss_out, use_graph,
+                    stream));
+  NVC_CUDA(h, cudaEventRecord(sl.done, s));
+  h->host_next = b ^ 1;
+  // read-back on the second copy stream
+  NVC_CUDA(h, cudaStreamWaitEvent(h->down_stream, sl.done, 0));
+  for (int v = 0; v < n_views; ++v) {
+    const nvc_view& hv = host_views[v];
+    const nvc_view& d = dv[v];
+    const int64_t n = hv.n_pixels;
+    if (n == 0) continue;
+    if (hv.idx)
+      NVC_CUDA(h, cudaMemcpyAsync(hv.idx, d.idx, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                                  h->down_stream));
+    if (hv.pdf)
+      NVC_CUDA(h, cudaMemcpyAsync(hv.pdf, d.pdf, sizeof(float) * n, cudaMemcpyDeviceToHost,
+                                  h->down_stream));
+    if (hv.wsum)
+      NVC_CUDA(h, cudaMemcpyAsync(hv.wsum, d.wsum, sizeof(float) * n, cudaMemcpyDeviceToHost,
+                                  h->down_stream));
+    if (hv.radiance)
+      NVC_CUDA(h, cudaMemcpyAsync(hv.radiance, d.radiance, sizeof(float) * n,
+                                  cudaMemcpyDeviceToHost, h->down_stream));
+  }
+  NVC_CUDA(h, cudaEventRecord(sl.down, h->down_stream));
+  return NVC_OK;
+}
+
+nvc_status nvc_host_frames_wait(nvc_handle* h, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->down_stream) return NVC_OK;
+  for (auto& sl : h->host_slot) NVC_CUDA(h, cudaStreamWaitEvent((cudaStream_t)stream, sl.down, 0));
   return NVC_OK;
 }
 

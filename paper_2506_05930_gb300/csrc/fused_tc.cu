@@ -791,7 +791,7 @@ __device__ __forceinline__ bool consumers_sync_or(bool v) {
 }
 
 template <int F, int PREC, int PW, bool PRE_C>
-__global__ void __launch_bounds__(kTileM + PW * 32, 1) fused_shade_ws_kernel(const __grid_constant__ FusedArgs a) {
+__global__ void __launch_bounds__(kTileM + PW * 32, PW == 4 ? 2 : 1) fused_shade_ws_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int kThreads = kTileM + PW * 32;
   constexpr int kParts = PW / 4;   // producer threads per pixel
   extern __shared__ __align__(1024) uint8_t smem[];

@@ -174,6 +174,18 @@ struct nvc_handle {
   float* t_logits = nullptr;  // [B][L]
   float* t_delta = nullptr;   // [n_layers][B][max(width, L)]
   float* t_dfeat = nullptr;   // [B][din]
+  // nvc_frame_host: two device slots of G-buffers and outputs, two copy
+  // streams, and the events that order uploads, frames and read-backs
+  struct HostSlot {
+    int64_t cap = 0;          // pixels the slot's buffers hold
+    float* pos = nullptr;     // [cap][3]
+    float* nrm = nullptr;     // [cap][3]
+    int32_t* idx = nullptr;   // [cap]
+    float* out = nullptr;     // [3][cap]: pdf, wsum, radiance
+    cudaEvent_t up = nullptr, done = nullptr, down = nullptr;
+  } host_slot[2];
+  int host_next = 0;
+  cudaStream_t up_stream = nullptr, down_stream = nullptr;
   double* loss_partials = nullptr;
   int n_loss_partials = 0;
   int loss_blocks = 0;                  // partials written by the last training pass

@@ -302,6 +302,49 @@ def nvc_frame(h, scene: Scene, views: Sequence[View], train_view, seed, frame, l
                         1 if use_graph else 0, _stream(stream)), h)
 
 
+def _host_ptr(t: Optional[torch.Tensor], dtype=torch.float32, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _host_view(v: "View") -> NvcView:
+    s = NvcView()
+    s.pos = _host_ptr(v.pos, name="pos")
+    s.nrm = _host_ptr(v.nrm, name="nrm")
+    s.n_pixels = v.pos.shape[0]
+    s.view_id = int(v.view_id)
+    s.idx = _host_ptr(v.idx, torch.int32, "idx")
+    s.pdf = _host_ptr(v.pdf, name="pdf")
+    s.wsum = _host_ptr(v.wsum, name="wsum")
+    s.radiance = _host_ptr(v.radiance, name="radiance")
+    return s
+
+
+def nvc_frame_host(h, scene: Scene, views: Sequence[View], train_view, seed, frame, loss_out=None,
+                   use_graph=True, stream=None):
+    """nvc_frame with every view's tensors in (pinned) host memory; returns
+    at once, the read-back completes in stream order after
+    nvc_host_frames_wait."""
+    arr = (NvcView * max(1, len(views)))(*[_host_view(v) for v in views])
+    check(lib.nvc_frame_host(h, scene.ref, arr, len(views),
+                             WORLD_ONLY if train_view is None else train_view, int(seed), int(frame),
+                             _ptr(loss_out, torch.float64, "loss_out"), 1 if use_graph else 0,
+                             _stream(stream)), h)
+
+
+def nvc_host_frames_wait(h, stream=None):
+    check(lib.nvc_host_frames_wait(h, _stream(stream)), h)
+
+
 def nvc_infer_noalloc(cfg: NvcConfig, params, pos, vis, stream=None):
     """nvc_infer for callers that cannot allocate GPU memory: parameters come
     from the caller, the library's fixed scratch array holds the encoded
