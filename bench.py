@@ -16,6 +16,7 @@ of the same frame, extrapolated to the whole frame.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -35,7 +36,7 @@ WORKLOAD = "frame_1080p"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, help="override the inference precision")
@@ -58,23 +59,39 @@ def peaks():
 # ------------------------------------------------------------------ clocks --
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of SM clock and throttle reasons during a region:
+    sampled every 50 ms with nvidia-smi's own timestamps; `ready` waits for
+    the first sample, `begin` / `stop` bracket the region on the host clock
+    and only the samples inside it are kept."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 50):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.t0 = self.t1 = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-i", str(gpu_index), "-lms", "200"],
+                                       "-i", str(gpu_index), "-lms", str(interval_ms)],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
+    def ready(self, timeout_s: float = 5.0):
+        end = time.time() + timeout_s
+        while self.p is not None and time.time() < end:
+            if os.path.getsize(self.f.name) > 0:
+                return
+            time.sleep(0.02)
+
+    def begin(self):
+        self.t0 = time.time()
+
     def stop(self):
+        self.t1 = time.time()
         if self.p is None:
             return None
+        time.sleep(0.06)                 # let the sample that covers the end land
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -85,15 +102,21 @@ class ClockSampler:
         sm, mx, reasons = [], None, set()
         for line in self.f.read().splitlines():
             c = [x.strip() for x in line.split(",")]
-            if len(c) < 9:
+            if len(c) < 10:
                 continue
             try:
-                sm.append(float(c[1]))
-                mx = float(c[2])
+                ts = datetime.datetime.strptime(c[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            if ts is not None and self.t0 is not None and not (self.t0 <= ts <= self.t1):
+                continue
+            try:
+                sm.append(float(c[2]))
+                mx = float(c[3])
             except ValueError:
                 continue
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-            for n, v in zip(names, c[5:9]):
+            for n, v in zip(names, c[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         os.unlink(self.f.name)
@@ -257,6 +280,9 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.ready()
+        clocks.begin()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -406,15 +432,21 @@ def run_ours(args):
 
 # ------------------------------------------------- the oracle on the CPU --
 
-def oracle_frame_sample(n_pixels=16384, n_positions=1024, seed=0):
+def oracle_frame_sample(n_pixels=16384, n_positions=1024, seed=0, adam_params=None, fixed=None):
     """Time the oracle on a sample of the frame and extrapolate to the whole
-    frame: shading scales with pixels, training forward/backward with
-    positions, the dense Adam update is timed over every parameter."""
+    frame.  Each part is modelled as a fixed cost plus a per-unit cost: the
+    oracle's calls carry work proportional to the whole parameter vector
+    (splitting and joining it, a full-size gradient) whatever the sample, so
+    `fixed` holds the times of the same calls on one pixel / one position
+    (oracle_fixed_costs) and only the rest is scaled: shading by pixels,
+    training forward/backward by positions, the dense Adam update by
+    parameters (all of them when adam_params is None)."""
     import numpy as np
     from oracle import nvc as O
     import nvc_synth as S
     cfg, sc, gb = workload()
     p = S.init_params(cfg, seed=seed)
+    st = O.TrainState.fresh(p)
     rng = np.random.default_rng(seed)
     pick = rng.choice(gb.n, n_pixels, replace=False)
     t0 = time.perf_counter()
@@ -424,19 +456,49 @@ def oracle_frame_sample(n_pixels=16384, n_positions=1024, seed=0):
     y = O.visibility(pos, sc.lights, sc.spheres, sc.boxes, np.float32)
     _, g = O.gradients(cfg, p, pos, y)
     t2 = time.perf_counter()
-    st = O.TrainState.fresh(p)
-    O.adam_update(st.params, g, st.m, st.v, 1, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps)
+    k = len(p) if adam_params is None else min(int(adam_params), len(p))
+    O.adam_update(st.params[:k], g[:k], st.m[:k], st.v[:k], 1, cfg.lr, cfg.beta1, cfg.beta2,
+                  cfg.eps)
     t3 = time.perf_counter()
-    frame_s = ((t1 - t0) * gb.n / n_pixels + (t2 - t1) * cfg.batch_positions / n_positions
-               + (t3 - t2))
+    f_shade, f_train = fixed if fixed else (0.0, 0.0)
+
+    def scaled(t, f, n, total):
+        return f + max(t - f, 0.0) * (total - 1) / max(n - 1, 1) if n > 1 else t * total
+
+    frame_s = (scaled(t1 - t0, f_shade, n_pixels, gb.n)
+               + scaled(t2 - t1, f_train, n_positions, cfg.batch_positions)
+               + (t3 - t2) * len(p) / k)
     return frame_s, t3 - t0, gb.n
+
+
+def oracle_fixed_costs(reps=2):
+    """The oracle's shading call on one pixel and its training forward/
+    backward on one position: the per-call costs the sample times carry."""
+    import numpy as np
+    from oracle import nvc as O
+    import nvc_synth as S
+    cfg, sc, gb = workload()
+    p = S.init_params(cfg, seed=0)
+    fs, ft = [], []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.shade(cfg, p, gb.pos[:1], gb.nrm[:1], sc.lights, seed=1, frame=0)
+        t1 = time.perf_counter()
+        pos = O.training_positions(1, sc.world_min, sc.world_max, gb.pos, 1, 0)
+        y = O.visibility(pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+        O.gradients(cfg, p, pos, y)
+        t2 = time.perf_counter()
+        fs.append(t1 - t0)
+        ft.append(t2 - t1)
+    return min(fs), min(ft)
 
 
 def cpu_baseline(seconds_target=15.0):
     """Run the oracle in a child process with one BLAS thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "f, w, P = bench.oracle_frame_sample(131072, 4096); print(json.dumps([f, w, P]))" % ROOT)
+            "fx = bench.oracle_fixed_costs(); "
+            "f, w, P = bench.oracle_frame_sample(131072, 4096, fixed=fx); print(json.dumps([f, w, P]))" % ROOT)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         return {"error": r.stderr[-300:]}
@@ -445,7 +507,8 @@ def cpu_baseline(seconds_target=15.0):
             "ms_per_frame": frame_s * 1e3, "wall_s": wall,
             "sample": "131,072 random pixels of the 1080p frame shaded (inference+WRS+DI), "
                       "training forward/backward on 4,096 of the 8,192 positions, one dense Adam "
-                      "update of all parameters; extrapolated linearly to the full frame"}
+                      "update of all parameters; each part extrapolated to the full frame as a "
+                      "fixed per-call cost (timed on one pixel / one position) plus a linear rest"}
 
 
 def run_reference(args):
@@ -454,12 +517,14 @@ def run_reference(args):
     if rank != 0:
         return
     cfg, _, _ = workload()
+    fixed = oracle_fixed_costs()
+    sample = dict(n_pixels=2048, n_positions=128, adam_params=1 << 19, fixed=fixed)
     for _ in range(args.warmup):
-        oracle_frame_sample(n_pixels=4096, n_positions=256)
+        oracle_frame_sample(**sample)
     frames, walls = [], []
     t0 = time.perf_counter()
     for k in range(args.steps):
-        f, w, P = oracle_frame_sample(n_pixels=4096, n_positions=256, seed=k)
+        f, w, P = oracle_frame_sample(seed=k, **sample)
         frames.append(f)
         walls.append(w)
     frame_s = sum(frames) / len(frames)
@@ -471,9 +536,11 @@ def run_reference(args):
         "data": "synthetic", "impl": "reference",
         "config": workload_config(world, P, cfg.batch_positions),
         "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
-                         "sample": "per step 4,096 pixels shaded, training forward/backward on "
-                                   "256 positions, one dense Adam update; extrapolated to the "
-                                   "1080p frame", "wall_s_per_step": sum(walls) / len(walls)},
+                         "sample": "per step 2,048 pixels shaded, training forward/backward on "
+                                   "128 positions, Adam over 2^19 of the 16.8M parameters; each "
+                                   "part extrapolated to the 1080p frame as a fixed per-call cost "
+                                   "(timed once on one pixel / one position) plus a linear rest",
+                         "wall_s_per_step": sum(walls) / len(walls)},
         "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

@@ -81,3 +81,38 @@ def test_host_frame_rejects_missing_inputs():
     assert st == _lib.NVC_ERR_INVALID_ARG
     assert "NULL" in nvc.nvc_last_error(cache.handle)
     cache.close()
+
+
+def test_host_frames_several_views_and_an_empty_one():
+    """Three views in one host frame, the middle one empty: each non-empty
+    view's outputs land in its own host tensors, bit-identical to the
+    device path, and the empty view is skipped."""
+    cfg = S.config_by_name("frame_1080p").with_(batch_positions=256)
+    sc = S.scene_heightfield(seed=6, n_lights=32, n_spheres=4, n_boxes=4)
+    gbs = [S.gbuffer_heightfield(seed=20, width=64, height=33),
+           S.gbuffer_heightfield(seed=21, width=1, height=1),
+           S.gbuffer_heightfield(seed=22, width=77, height=19)]
+    p = S.init_params(cfg, seed=5)
+    dev_cache, host_cache = nvc.VisibilityCache(cfg), nvc.VisibilityCache(cfg)
+    dev_cache.set_params(p)
+    host_cache.set_params(p)
+    scene = nvc.Scene.from_synth(sc)
+    dviews, hviews = [], []
+    for k, gb in enumerate(gbs):
+        n = 0 if k == 1 else gb.n
+        pos, nrm = gb.pos[:n], gb.nrm[:n]
+        dviews.append(nvc.View(torch.from_numpy(pos).cuda().reshape(n, 3),
+                               torch.from_numpy(nrm).cuda().reshape(n, 3), 10 + k, **_outputs(n, "cuda")))
+        hviews.append(nvc.View(_pinned(pos).reshape(n, 3), _pinned(nrm).reshape(n, 3), 10 + k,
+                               **_outputs(n, "cpu")))
+    nvc.nvc_frame(dev_cache.handle, scene, dviews, nvc.NO_TRAINING, 3, 9, use_graph=True)
+    nvc.nvc_frame_host(host_cache.handle, scene, hviews, nvc.NO_TRAINING, 3, 9, use_graph=True)
+    stream = torch.cuda.current_stream()
+    nvc.nvc_host_frames_wait(host_cache.handle, stream)
+    stream.synchronize()
+    for dv, hv in zip(dviews, hviews):
+        for k in ("idx", "pdf", "wsum", "radiance"):
+            assert torch.equal(getattr(hv, k), getattr(dv, k).cpu()), k
+    assert (hviews[2].idx >= 0).float().mean() > 0.5
+    dev_cache.close()
+    host_cache.close()
