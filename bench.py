@@ -445,8 +445,10 @@ def oracle_frame_sample(n_pixels=16384, n_positions=1024, seed=0, adam_params=No
     from oracle import nvc as O
     import nvc_synth as S
     cfg, sc, gb = workload()
-    p = S.init_params(cfg, seed=seed)
-    st = O.TrainState.fresh(p)
+    if "oracle_state" not in _WORKLOAD_CACHE:      # parameters and Adam state, made once
+        p0 = S.init_params(cfg, seed=0)
+        _WORKLOAD_CACHE["oracle_state"] = (p0, O.TrainState.fresh(p0))
+    p, st = _WORKLOAD_CACHE["oracle_state"]
     rng = np.random.default_rng(seed)
     pick = rng.choice(gb.n, n_pixels, replace=False)
     t0 = time.perf_counter()
