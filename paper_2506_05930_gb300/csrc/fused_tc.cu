@@ -11,8 +11,9 @@
 // x 16 bytes per core matrix; the K-adjacent core matrix 128 bytes on, the
 // next 8-row group K*2*8 bytes on).  All layers' weights are loaded once
 // per CTA; the activation tile is rewritten in place between layers.  One
-// elected thread issues K/16 tcgen05.mma (M=128, N=layer width, fp16 or
-// bf16 operands, fp32 accumulate) per layer and commits to an mbarrier.
+// elected thread issues the layer's tcgen05.mma (M=128, N=layer width, fp32
+// accumulate; K/16 of kind::f16 for fp16 / bf16 operands, K/32 of
+// kind::f8f6f4 for scaled E4M3) and commits to an mbarrier.
 // Several CTAs per SM overlap one CTA's gathers with another's MMAs and
 // sampler arithmetic; the TMEM columns per CTA are a power of two and the
 // CTAs per SM are capped so that their columns fit the 512 available.
@@ -20,6 +21,11 @@
 // Every wait on the mbarrier is bounded (about one second); a timeout sets
 // an error flag in the handle's status and every thread of the CTA leaves
 // the tile loop together, freeing TMEM on the way out.
+//
+// Two other kernels compute the same function for the autotuner: a
+// warp-specialised one (producer warps encode the next tile while consumer
+// warps run the MLP and the sampler) and one with two threads per pixel
+// (256-thread CTAs splitting levels, columns and lights).
 #include "nvc_internal.cuh"
 #include "hashgrid.cuh"
 #include "tc_common.cuh"
