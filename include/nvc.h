@@ -249,13 +249,17 @@ nvc_status nvc_calibrate(nvc_handle* h, const float* pos, int64_t n, void* strea
  *   4  as 3 with the contributions computed by the producers;
  *   5  two threads per pixel (256-thread CTAs): the halves split the
  *      encode's levels, the hidden layers' columns and the lights, and meet
- *      in shared memory for the weight maximum, sums and the pick.
- * 1-4 need n_outputs <= 32; 1-5 need FP16/BF16.  All make the same picks
- * from the same float32 weights; 0-4 give bit-identical outputs, 5 sums
- * w and the Neural DI terms over lights [0, H) and [H, L) separately
- * (H = ceil(ceil(L / 2) / 16) * 16), which can change the last bits of
- * wsum, pdf and radiance. */
-#define NVC_SHADE_VARIANTS 6
+ *      in shared memory for the weight maximum, sums and the pick;
+ *   6  two tile streams per CTA (256 threads) sharing one copy of the
+ *      weights, the light weights kept in shared memory between the
+ *      sampler's passes;
+ *   7  as 6 with four tile streams per CTA (512 threads).
+ * 1-4, 6 and 7 need n_outputs <= 32; 1-7 need FP16/BF16.  All make the same
+ * picks from the same float32 weights; all but 5 give bit-identical
+ * outputs, 5 sums w and the Neural DI terms over lights [0, H) and [H, L)
+ * separately (H = ceil(ceil(L / 2) / 16) * 16), which can change the last
+ * bits of wsum, pdf and radiance. */
+#define NVC_SHADE_VARIANTS 8
 
 /* Times every applicable variant on these pixels (CUDA events on `stream`,
  * a warm-up then `reps` launches each; synchronises) and keeps the fastest

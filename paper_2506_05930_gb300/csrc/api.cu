@@ -638,7 +638,7 @@ nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant) {
   if (variant != kShadeMono && h->cfg.precision == NVC_PREC_FP8)
     return fail(h, NVC_ERR_UNSUPPORTED, "E4M3 operands run the monolithic variant only");
   if (variant != kShadeMono && variant != kShadePair && h->L > 32)
-    return fail(h, NVC_ERR_UNSUPPORTED, "warp-specialised variants need n_outputs <= 32");
+    return fail(h, NVC_ERR_UNSUPPORTED, "variants 1-4, 6 and 7 need n_outputs <= 32");
   h->shade_variant = variant;
   return NVC_OK;
 }

@@ -129,7 +129,9 @@ enum ShadeVariant : int {
   kShadeWs8 = 3,    // 8 producer warps (two threads per pixel) + 4 consumers
   kShadeWs8C = 4,   // as kShadeWs8 with precomputed contributions
   kShadePair = 5,   // two threads per pixel: levels, columns and lights split in halves
-  kShadeVariants = 6
+  kShadeMulti2 = 6, // two tile streams per CTA sharing the weights
+  kShadeMulti4 = 7, // four tile streams per CTA sharing the weights
+  kShadeVariants = 8
 };
 
 // Adam scalars written on the device each step.

@@ -211,7 +211,7 @@ def nvc_sampler_weights(h, scene: Scene, pos, nrm, w, stream=None):
                                   _stream(stream)), h)
 
 
-SHADE_VARIANTS = 6
+SHADE_VARIANTS = 8
 
 
 def nvc_autotune_shade(h, scene: Scene, pos, nrm, idx=None, pdf=None, wsum=None, radiance=None,
