@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
 // and 128-thread named barrier -- while the weight image is held once per
 // CTA for all groups.  Between the sampler's two passes the group's
 // activation tile is idle, so it holds the pixels' light weights
-// ([light][pixel] floats) in place of 32 registers a thread.  Both savings
+// (a row of 36 floats per pixel) in place of 32 registers a thread.  Both savings
 // buy warps per SM.  L <= 32, 16-bit operands; outputs bit-identical to the
 // monolithic kernel's.
 __device__ __forceinline__ void group_sync(int g) {
@@ -525,7 +525,9 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
   const int g = t >> 7;                  // this thread's group
   const int rw = t & (kTileM - 1);       // pixel row within the group's tile = TMEM lane
   uint8_t* s_a = smem + a.multi_a + g * a.multi_stride;
-  float* s_wst = reinterpret_cast<float*>(s_a);   // light weights between the passes
+  // this pixel's 32 light weights between the passes: rows of 36 floats (16-byte
+  // accesses, four wavefronts a warp, the fewest for 16 bytes a thread)
+  float4* s_wst4 = reinterpret_cast<float4*>(s_a) + rw * 9;
   float4* s_l = reinterpret_cast<float4*>(smem + a.multi_l);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.multi_bar);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + TPC);
@@ -658,21 +660,33 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
         }
         float wmax = 0.0f, sum = 0.0f, di = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (j < L) {
-            const float v = sigmoid_fast(__uint_as_float(r[j]));
-            const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
-            const float w = fmaxf(v, bits_f(kVisClampBits)) * c;
-            wmax = fmaxf(wmax, w);
-            sum += w;
-            di = fmaf(v, c, di);
-            s_wst[j * kTileM + rw] = w;
+        for (int q4 = 0; q4 < 8; ++q4) {
+          float w4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = q4 * 4 + u;
+            float w = 0.0f;
+            if (j < L) {
+              const float v = sigmoid_fast(__uint_as_float(r[j]));
+              const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
+              w = fmaxf(v, bits_f(kVisClampBits)) * c;
+              wmax = fmaxf(wmax, w);
+              sum += w;
+              di = fmaf(v, c, di);
+            }
+            w4[u] = w;
           }
+          if (q4 * 4 < L) s_wst4[q4] = make_float4(w4[0], w4[1], w4[2], w4[3]);
         }
         if (V.w_out != nullptr && live) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j < L) V.w_out[row * L + j] = s_wst[j * kTileM + rw];
+          for (int q4 = 0; q4 < 8; ++q4) {
+            const float4 w4 = s_wst4[q4];
+            const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (q4 * 4 + u < L) V.w_out[row * L + q4 * 4 + u] = wv[u];
+          }
         }
         int sel = -1;
         float wsel = 0.0f;
@@ -683,10 +697,17 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
         uint32_t Q = 0;
         uint4 rr = make_uint4(0, 0, 0, 0);
         if (active) {
+          float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             if (j < L) {
-              const float w = __fmul_rn(s_wst[j * kTileM + rw], qs.pre);
+              if ((j & 3) == 0) {
+                w4 = s_wst4[j >> 2];
+                if (qs.pre != 1.0f)
+                  w4 = make_float4(__fmul_rn(w4.x, qs.pre), __fmul_rn(w4.y, qs.pre),
+                                   __fmul_rn(w4.z, qs.pre), __fmul_rn(w4.w, qs.pre));
+              }
+              const float w = (j & 3) == 0 ? w4.x : (j & 3) == 1 ? w4.y : (j & 3) == 2 ? w4.z : w4.w;
               if ((j & 3) == 0)
                 rr = philox_keyed(make_uint4(pixel, a.frame, V.view,
                                              ((uint32_t)(j >> 2) << 4) | kTagWrs),
@@ -1449,15 +1470,15 @@ size_t pair_smem(const nvc_handle* h, const PackArgs& p, FusedArgs* a = nullptr)
 }
 
 // Shared-memory plan of the several-tiles-per-CTA kernel: weight image, tpc
-// activation tiles (each also holding 128 x 32 float light weights), light
-// table, tpc mbarriers and the TMEM address word.
+// activation tiles (each also holding the 128 pixels' light weights in rows
+// of 36 floats), light table, tpc mbarriers and the TMEM address word.
 size_t multi_smem(const nvc_handle* h, const PackArgs& p, int tpc, FusedArgs* a = nullptr) {
   int kmax = 16;
   for (int k = 0; k < p.n_layers; ++k) kmax = p.K[k] > kmax ? p.K[k] : kmax;
   size_t off = ((size_t)p.byte_off[p.n_layers] + 127) & ~(size_t)127;
   const size_t a_off = off;
   size_t stride = (size_t)kTileM * kmax * p.esize;
-  if (stride < (size_t)kTileM * 32 * 4) stride = (size_t)kTileM * 32 * 4;
+  if (stride < (size_t)kTileM * 36 * 4) stride = (size_t)kTileM * 36 * 4;
   stride = (stride + 127) & ~(size_t)127;
   off += (size_t)tpc * stride;
   const size_t l_off = off;
