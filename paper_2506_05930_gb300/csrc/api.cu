@@ -728,9 +728,10 @@ static nvc_status train_forward_backward(nvc_handle* h, const nvc_scene* scene,
   const int64_t B = h->B;
   {
     StageScope sc(h, s, 0);
-    NVC_CUDA(h, launch_training_positions(scene, screen_pos, n_screen, B, seed, frame, h->t_pos, s));
-    NVC_CUDA(h, launch_trace_visibility(scene, h->t_pos, B, h->t_target, s));
-    count_launches(h, 2);
+    // positions and their shadow-ray targets in one kernel
+    NVC_CUDA(h, launch_training_data(scene, screen_pos, n_screen, B, seed, frame, h->t_pos,
+                                     h->t_target, s));
+    count_launches(h, 1);
   }
   StageScope sc(h, s, 1);
   if (h->cfg.train_precision == NVC_PREC_FP16) {

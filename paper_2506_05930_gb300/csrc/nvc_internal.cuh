@@ -297,6 +297,11 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
 
 // train_tc.cu
 bool train_tc_supported(const nvc_handle* h, std::string* why);
+// Training positions and their shadow-ray targets in one launch (the same
+// values as launch_training_positions followed by launch_trace_visibility).
+cudaError_t launch_training_data(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,
+                                 int64_t batch, uint64_t seed, uint32_t frame, float* pos,
+                                 float* vis, cudaStream_t s);
 cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStream_t s);
 
 }  // namespace nvc

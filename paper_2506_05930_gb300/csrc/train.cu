@@ -9,29 +9,33 @@ namespace {
 // ---- training positions ---------------------------------------------------
 // Samples [0, n_world) are uniform in the world box (stream tag 1); the rest
 // copy G-buffer pixel floor(r * n_screen / 2^32) (stream tag 2).
-__global__ void training_positions_kernel(float3 lo, float3 ext, const float* __restrict__ screen,
-                                          int64_t n_screen, int64_t batch, int64_t n_world,
-                                          uint32_t k0, uint32_t k1, uint32_t frame,
-                                          float* __restrict__ pos) {
+struct PosGen {
+  float3 lo, ext;
+  const float* screen;
+  int64_t n_screen, n_world;
+  uint32_t k0, k1, frame;
+};
+
+__device__ __forceinline__ float3 training_position(int64_t j, const PosGen& g) {
+  if (j < g.n_world) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)j, g.frame, 0u, kTagWorld), g.k0, g.k1);
+    return make_float3(__fadd_rn(g.lo.x, __fmul_rn(uniform24(r.x), g.ext.x)),
+                       __fadd_rn(g.lo.y, __fmul_rn(uniform24(r.y), g.ext.y)),
+                       __fadd_rn(g.lo.z, __fmul_rn(uniform24(r.z), g.ext.z)));
+  }
+  const uint32_t s = (uint32_t)(j - g.n_world);
+  const uint4 r = philox4x32_10(make_uint4(s, g.frame, 0u, kTagScreen), g.k0, g.k1);
+  const int64_t pix = (int64_t)(((uint64_t)r.x * (uint64_t)g.n_screen) >> 32);
+  return make_float3(g.screen[3 * pix], g.screen[3 * pix + 1], g.screen[3 * pix + 2]);
+}
+
+__global__ void training_positions_kernel(PosGen g, int64_t batch, float* __restrict__ pos) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= batch) return;
-  float x, y, z;
-  if (j < n_world) {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)j, frame, 0u, kTagWorld), k0, k1);
-    x = __fadd_rn(lo.x, __fmul_rn(uniform24(r.x), ext.x));
-    y = __fadd_rn(lo.y, __fmul_rn(uniform24(r.y), ext.y));
-    z = __fadd_rn(lo.z, __fmul_rn(uniform24(r.z), ext.z));
-  } else {
-    const uint32_t s = (uint32_t)(j - n_world);
-    const uint4 r = philox4x32_10(make_uint4(s, frame, 0u, kTagScreen), k0, k1);
-    const int64_t pix = (int64_t)(((uint64_t)r.x * (uint64_t)n_screen) >> 32);
-    x = screen[3 * pix];
-    y = screen[3 * pix + 1];
-    z = screen[3 * pix + 2];
-  }
-  pos[3 * j] = x;
-  pos[3 * j + 1] = y;
-  pos[3 * j + 2] = z;
+  const float3 q = training_position(j, g);
+  pos[3 * j] = q.x;
+  pos[3 * j + 1] = q.y;
+  pos[3 * j + 2] = q.z;
 }
 
 // ---- shadow rays ------------------------------------------------------------
@@ -76,10 +80,13 @@ __device__ __forceinline__ bool box_blocks(float px, float py, float pz, float d
   return !miss && tmin <= tmax;
 }
 
+// GEN: the kernel also makes the training positions (training_position),
+// the lane of light 0 storing each; otherwise it reads them from pos.
+template <bool GEN>
 __global__ void __launch_bounds__(256) trace_visibility_kernel(
     const float* __restrict__ lights, int L, const float* __restrict__ spheres, int n_sph,
-    const float* __restrict__ boxes, int n_box, const float* __restrict__ pos, int64_t n,
-    float* __restrict__ vis) {
+    const float* __restrict__ boxes, int n_box, float* __restrict__ pos, int64_t n,
+    float* __restrict__ vis, PosGen gen) {
   extern __shared__ float s_occ[];
   float4* s_sph = reinterpret_cast<float4*>(s_occ);
   float* s_box = s_occ + 4 * n_sph;
@@ -91,7 +98,22 @@ __global__ void __launch_bounds__(256) trace_visibility_kernel(
   if (t >= n * L) return;
   const int64_t p = t / L;
   const int i = (int)(t - p * L);
-  const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
+  float px, py, pz;
+  if constexpr (GEN) {
+    const float3 q = training_position(p, gen);
+    px = q.x;
+    py = q.y;
+    pz = q.z;
+    if (i == 0) {
+      pos[3 * p] = px;
+      pos[3 * p + 1] = py;
+      pos[3 * p + 2] = pz;
+    }
+  } else {
+    px = pos[3 * p];
+    py = pos[3 * p + 1];
+    pz = pos[3 * p + 2];
+  }
   const float4 lt = reinterpret_cast<const float4*>(lights)[i];
   const float dx = __fsub_rn(lt.x, px), dy = __fsub_rn(lt.y, py), dz = __fsub_rn(lt.z, pz);
   const float dd = dot3_rn(dx, dy, dz, dx, dy, dz);
@@ -291,19 +313,41 @@ __global__ void take_gradient_kernel(float* __restrict__ grad, float* __restrict
 
 }  // namespace
 
+static PosGen pos_gen(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,
+                      int64_t batch, uint64_t seed, uint32_t frame) {
+  const bool have_screen = screen_pos != nullptr && n_screen > 0;
+  PosGen g;
+  g.lo = make_float3(sc->world_min[0], sc->world_min[1], sc->world_min[2]);
+  g.ext = make_float3(sc->world_max[0] - sc->world_min[0], sc->world_max[1] - sc->world_min[1],
+                      sc->world_max[2] - sc->world_min[2]);
+  g.screen = screen_pos;
+  g.n_screen = have_screen ? n_screen : 0;
+  g.n_world = batch - (have_screen ? batch / 2 : 0);
+  g.k0 = (uint32_t)seed;
+  g.k1 = (uint32_t)(seed >> 32);
+  g.frame = frame;
+  return g;
+}
+
 cudaError_t launch_training_positions(const nvc_scene* sc, const float* screen_pos,
                                       int64_t n_screen, int64_t batch, uint64_t seed,
                                       uint32_t frame, float* pos, cudaStream_t s) {
   if (batch == 0) return cudaSuccess;
-  const bool have_screen = screen_pos != nullptr && n_screen > 0;
-  const int64_t n_world = batch - (have_screen ? batch / 2 : 0);
-  const float3 lo = make_float3(sc->world_min[0], sc->world_min[1], sc->world_min[2]);
-  const float3 ext = make_float3(sc->world_max[0] - sc->world_min[0],
-                                 sc->world_max[1] - sc->world_min[1],
-                                 sc->world_max[2] - sc->world_min[2]);
   training_positions_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(
-      lo, ext, screen_pos, have_screen ? n_screen : 0, batch, n_world, (uint32_t)seed,
-      (uint32_t)(seed >> 32), frame, pos);
+      pos_gen(sc, screen_pos, n_screen, batch, seed, frame), batch, pos);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_training_data(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,
+                                 int64_t batch, uint64_t seed, uint32_t frame, float* pos,
+                                 float* vis, cudaStream_t s) {
+  if (batch == 0) return cudaSuccess;
+  if (sc->n_lights < 1) return launch_training_positions(sc, screen_pos, n_screen, batch, seed, frame, pos, s);
+  const int64_t total = batch * sc->n_lights;
+  const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  trace_visibility_kernel<true><<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
+      sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes, pos, batch,
+      vis, pos_gen(sc, screen_pos, n_screen, batch, seed, frame));
   return cudaGetLastError();
 }
 
@@ -312,8 +356,9 @@ cudaError_t launch_trace_visibility(const nvc_scene* sc, const float* pos, int64
   if (n == 0) return cudaSuccess;
   const int64_t total = n * sc->n_lights;
   const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
-  trace_visibility_kernel<<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
-      sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes, pos, n, vis);
+  trace_visibility_kernel<false><<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
+      sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes,
+      const_cast<float*>(pos), n, vis, PosGen{});
   return cudaGetLastError();
 }
 
