@@ -1,0 +1,196 @@
+// Declarations shared by the fused shading kernels' translation units: the
+// kernel argument block, the weight-image geometry and the sampler's device
+// arithmetic.
+#pragma once
+#include "nvc_internal.cuh"
+#include "hashgrid.cuh"
+#include "tc_common.cuh"
+
+namespace nvc {
+namespace fz {
+
+using namespace tc;
+
+constexpr int kTileM = 128;
+constexpr int kMaxLayers = NVC_MAX_HIDDEN_LAYERS + 1;
+
+struct LayerDesc {
+  int K;           // reduction size (multiple of 16)
+  int N;           // MMA width (multiple of 16)
+  int N_real;      // real output neurons of the layer
+  int K_real;      // real inputs of the layer
+  int w_byte_off;  // offset of the packed matrix in the weight image
+  uint32_t idesc;  // tcgen05 instruction descriptor
+};
+
+constexpr int kMaxViews = 16;
+
+// One view of a launch: its pixels, outputs and first tile.
+struct ViewDesc {
+  const float* pos;
+  const float* nrm;
+  int64_t n;
+  int64_t tile_start;   // tiles of earlier views
+  int64_t pixel_offset;
+  uint32_t view;
+  int32_t* idx;
+  float* pdf;
+  float* wsum;
+  float* radiance;
+  float* vis_out;
+  float* w_out;
+};
+
+struct FusedArgs {
+  int n_views;
+  int64_t n_tiles;
+  ViewDesc v[kMaxViews];
+  const float* table;
+  EncodeParams ep;
+  int F;
+  const uint4* wimg;
+  int wimg_bytes;
+  int n_layers;
+  LayerDesc layer[kMaxLayers];
+  int kmax;
+  float slope;
+  int L;
+  uint32_t tmem_cols;
+  const float* lights;
+  uint32_t k0, k1, frame;
+  uint2 rkey[10];    // Philox round keys for (k0, k1)
+  int32_t* status;
+  const float* fp8_scales;   // [0, kMaxLayers): activation scales, [kMaxLayers, 2 kMaxLayers): weight scales
+  // warp-specialised layout (byte offsets into shared memory)
+  int ws_a0[2], ws_h, ws_c[2], ws_l, ws_bar, ws_cs;
+  // monolithic layout: activation tile, light table, mbarrier + TMEM word
+  int mono_a, mono_l, mono_bar;
+  int pair_x;   // two-threads-per-pixel kernel: the halves' exchange area
+  // several-tiles-per-CTA kernel: first activation tile, tile stride, light
+  // table, mbarriers; TMEM columns per group
+  int multi_a, multi_stride, multi_l, multi_bar, multi_cols;
+};
+
+// ---- the sampler's arithmetic ----------------------------------------------
+// The two-threads-per-pixel kernel gives lights [0, H) to one thread and
+// [H, L) to the other, H = ceil(L / 2) rounded up to a multiple of 16.
+__host__ __device__ __forceinline__ int split_h(int L) { return ((((L + 1) >> 1) + 15) >> 4) << 4; }
+
+__device__ __forceinline__ float sigmoid_fast(float z) {
+  return __fdividef(1.0f, 1.0f + __expf(-z));
+}
+
+// Unshadowed contribution of a point light (Lambertian, albedo 1):
+// (I/pi) * (n.d) / (|d| * max(|d|^2, 1e-6)) for n.d > 0, with a hardware
+// reciprocal square root.
+__device__ __forceinline__ float contribution_fast(float px, float py, float pz, float nx,
+                                                   float ny, float nz, float4 l) {
+  const float dx = l.x - px, dy = l.y - py, dz = l.z - pz;
+  const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float ndl = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
+  const float r = rsqrtf(fmaxf(d2, 1e-30f));
+  const float inv = d2 >= 1e-6f ? r * r : 1e6f;
+  return fmaxf(l.w * ndl * r * inv, 0.0f);   // n.d <= 0 gives c <= 0 -> 0
+}
+
+// Per-pixel scales for q = max(1, floor(w 2^(23 - e))), e = ilogb(wmax), by
+// exact multiplications only: when wmax < 2^-104 the weights are first
+// multiplied by 2^64 (a power of two, so exact, and every w <= wmax stays
+// far from overflow); then e' = ilogb(wmax 2^64) = e + 64 and
+// w 2^64 2^(23 - e') = w 2^(23 - e), with 2^(23 - e') a normal float.
+struct QuantScale {
+  float pre, scale;
+};
+__device__ __forceinline__ QuantScale quant_scale(float wmax) {
+  const bool tiny = (__float_as_uint(wmax) >> 23) < 23u;
+  const float pre = tiny ? 0x1p64f : 1.0f;
+  const uint32_t E = max(__float_as_uint(__fmul_rn(wmax, pre)) >> 23, 23u);
+  return {pre, __uint_as_float((277u - E) << 23)};   // 2^(150 - E) = 2^(23 - e')
+}
+
+// q = max(1, floor(w * scale)) for w > 0, else 0, with scale = 2^(23 - e)
+// from quant_scale (w already multiplied by its `pre`): the product is exact
+// whenever it is a normal float, and truncating a subnormal or zero product
+// gives 0, which the max(1, .) rule then lifts to 1.
+__device__ __forceinline__ uint32_t quantize_scaled(float w, float scale) {
+  const uint32_t q = __float2uint_rz(w * scale);
+  return (w > 0.0f && q == 0u) ? 1u : q;
+}
+
+// One 16-byte core-matrix row of an operand: 8 fp16/bf16 or 16 E4M3 values
+// (the latter multiplied by the tensor's scale first).
+template <int PREC, int CH>
+__device__ __forceinline__ uint4 pack_chunk(const float (&v)[CH], float scale) {
+  uint4 pk;
+  if constexpr (PREC == NVC_PREC_FP8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      w[q] = pack_e4m3x2(v[4 * q] * scale, v[4 * q + 1] * scale) |
+             (pack_e4m3x2(v[4 * q + 2] * scale, v[4 * q + 3] * scale) << 16);
+    pk = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    pk.x = pack2<PREC>(v[0], v[1]);
+    pk.y = pack2<PREC>(v[2], v[3]);
+    pk.z = pack2<PREC>(v[4], v[5]);
+    pk.w = pack2<PREC>(v[6], v[7]);
+  }
+  return pk;
+}
+
+// Two fp32 pre-activations -> packed 16-bit leaky ReLU (0 <= slope < 1).
+template <int PREC>
+__device__ __forceinline__ uint32_t leaky2(uint32_t za, uint32_t zb, float slope) {
+  if constexpr (PREC == NVC_PREC_FP8) {
+    return 0u;   // the E4M3 path converts in fp32 (see the hidden-layer store)
+  } else if constexpr (PREC == NVC_PREC_BF16) {
+    const __nv_bfloat162 z = __floats2bfloat162_rn(__uint_as_float(za), __uint_as_float(zb));
+    const __nv_bfloat162 h = __hmax2(z, __hmul2(z, __float2bfloat162_rn(slope)));
+    return *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    const __half2 z = __floats2half2_rn(__uint_as_float(za), __uint_as_float(zb));
+    const __half2 h = __hmax2(z, __hmul2(z, __float2half2_rn(slope)));
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+
+// Philox-4x32-10 with the ten round keys (k0 + r W0, k1 + r W1) given: the
+// same function as philox4x32_10, the key schedule done once on the host.
+__device__ __forceinline__ uint4 philox_keyed(uint4 c, const uint2 (&rk)[10]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk[r].x, lo1, hi0 ^ c.w ^ rk[r].y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t pick_word(uint4 r, int lane) {
+  return lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
+}
+
+// View that tile `tile` belongs to (views are few and tiles sorted by view).
+__device__ __forceinline__ int view_of(const FusedArgs& a, int64_t tile) {
+  int v = 0;
+  while (v + 1 < a.n_views && tile >= a.v[v + 1].tile_start) ++v;
+  return v;
+}
+
+// Geometry of the tensor-core weight image.
+struct PackArgs {
+  int n_layers;
+  int K[kMaxLayers], N[kMaxLayers], K_real[kMaxLayers], N_real[kMaxLayers];
+  int64_t w_off[kMaxLayers];     // float offset of W_k in the parameter vector
+  int byte_off[kMaxLayers + 1];  // byte offset of layer k in the image
+  int esize;
+};
+
+}  // namespace fz
+
+// Shading with several tile streams per CTA (fused_multi.cu); `a` holds the
+// other launches' fields, tpc is 2 or 4, L <= 32.
+cudaError_t launch_shade_multi(fz::FusedArgs a, const nvc_handle* h, const fz::PackArgs& p, int tpc,
+                               bool bf16, cudaStream_t s);
+
+}  // namespace nvc

@@ -1,0 +1,359 @@
+// Fused shading with several tile streams per CTA (variants 6 and 7 of
+// nvc_shade): the same per-pixel path as fused_tc.cu's kernels -- hash-grid
+// encode, tcgen05 MLP, sigmoid, light weights, weighted reservoir sampling
+// and Neural DI (Sections 3.1 to 3.3 of the paper) -- with the CTA's weight
+// image shared by its groups.  In its own translation unit so that the
+// library builds in parallel.
+#include "fused_common.cuh"
+
+namespace nvc {
+
+namespace {
+
+using namespace tc;
+using namespace fz;
+
+// ---- several tiles per CTA sharing one weight copy ---------------------------
+// TPC groups of four warps.  Group g runs its own stream of 128-pixel tiles
+// (tiles blockIdx.x TPC + g + k gridDim.x TPC) the way the monolithic kernel
+// does -- its own activation tile, mbarrier, TMEM columns [g C, (g + 1) C)
+// and 128-thread named barrier -- while the weight image is held once per
+// CTA for all groups.  Between the sampler's two passes the group's
+// activation tile is idle, so it holds the pixels' light weights
+// (a row of 36 floats per pixel) in place of 32 registers a thread.  Both savings
+// buy warps per SM.  L <= 32, 16-bit operands; outputs bit-identical to the
+// monolithic kernel's.  Instantiated separately for exactly 32 lights.
+__device__ __forceinline__ void group_sync(int g) {
+  switch (g) {
+    case 0: asm volatile("bar.sync 1, 128;" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 2, 128;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 3, 128;" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 128;" ::: "memory"); break;
+  }
+}
+
+__device__ __forceinline__ bool group_sync_or(int g, bool v) {
+  uint32_t r = 0;
+#define NVC_GROUP_OR(ID)                                                      \
+  asm volatile(                                                               \
+      "{\n\t.reg .pred p, q;\n\t"                                             \
+      "setp.ne.u32 q, %1, 0;\n\t"                                             \
+      "bar.red.or.pred p, " #ID ", 128, q;\n\t"                               \
+      "selp.u32 %0, 1, 0, p;\n\t}\n"                                          \
+      : "=r"(r)                                                               \
+      : "r"((uint32_t)v)                                                      \
+      : "memory")
+  switch (g) {
+    case 0: NVC_GROUP_OR(1); break;
+    case 1: NVC_GROUP_OR(2); break;
+    case 2: NVC_GROUP_OR(3); break;
+    default: NVC_GROUP_OR(4); break;
+  }
+#undef NVC_GROUP_OR
+  return r != 0;
+}
+
+template <int F, int PREC, int TPC, bool FULL>
+__global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
+    fused_shade_multi_kernel(const __grid_constant__ FusedArgs a) {
+  constexpr int kThreads = kTileM * TPC;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* s_w = smem;
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+  const int g = t >> 7;                  // this thread's group
+  const int rw = t & (kTileM - 1);       // pixel row within the group's tile = TMEM lane
+  uint8_t* s_a = smem + a.multi_a + g * a.multi_stride;
+  // this pixel's 32 light weights between the passes: rows of 36 floats (16-byte
+  // accesses, four wavefronts a warp, the fewest for 16 bytes a thread)
+  float4* s_wst4 = reinterpret_cast<float4*>(s_a) + rw * 9;
+  float4* s_l = reinterpret_cast<float4*>(smem + a.multi_l);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.multi_bar);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + TPC);
+
+  for (int e = t; e < a.wimg_bytes / 16; e += kThreads)
+    reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
+  if (a.lights) {
+    for (int e = t; e < a.L; e += kThreads) {
+      float4 l = reinterpret_cast<const float4*>(a.lights)[e];
+      l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+      s_l[e] = l;
+    }
+  }
+  if (t == 0) {
+    for (int gg = 0; gg < TPC; ++gg) mbar_init(smem_u32(s_bar + gg), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(s_tmem), a.tmem_cols);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_all = *s_tmem;
+  const uint32_t tmem = tmem_all + (uint32_t)(g * a.multi_cols);
+  const uint32_t t_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t bar = smem_u32(s_bar + g);
+  const uint32_t a_base = smem_u32(s_a);
+  const uint32_t w_base = smem_u32(s_w);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  constexpr int CH = 8;
+  constexpr int KS = 16;
+  const int din = a.ep.n_levels * F;
+  const int K0 = a.layer[0].K;
+  const int64_t n_tiles = a.n_tiles;
+  const int L = FULL ? 32 : a.L;   // <= 32; FULL: exactly 32, the light tests fold away
+
+  for (int64_t tile = (int64_t)blockIdx.x * TPC + g; tile < n_tiles && !failed;
+       tile += (int64_t)gridDim.x * TPC) {
+    const ViewDesc& V = a.v[view_of(a, tile)];
+    const int64_t row = (tile - V.tile_start) * kTileM + rw;
+    const bool live = row < V.n;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (live) {
+      px = __ldg(V.pos + 3 * row);
+      py = __ldg(V.pos + 3 * row + 1);
+      pz = __ldg(V.pos + 3 * row + 2);
+    }
+    // ---- encode ------------------------------------------------------------
+    {
+      const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
+      const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
+      const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
+      constexpr int LPC = F >= CH ? 1 : CH / F;
+      for (int c = 0; c < K0 / CH; ++c) {
+        float fv[CH];
+#pragma unroll
+        for (int s = 0; s < CH; ++s) fv[s] = 0.0f;
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < LPC; ++q) {
+            const int l = c * LPC + q;
+            if (l * F < din) {
+              float acc[F];
+              encode_level<F>(a.ep, a.table, l, x, y, z, acc);
+#pragma unroll
+              for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
+            }
+          }
+        }
+        *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, 2)) = pack_chunk<PREC, CH>(fv, 1.0f);
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    group_sync(g);
+
+    // ---- the MLP -------------------------------------------------------------
+    for (int k = 0; k < a.n_layers && !failed; ++k) {
+      const LayerDesc ld = a.layer[k];
+      if (rw == 0) {
+        tc_fence_after();
+        const uint32_t sbo = (uint32_t)ld.K * 16u;
+        const uint32_t wb = w_base + (uint32_t)ld.w_byte_off;
+        for (int kk = 0; kk < ld.K / KS; ++kk)
+          mma_f16(tmem, smem_desc(a_base + kk * 256, 128, sbo), smem_desc(wb + kk * 256, 128, sbo),
+                  ld.idesc, kk > 0 ? 1u : 0u);
+        mma_commit(bar);
+      }
+      const bool ok = mbar_wait_bounded(bar, phase);
+      phase ^= 1u;
+      tc_fence_after();
+      if (k + 1 < a.n_layers) {
+        const int Kn = ld.N;
+        for (int c0 = 0; c0 < ld.N; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(t_lane + (uint32_t)c0, r);
+#pragma unroll
+          for (int gq = 0; gq < 4; ++gq) {
+            uint4 pk;
+            pk.x = leaky2<PREC>(r[gq * 8 + 0], r[gq * 8 + 1], a.slope);
+            pk.y = leaky2<PREC>(r[gq * 8 + 2], r[gq * 8 + 3], a.slope);
+            pk.z = leaky2<PREC>(r[gq * 8 + 4], r[gq * 8 + 5], a.slope);
+            pk.w = leaky2<PREC>(r[gq * 8 + 6], r[gq * 8 + 7], a.slope);
+            if (c0 + gq * 8 < Kn) *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c0 + gq * 8, Kn, 2)) = pk;
+          }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        failed = group_sync_or(g, !ok);
+        continue;
+      }
+
+      // ---- output layer (the MMA that read this tile's A has completed) ------
+      uint32_t r[32];
+      tmem_ld32(t_lane, r);
+      if (V.vis_out) {
+        if (live) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < L) V.vis_out[row * L + j] = sigmoid_fast(__uint_as_float(r[j]));
+        }
+      } else {
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (live) {
+          nx = __ldg(V.nrm + 3 * row);
+          ny = __ldg(V.nrm + 3 * row + 1);
+          nz = __ldg(V.nrm + 3 * row + 2);
+        }
+        float wmax = 0.0f, sum = 0.0f, di = 0.0f;
+#pragma unroll
+        for (int q4 = 0; q4 < 8; ++q4) {
+          float w4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = q4 * 4 + u;
+            float w = 0.0f;
+            if (j < L) {
+              const float v = sigmoid_fast(__uint_as_float(r[j]));
+              const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
+              w = fmaxf(v, bits_f(kVisClampBits)) * c;
+              wmax = fmaxf(wmax, w);
+              sum += w;
+              di = fmaf(v, c, di);
+            }
+            w4[u] = w;
+          }
+          if (q4 * 4 < L) s_wst4[q4] = make_float4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        if (V.w_out != nullptr && live) {
+#pragma unroll
+          for (int q4 = 0; q4 < 8; ++q4) {
+            const float4 w4 = s_wst4[q4];
+            const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (q4 * 4 + u < L) V.w_out[row * L + q4 * 4 + u] = wv[u];
+          }
+        }
+        int sel = -1;
+        float wsel = 0.0f;
+        const bool active = live && wmax > 0.0f;
+        const QuantScale qs = quant_scale(wmax);
+        const float sum_q = __fmul_rn(sum, qs.pre);
+        const uint32_t pixel = (uint32_t)(V.pixel_offset + row);
+        uint32_t Q = 0;
+        uint4 rr = make_uint4(0, 0, 0, 0);
+        if (active) {
+          float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j < L) {
+              if ((j & 3) == 0) {
+                w4 = s_wst4[j >> 2];
+                if (qs.pre != 1.0f)
+                  w4 = make_float4(__fmul_rn(w4.x, qs.pre), __fmul_rn(w4.y, qs.pre),
+                                   __fmul_rn(w4.z, qs.pre), __fmul_rn(w4.w, qs.pre));
+              }
+              const float w = (j & 3) == 0 ? w4.x : (j & 3) == 1 ? w4.y : (j & 3) == 2 ? w4.z : w4.w;
+              if ((j & 3) == 0)
+                rr = philox_keyed(make_uint4(pixel, a.frame, V.view,
+                                             ((uint32_t)(j >> 2) << 4) | kTagWrs),
+                                  a.rkey);
+              const uint32_t q = quantize_scaled(w, qs.scale);
+              Q += q;
+              if (__umulhi(pick_word(rr, j & 3), Q) < q) sel = j;
+            }
+          }
+          // the picked weight, as the loop saw it
+          if (sel >= 0) wsel = __fmul_rn(reinterpret_cast<const float*>(s_wst4)[sel], qs.pre);
+        }
+        if (live) {
+          if (V.idx) V.idx[row] = sel;
+          if (V.pdf) V.pdf[row] = sel >= 0 ? wsel / sum_q : 0.0f;
+          if (V.wsum) V.wsum[row] = sum;
+          if (V.radiance) V.radiance[row] = di;
+        }
+      }
+      tc_fence_before();
+      // also keeps the next tile's encode from overwriting weights that a
+      // slower thread of the group still reads
+      failed = group_sync_or(g, !ok);
+    }
+  }
+  if (failed && rw == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
+  if (failed) mbar_wait_bounded(bar, phase ^ 1u);   // let an MMA in flight land
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem_all, a.tmem_cols);
+  }
+}
+
+// Shared-memory plan of the several-tiles-per-CTA kernel: weight image, tpc
+// activation tiles (each also holding the 128 pixels' light weights in rows
+// of 36 floats), light table, tpc mbarriers and the TMEM address word.
+size_t multi_smem(const nvc_handle* h, const PackArgs& p, int tpc, FusedArgs* a = nullptr) {
+  int kmax = 16;
+  for (int k = 0; k < p.n_layers; ++k) kmax = p.K[k] > kmax ? p.K[k] : kmax;
+  size_t off = ((size_t)p.byte_off[p.n_layers] + 127) & ~(size_t)127;
+  const size_t a_off = off;
+  size_t stride = (size_t)kTileM * kmax * p.esize;
+  if (stride < (size_t)kTileM * 36 * 4) stride = (size_t)kTileM * 36 * 4;
+  stride = (stride + 127) & ~(size_t)127;
+  off += (size_t)tpc * stride;
+  const size_t l_off = off;
+  off += 16 * (size_t)(h->L > 0 ? h->L : 1);
+  off = (off + 7) & ~(size_t)7;
+  const size_t bar_off = off;
+  off += 8 * (size_t)tpc + 8;
+  if (a) {
+    a->multi_a = (int)a_off;
+    a->multi_stride = (int)stride;
+    a->multi_l = (int)l_off;
+    a->multi_bar = (int)bar_off;
+  }
+  return off;
+}
+
+template <int F, int PREC, int TPC>
+cudaError_t launch_multi_typed(FusedArgs a, size_t smem_needed, int num_sms, cudaStream_t s) {
+  auto kern = a.L == 32 ? fused_shade_multi_kernel<F, PREC, TPC, true>
+                        : fused_shade_multi_kernel<F, PREC, TPC, false>;
+  a.multi_cols = (int)a.tmem_cols;              // per group
+  a.tmem_cols = a.tmem_cols * (uint32_t)TPC;    // per CTA (a power of two)
+  if (a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;
+  const int max_ctas = (int)(512u / a.tmem_cols);
+  size_t smem = smem_needed;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)kern);
+  if (e != cudaSuccess) return e;
+  const size_t dyn_max = 227 * 1024 - fa.sharedSizeBytes;
+  if (smem > dyn_max) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+  if (e != cudaSuccess) return e;
+  int occ = blocks_per_sm((const void*)kern, TPC * kTileM, smem);
+  while (occ > max_ctas && smem + 4096 <= dyn_max) {
+    smem += 4096;
+    occ = blocks_per_sm((const void*)kern, TPC * kTileM, smem);
+  }
+  if (occ < 1 || occ > max_ctas) return cudaErrorInvalidConfiguration;
+  const int64_t groups = (a.n_tiles + TPC - 1) / TPC;
+  const int64_t cap = (int64_t)occ * num_sms;
+  const int grid = (int)(groups < cap ? groups : cap);
+  kern<<<grid, TPC * kTileM, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_shade_multi(FusedArgs a, const nvc_handle* h, const PackArgs& p, int tpc,
+                               bool bf16, cudaStream_t s) {
+  const size_t smem = multi_smem(h, p, tpc, &a);
+#define NVC_MULTI(FF)                                                                          \
+  if (tpc == 2) return bf16 ? launch_multi_typed<FF, NVC_PREC_BF16, 2>(a, smem, h->num_sms, s) \
+                            : launch_multi_typed<FF, NVC_PREC_FP16, 2>(a, smem, h->num_sms, s); \
+  return bf16 ? launch_multi_typed<FF, NVC_PREC_BF16, 4>(a, smem, h->num_sms, s)               \
+              : launch_multi_typed<FF, NVC_PREC_FP16, 4>(a, smem, h->num_sms, s);
+  switch (h->F) {
+    case 1: NVC_MULTI(1)
+    case 2: NVC_MULTI(2)
+    case 4: NVC_MULTI(4)
+    case 8: NVC_MULTI(8)
+  }
+#undef NVC_MULTI
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nvc

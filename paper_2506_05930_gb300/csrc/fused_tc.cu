@@ -29,178 +29,14 @@
 #include "nvc_internal.cuh"
 #include "hashgrid.cuh"
 #include "tc_common.cuh"
+#include "fused_common.cuh"
 
 namespace nvc {
 
 namespace {
 
 using namespace tc;
-
-constexpr int kTileM = 128;
-constexpr int kMaxLayers = NVC_MAX_HIDDEN_LAYERS + 1;
-
-struct LayerDesc {
-  int K;           // reduction size (multiple of 16)
-  int N;           // MMA width (multiple of 16)
-  int N_real;      // real output neurons of the layer
-  int K_real;      // real inputs of the layer
-  int w_byte_off;  // offset of the packed matrix in the weight image
-  uint32_t idesc;  // tcgen05 instruction descriptor
-};
-
-constexpr int kMaxViews = 16;
-
-// One view of a launch: its pixels, outputs and first tile.
-struct ViewDesc {
-  const float* pos;
-  const float* nrm;
-  int64_t n;
-  int64_t tile_start;   // tiles of earlier views
-  int64_t pixel_offset;
-  uint32_t view;
-  int32_t* idx;
-  float* pdf;
-  float* wsum;
-  float* radiance;
-  float* vis_out;
-  float* w_out;
-};
-
-struct FusedArgs {
-  int n_views;
-  int64_t n_tiles;
-  ViewDesc v[kMaxViews];
-  const float* table;
-  EncodeParams ep;
-  int F;
-  const uint4* wimg;
-  int wimg_bytes;
-  int n_layers;
-  LayerDesc layer[kMaxLayers];
-  int kmax;
-  float slope;
-  int L;
-  uint32_t tmem_cols;
-  const float* lights;
-  uint32_t k0, k1, frame;
-  uint2 rkey[10];    // Philox round keys for (k0, k1)
-  int32_t* status;
-  const float* fp8_scales;   // [0, kMaxLayers): activation scales, [kMaxLayers, 2 kMaxLayers): weight scales
-  // warp-specialised layout (byte offsets into shared memory)
-  int ws_a0[2], ws_h, ws_c[2], ws_l, ws_bar, ws_cs;
-  // monolithic layout: activation tile, light table, mbarrier + TMEM word
-  int mono_a, mono_l, mono_bar;
-  int pair_x;   // two-threads-per-pixel kernel: the halves' exchange area
-  // several-tiles-per-CTA kernel: first activation tile, tile stride, light
-  // table, mbarriers; TMEM columns per group
-  int multi_a, multi_stride, multi_l, multi_bar, multi_cols;
-};
-
-// ---- the sampler's arithmetic ----------------------------------------------
-// The two-threads-per-pixel kernel gives lights [0, H) to one thread and
-// [H, L) to the other, H = ceil(L / 2) rounded up to a multiple of 16.
-__host__ __device__ __forceinline__ int split_h(int L) { return ((((L + 1) >> 1) + 15) >> 4) << 4; }
-
-__device__ __forceinline__ float sigmoid_fast(float z) {
-  return __fdividef(1.0f, 1.0f + __expf(-z));
-}
-
-// Unshadowed contribution of a point light (Lambertian, albedo 1):
-// (I/pi) * (n.d) / (|d| * max(|d|^2, 1e-6)) for n.d > 0, with a hardware
-// reciprocal square root.
-__device__ __forceinline__ float contribution_fast(float px, float py, float pz, float nx,
-                                                   float ny, float nz, float4 l) {
-  const float dx = l.x - px, dy = l.y - py, dz = l.z - pz;
-  const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  const float ndl = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
-  const float r = rsqrtf(fmaxf(d2, 1e-30f));
-  const float inv = d2 >= 1e-6f ? r * r : 1e6f;
-  return fmaxf(l.w * ndl * r * inv, 0.0f);   // n.d <= 0 gives c <= 0 -> 0
-}
-
-// Per-pixel scales for q = max(1, floor(w 2^(23 - e))), e = ilogb(wmax), by
-// exact multiplications only: when wmax < 2^-104 the weights are first
-// multiplied by 2^64 (a power of two, so exact, and every w <= wmax stays
-// far from overflow); then e' = ilogb(wmax 2^64) = e + 64 and
-// w 2^64 2^(23 - e') = w 2^(23 - e), with 2^(23 - e') a normal float.
-struct QuantScale {
-  float pre, scale;
-};
-__device__ __forceinline__ QuantScale quant_scale(float wmax) {
-  const bool tiny = (__float_as_uint(wmax) >> 23) < 23u;
-  const float pre = tiny ? 0x1p64f : 1.0f;
-  const uint32_t E = max(__float_as_uint(__fmul_rn(wmax, pre)) >> 23, 23u);
-  return {pre, __uint_as_float((277u - E) << 23)};   // 2^(150 - E) = 2^(23 - e')
-}
-
-// q = max(1, floor(w * scale)) for w > 0, else 0, with scale = 2^(23 - e)
-// from quant_scale (w already multiplied by its `pre`): the product is exact
-// whenever it is a normal float, and truncating a subnormal or zero product
-// gives 0, which the max(1, .) rule then lifts to 1.
-__device__ __forceinline__ uint32_t quantize_scaled(float w, float scale) {
-  const uint32_t q = __float2uint_rz(w * scale);
-  return (w > 0.0f && q == 0u) ? 1u : q;
-}
-
-// One 16-byte core-matrix row of an operand: 8 fp16/bf16 or 16 E4M3 values
-// (the latter multiplied by the tensor's scale first).
-template <int PREC, int CH>
-__device__ __forceinline__ uint4 pack_chunk(const float (&v)[CH], float scale) {
-  uint4 pk;
-  if constexpr (PREC == NVC_PREC_FP8) {
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      w[q] = pack_e4m3x2(v[4 * q] * scale, v[4 * q + 1] * scale) |
-             (pack_e4m3x2(v[4 * q + 2] * scale, v[4 * q + 3] * scale) << 16);
-    pk = make_uint4(w[0], w[1], w[2], w[3]);
-  } else {
-    pk.x = pack2<PREC>(v[0], v[1]);
-    pk.y = pack2<PREC>(v[2], v[3]);
-    pk.z = pack2<PREC>(v[4], v[5]);
-    pk.w = pack2<PREC>(v[6], v[7]);
-  }
-  return pk;
-}
-
-// Two fp32 pre-activations -> packed 16-bit leaky ReLU (0 <= slope < 1).
-template <int PREC>
-__device__ __forceinline__ uint32_t leaky2(uint32_t za, uint32_t zb, float slope) {
-  if constexpr (PREC == NVC_PREC_FP8) {
-    return 0u;   // the E4M3 path converts in fp32 (see the hidden-layer store)
-  } else if constexpr (PREC == NVC_PREC_BF16) {
-    const __nv_bfloat162 z = __floats2bfloat162_rn(__uint_as_float(za), __uint_as_float(zb));
-    const __nv_bfloat162 h = __hmax2(z, __hmul2(z, __float2bfloat162_rn(slope)));
-    return *reinterpret_cast<const uint32_t*>(&h);
-  } else {
-    const __half2 z = __floats2half2_rn(__uint_as_float(za), __uint_as_float(zb));
-    const __half2 h = __hmax2(z, __hmul2(z, __float2half2_rn(slope)));
-    return *reinterpret_cast<const uint32_t*>(&h);
-  }
-}
-
-// Philox-4x32-10 with the ten round keys (k0 + r W0, k1 + r W1) given: the
-// same function as philox4x32_10, the key schedule done once on the host.
-__device__ __forceinline__ uint4 philox_keyed(uint4 c, const uint2 (&rk)[10]) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
-    c = make_uint4(hi1 ^ c.y ^ rk[r].x, lo1, hi0 ^ c.w ^ rk[r].y, lo0);
-  }
-  return c;
-}
-
-__device__ __forceinline__ uint32_t pick_word(uint4 r, int lane) {
-  return lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
-}
-
-// View that tile `tile` belongs to (views are few and tiles sorted by view).
-__device__ __forceinline__ int view_of(const FusedArgs& a, int64_t tile) {
-  int v = 0;
-  while (v + 1 < a.n_views && tile >= a.v[v + 1].tile_start) ++v;
-  return v;
-}
+using namespace fz;
 
 // ---- the kernel ----------------------------------------------------------------
 template <int F, int PREC, bool LSMALL>
@@ -471,275 +307,6 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, a.tmem_cols);
-  }
-}
-
-// ---- several tiles per CTA sharing one weight copy ---------------------------
-// TPC groups of four warps.  Group g runs its own stream of 128-pixel tiles
-// (tiles blockIdx.x TPC + g + k gridDim.x TPC) the way the monolithic kernel
-// does -- its own activation tile, mbarrier, TMEM columns [g C, (g + 1) C)
-// and 128-thread named barrier -- while the weight image is held once per
-// CTA for all groups.  Between the sampler's two passes the group's
-// activation tile is idle, so it holds the pixels' light weights
-// (a row of 36 floats per pixel) in place of 32 registers a thread.  Both savings
-// buy warps per SM.  L <= 32, 16-bit operands; outputs bit-identical to the
-// monolithic kernel's.
-__device__ __forceinline__ void group_sync(int g) {
-  switch (g) {
-    case 0: asm volatile("bar.sync 1, 128;" ::: "memory"); break;
-    case 1: asm volatile("bar.sync 2, 128;" ::: "memory"); break;
-    case 2: asm volatile("bar.sync 3, 128;" ::: "memory"); break;
-    default: asm volatile("bar.sync 4, 128;" ::: "memory"); break;
-  }
-}
-
-__device__ __forceinline__ bool group_sync_or(int g, bool v) {
-  uint32_t r = 0;
-#define NVC_GROUP_OR(ID)                                                      \
-  asm volatile(                                                               \
-      "{\n\t.reg .pred p, q;\n\t"                                             \
-      "setp.ne.u32 q, %1, 0;\n\t"                                             \
-      "bar.red.or.pred p, " #ID ", 128, q;\n\t"                               \
-      "selp.u32 %0, 1, 0, p;\n\t}\n"                                          \
-      : "=r"(r)                                                               \
-      : "r"((uint32_t)v)                                                      \
-      : "memory")
-  switch (g) {
-    case 0: NVC_GROUP_OR(1); break;
-    case 1: NVC_GROUP_OR(2); break;
-    case 2: NVC_GROUP_OR(3); break;
-    default: NVC_GROUP_OR(4); break;
-  }
-#undef NVC_GROUP_OR
-  return r != 0;
-}
-
-template <int F, int PREC, int TPC>
-__global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
-    fused_shade_multi_kernel(const __grid_constant__ FusedArgs a) {
-  constexpr int kThreads = kTileM * TPC;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* s_w = smem;
-  const int t = threadIdx.x;
-  const int warp = t >> 5;
-  const int g = t >> 7;                  // this thread's group
-  const int rw = t & (kTileM - 1);       // pixel row within the group's tile = TMEM lane
-  uint8_t* s_a = smem + a.multi_a + g * a.multi_stride;
-  // this pixel's 32 light weights between the passes: rows of 36 floats (16-byte
-  // accesses, four wavefronts a warp, the fewest for 16 bytes a thread)
-  float4* s_wst4 = reinterpret_cast<float4*>(s_a) + rw * 9;
-  float4* s_l = reinterpret_cast<float4*>(smem + a.multi_l);
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.multi_bar);
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + TPC);
-
-  for (int e = t; e < a.wimg_bytes / 16; e += kThreads)
-    reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
-  if (a.lights) {
-    for (int e = t; e < a.L; e += kThreads) {
-      float4 l = reinterpret_cast<const float4*>(a.lights)[e];
-      l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
-      s_l[e] = l;
-    }
-  }
-  if (t == 0) {
-    for (int gg = 0; gg < TPC; ++gg) mbar_init(smem_u32(s_bar + gg), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) tmem_alloc(smem_u32(s_tmem), a.tmem_cols);
-  fence_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem_all = *s_tmem;
-  const uint32_t tmem = tmem_all + (uint32_t)(g * a.multi_cols);
-  const uint32_t t_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  const uint32_t bar = smem_u32(s_bar + g);
-  const uint32_t a_base = smem_u32(s_a);
-  const uint32_t w_base = smem_u32(s_w);
-  uint32_t phase = 0;
-  bool failed = false;
-
-  constexpr int CH = 8;
-  constexpr int KS = 16;
-  const int din = a.ep.n_levels * F;
-  const int K0 = a.layer[0].K;
-  const int64_t n_tiles = a.n_tiles;
-  const int L = a.L;   // <= 32
-
-  for (int64_t tile = (int64_t)blockIdx.x * TPC + g; tile < n_tiles && !failed;
-       tile += (int64_t)gridDim.x * TPC) {
-    const ViewDesc& V = a.v[view_of(a, tile)];
-    const int64_t row = (tile - V.tile_start) * kTileM + rw;
-    const bool live = row < V.n;
-    float px = 0.f, py = 0.f, pz = 0.f;
-    if (live) {
-      px = __ldg(V.pos + 3 * row);
-      py = __ldg(V.pos + 3 * row + 1);
-      pz = __ldg(V.pos + 3 * row + 2);
-    }
-    // ---- encode ------------------------------------------------------------
-    {
-      const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
-      const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
-      const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
-      constexpr int LPC = F >= CH ? 1 : CH / F;
-      for (int c = 0; c < K0 / CH; ++c) {
-        float fv[CH];
-#pragma unroll
-        for (int s = 0; s < CH; ++s) fv[s] = 0.0f;
-        if (live) {
-#pragma unroll
-          for (int q = 0; q < LPC; ++q) {
-            const int l = c * LPC + q;
-            if (l * F < din) {
-              float acc[F];
-              encode_level<F>(a.ep, a.table, l, x, y, z, acc);
-#pragma unroll
-              for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
-            }
-          }
-        }
-        *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, 2)) = pack_chunk<PREC, CH>(fv, 1.0f);
-      }
-    }
-    fence_async_smem();
-    tc_fence_before();
-    group_sync(g);
-
-    // ---- the MLP -------------------------------------------------------------
-    for (int k = 0; k < a.n_layers && !failed; ++k) {
-      const LayerDesc ld = a.layer[k];
-      if (rw == 0) {
-        tc_fence_after();
-        const uint32_t sbo = (uint32_t)ld.K * 16u;
-        const uint32_t wb = w_base + (uint32_t)ld.w_byte_off;
-        for (int kk = 0; kk < ld.K / KS; ++kk)
-          mma_f16(tmem, smem_desc(a_base + kk * 256, 128, sbo), smem_desc(wb + kk * 256, 128, sbo),
-                  ld.idesc, kk > 0 ? 1u : 0u);
-        mma_commit(bar);
-      }
-      const bool ok = mbar_wait_bounded(bar, phase);
-      phase ^= 1u;
-      tc_fence_after();
-      if (k + 1 < a.n_layers) {
-        const int Kn = ld.N;
-        for (int c0 = 0; c0 < ld.N; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld32(t_lane + (uint32_t)c0, r);
-#pragma unroll
-          for (int gq = 0; gq < 4; ++gq) {
-            uint4 pk;
-            pk.x = leaky2<PREC>(r[gq * 8 + 0], r[gq * 8 + 1], a.slope);
-            pk.y = leaky2<PREC>(r[gq * 8 + 2], r[gq * 8 + 3], a.slope);
-            pk.z = leaky2<PREC>(r[gq * 8 + 4], r[gq * 8 + 5], a.slope);
-            pk.w = leaky2<PREC>(r[gq * 8 + 6], r[gq * 8 + 7], a.slope);
-            if (c0 + gq * 8 < Kn) *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c0 + gq * 8, Kn, 2)) = pk;
-          }
-        }
-        fence_async_smem();
-        tc_fence_before();
-        failed = group_sync_or(g, !ok);
-        continue;
-      }
-
-      // ---- output layer (the MMA that read this tile's A has completed) ------
-      uint32_t r[32];
-      tmem_ld32(t_lane, r);
-      if (V.vis_out) {
-        if (live) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j < L) V.vis_out[row * L + j] = sigmoid_fast(__uint_as_float(r[j]));
-        }
-      } else {
-        float nx = 0.f, ny = 0.f, nz = 0.f;
-        if (live) {
-          nx = __ldg(V.nrm + 3 * row);
-          ny = __ldg(V.nrm + 3 * row + 1);
-          nz = __ldg(V.nrm + 3 * row + 2);
-        }
-        float wmax = 0.0f, sum = 0.0f, di = 0.0f;
-#pragma unroll
-        for (int q4 = 0; q4 < 8; ++q4) {
-          float w4[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int j = q4 * 4 + u;
-            float w = 0.0f;
-            if (j < L) {
-              const float v = sigmoid_fast(__uint_as_float(r[j]));
-              const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
-              w = fmaxf(v, bits_f(kVisClampBits)) * c;
-              wmax = fmaxf(wmax, w);
-              sum += w;
-              di = fmaf(v, c, di);
-            }
-            w4[u] = w;
-          }
-          if (q4 * 4 < L) s_wst4[q4] = make_float4(w4[0], w4[1], w4[2], w4[3]);
-        }
-        if (V.w_out != nullptr && live) {
-#pragma unroll
-          for (int q4 = 0; q4 < 8; ++q4) {
-            const float4 w4 = s_wst4[q4];
-            const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (q4 * 4 + u < L) V.w_out[row * L + q4 * 4 + u] = wv[u];
-          }
-        }
-        int sel = -1;
-        float wsel = 0.0f;
-        const bool active = live && wmax > 0.0f;
-        const QuantScale qs = quant_scale(wmax);
-        const float sum_q = __fmul_rn(sum, qs.pre);
-        const uint32_t pixel = (uint32_t)(V.pixel_offset + row);
-        uint32_t Q = 0;
-        uint4 rr = make_uint4(0, 0, 0, 0);
-        if (active) {
-          float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j < L) {
-              if ((j & 3) == 0) {
-                w4 = s_wst4[j >> 2];
-                if (qs.pre != 1.0f)
-                  w4 = make_float4(__fmul_rn(w4.x, qs.pre), __fmul_rn(w4.y, qs.pre),
-                                   __fmul_rn(w4.z, qs.pre), __fmul_rn(w4.w, qs.pre));
-              }
-              const float w = (j & 3) == 0 ? w4.x : (j & 3) == 1 ? w4.y : (j & 3) == 2 ? w4.z : w4.w;
-              if ((j & 3) == 0)
-                rr = philox_keyed(make_uint4(pixel, a.frame, V.view,
-                                             ((uint32_t)(j >> 2) << 4) | kTagWrs),
-                                  a.rkey);
-              const uint32_t q = quantize_scaled(w, qs.scale);
-              Q += q;
-              if (__umulhi(pick_word(rr, j & 3), Q) < q) {
-                sel = j;
-                wsel = w;
-              }
-            }
-          }
-        }
-        if (live) {
-          if (V.idx) V.idx[row] = sel;
-          if (V.pdf) V.pdf[row] = sel >= 0 ? wsel / sum_q : 0.0f;
-          if (V.wsum) V.wsum[row] = sum;
-          if (V.radiance) V.radiance[row] = di;
-        }
-      }
-      tc_fence_before();
-      // also keeps the next tile's encode from overwriting weights that a
-      // slower thread of the group still reads
-      failed = group_sync_or(g, !ok);
-    }
-  }
-  if (failed && rw == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
-  if (failed) mbar_wait_bounded(bar, phase ^ 1u);   // let an MMA in flight land
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tmem_dealloc(tmem_all, a.tmem_cols);
   }
 }
 
@@ -1336,13 +903,6 @@ __global__ void __launch_bounds__(kTileM + PW * 32, PW == 4 ? 2 : 1) fused_shade
 }
 
 // ---- weight packing (fp32 master -> tensor-core operand image) -------------
-struct PackArgs {
-  int n_layers;
-  int K[kMaxLayers], N[kMaxLayers], K_real[kMaxLayers], N_real[kMaxLayers];
-  int64_t w_off[kMaxLayers];     // float offset of W_k in the parameter vector
-  int byte_off[kMaxLayers + 1];  // byte offset of layer k in the image
-  int esize;
-};
 
 template <int PREC>
 __global__ void pack_mlp_kernel(const float* __restrict__ params, PackArgs p, uint8_t* out) {
@@ -1467,60 +1027,6 @@ size_t pair_smem(const nvc_handle* h, const PackArgs& p, FusedArgs* a = nullptr)
   off = (off + 15) & ~(size_t)15;
   if (a) a->pair_x = (int)off;
   return off + 2 * kTileM * 16 + kTileM * 4 + kTileM * 8;
-}
-
-// Shared-memory plan of the several-tiles-per-CTA kernel: weight image, tpc
-// activation tiles (each also holding the 128 pixels' light weights in rows
-// of 36 floats), light table, tpc mbarriers and the TMEM address word.
-size_t multi_smem(const nvc_handle* h, const PackArgs& p, int tpc, FusedArgs* a = nullptr) {
-  int kmax = 16;
-  for (int k = 0; k < p.n_layers; ++k) kmax = p.K[k] > kmax ? p.K[k] : kmax;
-  size_t off = ((size_t)p.byte_off[p.n_layers] + 127) & ~(size_t)127;
-  const size_t a_off = off;
-  size_t stride = (size_t)kTileM * kmax * p.esize;
-  if (stride < (size_t)kTileM * 36 * 4) stride = (size_t)kTileM * 36 * 4;
-  stride = (stride + 127) & ~(size_t)127;
-  off += (size_t)tpc * stride;
-  const size_t l_off = off;
-  off += 16 * (size_t)(h->L > 0 ? h->L : 1);
-  off = (off + 7) & ~(size_t)7;
-  const size_t bar_off = off;
-  off += 8 * (size_t)tpc + 8;
-  if (a) {
-    a->multi_a = (int)a_off;
-    a->multi_stride = (int)stride;
-    a->multi_l = (int)l_off;
-    a->multi_bar = (int)bar_off;
-  }
-  return off;
-}
-
-template <int F, int PREC, int TPC>
-cudaError_t launch_multi_typed(FusedArgs a, size_t smem_needed, int num_sms, cudaStream_t s) {
-  auto kern = fused_shade_multi_kernel<F, PREC, TPC>;
-  a.multi_cols = (int)a.tmem_cols;              // per group
-  a.tmem_cols = a.tmem_cols * (uint32_t)TPC;    // per CTA (a power of two)
-  if (a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;
-  const int max_ctas = (int)(512u / a.tmem_cols);
-  size_t smem = smem_needed;
-  cudaFuncAttributes fa{};
-  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)kern);
-  if (e != cudaSuccess) return e;
-  const size_t dyn_max = 227 * 1024 - fa.sharedSizeBytes;
-  if (smem > dyn_max) return cudaErrorInvalidConfiguration;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
-  if (e != cudaSuccess) return e;
-  int occ = blocks_per_sm((const void*)kern, TPC * kTileM, smem);
-  while (occ > max_ctas && smem + 4096 <= dyn_max) {
-    smem += 4096;
-    occ = blocks_per_sm((const void*)kern, TPC * kTileM, smem);
-  }
-  if (occ < 1 || occ > max_ctas) return cudaErrorInvalidConfiguration;
-  const int64_t groups = (a.n_tiles + TPC - 1) / TPC;
-  const int64_t cap = (int64_t)occ * num_sms;
-  const int grid = (int)(groups < cap ? groups : cap);
-  kern<<<grid, TPC * kTileM, smem, s>>>(a);
-  return cudaGetLastError();
 }
 
 template <int F, int PREC>
@@ -1743,23 +1249,8 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
   }
   const bool bf16 = h->cfg.precision == NVC_PREC_BF16;
   const int variant = h->shade_variant;
-  if ((variant == kShadeMulti2 || variant == kShadeMulti4) && h->L <= 32) {
-    const int tpc = variant == kShadeMulti2 ? 2 : 4;
-    const size_t smem_m = multi_smem(h, p, tpc, &a);
-#define NVC_MULTI(FF)                                                                        \
-  if (tpc == 2) return bf16 ? launch_multi_typed<FF, NVC_PREC_BF16, 2>(a, smem_m, h->num_sms, s) \
-                            : launch_multi_typed<FF, NVC_PREC_FP16, 2>(a, smem_m, h->num_sms, s); \
-  return bf16 ? launch_multi_typed<FF, NVC_PREC_BF16, 4>(a, smem_m, h->num_sms, s)               \
-              : launch_multi_typed<FF, NVC_PREC_FP16, 4>(a, smem_m, h->num_sms, s);
-    switch (h->F) {
-      case 1: NVC_MULTI(1)
-      case 2: NVC_MULTI(2)
-      case 4: NVC_MULTI(4)
-      case 8: NVC_MULTI(8)
-    }
-#undef NVC_MULTI
-    return cudaErrorInvalidValue;
-  }
+  if ((variant == kShadeMulti2 || variant == kShadeMulti4) && h->L <= 32)
+    return launch_shade_multi(a, h, p, variant == kShadeMulti2 ? 2 : 4, bf16, s);
   if (variant == kShadePair) {
     const size_t smem_p = pair_smem(h, p, &a);
     switch (h->F) {
