@@ -103,7 +103,9 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
   const int din = a.ep.n_levels * F;
   const int K0 = a.layer[0].K;
   const int64_t n_tiles = a.n_tiles;
-  const int L = FULL ? 32 : a.L;   // <= 32; FULL: exactly 32, the light tests fold away
+  // FULL: exactly 32 lights, so the light tests fold away, and every level's
+  // N_l + 1 < T (checked by the launcher), so the hash's x terms need no mask
+  const int L = FULL ? 32 : a.L;
 
   for (int64_t tile = (int64_t)blockIdx.x * TPC + g; tile < n_tiles && !failed;
        tile += (int64_t)gridDim.x * TPC) {
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
             const int l = c * LPC + q;
             if (l * F < din) {
               float acc[F];
-              encode_level<F>(a.ep, a.table, l, x, y, z, acc);
+              encode_level<F, FULL>(a.ep, a.table, l, x, y, z, acc);
 #pragma unroll
               for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
             }
@@ -309,8 +311,11 @@ size_t multi_smem(const nvc_handle* h, const PackArgs& p, int tpc, FusedArgs* a 
 
 template <int F, int PREC, int TPC>
 cudaError_t launch_multi_typed(FusedArgs a, size_t smem_needed, int num_sms, cudaStream_t s) {
-  auto kern = a.L == 32 ? fused_shade_multi_kernel<F, PREC, TPC, true>
-                        : fused_shade_multi_kernel<F, PREC, TPC, false>;
+  int rmax = 0;
+  for (int l = 0; l < a.ep.n_levels; ++l) rmax = a.ep.res[l] > rmax ? a.ep.res[l] : rmax;
+  const bool full = a.L == 32 && (int64_t)rmax + 1 < ((int64_t)1 << a.ep.log2_table);
+  auto kern = full ? fused_shade_multi_kernel<F, PREC, TPC, true>
+                   : fused_shade_multi_kernel<F, PREC, TPC, false>;
   a.multi_cols = (int)a.tmem_cols;              // per group
   a.tmem_cols = a.tmem_cols * (uint32_t)TPC;    // per CTA (a power of two)
   if (a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;

@@ -175,7 +175,7 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 // Same arithmetic as the separate encode kernel (float32 cell, hashed
 // corners, trilinear blend), with the hash's per-axis terms shared between
 // the corners that use them.
-template <int F>
+template <int F, bool XSMALL = false>
 __device__ __forceinline__ void encode_level(const EncodeParams& ep, const float* __restrict__ table,
                                              int l, float x, float y, float z, float (&acc)[F]) {
   const int n = ep.res[l];
@@ -190,8 +190,10 @@ __device__ __forceinline__ void encode_level(const EncodeParams& ep, const float
   const float fz = __fsub_rn(__fmul_rn(z, nf), (float)cz);
   const uint32_t mask = (1u << ep.log2_table) - 1u;
   // (a ^ b ^ c) & m = (a & m) ^ (b & m) ^ (c & m): masking the six axis
-  // terms leaves one three-input XOR per corner
-  const uint32_t hx[2] = {(uint32_t)cx & mask, ((uint32_t)cx + 1u) & mask};
+  // terms leaves one three-input XOR per corner.  XSMALL: the caller knows
+  // every level's N_l + 1 < T, so the x terms need no mask.
+  const uint32_t hx[2] = {XSMALL ? (uint32_t)cx : (uint32_t)cx & mask,
+                          XSMALL ? (uint32_t)cx + 1u : ((uint32_t)cx + 1u) & mask};
   const uint32_t hy0 = (uint32_t)cy * kPrime1, hz0 = (uint32_t)cz * kPrime2;
   const uint32_t hy[2] = {hy0 & mask, (hy0 + kPrime1) & mask};
   const uint32_t hz[2] = {hz0 & mask, (hz0 + kPrime2) & mask};
