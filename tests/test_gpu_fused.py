@@ -284,6 +284,29 @@ def test_multiview_frame_is_one_launch_equal_to_per_view_launches():
             assert torch.equal(getattr(v, k), ref[k]), (v.view_id, k)
 
 
+@pytest.mark.parametrize("variant", [6, 7])
+def test_multiview_frame_with_tile_stream_variants(variant):
+    """Variants 6 and 7 give each group of a CTA its own stream of tiles,
+    which may belong to different views: a four-view, 32-light frame (so
+    variant 7 takes its 32-light instantiation) is bit-identical to
+    variant 0's."""
+    cfg = S.config_by_name("frame_1080p").with_(batch_positions=256)
+    sc = S.scene_heightfield(seed=8, n_lights=32, n_spheres=8, n_boxes=8)
+    gbs = S.multiview_gbuffers(seed=4, sizes=((160, 90), (97, 33), (256, 144), (64, 64)))
+    cache, p = make(cfg, seed=1, table_scale=0.5)
+    scene = nvc.Scene.from_synth(sc)
+    outs = []
+    for v in (0, variant):
+        nvc.nvc_set_shade_variant(cache.handle, v)
+        views = _views(gbs)
+        nvc.nvc_frame(cache.handle, scene, views, nvc.NO_TRAINING, seed=5, frame=2, use_graph=True)
+        outs.append(views)
+    for a, b in zip(*outs):
+        for k in ("idx", "pdf", "wsum", "radiance"):
+            assert torch.equal(getattr(a, k), getattr(b, k)), (a.view_id, k)
+        assert (host(b.idx) >= 0).mean() > 0.5
+
+
 def test_multiview_full_workload_in_one_graph_launch_sampled():
     """The batched multi-view workload: 1280x720, 1920x1080, 2560x1440 and
     3840x2160 (14,976,000 pixels) with 128 lights, trained and shaded as
