@@ -219,7 +219,7 @@ def alu_peak_ops(sm_mhz=2070.0, n_sms=152, lanes=128):
 
 # Per-launch DRAM traffic of the dominant kernel from the ncu capture named in
 # profiles/ (None once the kernel has changed since that capture).
-KERNEL_TRAFFIC = {"fused_shade": 109.91e6, "adam": 428.34e6}
+KERNEL_TRAFFIC = {"fused_shade": 109.98e6, "adam": 428.34e6}
 
 
 # ------------------------------------------------------------- our arm ----
