@@ -373,6 +373,35 @@ def run_ours(args):
         base = {"ms_per_step": bm, "value": P / (bm * 1e-3) / 1e6}
         cache32.close()
 
+    # the shading pass (Section 3.1: one shadow ray per pixel to the picked
+    # light, running mean) and the all-lights exact DI that Section 4.4
+    # compares the cache's inference with; reported beside the frame
+    shading = None
+    if rank == 0:
+        acc = torch.zeros(P, device="cuda")
+        exact = torch.empty(P, device="cuda")
+        nvc.nvc_shade_estimate(scene, pos, nrm, view.idx, view.pdf, accum=acc, count=1)
+        nvc.nvc_exact_di(scene, pos, nrm, exact)
+        torch.cuda.synchronize()
+        x0 = torch.cuda.Event(enable_timing=True)
+        x1 = torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for k in range(20):
+            nvc.nvc_shade_estimate(scene, pos, nrm, view.idx, view.pdf, accum=acc, count=k + 2)
+        x1.record(stream)
+        torch.cuda.synchronize()
+        pass_ms = x0.elapsed_time(x1) / 20
+        x0.record(stream)
+        for k in range(5):
+            nvc.nvc_exact_di(scene, pos, nrm, exact)
+        x1.record(stream)
+        torch.cuda.synchronize()
+        exact_ms = x0.elapsed_time(x1) / 5
+        shading = {"shade_pass_ms": pass_ms, "exact_di_ms": exact_ms,
+                   "exact_di_over_inference": exact_ms / stage_ms[3] if stage_ms[3] > 0 else None,
+                   "note": "shade pass: one shadow ray per pixel to the sampled light, V c / p, "
+                           "running mean; exact DI: a shadow ray to every light from every pixel"}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -423,6 +452,8 @@ def run_ours(args):
     }
     if base:
         line["fp32_unfused_baseline"] = base
+    if shading:
+        line["shading_pass"] = shading
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(seconds_target=15.0)
     print(json.dumps(line), flush=True)

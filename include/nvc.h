@@ -274,6 +274,34 @@ nvc_status nvc_autotune_shade(nvc_handle* h, const nvc_scene* scene, const float
 /* Selects the fused shading kernel variant (0 .. NVC_SHADE_VARIANTS-1). */
 nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant);
 
+/* ---- the shading pass (Section 3.1) and exact direct illumination -------- */
+
+/* The one-sample estimate of Eq. 1 for the light each pixel's reservoir
+ * picked (Section 3.1): one shadow ray from pos[p] to light idx[p] (same
+ * segment and occluder tests as nvc_trace_visibility) and
+ *     estimate[p] = V c / pdf[p]   (0 when idx[p] < 0, pdf[p] <= 0, c = 0
+ *                                   or the ray is blocked),
+ * c the light's unshadowed contribution in the float32 order of
+ * nvc_light_weights, the division correctly rounded.  idx / pdf as
+ * nvc_wrs_sample or nvc_shade write them.  estimate (device [n], may be
+ * NULL) receives the estimate; accum (device [n], may be NULL) the running
+ * mean over frames: with count = the frame's number k >= 1,
+ *     accum[p] = e                               for k = 1,
+ *     accum[p] = accum[p] + (e - accum[p]) / k   otherwise (float32, each
+ *                                                 step correctly rounded).
+ * Asynchronous on `stream`. */
+nvc_status nvc_shade_estimate(const nvc_scene* scene, const float* pos, const float* nrm,
+                              int64_t n, const int32_t* idx, const float* pdf, float* estimate,
+                              float* accum, uint32_t count, void* stream);
+
+/* Direct illumination with a shadow ray from every pixel to every light:
+ * di[p] = sum over lights i in order of c_i for the unblocked ones (float32
+ * additions in light order; c_i as in nvc_shade_estimate).  The brute-force
+ * reference that the paper's Section 4.4 times against the cache's
+ * inference.  pos, nrm device [n][3]; di device [n].  Asynchronous. */
+nvc_status nvc_exact_di(const nvc_scene* scene, const float* pos, const float* nrm, int64_t n,
+                        float* di, void* stream);
+
 /* ---- training (Section 3.4) -------------------------------------------- */
 
 /* Binary visibility vis (device [n][n_lights], 0 or 1) of every light from

@@ -405,6 +405,64 @@ def visibility(pos, lights, spheres, boxes, dtype=np.float64) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# The shading pass (Section 3.1) and exact direct illumination (Section 4.4)
+# ----------------------------------------------------------------------------
+
+def shading_estimate(pos, nrm, lights, spheres, boxes, idx, pdf) -> np.ndarray:
+    """One-sample estimate of Eq. 1 for each pixel's sampled light (the
+    shading pass after light sampling, Section 3.1): one shadow ray towards
+    light s = idx[p], and
+
+        e[p] = V_s c_s / pdf[p]
+
+    with V_s the float32 shadow-ray decision of ``visibility`` and c_s the
+    float32 contribution of ``contributions``; the division rounds once to
+    float32.  Pixels with idx < 0 or pdf <= 0 give 0.  Averaged over the
+    sampler's choice (probability pdf of light s), e has mean sum_i V_i c_i:
+    the estimator is unbiased wherever every light with c_i > 0 can be
+    picked."""
+    pos = np.asarray(pos, np.float32)
+    nrm = np.asarray(nrm, np.float32)
+    idx = np.asarray(idx, np.int64)
+    pdf = np.asarray(pdf, np.float32)
+    est = np.zeros(len(pos), np.float32)
+    sel = np.nonzero((idx >= 0) & (pdf > 0))[0]
+    if len(sel) == 0:
+        return est
+    rows = np.arange(len(sel))
+    V = visibility(pos[sel], lights, spheres, boxes, np.float32)[rows, idx[sel]]
+    c = contributions(pos[sel], nrm[sel], lights, np.float32)[rows, idx[sel]]
+    ok = (V > 0) & (c > 0)
+    est[sel] = np.where(ok, c.astype(np.float32) / np.where(ok, pdf[sel], np.float32(1)),
+                        np.float32(0)).astype(np.float32)
+    return est
+
+
+def running_mean(accum, est, count: int) -> np.ndarray:
+    """Temporal accumulation of the per-frame estimates: the mean of the
+    first k frames, updated in place of the mean of k - 1 as
+    a <- a + (e - a) / k (each operation rounded to float32; a = e for
+    k = 1)."""
+    e = np.asarray(est, np.float32)
+    if count <= 1:
+        return e.copy()
+    a = np.asarray(accum, np.float32)
+    return (a + (e - a) / np.float32(count)).astype(np.float32)
+
+
+def exact_di_f32(V, c32) -> np.ndarray:
+    """exact_di evaluated as a float32 sum over the lights in order, each
+    unblocked light's float32 contribution added with one rounding."""
+    V = np.asarray(V)
+    c = np.asarray(c32, np.float32)
+    s = np.zeros(c.shape[0], np.float32)
+    for i in range(c.shape[1]):
+        take = (V[:, i] > 0) & (c[:, i] > 0)
+        s = np.where(take, (s + c[:, i]).astype(np.float32), s)
+    return s
+
+
+# ----------------------------------------------------------------------------
 # Loss, backpropagation and Adam (Sections 3.3 and 3.4)
 # ----------------------------------------------------------------------------
 

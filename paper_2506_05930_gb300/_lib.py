@@ -100,6 +100,8 @@ PROTOTYPES = {
     "nvc_frame_host": (c_int32, [_vp, _scp, POINTER(NvcView), c_int32, c_int32, c_uint64,
                                  c_uint32, _vp, c_int32, _vp]),
     "nvc_host_frames_wait": (c_int32, [_vp, _vp]),
+    "nvc_shade_estimate": (c_int32, [_scp, _vp, _vp, c_int64, _vp, _vp, _vp, _vp, c_uint32, _vp]),
+    "nvc_exact_di": (c_int32, [_scp, _vp, _vp, c_int64, _vp, _vp]),
     "nvc_infer_noalloc": (c_int32, [_cfgp, _vp, _vp, c_int64, _vp, _vp]),
     "nvc_set_profiling": (c_int32, [_vp, c_int32]),
     "nvc_stage_times": (c_int32, [_vp, POINTER(c_double), c_int32, POINTER(c_int64)]),

@@ -705,6 +705,50 @@ nvc_status nvc_trace_visibility(const nvc_scene* scene, const float* pos, int64_
   return NVC_OK;
 }
 
+static cudaError_t current_sms(int* n) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  return cudaDeviceGetAttribute(n, cudaDevAttrMultiProcessorCount, dev);
+}
+
+nvc_status nvc_shade_estimate(const nvc_scene* scene, const float* pos, const float* nrm,
+                              int64_t n, const int32_t* idx, const float* pdf, float* estimate,
+                              float* accum, uint32_t count, void* stream) {
+  NVC_TRY(check_scene(nullptr, scene, 0));
+  if (n < 0) return fail(nullptr, NVC_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(nullptr, pos, "pos"));
+  NVC_TRY(check_ptr(nullptr, nrm, "nrm"));
+  NVC_TRY(check_ptr(nullptr, idx, "idx"));
+  NVC_TRY(check_ptr(nullptr, pdf, "pdf"));
+  if (!estimate && !accum) return fail(nullptr, NVC_ERR_INVALID_ARG, "estimate and accum both NULL");
+  if (estimate) NVC_TRY(check_ptr(nullptr, estimate, "estimate"));
+  if (accum) {
+    NVC_TRY(check_ptr(nullptr, accum, "accum"));
+    if (count < 1) return fail(nullptr, NVC_ERR_INVALID_ARG, "count must be >= 1");
+  }
+  int sms = 0;
+  NVC_CUDA(nullptr, current_sms(&sms));
+  NVC_CUDA(nullptr, launch_shade_estimate(scene, pos, nrm, n, idx, pdf, estimate, accum, count,
+                                          sms, (cudaStream_t)stream));
+  return NVC_OK;
+}
+
+nvc_status nvc_exact_di(const nvc_scene* scene, const float* pos, const float* nrm, int64_t n,
+                        float* di, void* stream) {
+  NVC_TRY(check_scene(nullptr, scene, 0));
+  if (n < 0) return fail(nullptr, NVC_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(nullptr, pos, "pos"));
+  NVC_TRY(check_ptr(nullptr, nrm, "nrm"));
+  NVC_TRY(check_ptr(nullptr, di, "di"));
+  int sms = 0;
+  NVC_CUDA(nullptr, current_sms(&sms));
+  NVC_CUDA(nullptr, launch_exact_di(scene, pos, nrm, n, di, sms, (cudaStream_t)stream));
+  return NVC_OK;
+}
+
 nvc_status nvc_training_positions(const nvc_scene* scene, const float* screen_pos,
                                   int64_t n_screen, int64_t batch, uint64_t seed, uint32_t frame,
                                   float* pos, void* stream) {

@@ -297,6 +297,14 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
 
 // train_tc.cu
 bool train_tc_supported(const nvc_handle* h, std::string* why);
+// The shading pass's one-sample estimate (and running mean) and the
+// all-lights exact DI (shade_est.cu).
+cudaError_t launch_shade_estimate(const nvc_scene* sc, const float* pos, const float* nrm,
+                                  int64_t n, const int32_t* idx, const float* pdf,
+                                  float* estimate, float* accum, uint32_t count, int num_sms,
+                                  cudaStream_t s);
+cudaError_t launch_exact_di(const nvc_scene* sc, const float* pos, const float* nrm, int64_t n,
+                            float* di, int num_sms, cudaStream_t s);
 // Training positions and their shadow-ray targets in one launch (the same
 // values as launch_training_positions followed by launch_trace_visibility).
 cudaError_t launch_training_data(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,

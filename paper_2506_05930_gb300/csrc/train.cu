@@ -1,6 +1,7 @@
 // Online training (Section 3.4 of the paper): training positions, binary
 // shadow-ray targets, the loss and its gradient at the logits, and Adam.
 #include "nvc_internal.cuh"
+#include "shadow.cuh"
 
 namespace nvc {
 
@@ -38,48 +39,7 @@ __global__ void training_positions_kernel(PosGen g, int64_t batch, float* __rest
   pos[3 * j + 2] = q.z;
 }
 
-// ---- shadow rays ------------------------------------------------------------
-// One thread per (position, light); occluders staged in shared memory.  The
-// arithmetic is correctly rounded float32 in a fixed order, so the binary
-// decision is reproducible operation by operation.  The divisions are
-// taken once per (position, light): 1/|d|^2 for the spheres' closest-point
-// parameter and 1/d per axis for the boxes' slabs; each occluder then
-// costs multiplications only.
-__device__ __forceinline__ bool sphere_blocks(float px, float py, float pz, float dx, float dy,
-                                              float dz, float inv_dd, float4 s) {
-  const float t0 = bits_f(kSegT0Bits), t1 = bits_f(kSegT1Bits);
-  const float ox = __fsub_rn(s.x, px), oy = __fsub_rn(s.y, py), oz = __fsub_rn(s.z, pz);
-  float tc = __fmul_rn(dot3_rn(ox, oy, oz, dx, dy, dz), inv_dd);
-  tc = fminf(fmaxf(tc, t0), t1);
-  const float ex = __fsub_rn(s.x, __fadd_rn(px, __fmul_rn(tc, dx)));
-  const float ey = __fsub_rn(s.y, __fadd_rn(py, __fmul_rn(tc, dy)));
-  const float ez = __fsub_rn(s.z, __fadd_rn(pz, __fmul_rn(tc, dz)));
-  return dot3_rn(ex, ey, ez, ex, ey, ez) < __fmul_rn(s.w, s.w);
-}
-
-__device__ __forceinline__ void slab(float xa, float da, float inv_da, float lo, float hi,
-                                     float& tmin, float& tmax, bool& miss) {
-  if (da == 0.0f) {
-    miss = miss || xa < lo || xa > hi;
-    return;
-  }
-  const float ta = __fmul_rn(__fsub_rn(lo, xa), inv_da);
-  const float tb = __fmul_rn(__fsub_rn(hi, xa), inv_da);
-  tmin = fmaxf(tmin, fminf(ta, tb));
-  tmax = fminf(tmax, fmaxf(ta, tb));
-}
-
-__device__ __forceinline__ bool box_blocks(float px, float py, float pz, float dx, float dy,
-                                           float dz, float ix, float iy, float iz,
-                                           const float* b) {
-  float tmin = bits_f(kSegT0Bits), tmax = bits_f(kSegT1Bits);
-  bool miss = false;
-  slab(px, dx, ix, b[0], b[3], tmin, tmax, miss);
-  slab(py, dy, iy, b[1], b[4], tmin, tmax, miss);
-  slab(pz, dz, iz, b[2], b[5], tmin, tmax, miss);
-  return !miss && tmin <= tmax;
-}
-
+// ---- shadow rays (occluder tests in shadow.cuh) -------------------------------
 // GEN: the kernel also makes the training positions (training_position),
 // the lane of light 0 storing each; otherwise it reads them from pos.
 template <bool GEN>

@@ -345,6 +345,22 @@ def nvc_host_frames_wait(h, stream=None):
     check(lib.nvc_host_frames_wait(h, _stream(stream)), h)
 
 
+def nvc_shade_estimate(scene: Scene, pos, nrm, idx, pdf, estimate=None, accum=None, count=1,
+                       stream=None):
+    """V c / pdf for each pixel's sampled light (one shadow ray), and/or its
+    running mean over `count` frames into `accum`."""
+    check(lib.nvc_shade_estimate(scene.ref, _ptr(pos, name="pos"), _ptr(nrm, name="nrm"),
+                                 pos.shape[0], _ptr(idx, torch.int32, "idx"), _ptr(pdf, name="pdf"),
+                                 _ptr(estimate, name="estimate"), _ptr(accum, name="accum"),
+                                 int(count), _stream(stream)))
+
+
+def nvc_exact_di(scene: Scene, pos, nrm, di, stream=None):
+    """Sum over all lights of V_i c_i, one shadow ray per (pixel, light)."""
+    check(lib.nvc_exact_di(scene.ref, _ptr(pos, name="pos"), _ptr(nrm, name="nrm"), pos.shape[0],
+                           _ptr(di, name="di"), _stream(stream)))
+
+
 def nvc_infer_noalloc(cfg: NvcConfig, params, pos, vis, stream=None):
     """nvc_infer for callers that cannot allocate GPU memory: parameters come
     from the caller, the library's fixed scratch array holds the encoded

@@ -520,3 +520,72 @@ def test_e4m3_rounding_matches_torch_float8():
     np.testing.assert_array_equal(fp8.round_e4m3(x), want)
     # saturation above the largest finite value
     assert fp8.round_e4m3(np.array([1e4, -600.0])).tolist() == [448.0, -448.0]
+
+
+# ------------------------------------------------ shading pass, exact DI --
+
+def test_shading_estimate_is_unbiased_over_the_selection_law():
+    """Averaged over the sampler's choice, V_s c_s / p_s is sum_i V_i c_i
+    (Eq. 1; Section 3.1's estimator): sum_i p_i e(i, p_i) must equal the
+    exact DI, which pins both the visibility factor and the division."""
+    sc = S.scene_unit_cube(seed=2)
+    gb = S.gbuffer_points(3, 16, 16)
+    V = O.visibility(gb.pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    c32 = O.contributions(gb.pos, gb.nrm, sc.lights, np.float32)
+    w = O.light_weights_f32(np.full(c32.shape, 0.5, np.float32), c32)
+    law = O.selection_law(w)                                  # [n, L], sums to 1 or 0
+    mean = np.zeros(gb.n)
+    for i in range(c32.shape[1]):
+        pdf = law[:, i].astype(np.float32)
+        e = O.shading_estimate(gb.pos, gb.nrm, sc.lights, sc.spheres, sc.boxes,
+                               np.full(gb.n, i), pdf)
+        mean += law[:, i] * e.astype(np.float64)
+    exact = O.exact_di(V, O.contributions(gb.pos, gb.nrm, sc.lights))
+    assert (exact > 0).mean() > 0.3
+    assert ((V == 0) & (c32 > 0)).any()     # a dropped visibility factor would show
+    np.testing.assert_allclose(mean, exact, rtol=2e-6, atol=1e-12)
+
+
+def test_shading_estimate_special_cases():
+    """No pick or no probability gives 0; a light behind a sphere gives 0;
+    an unblocked light gives c / p in float32."""
+    pos = np.array([[0.0, 0.0, 0.0]] * 4, np.float32)
+    nrm = np.array([[0.0, 0.0, 1.0]] * 4, np.float32)
+    lights = np.array([[0.0, 0.0, 2.0, 3.0],          # above, behind the sphere
+                       [1.5, 0.0, 1.0, 2.0]], np.float32)   # off to the side, clear
+    spheres = np.array([[0.0, 0.0, 1.0, 0.2]], np.float32)
+    boxes = np.zeros((0, 6), np.float32)
+    idx = np.array([0, 1, -1, 1])
+    pdf = np.array([0.5, 0.25, 0.5, 0.0], np.float32)
+    e = O.shading_estimate(pos, nrm, lights, spheres, boxes, idx, pdf)
+    c = O.contributions(pos[:1], nrm[:1], lights, np.float32)[0]
+    assert c[0] > 0 and c[1] > 0
+    assert e[0] == 0.0                                   # blocked
+    assert e[1] == np.float32(c[1] / np.float32(0.25))   # c / p, one rounding
+    assert e[2] == 0.0 and e[3] == 0.0                   # no pick, no probability
+
+
+def test_running_mean_is_the_mean_of_the_frames():
+    rng = np.random.default_rng(4)
+    frames = rng.uniform(0, 3, (50, 64)).astype(np.float32)
+    a = None
+    for k in range(1, 51):
+        a = O.running_mean(a, frames[k - 1], k)
+        if k == 1:
+            assert np.array_equal(a, frames[0])
+    np.testing.assert_allclose(a, frames.astype(np.float64).mean(0), rtol=2e-6)
+    const = np.full(8, 1.75, np.float32)
+    b = None
+    for k in range(1, 20):
+        b = O.running_mean(b, const, k)
+    assert np.array_equal(b, const)
+
+
+def test_exact_di_float32_sum_matches_the_float64_sum():
+    sc = S.scene_heightfield(seed=3, n_lights=32, n_spheres=8, n_boxes=8)
+    gb = S.gbuffer_heightfield(seed=3, width=40, height=30)
+    V = O.visibility(gb.pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    c32 = O.contributions(gb.pos, gb.nrm, sc.lights, np.float32)
+    c64 = O.contributions(gb.pos, gb.nrm, sc.lights)
+    np.testing.assert_allclose(O.exact_di_f32(V, c32), O.exact_di(V, c64), rtol=2e-6, atol=1e-12)
+    assert (V == 0).mean() > 0.01        # some rays are blocked
