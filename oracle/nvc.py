@@ -463,6 +463,162 @@ def exact_di_f32(V, c32) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# Clustered NVC (Section 3.6)
+# ----------------------------------------------------------------------------
+
+RIS_CANDIDATES = 4   # candidates drawn in the chosen cluster (streaming RIS)
+
+
+def kmeans_lights(lights, init_idx, iters: int):
+    """Lloyd's k-means (Section 3.6) of the light positions, float64.
+
+    Centroids start at the lights ``init_idx`` (k distinct indices, drawn by
+    the caller); each iteration assigns every light to its nearest centroid
+    (squared distance (dx^2 + dy^2) + dz^2, ties to the lower index) and
+    moves each centroid to the mean of its members, summed in light order (a
+    cluster left empty keeps its centroid).  Returns (assign int32 [n],
+    centroids float64 [k, 3]) after ``iters`` iterations, the assignment
+    being the one the final centroids induce."""
+    P = np.asarray(lights, np.float64)[:, :3]
+    C = P[np.asarray(init_idx, np.int64)].copy()
+    k = C.shape[0]
+
+    def assign_to(C):
+        d = P[:, None, :] - C[None, :, :]
+        d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+        return np.argmin(d2, axis=1)          # first minimum: ties to the lower index
+
+    for _ in range(iters):
+        a = assign_to(C)
+        for y in range(k):
+            members = np.nonzero(a == y)[0]
+            if len(members) == 0:
+                continue
+            s = np.zeros(3)
+            for i in members:                   # light order
+                s = s + P[i]
+            C[y] = s / len(members)
+    return assign_to(C).astype(np.int32), C
+
+
+def cluster_table(assign, k: int):
+    """CSR cluster table: offsets [k + 1] and members [n], each cluster's
+    lights in increasing index order."""
+    assign = np.asarray(assign, np.int64)
+    order = np.argsort(assign, kind="stable")
+    counts = np.bincount(assign, minlength=k)
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    return offsets, order.astype(np.int32)
+
+
+def _member(offsets, members, y, r):
+    """The member of cluster y chosen by the 32-bit word r: floor(r m_y / 2^32)."""
+    m = (offsets[y + 1] - offsets[y]).astype(np.uint64)
+    j = (np.asarray(r, np.uint64) * m) >> np.uint64(32)
+    return members[offsets[y] + j.astype(np.int64)]
+
+
+def cluster_targets(pos, lights, spheres, boxes, offsets, members, sample_ids, seed: int,
+                    frame: int) -> np.ndarray:
+    """Training targets of the clustered cache (Section 3.6): for each
+    position and cluster y, the binary visibility of one member light drawn
+    uniformly (word y of the stream (sample, frame, 0, TAG_CLUSTER)), so the
+    network learns the cluster's average visibility.  [n, k] float64 0/1;
+    empty clusters give 0."""
+    offsets = np.asarray(offsets, np.int64)
+    members = np.asarray(members, np.int64)
+    k = len(offsets) - 1
+    n = len(pos)
+    r = _ph.stream_words(sample_ids, frame, 0, _ph.TAG_CLUSTER, k, seed)
+    V = visibility(pos, lights, spheres, boxes, np.float32)       # [n, L]
+    out = np.zeros((n, k))
+    for y in range(k):
+        if offsets[y + 1] == offsets[y]:
+            continue
+        x = _member(offsets, members, y, r[:, y])
+        out[:, y] = V[np.arange(n), x]
+    return out
+
+
+def cluster_contributions(c32, offsets, members) -> np.ndarray:
+    """c_hat_y = sum of the member lights' float32 contributions, in member
+    order (float32): positive exactly when some member contributes, so every
+    contributing light stays reachable through its cluster."""
+    c32 = np.asarray(c32, np.float32)
+    k = len(offsets) - 1
+    out = np.zeros((c32.shape[0], k), np.float32)
+    for y in range(k):
+        s = np.zeros(c32.shape[0], np.float32)
+        for i in members[offsets[y]:offsets[y + 1]]:
+            s = (s + c32[:, i]).astype(np.float32)
+        out[:, y] = s
+    return out
+
+
+def ris_weight(c_cand, j, w_y, w_sum, m_y):
+    """Unbiased contribution weight of candidate j after streaming RIS with
+    source pdf p(x) = (w(y) / w_sum) / m_y (the cluster's selection
+    probability times a uniform member) and target pdf c(x):
+        W = (sum_j c_j / M) / (p(x) c(x_j)),
+    every operation rounded to float32 in this order."""
+    c = np.asarray(c_cand, np.float32)
+    M = np.float32(c.shape[-1])
+    s = np.zeros(c.shape[:-1], np.float32)
+    for t in range(c.shape[-1]):
+        s = (s + c[..., t]).astype(np.float32)
+    mean = (s / M).astype(np.float32)
+    p = ((np.float32(w_y) / np.float32(w_sum)).astype(np.float32) / np.float32(m_y)).astype(np.float32)
+    den = (p * np.take_along_axis(c, np.asarray(j)[..., None], -1)[..., 0]).astype(np.float32)
+    return (mean / den).astype(np.float32)
+
+
+def sample_clustered(vis, pos, nrm, lights, offsets, members, pixel_ids, seed: int,
+                     frame: int, view: int):
+    """Two-step light sampling of the clustered cache (Section 3.6).
+
+    1. WRS over the k clusters with weights w_y = max(v_y, 0.001) c_hat_y
+       (the integer reservoir of ``wrs_select``, stream TAG_WRS).
+    2. Streaming RIS in the chosen cluster y: RIS_CANDIDATES members drawn
+       uniformly (words 0..M-1 of stream (pixel, frame, view, TAG_RIS)), one
+       kept by the integer reservoir on their float32 contributions (words
+       M..2M-1), and its contribution weight from ``ris_weight``.
+
+    vis: the cache's float32 cluster visibilities [n, k].  Returns (light
+    int32 [n], -1 when nothing contributes; W float32 [n])."""
+    offsets = np.asarray(offsets, np.int64)
+    members = np.asarray(members, np.int64)
+    c32 = contributions(pos, nrm, lights, np.float32)
+    chat = cluster_contributions(c32, offsets, members)
+    w = light_weights_f32(vis, chat)
+    y, _, _ = wrs_select(w, pixel_ids, seed, frame, view)
+    n = len(pos)
+    M = RIS_CANDIDATES
+    r = _ph.stream_words(pixel_ids, frame, view, _ph.TAG_RIS, 2 * M, seed)
+    light = np.full(n, -1, np.int32)
+    W = np.zeros(n, np.float32)
+    wsum = np.zeros(n, np.float32)
+    for t in range(w.shape[1]):
+        wsum = (wsum + w[:, t]).astype(np.float32)
+    for p in np.nonzero(y >= 0)[0]:
+        yy = int(y[p])
+        m_y = int(offsets[yy + 1] - offsets[yy])
+        cand = np.array([_member(offsets, members, yy, r[p, t]) for t in range(M)], np.int64)
+        cc = c32[p, cand].astype(np.float32)
+        if not (cc > 0).any():
+            continue
+        q = quantize_weights(cc[None, :])[0]
+        Q = np.uint64(0)
+        j = -1
+        for t in range(M):
+            Q = Q + q[t]
+            if q[t] > 0 and np.uint64(r[p, M + t]) * Q < q[t] * np.uint64(1 << 32):
+                j = t
+        light[p] = cand[j]
+        W[p] = ris_weight(cc, np.int64(j), w[p, yy], wsum[p], m_y)
+    return light, W
+
+
+# ----------------------------------------------------------------------------
 # Loss, backpropagation and Adam (Sections 3.3 and 3.4)
 # ----------------------------------------------------------------------------
 

@@ -78,6 +78,8 @@ TAG_WRS = 0
 TAG_WORLD = 1
 TAG_SCREEN = 2
 TAG_SHADE = 3
+TAG_RIS = 4        # clustered sampling: candidates in a cluster and their pick
+TAG_CLUSTER = 5    # clustered training targets: a member light per cluster
 
 
 def stream_words(ids: np.ndarray, frame: int, view: int, tag: int,

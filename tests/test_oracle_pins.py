@@ -589,3 +589,122 @@ def test_exact_di_float32_sum_matches_the_float64_sum():
     c64 = O.contributions(gb.pos, gb.nrm, sc.lights)
     np.testing.assert_allclose(O.exact_di_f32(V, c32), O.exact_di(V, c64), rtol=2e-6, atol=1e-12)
     assert (V == 0).mean() > 0.01        # some rays are blocked
+
+
+# ------------------------------------------------------- clustered NVC --
+
+def test_kmeans_separates_distant_groups_and_never_increases_its_objective():
+    rng = np.random.default_rng(7)
+    groups = [np.array([0.0, 0.0, 0.0]), np.array([10.0, 0.0, 0.0]), np.array([0.0, 10.0, 5.0])]
+    P = np.concatenate([g + rng.normal(0, 0.3, (20, 3)) for g in groups])
+    lights = np.concatenate([P, np.ones((60, 1))], 1)
+    a, C = O.kmeans_lights(lights, [0, 1, 2], 10)        # all three seeds in group 0
+    labels = [set(a[20 * g:20 * g + 20].tolist()) for g in range(3)]
+    assert all(len(l) == 1 for l in labels) and len(set.union(*labels)) == 3
+    for y in range(3):
+        np.testing.assert_allclose(C[y], P[a == y].mean(0), rtol=0, atol=1e-12)
+
+    def sse(a, C):
+        return sum(((P[a == y] - C[y]) ** 2).sum() for y in range(len(C)))
+
+    big = np.concatenate([rng.uniform(0, 10, (200, 3)), np.ones((200, 1))], 1)
+    P = big[:, :3]
+    init = rng.permutation(200)[:16]
+    prev = np.inf
+    for it in range(1, 8):
+        a, C = O.kmeans_lights(big, init, it)
+        cur = sse(a, C)
+        assert cur <= prev + 1e-9
+        prev = cur
+
+
+def test_cluster_targets_are_the_visibility_of_a_member_light():
+    sc = S.scene_heightfield(seed=2, n_lights=48, n_spheres=8, n_boxes=8)
+    rng = np.random.default_rng(1)
+    a, _ = O.kmeans_lights(sc.lights, rng.permutation(48)[:6], 8)
+    off, mem = O.cluster_table(a, 6)
+    gb = S.gbuffer_heightfield(seed=2, width=12, height=9)
+    V = O.visibility(gb.pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    T = O.cluster_targets(gb.pos, sc.lights, sc.spheres, sc.boxes, off, mem,
+                          np.arange(gb.n), 5, 3)
+    for y in range(6):
+        vm = V[:, mem[off[y]:off[y + 1]]]                    # members' visibilities
+        assert np.all((T[:, y][:, None] == vm).any(axis=1))
+    # over many frames a target averages to the cluster's mean visibility
+    y = int(np.argmax(np.diff(off)))
+    acc = np.zeros(gb.n)
+    F = 300
+    for f in range(F):
+        acc += O.cluster_targets(gb.pos, sc.lights, sc.spheres, sc.boxes, off, mem,
+                                 np.arange(gb.n), 5, f)[:, y]
+    mean_v = V[:, mem[off[y]:off[y + 1]]].mean(1)
+    sd = np.sqrt(np.maximum(mean_v * (1 - mean_v), 1e-12) / F)
+    assert np.all(np.abs(acc / F - mean_v) <= 5 * sd + 1e-12)
+
+
+def test_clustered_estimate_is_unbiased_by_exact_enumeration():
+    """E[V(x) c(x) W] over the cluster law, every uniform candidate tuple
+    and the pick law on it equals sum_x V_x c_x: the source pdf, the RIS
+    weight and both reservoirs agree (Section 3.6)."""
+    import itertools
+    sc = S.scene_heightfield(seed=9, n_lights=6, n_spheres=6, n_boxes=6)
+    assign = np.array([0, 1, 1, 2, 2, 2])
+    off, mem = O.cluster_table(assign, 3)
+    gb = S.gbuffer_heightfield(seed=9, width=6, height=4)
+    V = O.visibility(gb.pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    c32 = O.contributions(gb.pos, gb.nrm, sc.lights, np.float32)
+    vis = np.random.default_rng(3).uniform(0.1, 0.9, (gb.n, 3)).astype(np.float32)
+    chat = O.cluster_contributions(c32, off, mem)
+    w = O.light_weights_f32(vis, chat)
+    law = O.selection_law(w)
+    M = O.RIS_CANDIDATES
+    checked = 0
+    for p in range(gb.n):
+        wsum = np.float32(0)
+        for t in range(3):
+            wsum = np.float32(wsum + w[p, t])
+        E = 0.0
+        for y in range(3):
+            if law[p, y] == 0:
+                continue
+            ms = mem[off[y]:off[y + 1]]
+            for tup in itertools.product(ms, repeat=M):
+                cc = c32[p, list(tup)].astype(np.float32)
+                if not (cc > 0).any():
+                    continue
+                pick = O.selection_law(cc[None, :])[0]
+                for j in range(M):
+                    if pick[j] == 0:
+                        continue
+                    W = float(O.ris_weight(cc, np.int64(j), w[p, y], wsum, len(ms)))
+                    x = tup[j]
+                    E += law[p, y] * len(ms) ** -M * pick[j] * V[p, x] * float(c32[p, x]) * W
+        exact = float((V[p] * c32[p].astype(np.float64)).sum())
+        if exact > 0:
+            checked += 1
+        np.testing.assert_allclose(E, exact, rtol=2e-5, atol=1e-12)
+    assert checked >= 8
+    assert (V == 0).any()
+
+
+def test_sample_clustered_mean_estimate_converges_to_exact_di():
+    sc = S.scene_heightfield(seed=4, n_lights=24, n_spheres=8, n_boxes=8)
+    rng = np.random.default_rng(2)
+    a, _ = O.kmeans_lights(sc.lights, rng.permutation(24)[:5], 6)
+    off, mem = O.cluster_table(a, 5)
+    gb = S.gbuffer_heightfield(seed=4, width=8, height=6)
+    V = O.visibility(gb.pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    c32 = O.contributions(gb.pos, gb.nrm, sc.lights, np.float32)
+    vis = rng.uniform(0.2, 0.9, (gb.n, 5)).astype(np.float32)
+    F = 400
+    est = np.zeros((F, gb.n))
+    for f in range(F):
+        light, W = O.sample_clustered(vis, gb.pos, gb.nrm, sc.lights, off, mem,
+                                      np.arange(gb.n), 3, f, 0)
+        ok = light >= 0
+        x = np.maximum(light, 0)
+        est[f] = np.where(ok, V[np.arange(gb.n), x] * c32[np.arange(gb.n), x] * W, 0.0)
+    exact = (V * c32.astype(np.float64)).sum(1)
+    se = est.std(0) / np.sqrt(F)
+    assert np.all(np.abs(est.mean(0) - exact) <= 5 * se + 1e-9 * exact + 1e-12)
+    assert (exact > 0).mean() > 0.5
