@@ -44,7 +44,7 @@ extern "C" {
 #define NVC_MAX_FEATURES 8
 #define NVC_MAX_HIDDEN_LAYERS 8
 #define NVC_MAX_WIDTH 128
-#define NVC_MAX_LIGHTS 256
+#define NVC_MAX_LIGHTS 256      /* lights of a per-light cache (outputs); clustered calls take any number */
 #define NVC_MAX_OCCLUDERS 2048
 
 typedef enum nvc_status {
@@ -289,7 +289,7 @@ nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant);
  *     accum[p] = e                               for k = 1,
  *     accum[p] = accum[p] + (e - accum[p]) / k   otherwise (float32, each
  *                                                 step correctly rounded).
- * Asynchronous on `stream`. */
+ * The scene may hold any number of lights.  Asynchronous on `stream`. */
 nvc_status nvc_shade_estimate(const nvc_scene* scene, const float* pos, const float* nrm,
                               int64_t n, const int32_t* idx, const float* pdf, float* estimate,
                               float* accum, uint32_t count, void* stream);
@@ -298,9 +298,76 @@ nvc_status nvc_shade_estimate(const nvc_scene* scene, const float* pos, const fl
  * di[p] = sum over lights i in order of c_i for the unblocked ones (float32
  * additions in light order; c_i as in nvc_shade_estimate).  The brute-force
  * reference that the paper's Section 4.4 times against the cache's
- * inference.  pos, nrm device [n][3]; di device [n].  Asynchronous. */
+ * inference.  pos, nrm device [n][3]; di device [n].  Any number of
+ * lights: staged in shared memory when they fit beside the occluders,
+ * else read from global memory.  Asynchronous. */
 nvc_status nvc_exact_di(const nvc_scene* scene, const float* pos, const float* nrm, int64_t n,
                         float* di, void* stream);
+
+/* ---- clustered cache (Section 3.6) -------------------------------------- */
+
+/* Lights grouped into k clusters, in CSR form (device pointers): the members
+ * of cluster y are members[offsets[y] .. offsets[y + 1] - 1] (light indices
+ * into nvc_scene.lights, increasing).  The caller owns both arrays and
+ * keeps them valid: offsets[0] = 0, non-decreasing, offsets[k] = n_lights,
+ * every member in [0, n_lights).  The library does not read the table back
+ * to check it (that would cost a synchronisation per call); an invalid
+ * table makes the kernels read out of bounds.  With a clustered cache the
+ * configuration's n_outputs is k (at most 32) and each output is a
+ * cluster's average visibility; the scene may hold any number of lights. */
+typedef struct nvc_clusters {
+  int32_t k;
+  const int32_t* offsets;    /* [k + 1] */
+  const int32_t* members;    /* [n_lights] */
+} nvc_clusters;
+
+/* Lloyd's k-means of the light positions (host memory; Section 3.6), in
+ * float64: centroids start at the lights init[0..k-1]; each of `iters`
+ * iterations assigns every light to its nearest centroid (squared distance
+ * (dx^2 + dy^2) + dz^2, ties to the lower cluster) and moves each centroid to
+ * the mean of its members summed in light order (an empty cluster keeps its
+ * centroid); assign[i] (host [n]) is the final assignment; centroids (host
+ * [k][3], may be NULL) the final centroids.  Synchronous, host only. */
+nvc_status nvc_kmeans_lights(const float* lights, int32_t n_lights, const int32_t* init,
+                             int32_t k, int32_t iters, int32_t* assign, double* centroids);
+
+/* One training step of a clustered cache (Section 3.6): as nvc_train_step,
+ * but the target of output y at a training position is the binary
+ * visibility of one member of cluster y drawn uniformly (word y of the
+ * Philox stream (sample, frame, 0, tag 5)), so the network learns each
+ * cluster's average visibility.  clusters->k must equal n_outputs. */
+nvc_status nvc_train_step_clustered(nvc_handle* h, const nvc_scene* scene,
+                                    const nvc_clusters* clusters, const float* screen_pos,
+                                    int64_t n_screen, uint64_t seed, uint32_t frame,
+                                    double* loss_out, void* stream);
+
+/* Training targets of a clustered cache for given positions (device [n][3])
+ * into target (device [n][k]), sample ids 0..n-1: the data step of
+ * nvc_train_step_clustered.  Asynchronous. */
+nvc_status nvc_cluster_targets(const nvc_scene* scene, const nvc_clusters* clusters,
+                               const float* pos, int64_t n, uint64_t seed, uint32_t frame,
+                               float* target, void* stream);
+
+/* Two-step light sampling with a clustered cache (Section 3.6), per pixel:
+ *   1. c_hat_y = sum of the members' contributions (float32, member order),
+ *      w_y = max(vis[p][y], 0.001) c_hat_y, and cluster y picked by the
+ *      integer reservoir of nvc_wrs_sample (Philox tag 0, word y);
+ *   2. four members of y drawn uniformly (words 0-3 of tag 4), one kept by
+ *      the integer reservoir on their contributions (words 4-7), with the
+ *      unbiased contribution weight of streaming RIS
+ *        W = (sum_j c_j / 4) / (p(x) c(x)),  p(x) = (w_y / sum w) / m_y.
+ * vis: device [n][k], the cache's cluster visibilities (nvc_infer).
+ * light (device [n], -1 when nothing contributes), weight (W) and estimate
+ * (V(x) c(x) W with one shadow ray, 0 when blocked) may each be NULL.
+ * Pixel ids are pixel_offset + p.  The scene's lights are staged in shared
+ * memory when they fit beside the occluders (about 14,000 lights), else
+ * read from global memory; step 1 costs one contribution per light and
+ * pixel.  Asynchronous. */
+nvc_status nvc_sample_clustered(const nvc_scene* scene, const nvc_clusters* clusters,
+                                const float* vis, const float* pos, const float* nrm, int64_t n,
+                                int64_t pixel_offset, uint64_t seed, uint32_t frame,
+                                uint32_t view, int32_t* light, float* weight, float* estimate,
+                                void* stream);
 
 /* ---- training (Section 3.4) -------------------------------------------- */
 
@@ -311,7 +378,8 @@ nvc_status nvc_exact_di(const nvc_scene* scene, const float* pos, const float* n
 nvc_status nvc_trace_visibility(const nvc_scene* scene, const float* pos, int64_t n,
                                 float* vis, void* stream);
 
-/* Training positions (device [batch][3]): the first half (all of them when
+/* Training positions (device [batch][3]; the scene may hold any number of
+ * lights, only its world box is used): the first half (all of them when
  * screen_pos is NULL or n_screen = 0) uniform in the scene's world box,
  * x = lo + u * (hi - lo), u the top 24 bits of Philox stream
  * (j, frame, 0, 1) times 2^-24; the rest are G-buffer pixels

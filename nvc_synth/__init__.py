@@ -20,12 +20,13 @@ Conventions (identical for every consumer):
 from .configs import (NVCConfig, CONFIGS, config_by_name, param_layout,
                       param_count)
 from .scenes import (Scene, GBuffer, scene_unit_cube, scene_heightfield,
-                     gbuffer_points, gbuffer_heightfield, gbuffer_camera_path,
+                     scene_many_lights, scene_rooms, kmeans_init, gbuffer_points, gbuffer_heightfield, gbuffer_camera_path,
                      init_params, multiview_gbuffers)
 
 __all__ = [
     "NVCConfig", "CONFIGS", "config_by_name", "param_layout", "param_count",
     "Scene", "GBuffer", "scene_unit_cube", "scene_heightfield",
+    "scene_many_lights", "scene_rooms", "kmeans_init",
     "gbuffer_points", "gbuffer_heightfield", "gbuffer_camera_path",
     "init_params", "multiview_gbuffers",
 ]

@@ -159,6 +159,82 @@ def scene_heightfield(seed: int = 1, n_lights: int = 32, n_spheres: int = 32,
                  world_max=_f32([extent, extent, extent]))
 
 
+def scene_many_lights(seed: int = 1, n_lights: int = 1024, n_groups: int = 64,
+                      n_spheres: int = 32, n_boxes: int = 32,
+                      extent: float = 10.0) -> Scene:
+    """Many-lights variant of the heightfield scene: the occluders of
+    ``scene_heightfield(seed, n_lights=n_groups, ...)`` and ``n_lights``
+    point lights in ``n_groups`` fixtures, each fixture's lights spread
+    N(0, 0.25^2) per axis around the heightfield scene's light position
+    (clipped to x, y in [0, extent], z in [0.4 extent, extent]).  Intensities
+    U(20, 100) * 32 / n_lights keep the total power of 32 lights.  The
+    fixtures give the lights the grouped structure (lamps, strips) that
+    clustering exploits; the G-buffer is ``gbuffer_heightfield(seed)``."""
+    base = scene_heightfield(seed, n_lights=n_groups, n_spheres=n_spheres,
+                             n_boxes=n_boxes, extent=extent)
+    rng = np.random.Generator(np.random.PCG64([seed, 7]))
+    g = rng.integers(0, n_groups, n_lights)
+    p = base.lights[g, :3].astype(np.float64) + rng.normal(0.0, 0.25, (n_lights, 3))
+    p[:, :2] = np.clip(p[:, :2], 0.0, extent)
+    p[:, 2] = np.clip(p[:, 2], 0.4 * extent, extent)
+    li = rng.uniform(20.0, 100.0, (n_lights, 1)) * (32.0 / n_lights)
+    return Scene(lights=_f32(np.hstack([p, li])), spheres=base.spheres,
+                 boxes=base.boxes, world_min=base.world_min,
+                 world_max=base.world_max)
+
+
+def scene_rooms(seed: int = 1, n_lights: int = 1024, rooms: int = 4,
+                fixtures_per_room: int = 2, n_spheres: int = 32, n_boxes: int = 32,
+                extent: float = 10.0, wall: float = 0.08, door_width: float = 0.8,
+                door_height: float = 5.0) -> Scene:
+    """Interior of ``rooms`` x ``rooms`` rooms over the heightfield: the
+    occluders of ``scene_heightfield(seed, ...)`` plus full-height walls
+    (boxes ``wall`` thick on the lines x, y = i * extent / rooms) with a
+    doorway ``door_width`` wide and ``door_height`` high in the middle of
+    every room edge.  Each room has ``fixtures_per_room`` ceiling fixtures
+    (x, y uniform 0.3 inside the room, z U(7, 9.5)); every light joins a
+    uniformly drawn fixture with an N(0, 0.15^2) offset per axis (clipped
+    0.1 inside its room, z in [4, 9.9]), intensity U(20, 100) * 32 / n_lights.
+    Lights of other rooms are seen only through doorways: the many-rooms
+    structure clustering exploits.  G-buffer: ``gbuffer_heightfield(seed)``."""
+    base = scene_heightfield(seed, n_lights=1, n_spheres=n_spheres,
+                             n_boxes=n_boxes, extent=extent)
+    rng = np.random.Generator(np.random.PCG64([seed, 13]))
+    s = extent / rooms
+    n_fix = rooms * rooms * fixtures_per_room
+    room = np.repeat(np.arange(rooms * rooms), fixtures_per_room)
+    rx, ry = (room % rooms) * s, (room // rooms) * s
+    fx = rx + rng.uniform(0.3, s - 0.3, n_fix)
+    fy = ry + rng.uniform(0.3, s - 0.3, n_fix)
+    fz = rng.uniform(7.0, 9.5, n_fix)
+    g = rng.integers(0, n_fix, n_lights)
+    p = np.stack([fx[g], fy[g], fz[g]], 1) + rng.normal(0.0, 0.15, (n_lights, 3))
+    p[:, 0] = np.clip(p[:, 0], rx[g] + 0.1, rx[g] + s - 0.1)
+    p[:, 1] = np.clip(p[:, 1], ry[g] + 0.1, ry[g] + s - 0.1)
+    p[:, 2] = np.clip(p[:, 2], 4.0, 9.9)
+    li = rng.uniform(20.0, 100.0, (n_lights, 1)) * (32.0 / n_lights)
+    t, hw = 0.5 * wall, 0.5 * door_width
+    walls = []
+    for i in range(1, rooms):
+        c = i * s
+        for b in range(rooms):
+            a0, a1, m = b * s, (b + 1) * s, (b + 0.5) * s
+            for lo, hi in ((a0, m - hw), (m + hw, a1)):
+                walls.append([c - t, lo, 0.0, c + t, hi, extent])     # wall along y
+                walls.append([lo, c - t, 0.0, hi, c + t, extent])     # wall along x
+            walls.append([c - t, m - hw, door_height, c + t, m + hw, extent])
+            walls.append([m - hw, c - t, door_height, m + hw, c + t, extent])
+    return Scene(lights=_f32(np.hstack([p, li])), spheres=base.spheres,
+                 boxes=_f32(np.vstack([base.boxes, np.asarray(walls)])),
+                 world_min=base.world_min, world_max=base.world_max)
+
+
+def kmeans_init(n_lights: int, k: int, seed: int = 0) -> np.ndarray:
+    """k distinct light indices drawn uniformly: the seeds of k-means."""
+    rng = np.random.Generator(np.random.PCG64([seed, 11]))
+    return rng.choice(n_lights, k, replace=False).astype(np.int32)
+
+
 def gbuffer_heightfield(seed: int = 1, width: int = 1920, height: int = 1080,
                         extent: float = 10.0, window=None) -> GBuffer:
     """Orthographic top-down view of the heightfield + boxes.

@@ -47,6 +47,10 @@ class NvcScene(Structure):
         ("world_min", c_float * 3), ("world_max", c_float * 3)]
 
 
+class NvcClusters(Structure):
+    _fields_ = [("k", c_int32), ("offsets", c_void_p), ("members", c_void_p)]
+
+
 class NvcCounters(Structure):
     _fields_ = [("step", c_int32), ("skipped", c_int32), ("error_flags", c_int32),
                 ("frames", c_int32)]
@@ -60,6 +64,7 @@ class NvcView(Structure):
 
 _cfgp = POINTER(NvcConfig)
 _scp = POINTER(NvcScene)
+_clp = POINTER(NvcClusters)
 _vp = c_void_p
 
 PROTOTYPES = {
@@ -102,6 +107,12 @@ PROTOTYPES = {
     "nvc_host_frames_wait": (c_int32, [_vp, _vp]),
     "nvc_shade_estimate": (c_int32, [_scp, _vp, _vp, c_int64, _vp, _vp, _vp, _vp, c_uint32, _vp]),
     "nvc_exact_di": (c_int32, [_scp, _vp, _vp, c_int64, _vp, _vp]),
+    "nvc_kmeans_lights": (c_int32, [_vp, c_int32, _vp, c_int32, c_int32, _vp, _vp]),
+    "nvc_train_step_clustered": (c_int32, [_vp, _scp, _clp, _vp, c_int64, c_uint64, c_uint32,
+                                           _vp, _vp]),
+    "nvc_cluster_targets": (c_int32, [_scp, _clp, _vp, c_int64, c_uint64, c_uint32, _vp, _vp]),
+    "nvc_sample_clustered": (c_int32, [_scp, _clp, _vp, _vp, _vp, c_int64, c_int64, c_uint64,
+                                       c_uint32, c_uint32, _vp, _vp, _vp, _vp]),
     "nvc_infer_noalloc": (c_int32, [_cfgp, _vp, _vp, c_int64, _vp, _vp]),
     "nvc_set_profiling": (c_int32, [_vp, c_int32]),
     "nvc_stage_times": (c_int32, [_vp, POINTER(c_double), c_int32, POINTER(c_int64)]),

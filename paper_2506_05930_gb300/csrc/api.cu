@@ -85,11 +85,18 @@ nvc_status check_config(const nvc_config* c, std::string* why) {
   return NVC_OK;
 }
 
-nvc_status check_scene(nvc_handle* h, const nvc_scene* sc, int expect_lights) {
+// Scene checks.  Calls with a per-light output or network neuron take at
+// most NVC_MAX_LIGHTS lights; those that only loop over the lights (the
+// clustered cache, the shading estimate, the exact DI, the training
+// positions) pass kAnyLights.
+constexpr int kAnyLights = 0x7fffffff;
+
+nvc_status check_scene(nvc_handle* h, const nvc_scene* sc, int expect_lights,
+                       int max_lights = NVC_MAX_LIGHTS) {
   if (!sc) return fail(h, NVC_ERR_INVALID_ARG, "scene is NULL");
   if (!sc->lights || !aligned(sc->lights, 16))
     return fail(h, NVC_ERR_INVALID_ARG, "scene lights NULL or not 16-byte aligned");
-  if (sc->n_lights < 1 || sc->n_lights > NVC_MAX_LIGHTS)
+  if (sc->n_lights < 1 || sc->n_lights > max_lights)
     return fail(h, NVC_ERR_INVALID_ARG, "n_lights out of range");
   if (expect_lights > 0 && sc->n_lights != expect_lights)
     return fail(h, NVC_ERR_INVALID_ARG, "n_lights (%d) != n_outputs (%d)", sc->n_lights,
@@ -715,7 +722,7 @@ static cudaError_t current_sms(int* n) {
 nvc_status nvc_shade_estimate(const nvc_scene* scene, const float* pos, const float* nrm,
                               int64_t n, const int32_t* idx, const float* pdf, float* estimate,
                               float* accum, uint32_t count, void* stream) {
-  NVC_TRY(check_scene(nullptr, scene, 0));
+  NVC_TRY(check_scene(nullptr, scene, 0, kAnyLights));
   if (n < 0) return fail(nullptr, NVC_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return NVC_OK;
   NVC_TRY(check_ptr(nullptr, pos, "pos"));
@@ -737,7 +744,7 @@ nvc_status nvc_shade_estimate(const nvc_scene* scene, const float* pos, const fl
 
 nvc_status nvc_exact_di(const nvc_scene* scene, const float* pos, const float* nrm, int64_t n,
                         float* di, void* stream) {
-  NVC_TRY(check_scene(nullptr, scene, 0));
+  NVC_TRY(check_scene(nullptr, scene, 0, kAnyLights));
   if (n < 0) return fail(nullptr, NVC_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return NVC_OK;
   NVC_TRY(check_ptr(nullptr, pos, "pos"));
@@ -752,7 +759,7 @@ nvc_status nvc_exact_di(const nvc_scene* scene, const float* pos, const float* n
 nvc_status nvc_training_positions(const nvc_scene* scene, const float* screen_pos,
                                   int64_t n_screen, int64_t batch, uint64_t seed, uint32_t frame,
                                   float* pos, void* stream) {
-  NVC_TRY(check_scene(nullptr, scene, 0));
+  NVC_TRY(check_scene(nullptr, scene, 0, kAnyLights));
   if (batch < 0 || n_screen < 0 || n_screen > ((int64_t)1 << 32))
     return fail(nullptr, NVC_ERR_INVALID_ARG, "batch or n_screen out of range");
   if (batch > ((int64_t)1 << 32)) return fail(nullptr, NVC_ERR_INVALID_ARG, "batch above 2^32");
@@ -768,14 +775,22 @@ nvc_status nvc_training_positions(const nvc_scene* scene, const float* screen_po
 // scale); positions are generated unless `given_pos` is set.
 static nvc_status train_forward_backward(nvc_handle* h, const nvc_scene* scene,
                                          const float* screen_pos, int64_t n_screen,
-                                         uint64_t seed, uint32_t frame, cudaStream_t s) {
+                                         uint64_t seed, uint32_t frame, cudaStream_t s,
+                                         const nvc_clusters* clusters = nullptr) {
   const int64_t B = h->B;
   {
     StageScope sc(h, s, 0);
-    // positions and their shadow-ray targets in one kernel
-    NVC_CUDA(h, launch_training_data(scene, screen_pos, n_screen, B, seed, frame, h->t_pos,
-                                     h->t_target, s));
-    count_launches(h, 1);
+    if (clusters) {
+      // positions, then one member's visibility per cluster (Section 3.6)
+      NVC_CUDA(h, launch_training_positions(scene, screen_pos, n_screen, B, seed, frame, h->t_pos, s));
+      NVC_CUDA(h, launch_cluster_targets(scene, clusters, h->t_pos, B, seed, frame, h->t_target, s));
+      count_launches(h, 2);
+    } else {
+      // positions and their shadow-ray targets in one kernel
+      NVC_CUDA(h, launch_training_data(scene, screen_pos, n_screen, B, seed, frame, h->t_pos,
+                                       h->t_target, s));
+      count_launches(h, 1);
+    }
   }
   StageScope sc(h, s, 1);
   if (h->cfg.train_precision == NVC_PREC_FP16) {
@@ -807,8 +822,9 @@ static nvc_status train_checks(nvc_handle* h, const nvc_scene* scene, const floa
 
 static nvc_status train_step_impl(nvc_handle* h, const nvc_scene* scene, const float* screen_pos,
                                   int64_t n_screen, uint64_t seed, uint32_t frame,
-                                  double* loss_out, cudaStream_t s) {
-  NVC_TRY(train_forward_backward(h, scene, screen_pos, n_screen, seed, frame, s));
+                                  double* loss_out, cudaStream_t s,
+                                  const nvc_clusters* clusters = nullptr) {
+  NVC_TRY(train_forward_backward(h, scene, screen_pos, n_screen, seed, frame, s, clusters));
   StageScope sc(h, s, 2);
   NVC_CUDA(h, launch_adam(h, loss_out, true, s));
   NVC_CUDA(h, launch_pack_mlp(h, s));
@@ -823,6 +839,87 @@ nvc_status nvc_train_step(nvc_handle* h, const nvc_scene* scene, const float* sc
   if (loss_out) NVC_TRY(check_ptr(h, loss_out, "loss_out", 8));
   return train_step_impl(h, scene, screen_pos, n_screen, seed, frame, loss_out,
                          (cudaStream_t)stream);
+}
+
+static nvc_status check_clusters(nvc_handle* h, const nvc_scene* scene, const nvc_clusters* cl,
+                                 int expect_k) {
+  if (!cl) return fail(h, NVC_ERR_INVALID_ARG, "clusters is NULL");
+  if (cl->k < 1 || cl->k > 32) return fail(h, NVC_ERR_INVALID_ARG, "clusters: k must be 1..32");
+  if (expect_k > 0 && cl->k != expect_k)
+    return fail(h, NVC_ERR_INVALID_ARG, "clusters: k must equal n_outputs");
+  if (!cl->offsets || !cl->members) return fail(h, NVC_ERR_INVALID_ARG, "clusters: NULL table");
+  NVC_TRY(check_ptr(h, cl->offsets, "clusters.offsets"));
+  NVC_TRY(check_ptr(h, cl->members, "clusters.members"));
+  if (scene->n_lights < 1) return fail(h, NVC_ERR_INVALID_ARG, "clustered scene without lights");
+  return NVC_OK;
+}
+
+nvc_status nvc_kmeans_lights(const float* lights, int32_t n_lights, const int32_t* init,
+                             int32_t k, int32_t iters, int32_t* assign, double* centroids) {
+  if (!lights || !init || !assign) return fail(nullptr, NVC_ERR_INVALID_ARG, "NULL argument");
+  if (n_lights < 1 || k < 1 || k > n_lights || iters < 0)
+    return fail(nullptr, NVC_ERR_INVALID_ARG, "need 1 <= k <= n_lights and iters >= 0");
+  for (int y = 0; y < k; ++y)
+    if (init[y] < 0 || init[y] >= n_lights)
+      return fail(nullptr, NVC_ERR_INVALID_ARG, "init[%d] out of range", y);
+  kmeans_host(lights, n_lights, init, k, iters, assign, centroids);
+  return NVC_OK;
+}
+
+nvc_status nvc_train_step_clustered(nvc_handle* h, const nvc_scene* scene,
+                                    const nvc_clusters* clusters, const float* screen_pos,
+                                    int64_t n_screen, uint64_t seed, uint32_t frame,
+                                    double* loss_out, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  NVC_TRY(check_scene(h, scene, 0, kAnyLights));
+  NVC_TRY(check_clusters(h, scene, clusters, h->L));
+  if (n_screen < 0 || n_screen > ((int64_t)1 << 32))
+    return fail(h, NVC_ERR_INVALID_ARG, "n_screen out of range");
+  if (n_screen > 0 && screen_pos) NVC_TRY(check_ptr(h, screen_pos, "screen_pos"));
+  if (loss_out) NVC_TRY(check_ptr(h, loss_out, "loss_out", 8));
+  return train_step_impl(h, scene, screen_pos, n_screen, seed, frame, loss_out,
+                         (cudaStream_t)stream, clusters);
+}
+
+nvc_status nvc_cluster_targets(const nvc_scene* scene, const nvc_clusters* clusters,
+                               const float* pos, int64_t n, uint64_t seed, uint32_t frame,
+                               float* target, void* stream) {
+  NVC_TRY(check_scene(nullptr, scene, 0, kAnyLights));
+  NVC_TRY(check_clusters(nullptr, scene, clusters, 0));
+  if (n < 0) return fail(nullptr, NVC_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(nullptr, pos, "pos"));
+  NVC_TRY(check_ptr(nullptr, target, "target"));
+  NVC_CUDA(nullptr, launch_cluster_targets(scene, clusters, pos, n, seed, frame, target,
+                                           (cudaStream_t)stream));
+  return NVC_OK;
+}
+
+nvc_status nvc_sample_clustered(const nvc_scene* scene, const nvc_clusters* clusters,
+                                const float* vis, const float* pos, const float* nrm, int64_t n,
+                                int64_t pixel_offset, uint64_t seed, uint32_t frame,
+                                uint32_t view, int32_t* light, float* weight, float* estimate,
+                                void* stream) {
+  NVC_TRY(check_scene(nullptr, scene, 0, kAnyLights));
+  NVC_TRY(check_clusters(nullptr, scene, clusters, 0));
+  if (n < 0 || pixel_offset < 0 || pixel_offset + n > ((int64_t)1 << 32))
+    return fail(nullptr, NVC_ERR_INVALID_ARG, "n or pixel ids out of range");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(nullptr, vis, "vis"));
+  NVC_TRY(check_ptr(nullptr, pos, "pos"));
+  NVC_TRY(check_ptr(nullptr, nrm, "nrm"));
+  if (!light && !weight && !estimate) return fail(nullptr, NVC_ERR_INVALID_ARG, "no output");
+  if (light) NVC_TRY(check_ptr(nullptr, light, "light"));
+  if (weight) NVC_TRY(check_ptr(nullptr, weight, "weight"));
+  if (estimate) NVC_TRY(check_ptr(nullptr, estimate, "estimate"));
+  if (sample_clustered_smem(scene) > 227 * 1024)
+    return fail(nullptr, NVC_ERR_UNSUPPORTED, "too many occluders for shared memory");
+  int sms = 0;
+  NVC_CUDA(nullptr, current_sms(&sms));
+  NVC_CUDA(nullptr, launch_sample_clustered(scene, clusters, vis, pos, nrm, n, pixel_offset, seed,
+                                            frame, view, light, weight, estimate, sms,
+                                            (cudaStream_t)stream));
+  return NVC_OK;
 }
 
 nvc_status nvc_train_gradient(nvc_handle* h, const nvc_scene* scene, const float* screen_pos,

@@ -1,0 +1,305 @@
+// Clustered neural visibility cache (Section 3.6 of the paper): the lights
+// are grouped by k-means, the network's outputs are the clusters' average
+// visibilities, and a light is sampled in two steps -- a weighted reservoir
+// over the clusters, then streaming resampled importance sampling (RIS)
+// among a few members of the chosen cluster.
+//
+// k-means runs on the host in float64 (Lloyd's iterations from given seed
+// lights).  On the device:
+//   cluster_targets_kernel   training targets: for each (position, cluster)
+//                            the binary visibility of one member drawn
+//                            uniformly, so the network learns the average;
+//   sample_clustered_kernel  per pixel: c_hat_y = sum of the members'
+//                            contributions, w_y = max(v_y, 0.001) c_hat_y,
+//                            the integer reservoir over the clusters, then
+//                            kRis uniform members of cluster y, one kept by
+//                            the integer reservoir on their contributions,
+//                            and its unbiased contribution weight
+//                            W = (sum_j c_j / M) / (p(x) c(x)),
+//                            p(x) = (w(y) / w_sum) / m_y.
+// Every float32 result is rounded in a fixed order and every random choice
+// is a fixed Philox word, so both kernels are reproducible bit for bit.
+#include <vector>
+
+#include "nvc_internal.cuh"
+#include "shadow.cuh"
+
+namespace nvc {
+
+namespace {
+
+constexpr uint32_t kTagRis = 4;       // candidates in the chosen cluster and their pick
+constexpr uint32_t kTagCluster = 5;   // a member light per cluster for the training targets
+constexpr int kRis = 4;               // RIS candidates
+constexpr int kMaxClusters = 32;
+
+// Word i of the stream (id, frame, view, tag).
+__device__ __forceinline__ uint32_t stream_word(uint32_t id, uint32_t frame, uint32_t view,
+                                                uint32_t tag, int i, uint32_t k0, uint32_t k1) {
+  const uint4 r = philox4x32_10(make_uint4(id, frame, view, ((uint32_t)(i >> 2) << 4) | tag), k0, k1);
+  const int l = i & 3;
+  return l == 0 ? r.x : l == 1 ? r.y : l == 2 ? r.z : r.w;
+}
+
+// Member of cluster y chosen by the word r: floor(r m_y / 2^32).
+__device__ __forceinline__ int member_of(const int32_t* off, const int32_t* mem, int y, uint32_t r) {
+  const uint32_t m = (uint32_t)(off[y + 1] - off[y]);
+  return mem[off[y] + (int)(((uint64_t)r * m) >> 32)];
+}
+
+__global__ void __launch_bounds__(256) cluster_targets_kernel(
+    const float* __restrict__ lights, const float* __restrict__ spheres, int n_sph,
+    const float* __restrict__ boxes, int n_box, const int32_t* __restrict__ off,
+    const int32_t* __restrict__ mem, int k, const float* __restrict__ pos, int64_t n,
+    uint32_t k0, uint32_t k1, uint32_t frame, float* __restrict__ target) {
+  extern __shared__ float s_occ[];
+  float4* s_sph = reinterpret_cast<float4*>(s_occ);
+  float* s_box = s_occ + 4 * n_sph;
+  for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
+    s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
+  for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int64_t b = t / k;
+  const int y = (int)(t - b * k);
+  float v = 0.0f;
+  if (off[y + 1] > off[y]) {
+    const int x = member_of(off, mem, y, stream_word((uint32_t)b, frame, 0u, kTagCluster, y, k0, k1));
+    const float4 l = reinterpret_cast<const float4*>(lights)[x];
+    const float px = pos[3 * b], py = pos[3 * b + 1], pz = pos[3 * b + 2];
+    v = segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box) ? 0.0f : 1.0f;
+  }
+  target[t] = v;
+}
+
+// Integer reservoir over the first n of N float32 weights w (>= 0) with the
+// words r_i: candidate i replaces the pick when r_i Q_i < q_i 2^32, Q_i the
+// running sum of the quantised weights (< 2^32).  Loops run over N so the
+// arrays stay in registers.
+template <int N>
+__device__ __forceinline__ int integer_reservoir(const float (&w)[N], int n, const uint32_t (&r)[N]) {
+  float wmax = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) wmax = fmaxf(wmax, w[i]);
+  if (!(wmax > 0.0f)) return -1;
+  const int e = ilogbf(wmax);
+  uint32_t Q = 0;
+  int sel = -1;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (i < n) {
+      const uint32_t q = quantize_weight(w[i], e);
+      Q += q;
+      if (q > 0u && __umulhi(r[i], Q) < q) sel = i;
+    }
+  }
+  return sel;
+}
+
+// Light e with I / pi in .w: from the shared copy, or from global memory
+// (scaled here, the same rounding) when the lights do not fit on chip.
+template <bool kSmemLights>
+__device__ __forceinline__ float4 light_at(const float4* s_lt, const float* lights, int e) {
+  if (kSmemLights) return s_lt[e];
+  float4 l = __ldg(reinterpret_cast<const float4*>(lights) + e);
+  l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+  return l;
+}
+
+template <bool kSmemLights>
+__global__ void __launch_bounds__(128) sample_clustered_kernel(
+    const float* __restrict__ lights, int n_lights, const float* __restrict__ spheres, int n_sph,
+    const float* __restrict__ boxes, int n_box, const int32_t* __restrict__ off,
+    const int32_t* __restrict__ mem, int k, const float* __restrict__ vis,
+    const float* __restrict__ pos, const float* __restrict__ nrm, int64_t n,
+    int64_t pixel_offset, uint32_t k0, uint32_t k1, uint32_t frame, uint32_t view,
+    int32_t* __restrict__ light_out, float* __restrict__ weight_out, float* __restrict__ estimate) {
+  extern __shared__ float s_scene[];
+  const int n_lt_s = kSmemLights ? n_lights : 0;
+  float4* s_lt = reinterpret_cast<float4*>(s_scene);
+  float4* s_sph = s_lt + n_lt_s;
+  float* s_box = reinterpret_cast<float*>(s_sph + n_sph);
+  for (int e = threadIdx.x; e < n_lt_s; e += blockDim.x) {
+    float4 l = reinterpret_cast<const float4*>(lights)[e];
+    l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+    s_lt[e] = l;
+  }
+  for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
+    s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
+  for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
+  __syncthreads();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
+    const float nx = nrm[3 * p], ny = nrm[3 * p + 1], nz = nrm[3 * p + 2];
+    const uint32_t pixel = (uint32_t)(pixel_offset + p);
+    // step 1: the clusters' weights and the reservoir over them
+    float w[kMaxClusters];
+    uint32_t r[kMaxClusters];
+    float wsum = 0.0f;
+#pragma unroll
+    for (int y = 0; y < kMaxClusters; ++y) {
+      w[y] = 0.0f;
+      r[y] = 0u;
+      if (y < k) {
+        float ch = 0.0f;
+        const int end = off[y + 1];
+        for (int i = off[y]; i < end; ++i) {
+          const float4 l = light_at<kSmemLights>(s_lt, lights, mem[i]);
+          ch = __fadd_rn(ch, contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w));
+        }
+        w[y] = __fmul_rn(fmaxf(vis[p * k + y], bits_f(kVisClampBits)), ch);
+        wsum = __fadd_rn(wsum, w[y]);
+        r[y] = stream_word(pixel, frame, view, kTagWrs, y, k0, k1);
+      }
+    }
+    const int y = integer_reservoir(w, k, r);
+    int sel_light = -1;
+    float W = 0.0f, cx = 0.0f;
+    if (y >= 0) {
+      float w_y = 0.0f;
+#pragma unroll
+      for (int t = 0; t < kMaxClusters; ++t)
+        if (t == y) w_y = w[t];
+      // step 2: streaming RIS among kRis uniform members of cluster y
+      const int m_y = off[y + 1] - off[y];
+      int cand[kRis];
+      float cc[kRis];
+      uint32_t rr[kRis];
+#pragma unroll
+      for (int t = 0; t < kRis; ++t) {
+        cand[t] = member_of(off, mem, y, stream_word(pixel, frame, view, kTagRis, t, k0, k1));
+        const float4 l = light_at<kSmemLights>(s_lt, lights, cand[t]);
+        cc[t] = contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w);
+        rr[t] = stream_word(pixel, frame, view, kTagRis, kRis + t, k0, k1);
+      }
+      const int j = integer_reservoir(cc, kRis, rr);
+      if (j >= 0) {
+        float s = 0.0f;
+#pragma unroll
+        for (int t = 0; t < kRis; ++t) s = __fadd_rn(s, cc[t]);
+        float c_j = 0.0f;
+        int x_j = -1;
+#pragma unroll
+        for (int t = 0; t < kRis; ++t)
+          if (t == j) {
+            c_j = cc[t];
+            x_j = cand[t];
+          }
+        const float mean = __fdiv_rn(s, (float)kRis);
+        const float pr = __fdiv_rn(__fdiv_rn(w_y, wsum), (float)m_y);
+        W = __fdiv_rn(mean, __fmul_rn(pr, c_j));
+        sel_light = x_j;
+        cx = c_j;
+      }
+    }
+    if (light_out) light_out[p] = sel_light;
+    if (weight_out) weight_out[p] = W;
+    if (estimate) {
+      float e = 0.0f;
+      if (sel_light >= 0) {
+        const float4 l = light_at<kSmemLights>(s_lt, lights, sel_light);
+        if (!segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box))
+          e = __fmul_rn(cx, W);
+      }
+      estimate[p] = e;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_cluster_targets(const nvc_scene* sc, const nvc_clusters* cl, const float* pos,
+                                   int64_t n, uint64_t seed, uint32_t frame, float* target,
+                                   cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t total = n * cl->k;
+  const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  cluster_targets_kernel<<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
+      sc->lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes, cl->offsets, cl->members,
+      cl->k, pos, n, (uint32_t)seed, (uint32_t)(seed >> 32), frame, target);
+  return cudaGetLastError();
+}
+
+// Shared memory of the sampler: the occluders, plus the lights when they fit
+// in the 227 KB a block may opt into (about 14,000 lights); beyond that the
+// lights are read through the read-only cache.
+constexpr size_t kSmemOptin = 227 * 1024;
+
+size_t sample_clustered_smem(const nvc_scene* sc) {
+  const size_t occ = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  const size_t lt = sizeof(float) * 4 * (size_t)sc->n_lights;
+  return occ + lt <= kSmemOptin ? occ + lt : occ;
+}
+
+cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl, const float* vis,
+                                    const float* pos, const float* nrm, int64_t n,
+                                    int64_t pixel_offset, uint64_t seed, uint32_t frame,
+                                    uint32_t view, int32_t* light, float* weight, float* estimate,
+                                    int num_sms, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const size_t smem = sample_clustered_smem(sc);
+  const bool lights_on_chip =
+      smem == sizeof(float) * (4 * (size_t)sc->n_lights + 4 * (size_t)sc->n_spheres +
+                               6 * (size_t)sc->n_boxes);
+  auto kern = lights_on_chip ? sample_clustered_kernel<true> : sample_clustered_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t want = (n + 127) / 128;
+  const int64_t cap = (int64_t)num_sms * 8;
+  const int grid = (int)(want < cap ? want : cap);
+  kern<<<grid, 128, smem, s>>>(sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes,
+                               sc->n_boxes, cl->offsets, cl->members, cl->k, vis, pos, nrm, n,
+                               pixel_offset, (uint32_t)seed, (uint32_t)(seed >> 32), frame, view,
+                               light, weight, estimate);
+  return cudaGetLastError();
+}
+
+// Lloyd's k-means in float64, the same steps as the oracle: squared
+// distances (dx^2 + dy^2) + dz^2, the first nearest centroid, centroids the
+// mean of their members summed in light order, empty clusters unchanged.
+void kmeans_host(const float* lights, int n, const int32_t* init, int k, int iters,
+                 int32_t* assign, double* centroids_out) {
+  std::vector<double> C(3 * (size_t)k);
+  for (int y = 0; y < k; ++y)
+    for (int d = 0; d < 3; ++d) C[3 * y + d] = (double)lights[4 * (size_t)init[y] + d];
+  auto assign_all = [&]() {
+    for (int i = 0; i < n; ++i) {
+      double best = 0.0;
+      int arg = 0;
+      for (int y = 0; y < k; ++y) {
+        const double dx = (double)lights[4 * (size_t)i] - C[3 * y];
+        const double dy = (double)lights[4 * (size_t)i + 1] - C[3 * y + 1];
+        const double dz = (double)lights[4 * (size_t)i + 2] - C[3 * y + 2];
+        const double d2 = (dx * dx + dy * dy) + dz * dz;
+        if (y == 0 || d2 < best) {
+          best = d2;
+          arg = y;
+        }
+      }
+      assign[i] = arg;
+    }
+  };
+  std::vector<double> S(3 * (size_t)k);
+  std::vector<int> cnt((size_t)k);
+  for (int it = 0; it < iters; ++it) {
+    assign_all();
+    std::fill(S.begin(), S.end(), 0.0);
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int i = 0; i < n; ++i) {
+      const int y = assign[i];
+      for (int d = 0; d < 3; ++d) S[3 * y + d] = S[3 * y + d] + (double)lights[4 * (size_t)i + d];
+      ++cnt[y];
+    }
+    for (int y = 0; y < k; ++y)
+      if (cnt[y] > 0)
+        for (int d = 0; d < 3; ++d) C[3 * y + d] = S[3 * y + d] / (double)cnt[y];
+  }
+  assign_all();
+  if (centroids_out)
+    for (size_t i = 0; i < C.size(); ++i) centroids_out[i] = C[i];
+}
+
+}  // namespace nvc

@@ -305,6 +305,18 @@ cudaError_t launch_shade_estimate(const nvc_scene* sc, const float* pos, const f
                                   cudaStream_t s);
 cudaError_t launch_exact_di(const nvc_scene* sc, const float* pos, const float* nrm, int64_t n,
                             float* di, int num_sms, cudaStream_t s);
+// Clustered cache (clusters.cu).
+cudaError_t launch_cluster_targets(const nvc_scene* sc, const nvc_clusters* cl, const float* pos,
+                                   int64_t n, uint64_t seed, uint32_t frame, float* target,
+                                   cudaStream_t s);
+size_t sample_clustered_smem(const nvc_scene* sc);
+cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl, const float* vis,
+                                    const float* pos, const float* nrm, int64_t n,
+                                    int64_t pixel_offset, uint64_t seed, uint32_t frame,
+                                    uint32_t view, int32_t* light, float* weight, float* estimate,
+                                    int num_sms, cudaStream_t s);
+void kmeans_host(const float* lights, int n, const int32_t* init, int k, int iters,
+                 int32_t* assign, double* centroids_out);
 // Training positions and their shadow-ray targets in one launch (the same
 // values as launch_training_positions followed by launch_trace_visibility).
 cudaError_t launch_training_data(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,

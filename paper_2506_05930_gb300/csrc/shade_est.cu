@@ -71,22 +71,33 @@ __global__ void __launch_bounds__(256) shade_estimate_kernel(
   }
 }
 
+// kSmemLights: the lights (with I / pi) are staged after the spheres;
+// otherwise they are read through the read-only cache and scaled here (the
+// same rounding), for scenes whose lights do not fit on chip.
+template <bool kSmemLights>
 __global__ void __launch_bounds__(256) exact_di_kernel(
     const float* __restrict__ lights, int L, const float* __restrict__ spheres, int n_sph,
     const float* __restrict__ boxes, int n_box, const float* __restrict__ pos,
     const float* __restrict__ nrm, int64_t n, float* __restrict__ di) {
   extern __shared__ float s_scene[];
-  stage_scene(s_scene, spheres, n_sph, boxes, n_box, lights, L);
+  const int L_s = kSmemLights ? L : 0;
+  stage_scene(s_scene, spheres, n_sph, boxes, n_box, lights, L_s);
   const float4* s_sph = reinterpret_cast<const float4*>(s_scene);
   const float4* s_lt = reinterpret_cast<const float4*>(s_scene + 4 * n_sph);
-  const float* s_box = s_scene + 4 * n_sph + 4 * L;
+  const float* s_box = s_scene + 4 * n_sph + 4 * L_s;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
     const float nx = nrm[3 * p], ny = nrm[3 * p + 1], nz = nrm[3 * p + 2];
     float sum = 0.0f;
     for (int i = 0; i < L; ++i) {
-      const float4 l = s_lt[i];
+      float4 l;
+      if (kSmemLights) {
+        l = s_lt[i];
+      } else {
+        l = __ldg(reinterpret_cast<const float4*>(lights) + i);
+        l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+      }
       const float c = contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w);
       if (c > 0.0f && !segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box))
         sum = __fadd_rn(sum, c);
@@ -118,11 +129,16 @@ cudaError_t launch_shade_estimate(const nvc_scene* sc, const float* pos, const f
 cudaError_t launch_exact_di(const nvc_scene* sc, const float* pos, const float* nrm, int64_t n,
                             float* di, int num_sms, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 4 * (size_t)sc->n_lights +
-                                       6 * (size_t)sc->n_boxes);
-  exact_di_kernel<<<grid_for(n, num_sms), 256, smem, s>>>(sc->lights, sc->n_lights, sc->spheres,
-                                                          sc->n_spheres, sc->boxes, sc->n_boxes,
-                                                          pos, nrm, n, di);
+  const size_t occ = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  const size_t lt = sizeof(float) * 4 * (size_t)sc->n_lights;
+  const bool on_chip = occ + lt <= 227 * 1024;
+  const size_t smem = on_chip ? occ + lt : occ;
+  auto kern = on_chip ? exact_di_kernel<true> : exact_di_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid_for(n, num_sms), 256, smem, s>>>(sc->lights, sc->n_lights, sc->spheres,
+                                               sc->n_spheres, sc->boxes, sc->n_boxes, pos, nrm,
+                                               n, di);
   return cudaGetLastError();
 }
 

@@ -15,7 +15,7 @@ from typing import Optional, Sequence
 import torch
 
 from . import _lib
-from ._lib import NvcConfig, NvcCounters, NvcScene, NvcView, NVCError, check
+from ._lib import NvcClusters, NvcConfig, NvcCounters, NvcScene, NvcView, NVCError, check
 
 lib = _lib.load()
 
@@ -359,6 +359,62 @@ def nvc_exact_di(scene: Scene, pos, nrm, di, stream=None):
     """Sum over all lights of V_i c_i, one shadow ray per (pixel, light)."""
     check(lib.nvc_exact_di(scene.ref, _ptr(pos, name="pos"), _ptr(nrm, name="nrm"), pos.shape[0],
                            _ptr(di, name="di"), _stream(stream)))
+
+
+def nvc_kmeans_lights(lights, init, iters):
+    """Lloyd's k-means of the light positions (host, float64) from the seed
+    lights `init`; returns (assign int32 [n], centroids float64 [k, 3])."""
+    import numpy as np
+    L = np.ascontiguousarray(np.asarray(lights, np.float32).reshape(-1, 4))
+    init = np.ascontiguousarray(np.asarray(init, np.int32))
+    assign = np.empty(L.shape[0], np.int32)
+    cent = np.empty((init.shape[0], 3), np.float64)
+    check(lib.nvc_kmeans_lights(L.ctypes.data, L.shape[0], init.ctypes.data, init.shape[0],
+                                int(iters), assign.ctypes.data, cent.ctypes.data))
+    return assign, cent
+
+
+class Clusters:
+    """Device CSR table of a light clustering and its nvc_clusters view."""
+
+    def __init__(self, assign, k, device="cuda"):
+        import numpy as np
+        assign = np.asarray(assign, np.int64)
+        order = np.argsort(assign, kind="stable")
+        counts = np.bincount(assign, minlength=k)
+        self.offsets = torch.as_tensor(np.concatenate([[0], np.cumsum(counts)]), dtype=torch.int32).to(device)
+        self.members = torch.as_tensor(order, dtype=torch.int32).to(device)
+        c = NvcClusters()
+        c.k = int(k)
+        c.offsets = self.offsets.data_ptr()
+        c.members = self.members.data_ptr()
+        self.struct = c
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+def nvc_train_step_clustered(h, scene: Scene, clusters: Clusters, screen_pos, seed, frame,
+                             loss_out=None, stream=None):
+    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    check(lib.nvc_train_step_clustered(h, scene.ref, clusters.ref, _ptr(screen_pos), n_screen,
+                                       int(seed), int(frame), _ptr(loss_out, torch.float64, "loss_out"),
+                                       _stream(stream)), h)
+
+
+def nvc_cluster_targets(scene: Scene, clusters: Clusters, pos, seed, frame, target, stream=None):
+    check(lib.nvc_cluster_targets(scene.ref, clusters.ref, _ptr(pos, name="pos"), pos.shape[0],
+                                  int(seed), int(frame), _ptr(target, name="target"), _stream(stream)))
+
+
+def nvc_sample_clustered(scene: Scene, clusters: Clusters, vis, pos, nrm, seed, frame, view=0,
+                         pixel_offset=0, light=None, weight=None, estimate=None, stream=None):
+    check(lib.nvc_sample_clustered(scene.ref, clusters.ref, _ptr(vis, name="vis"),
+                                   _ptr(pos, name="pos"), _ptr(nrm, name="nrm"), pos.shape[0],
+                                   int(pixel_offset), int(seed), int(frame), int(view),
+                                   _ptr(light, torch.int32, "light"), _ptr(weight, name="weight"),
+                                   _ptr(estimate, name="estimate"), _stream(stream)))
 
 
 def nvc_infer_noalloc(cfg: NvcConfig, params, pos, vis, stream=None):

@@ -51,7 +51,8 @@ def _cfg(name="frame_1080p", **kw):
 
 def test_param_count_and_level_resolutions_match_the_layout(lib):
     import paper_2506_05930_gb300.nvc as nvc
-    for name in ("tiny_fp32", "frame_1080p", "multiview", "precision_4k", "paper"):
+    for name in ("tiny_fp32", "frame_1080p", "multiview", "precision_4k", "clustered_1080p",
+                 "paper"):
         c = S.config_by_name(name)
         cc = nvc.make_config(c)
         assert nvc.nvc_param_count(cc) == S.param_count(c)
@@ -86,3 +87,31 @@ def test_null_arguments_rejected_without_a_gpu(lib):
     # zero-size work is a no-op that touches nothing
     assert lib.nvc_wrs_from_weights(None, 0, 4, 0, 0, 0, 0, None, None, None, None) == 0
     lib.nvc_destroy(None)
+
+
+def test_host_kmeans_matches_the_oracle_bit_for_bit(lib):
+    """nvc_kmeans_lights runs on the host: assignments and float64 centroids
+    equal the oracle's Lloyd iterations exactly, on the many-lights scene."""
+    import numpy as np
+    import paper_2506_05930_gb300.nvc as nvc
+    sc = S.scene_many_lights(seed=1, n_lights=1024)
+    init = S.kmeans_init(1024, 32, seed=0)
+    for iters in (0, 1, 10):
+        a, c = nvc.nvc_kmeans_lights(sc.lights, init, iters)
+        ra, rc = O.kmeans_lights(sc.lights, init, iters)
+        assert np.array_equal(a, ra), iters
+        assert np.array_equal(c, rc), iters
+    assert len(np.unique(a)) > 24
+
+
+def test_host_kmeans_rejects_bad_arguments(lib):
+    import numpy as np
+    import paper_2506_05930_gb300.nvc as nvc
+    from paper_2506_05930_gb300 import _lib
+    L = S.scene_many_lights(seed=2, n_lights=40).lights
+    with pytest.raises(_lib.NVCError):
+        nvc.nvc_kmeans_lights(L, np.array([0, 40], np.int32), 3)      # index out of range
+    with pytest.raises(_lib.NVCError):
+        nvc.nvc_kmeans_lights(L, np.arange(41, dtype=np.int32), 3)    # k > n_lights
+    with pytest.raises(_lib.NVCError):
+        nvc.nvc_kmeans_lights(L, np.arange(4, dtype=np.int32), -1)
