@@ -217,12 +217,103 @@ def alu_peak_ops(sm_mhz=2070.0, n_sms=152, lanes=128):
     return n_sms * lanes * sm_mhz * 1e6
 
 
+# Clustered sampler (Section 3.6), per pixel: per light a contribution (15)
+# and its add to the cluster sum (1); per cluster weight 2, sum 1, reservoir
+# 8, Philox 10; the RIS step: 4 candidates x (pick 2, contribution 15,
+# reservoir 8), Philox 20, the contribution weight 8.
+CLUSTER_OPS = dict(light=16, cluster=21, ris=128)
+
+
+def clustered_alu_ops(n_lights, k, n_pixels):
+    return (CLUSTER_OPS["light"] * n_lights + CLUSTER_OPS["cluster"] * k
+            + CLUSTER_OPS["ris"]) * n_pixels
+
+
 # Per-launch DRAM traffic of the dominant kernel from the ncu capture named in
 # profiles/ (None once the kernel has changed since that capture).
 KERNEL_TRAFFIC = {"fused_shade": 109.98e6, "adam": 428.34e6}
 
 
 # ------------------------------------------------------------- our arm ----
+
+CLUSTERED_LIGHTS = 1024
+
+
+def measure_clustered(args, gb, stream):
+    """The clustered cache (Section 3.6) on the same G-buffer: the 16-room
+    scene with 1024 lights in k = 32 k-means clusters, one frame = a
+    clustered training step (49,152 positions), inference of the cluster
+    visibilities, and the two-step sampler with its one shadow ray.  Timed
+    with CUDA events over 20 frames after 3 warm-up frames."""
+    import torch
+    from paper_2506_05930_gb300 import nvc
+    import nvc_synth as S
+    cfg = S.config_by_name("clustered_1080p")
+    sc = S.scene_rooms(seed=1, n_lights=CLUSTERED_LIGHTS)
+    k = cfg.n_outputs
+    assign, _ = nvc.nvc_kmeans_lights(sc.lights, S.kmeans_init(CLUSTERED_LIGHTS, k, seed=0), 10)
+    cl = nvc.Clusters(assign, k)
+    scene = nvc.Scene.from_synth(sc)
+    P = gb.n
+    pos = torch.from_numpy(gb.pos).cuda()
+    nrm = torch.from_numpy(gb.nrm).cuda()
+    cache = nvc.VisibilityCache(cfg)
+    cache.set_params(S.init_params(cfg, seed=0))
+    nvc.nvc_set_staging(cache.handle, P)
+    vis = torch.empty((P, k), device="cuda")
+    light = torch.empty(P, dtype=torch.int32, device="cuda")
+    W = torch.empty(P, device="cuda")
+    est = torch.empty(P, device="cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else None
+
+    def frame(f, parts=("train", "infer", "sample")):
+        if "train" in parts:
+            nvc.nvc_train_step_clustered(cache.handle, scene, cl, pos, 5, f, loss, stream=s)
+        if "infer" in parts:
+            nvc.nvc_infer(cache.handle, pos, vis, stream=s)
+        if "sample" in parts:
+            nvc.nvc_sample_clustered(scene, cl, vis, pos, nrm, 7, f, light=light, weight=W,
+                                     estimate=est, stream=s)
+        if "sample_only" in parts:
+            nvc.nvc_sample_clustered(scene, cl, vis, pos, nrm, 7, f, light=light, weight=W,
+                                     stream=s)
+
+    def timed(parts, n=20):
+        for w in range(3):
+            frame(w, parts)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for f in range(n):
+            frame(100 + f, parts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    frame_ms = timed(("train", "infer", "sample"))
+    train_ms = timed(("train",))
+    infer_ms = timed(("infer",))
+    sample_ms = timed(("sample",))
+    sampler_ms = timed(("sample_only",))
+    cache.close()
+    ops = clustered_alu_ops(CLUSTERED_LIGHTS, k, P)
+    peak = alu_peak_ops()
+    return {
+        "workload": f"16-room scene, {CLUSTERED_LIGHTS} lights in k = {k} clusters, "
+                    f"{gb.width}x{gb.height} heightfield G-buffer, 49,152 training positions",
+        "value": P / (frame_ms * 1e-3) / 1e6, "unit": "Mpixels/s", "frame_ms": frame_ms,
+        "train_ms": train_ms, "infer_ms": infer_ms, "sample_with_shadow_ray_ms": sample_ms,
+        "sampler_ms": sampler_ms,
+        "roofline": {"kernel": "sample_clustered_kernel (no shadow ray)", "bound": "alu",
+                     "achieved": ops / (sampler_ms * 1e-3) / 1e12, "peak": peak / 1e12,
+                     "unit": "Tops/s", "frac": ops / (sampler_ms * 1e-3) / peak,
+                     "ops_per_pixel": ops / P,
+                     "peak_source": "152 SMs x 128 lanes x 2070 MHz (max SM clock)"},
+    }
+
+
 
 def run_ours(args):
     import numpy as np
@@ -402,6 +493,8 @@ def run_ours(args):
                    "note": "shade pass: one shadow ray per pixel to the sampled light, V c / p, "
                            "running mean; exact DI: a shadow ray to every light from every pixel"}
 
+    clustered = measure_clustered(args, gb, stream) if rank == 0 else None
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -454,6 +547,8 @@ def run_ours(args):
         line["fp32_unfused_baseline"] = base
     if shading:
         line["shading_pass"] = shading
+    if clustered:
+        line["clustered"] = clustered
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(seconds_target=15.0)
     print(json.dumps(line), flush=True)

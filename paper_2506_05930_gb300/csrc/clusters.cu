@@ -108,6 +108,43 @@ __device__ __forceinline__ float4 light_at(const float4* s_lt, const float* ligh
   return l;
 }
 
+// Integer reservoir over the k cluster weights w with the words of stream
+// (pixel, frame, view, kTagWrs), drawn four at a time as the scan reaches
+// them: the same picks as integer_reservoir with r[y] = word y.
+__device__ __forceinline__ int cluster_reservoir(const float (&w)[kMaxClusters], int k,
+                                                 uint32_t pixel, uint32_t frame, uint32_t view,
+                                                 uint32_t k0, uint32_t k1) {
+  float wmax = 0.0f;
+#pragma unroll
+  for (int y = 0; y < kMaxClusters; ++y)
+    if (y < k) wmax = fmaxf(wmax, w[y]);
+  if (!(wmax > 0.0f)) return -1;
+  const int e = ilogbf(wmax);
+  uint32_t Q = 0;
+  int sel = -1;
+#pragma unroll
+  for (int g = 0; g < kMaxClusters / 4; ++g) {
+    if (4 * g < k) {
+      const uint4 r4 = philox4x32_10(make_uint4(pixel, frame, view, ((uint32_t)g << 4) | kTagWrs), k0, k1);
+      const uint32_t r[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int y = 4 * g + l;
+        if (y < k) {
+          const uint32_t q = quantize_weight(w[y], e);
+          Q += q;
+          if (q > 0u && __umulhi(r[l], Q) < q) sel = y;
+        }
+      }
+    }
+  }
+  return sel;
+}
+
+// Shared-memory layout: [the lights in cluster-table order, I / pi in .w
+// (kSmemLights only)] [spheres] [offsets k + 1, as float4 slots] [boxes].
+// With the lights in table order the members of cluster y are the
+// contiguous slots offsets[y] .. offsets[y + 1] - 1.
 template <bool kSmemLights>
 __global__ void __launch_bounds__(128) sample_clustered_kernel(
     const float* __restrict__ lights, int n_lights, const float* __restrict__ spheres, int n_sph,
@@ -116,18 +153,20 @@ __global__ void __launch_bounds__(128) sample_clustered_kernel(
     const float* __restrict__ pos, const float* __restrict__ nrm, int64_t n,
     int64_t pixel_offset, uint32_t k0, uint32_t k1, uint32_t frame, uint32_t view,
     int32_t* __restrict__ light_out, float* __restrict__ weight_out, float* __restrict__ estimate) {
-  extern __shared__ float s_scene[];
+  extern __shared__ float4 s_scene4[];
   const int n_lt_s = kSmemLights ? n_lights : 0;
-  float4* s_lt = reinterpret_cast<float4*>(s_scene);
+  float4* s_lt = s_scene4;
   float4* s_sph = s_lt + n_lt_s;
-  float* s_box = reinterpret_cast<float*>(s_sph + n_sph);
+  int32_t* s_off = reinterpret_cast<int32_t*>(s_sph + n_sph);
+  float* s_box = reinterpret_cast<float*>(s_sph + n_sph + (kMaxClusters + 4) / 4);
   for (int e = threadIdx.x; e < n_lt_s; e += blockDim.x) {
-    float4 l = reinterpret_cast<const float4*>(lights)[e];
+    float4 l = reinterpret_cast<const float4*>(lights)[mem[e]];
     l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
     s_lt[e] = l;
   }
   for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
     s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
+  for (int e = threadIdx.x; e <= k; e += blockDim.x) s_off[e] = off[e];
   for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
   __syncthreads();
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
@@ -135,27 +174,25 @@ __global__ void __launch_bounds__(128) sample_clustered_kernel(
     const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
     const float nx = nrm[3 * p], ny = nrm[3 * p + 1], nz = nrm[3 * p + 2];
     const uint32_t pixel = (uint32_t)(pixel_offset + p);
-    // step 1: the clusters' weights and the reservoir over them
+    // step 1: the clusters' weights, then the reservoir over them
     float w[kMaxClusters];
-    uint32_t r[kMaxClusters];
     float wsum = 0.0f;
 #pragma unroll
     for (int y = 0; y < kMaxClusters; ++y) {
       w[y] = 0.0f;
-      r[y] = 0u;
       if (y < k) {
         float ch = 0.0f;
-        const int end = off[y + 1];
-        for (int i = off[y]; i < end; ++i) {
-          const float4 l = light_at<kSmemLights>(s_lt, lights, mem[i]);
+        const int end = s_off[y + 1];
+#pragma unroll 4
+        for (int i = s_off[y]; i < end; ++i) {
+          const float4 l = kSmemLights ? s_lt[i] : light_at<false>(s_lt, lights, mem[i]);
           ch = __fadd_rn(ch, contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w));
         }
         w[y] = __fmul_rn(fmaxf(vis[p * k + y], bits_f(kVisClampBits)), ch);
         wsum = __fadd_rn(wsum, w[y]);
-        r[y] = stream_word(pixel, frame, view, kTagWrs, y, k0, k1);
       }
     }
-    const int y = integer_reservoir(w, k, r);
+    const int y = cluster_reservoir(w, k, pixel, frame, view, k0, k1);
     int sel_light = -1;
     float W = 0.0f, cx = 0.0f;
     if (y >= 0) {
@@ -164,34 +201,37 @@ __global__ void __launch_bounds__(128) sample_clustered_kernel(
       for (int t = 0; t < kMaxClusters; ++t)
         if (t == y) w_y = w[t];
       // step 2: streaming RIS among kRis uniform members of cluster y
-      const int m_y = off[y + 1] - off[y];
-      int cand[kRis];
+      const int base = s_off[y];
+      const uint32_t m_y = (uint32_t)(s_off[y + 1] - base);
+      const uint4 u = philox4x32_10(make_uint4(pixel, frame, view, (0u << 4) | kTagRis), k0, k1);
+      const uint4 v = philox4x32_10(make_uint4(pixel, frame, view, (1u << 4) | kTagRis), k0, k1);
+      const uint32_t ru[kRis] = {u.x, u.y, u.z, u.w};
+      const uint32_t rr[kRis] = {v.x, v.y, v.z, v.w};
+      int slot[kRis];
       float cc[kRis];
-      uint32_t rr[kRis];
 #pragma unroll
       for (int t = 0; t < kRis; ++t) {
-        cand[t] = member_of(off, mem, y, stream_word(pixel, frame, view, kTagRis, t, k0, k1));
-        const float4 l = light_at<kSmemLights>(s_lt, lights, cand[t]);
+        slot[t] = base + (int)(((uint64_t)ru[t] * m_y) >> 32);
+        const float4 l = kSmemLights ? s_lt[slot[t]] : light_at<false>(s_lt, lights, mem[slot[t]]);
         cc[t] = contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w);
-        rr[t] = stream_word(pixel, frame, view, kTagRis, kRis + t, k0, k1);
       }
       const int j = integer_reservoir(cc, kRis, rr);
       if (j >= 0) {
-        float s = 0.0f;
+        float sum = 0.0f;
 #pragma unroll
-        for (int t = 0; t < kRis; ++t) s = __fadd_rn(s, cc[t]);
+        for (int t = 0; t < kRis; ++t) sum = __fadd_rn(sum, cc[t]);
         float c_j = 0.0f;
-        int x_j = -1;
+        int s_j = 0;
 #pragma unroll
         for (int t = 0; t < kRis; ++t)
           if (t == j) {
             c_j = cc[t];
-            x_j = cand[t];
+            s_j = slot[t];
           }
-        const float mean = __fdiv_rn(s, (float)kRis);
+        const float mean = __fdiv_rn(sum, (float)kRis);
         const float pr = __fdiv_rn(__fdiv_rn(w_y, wsum), (float)m_y);
         W = __fdiv_rn(mean, __fmul_rn(pr, c_j));
-        sel_light = x_j;
+        sel_light = mem[s_j];
         cx = c_j;
       }
     }
@@ -200,7 +240,7 @@ __global__ void __launch_bounds__(128) sample_clustered_kernel(
     if (estimate) {
       float e = 0.0f;
       if (sel_light >= 0) {
-        const float4 l = light_at<kSmemLights>(s_lt, lights, sel_light);
+        const float4 l = reinterpret_cast<const float4*>(lights)[sel_light];
         if (!segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box))
           e = __fmul_rn(cx, W);
       }
@@ -229,7 +269,8 @@ cudaError_t launch_cluster_targets(const nvc_scene* sc, const nvc_clusters* cl, 
 constexpr size_t kSmemOptin = 227 * 1024;
 
 size_t sample_clustered_smem(const nvc_scene* sc) {
-  const size_t occ = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  const size_t occ = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes) +
+                     sizeof(float4) * ((kMaxClusters + 4) / 4);
   const size_t lt = sizeof(float) * 4 * (size_t)sc->n_lights;
   return occ + lt <= kSmemOptin ? occ + lt : occ;
 }
@@ -241,14 +282,18 @@ cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl,
                                     int num_sms, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const size_t smem = sample_clustered_smem(sc);
-  const bool lights_on_chip =
-      smem == sizeof(float) * (4 * (size_t)sc->n_lights + 4 * (size_t)sc->n_spheres +
-                               6 * (size_t)sc->n_boxes);
+  const bool lights_on_chip = smem > sizeof(float) * (4 * (size_t)sc->n_spheres +
+                                                      6 * (size_t)sc->n_boxes) +
+                                         sizeof(float4) * ((kMaxClusters + 4) / 4);
   auto kern = lights_on_chip ? sample_clustered_kernel<true> : sample_clustered_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // one wave of resident blocks, each striding over the pixels
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
+  if (e != cudaSuccess) return e;
   const int64_t want = (n + 127) / 128;
-  const int64_t cap = (int64_t)num_sms * 8;
+  const int64_t cap = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
   const int grid = (int)(want < cap ? want : cap);
   kern<<<grid, 128, smem, s>>>(sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes,
                                sc->n_boxes, cl->offsets, cl->members, cl->k, vis, pos, nrm, n,
