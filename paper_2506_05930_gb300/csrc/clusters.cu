@@ -146,7 +146,7 @@ __device__ __forceinline__ int cluster_reservoir(const float (&w)[kMaxClusters],
 // With the lights in table order the members of cluster y are the
 // contiguous slots offsets[y] .. offsets[y + 1] - 1.
 template <bool kSmemLights>
-__global__ void __launch_bounds__(128) sample_clustered_kernel(
+__global__ void __launch_bounds__(1024) sample_clustered_kernel(
     const float* __restrict__ lights, int n_lights, const float* __restrict__ spheres, int n_sph,
     const float* __restrict__ boxes, int n_box, const int32_t* __restrict__ off,
     const int32_t* __restrict__ mem, int k, const float* __restrict__ vis,
@@ -174,23 +174,30 @@ __global__ void __launch_bounds__(128) sample_clustered_kernel(
     const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
     const float nx = nrm[3 * p], ny = nrm[3 * p + 1], nz = nrm[3 * p + 2];
     const uint32_t pixel = (uint32_t)(pixel_offset + p);
-    // step 1: the clusters' weights, then the reservoir over them
+    // step 1: the clusters' weights, then the reservoir over them.  The
+    // cluster loop stays a loop (one copy of the member loop in the code, so
+    // warps at different clusters share the instruction cache); the weights
+    // stay in registers through compare-and-select writes.
     float w[kMaxClusters];
-    float wsum = 0.0f;
 #pragma unroll
-    for (int y = 0; y < kMaxClusters; ++y) {
-      w[y] = 0.0f;
-      if (y < k) {
-        float ch = 0.0f;
-        const int end = s_off[y + 1];
+    for (int t = 0; t < kMaxClusters; ++t) w[t] = 0.0f;
+    float wsum = 0.0f;
+    const float* vrow = vis + p * k;
+#pragma unroll 1
+    for (int y = 0; y < k; ++y) {
+      const float v = __ldg(vrow + y);
+      float ch = 0.0f;
+      const int end = s_off[y + 1];
 #pragma unroll 4
-        for (int i = s_off[y]; i < end; ++i) {
-          const float4 l = kSmemLights ? s_lt[i] : light_at<false>(s_lt, lights, mem[i]);
-          ch = __fadd_rn(ch, contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w));
-        }
-        w[y] = __fmul_rn(fmaxf(vis[p * k + y], bits_f(kVisClampBits)), ch);
-        wsum = __fadd_rn(wsum, w[y]);
+      for (int i = s_off[y]; i < end; ++i) {
+        const float4 l = kSmemLights ? s_lt[i] : light_at<false>(s_lt, lights, mem[i]);
+        ch = __fadd_rn(ch, contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w));
       }
+      const float wy = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), ch);
+#pragma unroll
+      for (int t = 0; t < kMaxClusters; ++t)
+        if (t == y) w[t] = wy;
+      wsum = __fadd_rn(wsum, wy);
     }
     const int y = cluster_reservoir(w, k, pixel, frame, view, k0, k1);
     int sel_light = -1;
@@ -288,17 +295,28 @@ cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl,
   auto kern = lights_on_chip ? sample_clustered_kernel<true> : sample_clustered_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // one wave of resident blocks, each striding over the pixels
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
-  if (e != cudaSuccess) return e;
-  const int64_t want = (n + 127) / 128;
-  const int64_t cap = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+  // The staged lights are shared by a CTA's threads: take the smallest CTA
+  // (128 .. 1024 threads) that keeps the most threads resident per SM, so a
+  // large light set does not cut residency.  One wave of resident CTAs
+  // strides over the pixels.
+  int threads = 128, best = 0;
+  for (int t = 128; t <= 1024; t *= 2) {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm * t > best) {
+      best = per_sm * t;
+      threads = t;
+    }
+  }
+  if (best == 0) return cudaErrorInvalidConfiguration;
+  const int64_t want = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms * (best / threads);
   const int grid = (int)(want < cap ? want : cap);
-  kern<<<grid, 128, smem, s>>>(sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes,
-                               sc->n_boxes, cl->offsets, cl->members, cl->k, vis, pos, nrm, n,
-                               pixel_offset, (uint32_t)seed, (uint32_t)(seed >> 32), frame, view,
-                               light, weight, estimate);
+  kern<<<grid, threads, smem, s>>>(sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes,
+                                   sc->n_boxes, cl->offsets, cl->members, cl->k, vis, pos, nrm, n,
+                                   pixel_offset, (uint32_t)seed, (uint32_t)(seed >> 32), frame,
+                                   view, light, weight, estimate);
   return cudaGetLastError();
 }
 
