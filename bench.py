@@ -231,7 +231,9 @@ def clustered_alu_ops(n_lights, k, n_pixels):
 
 # Per-launch DRAM traffic of the dominant kernel from the ncu capture named in
 # profiles/ (None once the kernel has changed since that capture).
-KERNEL_TRAFFIC = {"fused_shade": 109.98e6, "adam": 428.34e6}
+KERNEL_TRAFFIC = {"fused_shade": 109.98e6, "adam": 428.34e6,
+                  # 1080p launch with the shadow ray (light, W and estimate written)
+                  "sample_clustered": 336.47e6}
 
 
 # ------------------------------------------------------------- our arm ----
@@ -310,6 +312,8 @@ def measure_clustered(args, gb, stream):
                      "achieved": ops / (sampler_ms * 1e-3) / 1e12, "peak": peak / 1e12,
                      "unit": "Tops/s", "frac": ops / (sampler_ms * 1e-3) / peak,
                      "ops_per_pixel": ops / P,
+                     "traffic": KERNEL_TRAFFIC["sample_clustered"] if P == 1920 * 1080 else None,
+                     "traffic_launch": "ncu, 1080p launch with the shadow ray",
                      "peak_source": "152 SMs x 128 lanes x 2070 MHz (max SM clock)"},
     }
 
