@@ -326,17 +326,23 @@ def estimator_moments(V, c, p):
 # ----------------------------------------------------------------------------
 
 def training_positions(batch: int, world_min, world_max, screen_pos,
-                       seed: int, frame: int) -> np.ndarray:
-    """float32 [batch, 3]: world-space then screen-space training positions.
+                       seed: int, frame: int, n_world: Optional[int] = None) -> np.ndarray:
+    """float32 [batch, 3]: world-space then screen-space training positions
+    (Section 3.4 compares the two placements and their combination).
 
-    Half the batch (all of it when no screen positions are given) is uniform
+    The first n_world positions (by default ceil(batch / 2), the paper's
+    equal split; all of them when no screen positions are given) are uniform
     in the scene bounds: x = lo + u * (hi - lo) with u = 24-bit uniforms of
-    stream (j, frame, 0, world); the rest picks G-buffer pixel
-    floor(r * P / 2^32), r = word 0 of stream (j, frame, 0, screen).
+    stream (j, frame, 0, world); position n_world + s picks G-buffer pixel
+    floor(r * P / 2^32), r = word 0 of stream (s, frame, 0, screen).
     """
     have_screen = screen_pos is not None and len(screen_pos) > 0
-    n_screen = batch // 2 if have_screen else 0
-    n_world = batch - n_screen
+    if not have_screen:
+        n_world = batch
+    elif n_world is None:
+        n_world = batch - batch // 2
+    n_world = min(max(int(n_world), 0), batch)
+    n_screen = batch - n_world
     lo = np.asarray(world_min, np.float32)
     ext = np.asarray(world_max, np.float32) - lo
     out = np.empty((batch, 3), np.float32)
@@ -707,12 +713,12 @@ def gradients(cfg, params, pos, targets):
 
 
 def train_step(cfg, state: TrainState, scene, screen_pos, seed: int,
-               frame: int):
+               frame: int, n_world: Optional[int] = None):
     """One online training step (Section 3.4): positions -> shadow-ray
     targets -> loss -> gradients -> Adam.  A non-finite gradient skips the
     update and counts it.  Returns the loss."""
     pos = training_positions(cfg.batch_positions, scene.world_min,
-                             scene.world_max, screen_pos, seed, frame)
+                             scene.world_max, screen_pos, seed, frame, n_world)
     y = visibility(pos, scene.lights, scene.spheres, scene.boxes, np.float32)
     loss, g = gradients(cfg, state.params, pos, y)
     if not np.all(np.isfinite(g)):

@@ -476,6 +476,32 @@ def test_training_positions_split_and_ranges():
     np.testing.assert_array_equal(allw[:32], pos[:32])
 
 
+def test_training_positions_placement_options():
+    """The placements of Section 3.4: world space only, screen space only,
+    and any split.  World rows are a prefix of one stream (row j of every
+    split is the same point), screen rows index their own stream from 0
+    (row n_world + s of every split is the same G-buffer point), so a split
+    that reused the world index for the screen stream, or the other way
+    round, would fail; the default is ceil(batch / 2) world rows."""
+    sc = S.scene_heightfield(seed=1, n_lights=4, n_spheres=2, n_boxes=2)
+    gb = S.gbuffer_points(2, 16, 16, lo=(1, 2, 3), hi=(2, 3, 4))
+    rows = {tuple(r) for r in gb.pos}
+    B = 65
+    args = (sc.world_min, sc.world_max, gb.pos, 5, 9)
+    world = O.training_positions(B, *args, n_world=B)
+    screen = O.training_positions(B, *args, n_world=0)
+    assert np.all((world >= 0) & (world < 10)) and not any(tuple(r) in rows for r in world)
+    assert all(tuple(r) in rows for r in screen)
+    np.testing.assert_array_equal(world, O.training_positions(B, sc.world_min, sc.world_max,
+                                                              None, 5, 9))
+    for nw in (1, 17, 33, 64):
+        split = O.training_positions(B, *args, n_world=nw)
+        np.testing.assert_array_equal(split[:nw], world[:nw])
+        np.testing.assert_array_equal(split[nw:], screen[:B - nw])
+    np.testing.assert_array_equal(O.training_positions(B, *args),
+                                  O.training_positions(B, *args, n_world=33))
+
+
 # ------------------------------------------------------------ learned part --
 
 def test_oracle_training_converges_to_brute_force_visibility_and_gains():
