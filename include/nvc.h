@@ -379,14 +379,31 @@ nvc_status nvc_trace_visibility(const nvc_scene* scene, const float* pos, int64_
                                 float* vis, void* stream);
 
 /* Training positions (device [batch][3]; the scene may hold any number of
- * lights, only its world box is used): the first half (all of them when
- * screen_pos is NULL or n_screen = 0) uniform in the scene's world box,
- * x = lo + u * (hi - lo), u the top 24 bits of Philox stream
- * (j, frame, 0, 1) times 2^-24; the rest are G-buffer pixels
- * screen_pos[floor(r * n_screen / 2^32)], r from stream (j, frame, 0, 2). */
+ * lights, only its world box is used), Section 3.4: positions j < n_w are
+ * uniform in the scene's world box, x = lo + u * (hi - lo), u the top 24
+ * bits of the words of Philox stream (j, frame, 0, 1) times 2^-24; the rest
+ * are G-buffer pixels screen_pos[floor(r * n_screen / 2^32)], r word 0 of
+ * stream (j - n_w, frame, 0, 2).  n_w = ceil(batch / 2), the paper's equal
+ * world/screen split; n_w = batch when screen_pos is NULL or n_screen = 0. */
 nvc_status nvc_training_positions(const nvc_scene* scene, const float* screen_pos,
                                   int64_t n_screen, int64_t batch, uint64_t seed,
                                   uint32_t frame, float* pos, void* stream);
+
+/* nvc_training_positions with a chosen split (the placement options of
+ * Section 3.4): n_world world-space positions (0 = screen space only,
+ * batch = world space only, -1 = the default ceil(batch / 2)), the rest
+ * screen space.  Without screen positions every position is world space.
+ * NVC_ERR_INVALID_ARG unless -1 <= n_world <= batch. */
+nvc_status nvc_training_positions_split(const nvc_scene* scene, const float* screen_pos,
+                                        int64_t n_screen, int64_t batch, int64_t n_world,
+                                        uint64_t seed, uint32_t frame, float* pos, void* stream);
+
+/* Placement of the handle's training positions for the following training
+ * steps and frames (per-light and clustered): n_world of the
+ * batch_positions positions in world space, as nvc_training_positions_split
+ * (-1 restores the default split).  Host only; takes effect at the next
+ * step, including captured frame graphs (they are recaptured per frame). */
+nvc_status nvc_set_training_placement(nvc_handle* h, int64_t n_world);
 
 /* One online training step: batch_positions positions (as
  * nvc_training_positions), shadow-ray targets, forward, loss (L2 or BCE,

@@ -95,6 +95,9 @@ PROTOTYPES = {
     "nvc_trace_visibility": (c_int32, [_scp, _vp, c_int64, _vp, _vp]),
     "nvc_training_positions": (c_int32, [_scp, _vp, c_int64, c_int64, c_uint64, c_uint32, _vp,
                                          _vp]),
+    "nvc_training_positions_split": (c_int32, [_scp, _vp, c_int64, c_int64, c_int64, c_uint64,
+                                               c_uint32, _vp, _vp]),
+    "nvc_set_training_placement": (c_int32, [_vp, c_int64]),
     "nvc_train_step": (c_int32, [_vp, _scp, _vp, c_int64, c_uint64, c_uint32, _vp, _vp]),
     "nvc_train_gradient": (c_int32, [_vp, _scp, _vp, c_int64, c_uint64, c_uint32, _vp, _vp,
                                      _vp]),

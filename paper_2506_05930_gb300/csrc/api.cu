@@ -756,18 +756,35 @@ nvc_status nvc_exact_di(const nvc_scene* scene, const float* pos, const float* n
   return NVC_OK;
 }
 
-nvc_status nvc_training_positions(const nvc_scene* scene, const float* screen_pos,
-                                  int64_t n_screen, int64_t batch, uint64_t seed, uint32_t frame,
-                                  float* pos, void* stream) {
+nvc_status nvc_training_positions_split(const nvc_scene* scene, const float* screen_pos,
+                                        int64_t n_screen, int64_t batch, int64_t n_world,
+                                        uint64_t seed, uint32_t frame, float* pos, void* stream) {
   NVC_TRY(check_scene(nullptr, scene, 0, kAnyLights));
   if (batch < 0 || n_screen < 0 || n_screen > ((int64_t)1 << 32))
     return fail(nullptr, NVC_ERR_INVALID_ARG, "batch or n_screen out of range");
   if (batch > ((int64_t)1 << 32)) return fail(nullptr, NVC_ERR_INVALID_ARG, "batch above 2^32");
+  if (n_world < -1 || n_world > batch)
+    return fail(nullptr, NVC_ERR_INVALID_ARG, "n_world must be -1 or 0..batch");
   if (batch == 0) return NVC_OK;
   NVC_TRY(check_ptr(nullptr, pos, "pos"));
   if (n_screen > 0 && screen_pos) NVC_TRY(check_ptr(nullptr, screen_pos, "screen_pos"));
   NVC_CUDA(nullptr, launch_training_positions(scene, screen_pos, n_screen, batch, seed, frame, pos,
-                                              (cudaStream_t)stream));
+                                              (cudaStream_t)stream, n_world));
+  return NVC_OK;
+}
+
+nvc_status nvc_training_positions(const nvc_scene* scene, const float* screen_pos,
+                                  int64_t n_screen, int64_t batch, uint64_t seed, uint32_t frame,
+                                  float* pos, void* stream) {
+  return nvc_training_positions_split(scene, screen_pos, n_screen, batch, -1, seed, frame, pos,
+                                      stream);
+}
+
+nvc_status nvc_set_training_placement(nvc_handle* h, int64_t n_world) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_world < -1 || n_world > h->B)
+    return fail(h, NVC_ERR_INVALID_ARG, "n_world must be -1 or 0..batch_positions");
+  h->n_world = n_world;
   return NVC_OK;
 }
 
@@ -782,13 +799,14 @@ static nvc_status train_forward_backward(nvc_handle* h, const nvc_scene* scene,
     StageScope sc(h, s, 0);
     if (clusters) {
       // positions, then one member's visibility per cluster (Section 3.6)
-      NVC_CUDA(h, launch_training_positions(scene, screen_pos, n_screen, B, seed, frame, h->t_pos, s));
+      NVC_CUDA(h, launch_training_positions(scene, screen_pos, n_screen, B, seed, frame, h->t_pos, s,
+                                            h->n_world));
       NVC_CUDA(h, launch_cluster_targets(scene, clusters, h->t_pos, B, seed, frame, h->t_target, s));
       count_launches(h, 2);
     } else {
       // positions and their shadow-ray targets in one kernel
       NVC_CUDA(h, launch_training_data(scene, screen_pos, n_screen, B, seed, frame, h->t_pos,
-                                       h->t_target, s));
+                                       h->t_target, s, h->n_world));
       count_launches(h, 1);
     }
   }

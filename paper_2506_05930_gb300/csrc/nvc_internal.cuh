@@ -201,6 +201,9 @@ struct nvc_handle {
 
   // fused shading kernel variant (nvc::ShadeVariant)
   int shade_variant = 0;
+  // world-space share of the training positions (nvc_set_training_placement;
+  // -1: the default split, ceil(B / 2) world-space)
+  int64_t n_world = -1;
   // E4M3 per-tensor scales: [0, 9) activations (set by nvc_calibrate),
   // [9, 18) weights (set by the weight packing)
   float* fp8_scales = nullptr;
@@ -258,9 +261,12 @@ cudaError_t launch_shade_from_vis(const nvc_scene* sc, const float* pos, const f
                                   float* pdf, float* wsum, float* radiance, cudaStream_t s);
 
 // train.cu
+// n_world: world-space positions in the batch, -1 for ceil(batch / 2); every
+// position is world-space when no screen positions are given.
 cudaError_t launch_training_positions(const nvc_scene* sc, const float* screen_pos,
                                       int64_t n_screen, int64_t batch, uint64_t seed,
-                                      uint32_t frame, float* pos, cudaStream_t s);
+                                      uint32_t frame, float* pos, cudaStream_t s,
+                                      int64_t n_world = -1);
 cudaError_t launch_trace_visibility(const nvc_scene* sc, const float* pos, int64_t n,
                                     float* vis, cudaStream_t s);
 cudaError_t launch_loss_grad(nvc_handle* h, int64_t n, cudaStream_t s);
@@ -321,7 +327,7 @@ void kmeans_host(const float* lights, int n, const int32_t* init, int k, int ite
 // values as launch_training_positions followed by launch_trace_visibility).
 cudaError_t launch_training_data(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,
                                  int64_t batch, uint64_t seed, uint32_t frame, float* pos,
-                                 float* vis, cudaStream_t s);
+                                 float* vis, cudaStream_t s, int64_t n_world = -1);
 cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStream_t s);
 
 }  // namespace nvc

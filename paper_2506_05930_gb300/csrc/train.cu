@@ -274,7 +274,7 @@ __global__ void take_gradient_kernel(float* __restrict__ grad, float* __restrict
 }  // namespace
 
 static PosGen pos_gen(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,
-                      int64_t batch, uint64_t seed, uint32_t frame) {
+                      int64_t batch, uint64_t seed, uint32_t frame, int64_t n_world) {
   const bool have_screen = screen_pos != nullptr && n_screen > 0;
   PosGen g;
   g.lo = make_float3(sc->world_min[0], sc->world_min[1], sc->world_min[2]);
@@ -282,7 +282,8 @@ static PosGen pos_gen(const nvc_scene* sc, const float* screen_pos, int64_t n_sc
                       sc->world_max[2] - sc->world_min[2]);
   g.screen = screen_pos;
   g.n_screen = have_screen ? n_screen : 0;
-  g.n_world = batch - (have_screen ? batch / 2 : 0);
+  g.n_world = !have_screen ? batch : n_world < 0 ? batch - batch / 2
+                                                 : (n_world < batch ? n_world : batch);
   g.k0 = (uint32_t)seed;
   g.k1 = (uint32_t)(seed >> 32);
   g.frame = frame;
@@ -291,23 +292,25 @@ static PosGen pos_gen(const nvc_scene* sc, const float* screen_pos, int64_t n_sc
 
 cudaError_t launch_training_positions(const nvc_scene* sc, const float* screen_pos,
                                       int64_t n_screen, int64_t batch, uint64_t seed,
-                                      uint32_t frame, float* pos, cudaStream_t s) {
+                                      uint32_t frame, float* pos, cudaStream_t s,
+                                      int64_t n_world) {
   if (batch == 0) return cudaSuccess;
   training_positions_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(
-      pos_gen(sc, screen_pos, n_screen, batch, seed, frame), batch, pos);
+      pos_gen(sc, screen_pos, n_screen, batch, seed, frame, n_world), batch, pos);
   return cudaGetLastError();
 }
 
 cudaError_t launch_training_data(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,
                                  int64_t batch, uint64_t seed, uint32_t frame, float* pos,
-                                 float* vis, cudaStream_t s) {
+                                 float* vis, cudaStream_t s, int64_t n_world) {
   if (batch == 0) return cudaSuccess;
-  if (sc->n_lights < 1) return launch_training_positions(sc, screen_pos, n_screen, batch, seed, frame, pos, s);
+  if (sc->n_lights < 1)
+    return launch_training_positions(sc, screen_pos, n_screen, batch, seed, frame, pos, s, n_world);
   const int64_t total = batch * sc->n_lights;
   const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
   trace_visibility_kernel<true><<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
       sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes, pos, batch,
-      vis, pos_gen(sc, screen_pos, n_screen, batch, seed, frame));
+      vis, pos_gen(sc, screen_pos, n_screen, batch, seed, frame, n_world));
   return cudaGetLastError();
 }
 

@@ -247,6 +247,18 @@ def nvc_training_positions(scene: Scene, screen_pos, batch, seed, frame, pos, st
                                      int(seed), int(frame), _ptr(pos), _stream(stream)))
 
 
+def nvc_training_positions_split(scene: Scene, screen_pos, batch, n_world, seed, frame, pos,
+                                 stream=None):
+    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    check(lib.nvc_training_positions_split(scene.ref, _ptr(screen_pos), n_screen, int(batch),
+                                           int(n_world), int(seed), int(frame), _ptr(pos),
+                                           _stream(stream)))
+
+
+def nvc_set_training_placement(h, n_world: int):
+    check(lib.nvc_set_training_placement(h, int(n_world)), h)
+
+
 def nvc_train_step(h, scene: Scene, screen_pos, seed, frame, loss_out=None, stream=None):
     n_screen = 0 if screen_pos is None else screen_pos.shape[0]
     check(lib.nvc_train_step(h, scene.ref, _ptr(screen_pos), n_screen, int(seed), int(frame),
