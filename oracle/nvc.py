@@ -561,6 +561,30 @@ def cluster_contributions(c32, offsets, members) -> np.ndarray:
     return out
 
 
+CLUSTER_WEIGHT_MODES = ("sum", "visibility")
+
+
+def cluster_weights(vis, c32, offsets, members, mode: str = "sum") -> np.ndarray:
+    """float32 [n, k] weights of the first sampling step (Section 3.6).
+
+    "sum":        w_y = max(v_y, 0.001) * c_hat_y, the cluster's inferred
+                  average visibility times its members' summed contribution;
+    "visibility": w_y = max(v_y, 0.001), the inferred average visibility
+                  alone (the step's weight as the paper words it; the
+                  contributions enter only through the RIS step).
+    Empty clusters weigh 0 in both modes.  Every non-empty cluster whose
+    members contribute keeps w_y > 0, so every contributing light stays
+    reachable."""
+    offsets = np.asarray(offsets, np.int64)
+    m = (offsets[1:] - offsets[:-1]) > 0
+    if mode == "sum":
+        return light_weights_f32(vis, cluster_contributions(c32, offsets, members))
+    if mode == "visibility":
+        v = np.maximum(np.asarray(vis, np.float32), np.float32(0.001))
+        return np.where(m[None, :], v, np.float32(0.0)).astype(np.float32)
+    raise ValueError(mode)
+
+
 def ris_weight(c_cand, j, w_y, w_sum, m_y):
     """Unbiased contribution weight of candidate j after streaming RIS with
     source pdf p(x) = (w(y) / w_sum) / m_y (the cluster's selection
@@ -579,11 +603,12 @@ def ris_weight(c_cand, j, w_y, w_sum, m_y):
 
 
 def sample_clustered(vis, pos, nrm, lights, offsets, members, pixel_ids, seed: int,
-                     frame: int, view: int):
+                     frame: int, view: int, mode: str = "sum"):
     """Two-step light sampling of the clustered cache (Section 3.6).
 
-    1. WRS over the k clusters with weights w_y = max(v_y, 0.001) c_hat_y
-       (the integer reservoir of ``wrs_select``, stream TAG_WRS).
+    1. WRS over the k clusters with the weights of ``cluster_weights``
+       (by default w_y = max(v_y, 0.001) c_hat_y; the integer reservoir of
+       ``wrs_select``, stream TAG_WRS).
     2. Streaming RIS in the chosen cluster y: RIS_CANDIDATES members drawn
        uniformly (words 0..M-1 of stream (pixel, frame, view, TAG_RIS)), one
        kept by the integer reservoir on their float32 contributions (words
@@ -594,8 +619,7 @@ def sample_clustered(vis, pos, nrm, lights, offsets, members, pixel_ids, seed: i
     offsets = np.asarray(offsets, np.int64)
     members = np.asarray(members, np.int64)
     c32 = contributions(pos, nrm, lights, np.float32)
-    chat = cluster_contributions(c32, offsets, members)
-    w = light_weights_f32(vis, chat)
+    w = cluster_weights(vis, c32, offsets, members, mode)
     y, _, _ = wrs_select(w, pixel_ids, seed, frame, view)
     n = len(pos)
     M = RIS_CANDIDATES

@@ -668,10 +668,12 @@ def test_cluster_targets_are_the_visibility_of_a_member_light():
     assert np.all(np.abs(acc / F - mean_v) <= 5 * sd + 1e-12)
 
 
-def test_clustered_estimate_is_unbiased_by_exact_enumeration():
+@pytest.mark.parametrize("mode", ["sum", "visibility"])
+def test_clustered_estimate_is_unbiased_by_exact_enumeration(mode):
     """E[V(x) c(x) W] over the cluster law, every uniform candidate tuple
     and the pick law on it equals sum_x V_x c_x: the source pdf, the RIS
-    weight and both reservoirs agree (Section 3.6)."""
+    weight and both reservoirs agree (Section 3.6), for either choice of
+    the first step's cluster weights."""
     import itertools
     sc = S.scene_heightfield(seed=9, n_lights=6, n_spheres=6, n_boxes=6)
     assign = np.array([0, 1, 1, 2, 2, 2])
@@ -680,8 +682,12 @@ def test_clustered_estimate_is_unbiased_by_exact_enumeration():
     V = O.visibility(gb.pos, sc.lights, sc.spheres, sc.boxes, np.float32)
     c32 = O.contributions(gb.pos, gb.nrm, sc.lights, np.float32)
     vis = np.random.default_rng(3).uniform(0.1, 0.9, (gb.n, 3)).astype(np.float32)
-    chat = O.cluster_contributions(c32, off, mem)
-    w = O.light_weights_f32(vis, chat)
+    w = O.cluster_weights(vis, c32, off, mem, mode)
+    if mode == "sum":
+        np.testing.assert_array_equal(
+            w, O.light_weights_f32(vis, O.cluster_contributions(c32, off, mem)))
+    else:
+        np.testing.assert_array_equal(w, np.maximum(vis, np.float32(0.001)))
     law = O.selection_law(w)
     M = O.RIS_CANDIDATES
     checked = 0
@@ -713,7 +719,8 @@ def test_clustered_estimate_is_unbiased_by_exact_enumeration():
     assert (V == 0).any()
 
 
-def test_sample_clustered_mean_estimate_converges_to_exact_di():
+@pytest.mark.parametrize("mode", ["sum", "visibility"])
+def test_sample_clustered_mean_estimate_converges_to_exact_di(mode):
     sc = S.scene_heightfield(seed=4, n_lights=24, n_spheres=8, n_boxes=8)
     rng = np.random.default_rng(2)
     a, _ = O.kmeans_lights(sc.lights, rng.permutation(24)[:5], 6)
@@ -726,7 +733,7 @@ def test_sample_clustered_mean_estimate_converges_to_exact_di():
     est = np.zeros((F, gb.n))
     for f in range(F):
         light, W = O.sample_clustered(vis, gb.pos, gb.nrm, sc.lights, off, mem,
-                                      np.arange(gb.n), 3, f, 0)
+                                      np.arange(gb.n), 3, f, 0, mode)
         ok = light >= 0
         x = np.maximum(light, 0)
         est[f] = np.where(ok, V[np.arange(gb.n), x] * c32[np.arange(gb.n), x] * W, 0.0)
