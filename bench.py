@@ -239,6 +239,7 @@ KERNEL_TRAFFIC = {"fused_shade": 109.98e6, "adam": 428.34e6,
 # ------------------------------------------------------------- our arm ----
 
 CLUSTERED_LIGHTS = 1024
+PAPER_SCALE_LIGHTS = 59000      # the light count of the paper's many-lights scene
 
 
 def measure_clustered(args, gb, stream):
@@ -255,6 +256,7 @@ def measure_clustered(args, gb, stream):
     k = cfg.n_outputs
     assign, _ = nvc.nvc_kmeans_lights(sc.lights, S.kmeans_init(CLUSTERED_LIGHTS, k, seed=0), 10)
     cl = nvc.Clusters(assign, k)
+    cl_vis = nvc.Clusters(assign, k, weights="visibility")
     scene = nvc.Scene.from_synth(sc)
     P = gb.n
     pos = torch.from_numpy(gb.pos).cuda()
@@ -280,6 +282,9 @@ def measure_clustered(args, gb, stream):
         if "sample_only" in parts:
             nvc.nvc_sample_clustered(scene, cl, vis, pos, nrm, 7, f, light=light, weight=W,
                                      stream=s)
+        if "sample_vis" in parts:
+            nvc.nvc_sample_clustered(scene_v, cl_v, vis, pos, nrm, 7, f, light=light,
+                                     weight=W, estimate=est, stream=s)
 
     def timed(parts, n=20):
         for w in range(3):
@@ -299,6 +304,17 @@ def measure_clustered(args, gb, stream):
     infer_ms = timed(("infer",))
     sample_ms = timed(("sample",))
     sampler_ms = timed(("sample_only",))
+    # the visibility-only first-step weights: cost independent of the light
+    # count, timed at 1024 lights and at the paper's many-lights scale
+    scene_v, cl_v = scene, cl_vis
+    sample_vis_ms = timed(("sample_vis",))
+    frame_vis_ms = timed(("train", "infer", "sample_vis"))
+    sc_big = S.scene_rooms(seed=1, n_lights=PAPER_SCALE_LIGHTS)
+    assign_big, _ = nvc.nvc_kmeans_lights(sc_big.lights,
+                                          S.kmeans_init(PAPER_SCALE_LIGHTS, k, seed=0), 10)
+    scene_v = nvc.Scene.from_synth(sc_big)
+    cl_v = nvc.Clusters(assign_big, k, weights="visibility")
+    sample_vis_big_ms = timed(("sample_vis",))
     cache.close()
     ops = clustered_alu_ops(CLUSTERED_LIGHTS, k, P)
     peak = alu_peak_ops()
@@ -308,6 +324,11 @@ def measure_clustered(args, gb, stream):
         "value": P / (frame_ms * 1e-3) / 1e6, "unit": "Mpixels/s", "frame_ms": frame_ms,
         "train_ms": train_ms, "infer_ms": infer_ms, "sample_with_shadow_ray_ms": sample_ms,
         "sampler_ms": sampler_ms,
+        "visibility_weights": {
+            "frame_ms": frame_vis_ms, "value": P / (frame_vis_ms * 1e-3) / 1e6,
+            "sample_with_shadow_ray_ms": sample_vis_ms,
+            f"sample_with_shadow_ray_ms_at_{PAPER_SCALE_LIGHTS}_lights": sample_vis_big_ms,
+            "note": "first-step weights max(v, 0.001) alone (NVC_CLUSTER_WEIGHT_VISIBILITY)"},
         "roofline": {"kernel": "sample_clustered_kernel (no shadow ray)", "bound": "alu",
                      "achieved": ops / (sampler_ms * 1e-3) / 1e12, "peak": peak / 1e12,
                      "unit": "Tops/s", "frac": ops / (sampler_ms * 1e-3) / peak,

@@ -315,10 +315,22 @@ nvc_status nvc_exact_di(const nvc_scene* scene, const float* pos, const float* n
  * table makes the kernels read out of bounds.  With a clustered cache the
  * configuration's n_outputs is k (at most 32) and each output is a
  * cluster's average visibility; the scene may hold any number of lights. */
+/* Weights of the first sampling step (nvc_sample_clustered):
+ *   NVC_CLUSTER_WEIGHT_SUM         w_y = max(v_y, 0.001) * sum of the members'
+ *                                  contributions (one contribution per light
+ *                                  and pixel);
+ *   NVC_CLUSTER_WEIGHT_VISIBILITY  w_y = max(v_y, 0.001), the inferred average
+ *                                  visibility alone (cost independent of the
+ *                                  light count).
+ * Empty clusters weigh 0 in both; both estimators are unbiased. */
+#define NVC_CLUSTER_WEIGHT_SUM 0
+#define NVC_CLUSTER_WEIGHT_VISIBILITY 1
+
 typedef struct nvc_clusters {
   int32_t k;
   const int32_t* offsets;    /* [k + 1] */
   const int32_t* members;    /* [n_lights] */
+  int32_t weights;           /* NVC_CLUSTER_WEIGHT_*; 0 (zero-initialised) = SUM */
 } nvc_clusters;
 
 /* Lloyd's k-means of the light positions (host memory; Section 3.6), in
@@ -349,8 +361,9 @@ nvc_status nvc_cluster_targets(const nvc_scene* scene, const nvc_clusters* clust
                                float* target, void* stream);
 
 /* Two-step light sampling with a clustered cache (Section 3.6), per pixel:
- *   1. c_hat_y = sum of the members' contributions (float32, member order),
- *      w_y = max(vis[p][y], 0.001) c_hat_y, and cluster y picked by the
+ *   1. the cluster weights of clusters->weights (for SUM, c_hat_y = sum of
+ *      the members' contributions in float32 member order and
+ *      w_y = max(vis[p][y], 0.001) c_hat_y), and cluster y picked by the
  *      integer reservoir of nvc_wrs_sample (Philox tag 0, word y);
  *   2. four members of y drawn uniformly (words 0-3 of tag 4), one kept by
  *      the integer reservoir on their contributions (words 4-7), with the

@@ -47,8 +47,12 @@ class NvcScene(Structure):
         ("world_min", c_float * 3), ("world_max", c_float * 3)]
 
 
+CLUSTER_WEIGHTS = {"sum": 0, "visibility": 1}
+
+
 class NvcClusters(Structure):
-    _fields_ = [("k", c_int32), ("offsets", c_void_p), ("members", c_void_p)]
+    _fields_ = [("k", c_int32), ("offsets", c_void_p), ("members", c_void_p),
+                ("weights", c_int32)]
 
 
 class NvcCounters(Structure):

@@ -866,6 +866,8 @@ static nvc_status check_clusters(nvc_handle* h, const nvc_scene* scene, const nv
   if (expect_k > 0 && cl->k != expect_k)
     return fail(h, NVC_ERR_INVALID_ARG, "clusters: k must equal n_outputs");
   if (!cl->offsets || !cl->members) return fail(h, NVC_ERR_INVALID_ARG, "clusters: NULL table");
+  if (cl->weights != NVC_CLUSTER_WEIGHT_SUM && cl->weights != NVC_CLUSTER_WEIGHT_VISIBILITY)
+    return fail(h, NVC_ERR_INVALID_ARG, "clusters: unknown weight mode");
   NVC_TRY(check_ptr(h, cl->offsets, "clusters.offsets"));
   NVC_TRY(check_ptr(h, cl->members, "clusters.members"));
   if (scene->n_lights < 1) return fail(h, NVC_ERR_INVALID_ARG, "clustered scene without lights");
@@ -930,7 +932,7 @@ nvc_status nvc_sample_clustered(const nvc_scene* scene, const nvc_clusters* clus
   if (light) NVC_TRY(check_ptr(nullptr, light, "light"));
   if (weight) NVC_TRY(check_ptr(nullptr, weight, "weight"));
   if (estimate) NVC_TRY(check_ptr(nullptr, estimate, "estimate"));
-  if (sample_clustered_smem(scene) > 227 * 1024)
+  if (sample_clustered_smem(scene, clusters) > 227 * 1024)
     return fail(nullptr, NVC_ERR_UNSUPPORTED, "too many occluders for shared memory");
   int sms = 0;
   NVC_CUDA(nullptr, current_sms(&sms));

@@ -145,7 +145,9 @@ __device__ __forceinline__ int cluster_reservoir(const float (&w)[kMaxClusters],
 // (kSmemLights only)] [spheres] [offsets k + 1, as float4 slots] [boxes].
 // With the lights in table order the members of cluster y are the
 // contiguous slots offsets[y] .. offsets[y + 1] - 1.
-template <bool kSmemLights>
+// kSum: first-step weights max(v, 0.001) * c_hat (else max(v, 0.001) alone,
+// and no light loop).
+template <bool kSmemLights, bool kSum>
 __global__ void __launch_bounds__(1024) sample_clustered_kernel(
     const float* __restrict__ lights, int n_lights, const float* __restrict__ spheres, int n_sph,
     const float* __restrict__ boxes, int n_box, const int32_t* __restrict__ off,
@@ -186,14 +188,19 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
 #pragma unroll 1
     for (int y = 0; y < k; ++y) {
       const float v = __ldg(vrow + y);
-      float ch = 0.0f;
-      const int end = s_off[y + 1];
+      const int begin = s_off[y], end = s_off[y + 1];
+      float wy;
+      if (kSum) {
+        float ch = 0.0f;
 #pragma unroll 4
-      for (int i = s_off[y]; i < end; ++i) {
-        const float4 l = kSmemLights ? s_lt[i] : light_at<false>(s_lt, lights, mem[i]);
-        ch = __fadd_rn(ch, contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w));
+        for (int i = begin; i < end; ++i) {
+          const float4 l = kSmemLights ? s_lt[i] : light_at<false>(s_lt, lights, mem[i]);
+          ch = __fadd_rn(ch, contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w));
+        }
+        wy = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), ch);
+      } else {
+        wy = end > begin ? fmaxf(v, bits_f(kVisClampBits)) : 0.0f;
       }
-      const float wy = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), ch);
 #pragma unroll
       for (int t = 0; t < kMaxClusters; ++t)
         if (t == y) w[t] = wy;
@@ -275,9 +282,10 @@ cudaError_t launch_cluster_targets(const nvc_scene* sc, const nvc_clusters* cl, 
 // lights are read through the read-only cache.
 constexpr size_t kSmemOptin = 227 * 1024;
 
-size_t sample_clustered_smem(const nvc_scene* sc) {
+size_t sample_clustered_smem(const nvc_scene* sc, const nvc_clusters* cl) {
   const size_t occ = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes) +
                      sizeof(float4) * ((kMaxClusters + 4) / 4);
+  if (cl->weights == NVC_CLUSTER_WEIGHT_VISIBILITY) return occ;   // no light loop
   const size_t lt = sizeof(float) * 4 * (size_t)sc->n_lights;
   return occ + lt <= kSmemOptin ? occ + lt : occ;
 }
@@ -288,11 +296,13 @@ cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl,
                                     uint32_t view, int32_t* light, float* weight, float* estimate,
                                     int num_sms, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const size_t smem = sample_clustered_smem(sc);
+  const size_t smem = sample_clustered_smem(sc, cl);
   const bool lights_on_chip = smem > sizeof(float) * (4 * (size_t)sc->n_spheres +
                                                       6 * (size_t)sc->n_boxes) +
                                          sizeof(float4) * ((kMaxClusters + 4) / 4);
-  auto kern = lights_on_chip ? sample_clustered_kernel<true> : sample_clustered_kernel<false>;
+  auto kern = cl->weights == NVC_CLUSTER_WEIGHT_VISIBILITY ? sample_clustered_kernel<false, false>
+              : lights_on_chip                             ? sample_clustered_kernel<true, true>
+                                                           : sample_clustered_kernel<false, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // The staged lights are shared by a CTA's threads: take the smallest CTA

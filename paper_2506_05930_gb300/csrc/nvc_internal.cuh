@@ -315,7 +315,7 @@ cudaError_t launch_exact_di(const nvc_scene* sc, const float* pos, const float* 
 cudaError_t launch_cluster_targets(const nvc_scene* sc, const nvc_clusters* cl, const float* pos,
                                    int64_t n, uint64_t seed, uint32_t frame, float* target,
                                    cudaStream_t s);
-size_t sample_clustered_smem(const nvc_scene* sc);
+size_t sample_clustered_smem(const nvc_scene* sc, const nvc_clusters* cl);
 cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl, const float* vis,
                                     const float* pos, const float* nrm, int64_t n,
                                     int64_t pixel_offset, uint64_t seed, uint32_t frame,

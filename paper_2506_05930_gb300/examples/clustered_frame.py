@@ -23,6 +23,8 @@ def main():
     ap.add_argument("--lights", type=int, default=1024)
     ap.add_argument("--train-frames", type=int, default=20)
     ap.add_argument("--frames", type=int, default=4)
+    ap.add_argument("--weights", default="sum", choices=["sum", "visibility"],
+                    help="first-step cluster weights (NVC_CLUSTER_WEIGHT_*)")
     args = ap.parse_args()
 
     cfg = S.config_by_name("clustered_1080p")
@@ -30,7 +32,7 @@ def main():
     sc = S.scene_rooms(seed=1, n_lights=args.lights)
     gb = S.gbuffer_heightfield(seed=1, width=args.width, height=args.height)
     assign, _ = nvc.nvc_kmeans_lights(sc.lights, S.kmeans_init(args.lights, k, seed=0), 10)
-    clusters = nvc.Clusters(assign, k)
+    clusters = nvc.Clusters(assign, k, weights=args.weights)
     scene = nvc.Scene.from_synth(sc)
     pos = torch.from_numpy(gb.pos).cuda()
     nrm = torch.from_numpy(gb.nrm).cuda()
@@ -63,7 +65,8 @@ def main():
     mean = acc.cpu().numpy() / args.frames
     ex = exact.cpu().numpy().astype(np.float64)
     times /= max(args.frames, 1)
-    print(f"{gb.width}x{gb.height}, {args.lights} lights, k = {k}: train {times[0]:.3f} ms, "
+    print(f"{gb.width}x{gb.height}, {args.lights} lights, k = {k}, {args.weights} weights: "
+          f"train {times[0]:.3f} ms, "
           f"infer {times[1]:.3f} ms, sample + shadow ray {times[2]:.3f} ms; "
           f"loss {loss.item():.4f}; relative RMS error of the {args.frames}-frame mean "
           f"{np.sqrt(np.mean((mean - ex) ** 2)) / max(np.sqrt(np.mean(ex ** 2)), 1e-30):.3f}")

@@ -387,9 +387,11 @@ def nvc_kmeans_lights(lights, init, iters):
 
 
 class Clusters:
-    """Device CSR table of a light clustering and its nvc_clusters view."""
+    """Device CSR table of a light clustering and its nvc_clusters view;
+    `weights` names the sampler's first-step weights ("sum" or
+    "visibility", NVC_CLUSTER_WEIGHT_*)."""
 
-    def __init__(self, assign, k, device="cuda"):
+    def __init__(self, assign, k, device="cuda", weights="sum"):
         import numpy as np
         assign = np.asarray(assign, np.int64)
         order = np.argsort(assign, kind="stable")
@@ -400,6 +402,7 @@ class Clusters:
         c.k = int(k)
         c.offsets = self.offsets.data_ptr()
         c.members = self.members.data_ptr()
+        c.weights = _lib.CLUSTER_WEIGHTS[weights]
         self.struct = c
 
     @property

@@ -32,7 +32,7 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def clustering(sc, k, seed=0, iters=8, empty=None):
+def clustering(sc, k, seed=0, iters=8, empty=None, weights="sum"):
     """k-means clusters of the scene's lights; `empty` names a cluster whose
     members are moved to cluster 0, so the table holds an empty cluster."""
     init = S.kmeans_init(len(sc.lights), k, seed=seed)
@@ -40,7 +40,7 @@ def clustering(sc, k, seed=0, iters=8, empty=None):
     if empty is not None:
         assign = np.where(assign == empty, 0, assign).astype(np.int32)
     off, mem = O.cluster_table(assign, k)
-    return nvc.Clusters(assign, k), off, mem
+    return nvc.Clusters(assign, k, weights=weights), off, mem
 
 
 def world_points(seed, n, sc):
@@ -87,12 +87,16 @@ def _estimate_ref(sc, pos, nrm, light, W):
     return est
 
 
-@pytest.mark.parametrize("n_lights,k,empty", [(300, 32, None), (300, 9, 3), (15000, 32, None)])
-def test_sample_clustered_bitexact(n_lights, k, empty):
-    """Light and contribution weight bit-exact against the oracle; the third
-    case holds more lights than shared memory (lights read from global)."""
+@pytest.mark.parametrize("n_lights,k,empty,weights",
+                         [(300, 32, None, "sum"), (300, 9, 3, "sum"), (15000, 32, None, "sum"),
+                          (300, 32, None, "visibility"), (300, 9, 3, "visibility"),
+                          (15000, 32, 7, "visibility")])
+def test_sample_clustered_bitexact(n_lights, k, empty, weights):
+    """Light and contribution weight bit-exact against the oracle, for both
+    first-step weights; the 15,000-light cases hold more lights than shared
+    memory (lights read from global)."""
     sc = S.scene_many_lights(seed=4, n_lights=n_lights, n_groups=40)
-    cl, off, mem = clustering(sc, k, empty=empty, iters=5)
+    cl, off, mem = clustering(sc, k, empty=empty, iters=5, weights=weights)
     gb = S.gbuffer_heightfield(seed=4, width=53, height=37)
     scene = nvc.Scene.from_synth(sc)
     vis = _vis(5, gb.n, k)
@@ -103,23 +107,26 @@ def test_sample_clustered_bitexact(n_lights, k, empty):
     nvc.nvc_sample_clustered(scene, cl, dev(vis), dev(gb.pos), dev(gb.nrm), seed, frame, view,
                              pixel_offset=off_px, light=light, weight=W, estimate=est)
     rl, rW = O.sample_clustered(vis, gb.pos, gb.nrm, sc.lights, off, mem,
-                                off_px + np.arange(gb.n), seed, frame, view)
+                                off_px + np.arange(gb.n), seed, frame, view, weights)
     gl, gW = host(light), host(W)
     assert np.array_equal(gl, rl)
     assert np.array_equal(gW, rW)
-    assert (gl >= 0).mean() > 0.9
+    # visibility-only weights also pick clusters whose members all face away
+    # (no light then, an unbiased zero estimate)
+    assert (gl >= 0).mean() > (0.9 if weights == "sum" else 0.8)
     sub = np.arange(0, gb.n, 7)
     ref_est = _estimate_ref(sc, gb.pos[sub], gb.nrm[sub], rl[sub], rW[sub])
     assert np.array_equal(host(est)[sub], ref_est)
     assert (ref_est > 0).any() and (ref_est[rl[sub] >= 0] == 0).any()
 
 
-def test_sample_clustered_is_unbiased_against_exact_di():
+@pytest.mark.parametrize("weights", ["sum", "visibility"])
+def test_sample_clustered_is_unbiased_against_exact_di(weights):
     """Averaged over frames, V c W of the two-step sampler converges to the
     all-lights DI of each pixel: the estimator is unbiased for any cluster
-    visibilities (here fixed random ones)."""
+    visibilities (here fixed random ones) and either first-step weights."""
     sc = S.scene_many_lights(seed=6, n_lights=512, n_groups=32)
-    cl, _, _ = clustering(sc, 32)
+    cl, _, _ = clustering(sc, 32, weights=weights)
     gb = S.gbuffer_heightfield(seed=6, width=64, height=32)
     scene = nvc.Scene.from_synth(sc)
     pos, nrm = dev(gb.pos), dev(gb.nrm)
@@ -219,17 +226,22 @@ def test_trained_clustered_cache_learns_cluster_visibility_and_lowers_error():
     exact = torch.empty(gb.n, device="cuda")
     nvc.nvc_exact_di(scene, pos, nrm, exact)
     ex = host(exact).astype(np.float64)
-    mse = []
-    for cache in (trained, untrained):
-        vis = cache.infer(pos)
-        est = torch.empty(gb.n, device="cuda")
-        acc = torch.zeros(gb.n, dtype=torch.float64, device="cuda")
-        for f in range(16):
-            nvc.nvc_sample_clustered(scene, cl, vis, pos, nrm, 21, 1000 + f, estimate=est)
-            acc += est.double()
-        d = host(acc) / 16 - ex
-        mse.append(np.mean(d * d))
-    assert mse[0] < 0.6 * mse[1], mse
+    cl_vis = nvc.Clusters(nvc.nvc_kmeans_lights(sc.lights, S.kmeans_init(1024, 32, seed=0),
+                                                10)[0], 32, weights="visibility")
+    mse = {}
+    for weights, clw in (("sum", cl), ("visibility", cl_vis)):
+        for name, cache in (("trained", trained), ("untrained", untrained)):
+            vis = cache.infer(pos)
+            est = torch.empty(gb.n, device="cuda")
+            acc = torch.zeros(gb.n, dtype=torch.float64, device="cuda")
+            for f in range(16):
+                nvc.nvc_sample_clustered(scene, clw, vis, pos, nrm, 21, 1000 + f, estimate=est)
+                acc += est.double()
+            d = host(acc) / 16 - ex
+            mse[(weights, name)] = float(np.mean(d * d))
+    print("\nclustered estimate MSE after 16 frames:", mse)
+    for weights in ("sum", "visibility"):
+        assert mse[(weights, "trained")] < 0.6 * mse[(weights, "untrained")], mse
     trained.close()
     untrained.close()
 
@@ -253,6 +265,10 @@ def test_empty_and_invalid_inputs():
         nvc.nvc_cluster_targets(scene, bad, p, 1, 1, v)
     bad.struct.k = 0
     with pytest.raises(_lib.NVCError):
+        nvc.nvc_sample_clustered(scene, bad, v, p, p, 1, 1, estimate=torch.zeros(4, device="cuda"))
+    bad.struct.k = 8
+    bad.struct.weights = 2
+    with pytest.raises(_lib.NVCError):                      # unknown weight mode
         nvc.nvc_sample_clustered(scene, bad, v, p, p, 1, 1, estimate=torch.zeros(4, device="cuda"))
     cache = nvc.VisibilityCache(S.config_by_name("clustered_1080p"))
     with pytest.raises(_lib.NVCError):           # k must equal n_outputs (32)
