@@ -238,6 +238,42 @@ KERNEL_TRAFFIC = {"fused_shade": 109.98e6, "adam": 428.34e6,
 
 # ------------------------------------------------------------- our arm ----
 
+def measure_tiny(stream, use_graph):
+    """The launch-bound tiny workload (64x64 points, 4 lights, FP32): one
+    frame = a training step on 1024 positions x 4 lights, then inference,
+    WRS and Neural DI of the 4096 points, as one captured CUDA graph.
+    Reported in microseconds per frame (200 frames after 10 warm-up)."""
+    import torch
+    from paper_2506_05930_gb300 import nvc
+    import nvc_synth as S
+    cfg = S.config_by_name("tiny_fp32")
+    sc = S.scene_unit_cube(seed=0)
+    gb = S.gbuffer_points(0, 64, 64)
+    cache = nvc.VisibilityCache(cfg)
+    cache.set_params(S.init_params(cfg, seed=0))
+    scene = nvc.Scene.from_synth(sc)
+    n = gb.n
+    view = nvc.View(torch.from_numpy(gb.pos).cuda(), torch.from_numpy(gb.nrm).cuda(), 0,
+                    torch.empty(n, dtype=torch.int32, device="cuda"),
+                    torch.empty(n, device="cuda"), torch.empty(n, device="cuda"),
+                    torch.empty(n, device="cuda"))
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    for f in range(10):
+        nvc.nvc_frame(cache.handle, scene, [view], 0, 3, f, loss, use_graph=use_graph)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for f in range(200):
+        nvc.nvc_frame(cache.handle, scene, [view], 0, 3, 10 + f, loss, use_graph=use_graph)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cache.close()
+    return {"workload": "tiny_fp32: 64x64 points, 4 lights, 4 spheres; training 1024 "
+                        "positions x 4 lights; FP32", "us_per_frame": e0.elapsed_time(e1) / 200 * 1e3,
+            "cuda_graph": use_graph}
+
+
 CLUSTERED_LIGHTS = 1024
 PAPER_SCALE_LIGHTS = 59000      # the light count of the paper's many-lights scene
 
@@ -519,6 +555,7 @@ def run_ours(args):
                            "running mean; exact DI: a shadow ray to every light from every pixel"}
 
     clustered = measure_clustered(args, gb, stream) if rank == 0 else None
+    tiny = measure_tiny(stream, use_graph) if rank == 0 else None
 
     if rank != 0:
         if world > 1:
@@ -562,6 +599,11 @@ def run_ours(args):
                       "adam": stage_ms[2], "shade": stage_ms[3], "eager_frame": eager_ms},
         "infer_mpixels_s": P / shade_s / 1e6 if shade_s > 0 else None,
         "train_ms": stage_ms[0] + stage_ms[1] + stage_ms[2],
+        "train_rates": {
+            "positions_per_s": cfg.batch_positions / ((stage_ms[0] + stage_ms[1] + stage_ms[2]) * 1e-3),
+            "targets_per_s": cfg.batch_positions * cfg.n_outputs
+                             / ((stage_ms[0] + stage_ms[1] + stage_ms[2]) * 1e-3),
+            "note": "training step = positions + shadow-ray targets, forward/backward, Adam"},
         "e2e": {"value": job_throughput(world, P, e_ms), "unit": "Mpixels/s",
                 "ms_per_step": e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -574,8 +616,12 @@ def run_ours(args):
         line["shading_pass"] = shading
     if clustered:
         line["clustered"] = clustered
+    if tiny:
+        line["tiny_frame"] = tiny
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(seconds_target=15.0)
+        line["cpu_baseline_all_cores"] = cpu_baseline(seconds_target=15.0,
+                                                      threads=os.cpu_count() or 1)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -646,9 +692,12 @@ def oracle_fixed_costs(reps=2):
     return min(fs), min(ft)
 
 
-def cpu_baseline(seconds_target=15.0):
-    """Run the oracle in a child process with one BLAS thread."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def cpu_baseline(seconds_target=15.0, threads=1):
+    """Run the oracle in a child process with `threads` BLAS threads (the
+    oracle's matrix products use them; its elementwise numpy steps run on
+    one core whatever the count)."""
+    t = str(int(threads))
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
             "fx = bench.oracle_fixed_costs(); "
             "f, w, P = bench.oracle_frame_sample(131072, 4096, fixed=fx); print(json.dumps([f, w, P]))" % ROOT)
@@ -656,8 +705,8 @@ def cpu_baseline(seconds_target=15.0):
     if r.returncode != 0:
         return {"error": r.stderr[-300:]}
     frame_s, wall, P = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": P / frame_s / 1e6, "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
-            "ms_per_frame": frame_s * 1e3, "wall_s": wall,
+    return {"value": P / frame_s / 1e6, "unit": "Mpixels/s", "cores": int(threads),
+            "kind": "oracle", "ms_per_frame": frame_s * 1e3, "wall_s": wall,
             "sample": "131,072 random pixels of the 1080p frame shaded (inference+WRS+DI), "
                       "training forward/backward on 4,096 of the 8,192 positions, one dense Adam "
                       "update of all parameters; each part extrapolated to the full frame as a "

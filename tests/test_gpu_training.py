@@ -122,3 +122,56 @@ def test_online_training_1000_frames_converges_and_beats_no_cache():
     assert var1 < 0.8 * var_none.mean(), (var1, var_none.mean())
     assert var1 < var0
     assert di1 < 0.5 * di0, (di0, di1)
+
+
+def test_adaptation_after_an_abrupt_scene_change(capsys):
+    """Section 3.5: after the geometry changes abruptly the cache predicts
+    the old shadows until online training catches up, and a second
+    training step per frame shortens that.  The 1080p workload's cache is
+    trained for 300 frames, then every occluder jumps 2 units in x; the
+    visibility error on the view is followed for 32 frames with one and
+    with two training steps per frame."""
+    cfg = S.config_by_name("frame_1080p")
+    sc = S.scene_heightfield(seed=1, n_lights=32, n_spheres=32, n_boxes=32)
+    gb = S.gbuffer_heightfield(seed=1, width=320, height=180)
+    pos = dev(gb.pos)
+    before = nvc.Scene.from_synth(sc)
+    shift = np.array([2.0, 0.0, 0.0], np.float32)
+    moved_sph = sc.spheres.copy()
+    moved_sph[:, :3] += shift
+    moved_box = sc.boxes.copy()
+    moved_box[:, :3] += shift
+    moved_box[:, 3:] += shift
+    after = nvc.Scene(sc.lights, moved_sph, moved_box, sc.world_min, sc.world_max)
+    truth = torch.empty((gb.n, 32), device="cuda")
+    nvc.nvc_trace_visibility(after, pos, truth)
+    base = nvc.VisibilityCache(cfg)
+    base.set_params(S.init_params(cfg, seed=0))
+    for f in range(300):
+        nvc.nvc_train_step(base.handle, before, pos, 11, f)
+    state = [host(t) for t in base.state()]
+    step0 = base.counters()["step"]
+    base.close()
+
+    def err(cache):
+        d = cache.infer(pos) - truth
+        return float((d * d).mean())
+
+    curves = {}
+    for steps in (1, 2):
+        cache = nvc.VisibilityCache(cfg)
+        cache.set_params(*state, step=step0)
+        curve = [err(cache)]
+        for f in range(32):
+            for s in range(steps):
+                nvc.nvc_train_step(cache.handle, after, pos, 13, 1000 + 2 * f + s)
+            curve.append(err(cache))
+        curves[steps] = curve
+        cache.close()
+    with capsys.disabled():
+        print("\nMSE after the change, frames 0/4/8/16/32:",
+              {k: [round(v[i], 4) for i in (0, 4, 8, 16, 32)] for k, v in curves.items()})
+    one, two = curves[1], curves[2]
+    assert one[0] > 2 * one[32]                 # the jump is visible, and training recovers
+    assert one[16] < 0.5 * one[0]               # within 16 frames the error at least halves
+    assert two[8] < one[8]                      # two steps per frame adapt faster
