@@ -21,8 +21,12 @@ namespace nvc {
 
 namespace {
 
-constexpr int kRows = 128;       // samples per tile = threads per block
-constexpr int kStride = 129;     // padded row stride of the shared activations
+// Samples per tile = threads per block: 128, or 32 when a batch has fewer
+// 128-row tiles than SMs (so a small training batch still spreads over the
+// GPU).  Shared activation rows are padded to R + 1 floats (no bank
+// conflicts between the threads' columns).
+constexpr int kRows = 128;
+constexpr int kRowsSmall = 32;
 
 struct MlpDims {
   int n_layers;
@@ -61,15 +65,16 @@ MlpDims make_dims(const nvc_handle* h, bool transposed) {
   return d;
 }
 
-size_t smem_bytes(const MlpDims& d) {
-  return sizeof(float) * ((size_t)d.s_weights + 2 * (size_t)round8(d.maxdim) * kStride);
+size_t smem_bytes(const MlpDims& d, int rows = kRows) {
+  return sizeof(float) * ((size_t)d.s_weights + 2 * (size_t)round8(d.maxdim) * (rows + 1));
 }
 
 __device__ __forceinline__ float act_fn(float z, float slope) { return z > 0.0f ? z : slope * z; }
 
 __device__ __forceinline__ float sigmoid_f(float z) { return 1.0f / (1.0f + expf(-z)); }
 
-__global__ void __launch_bounds__(kRows) mlp_fwd_kernel(const float* __restrict__ feat, int64_t n,
+template <int R>
+__global__ void __launch_bounds__(R) mlp_fwd_kernel(const float* __restrict__ feat, int64_t n,
                                                         const float* __restrict__ params,
                                                         MlpDims d, float* __restrict__ y,
                                                         int sigmoid_out,
@@ -78,13 +83,13 @@ __global__ void __launch_bounds__(kRows) mlp_fwd_kernel(const float* __restrict_
   extern __shared__ float smem[];
   float* sw = smem;
   float* buf0 = smem + d.s_weights;
-  float* buf1 = buf0 + round8(d.maxdim) * kStride;
+  float* buf1 = buf0 + round8(d.maxdim) * (R + 1);
   const int t = threadIdx.x;
 
   // weights, transposed to [in][pad_out] with zero padding
   for (int k = 0; k < d.n_layers; ++k) {
     const int in = d.in[k], out = d.out[k], po = d.pad_out[k];
-    for (int e = t; e < in * po; e += kRows) {
+    for (int e = t; e < in * po; e += R) {
       const int i = e / po, j = e - i * po;
       sw[d.s_off[k] + e] = j < out ? __ldg(params + d.w_off[k] + (int64_t)j * in + i) : 0.0f;
     }
@@ -92,14 +97,14 @@ __global__ void __launch_bounds__(kRows) mlp_fwd_kernel(const float* __restrict_
   __syncthreads();
 
   const int din = d.in[0];
-  const int64_t n_tiles = (n + kRows - 1) / kRows;
+  const int64_t n_tiles = (n + R - 1) / R;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int64_t row0 = tile * kRows;
-    const int rows = (int)(n - row0 < kRows ? n - row0 : kRows);
+    const int64_t row0 = tile * R;
+    const int rows = (int)(n - row0 < R ? n - row0 : R);
     // cooperative, coalesced load of the tile's inputs into buf0[k][row]
-    for (int e = t; e < kRows * din; e += kRows) {
+    for (int e = t; e < R * din; e += R) {
       const int r = e / din, k = e - r * din;
-      buf0[k * kStride + r] = r < rows ? __ldg(feat + (row0 + r) * din + k) : 0.0f;
+      buf0[k * (R + 1) + r] = r < rows ? __ldg(feat + (row0 + r) * din + k) : 0.0f;
     }
     __syncthreads();
     float* src = buf0;
@@ -113,7 +118,7 @@ __global__ void __launch_bounds__(kRows) mlp_fwd_kernel(const float* __restrict_
       for (int jb = 0; jb < po; jb += 8) {
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int i = 0; i < in; ++i) {
-          const float x = src[i * kStride + t];
+          const float x = src[i * (R + 1) + t];
           const float4 w0 = *reinterpret_cast<const float4*>(wk + i * po + jb);
           const float4 w1 = *reinterpret_cast<const float4*>(wk + i * po + jb + 4);
           acc[0] = fmaf(w0.x, x, acc[0]);
@@ -132,7 +137,7 @@ __global__ void __launch_bounds__(kRows) mlp_fwd_kernel(const float* __restrict_
             const int j = jb + q;
             if (j < nout) {
               const float a = act_fn(acc[q], d.slope);
-              dst[j * kStride + t] = a;
+              dst[j * (R + 1) + t] = a;
               if (a_row && live) a_row[j] = a;
             }
           }
@@ -152,7 +157,8 @@ __global__ void __launch_bounds__(kRows) mlp_fwd_kernel(const float* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(kRows) mlp_bwd_kernel(int64_t n, const float* __restrict__ params,
+template <int R>
+__global__ void __launch_bounds__(R) mlp_bwd_kernel(int64_t n, const float* __restrict__ params,
                                                         MlpDims d, const float* __restrict__ act,
                                                         int64_t act_layer_stride,
                                                         float* __restrict__ delta,
@@ -161,12 +167,12 @@ __global__ void __launch_bounds__(kRows) mlp_bwd_kernel(int64_t n, const float* 
   extern __shared__ float smem[];
   float* sw = smem;
   float* buf0 = smem + d.s_weights;
-  float* buf1 = buf0 + round8(d.maxdim) * kStride;
+  float* buf1 = buf0 + round8(d.maxdim) * (R + 1);
   const int t = threadIdx.x;
   // weights in [out][pad_in] (rows contiguous), zero padding
   for (int k = 0; k < d.n_layers; ++k) {
     const int in = d.in[k], out = d.out[k], pi = d.pad_in[k];
-    for (int e = t; e < out * pi; e += kRows) {
+    for (int e = t; e < out * pi; e += R) {
       const int j = e / pi, i = e - j * pi;
       sw[d.s_off[k] + e] = i < in ? __ldg(params + d.w_off[k] + (int64_t)j * in + i) : 0.0f;
     }
@@ -174,10 +180,10 @@ __global__ void __launch_bounds__(kRows) mlp_bwd_kernel(int64_t n, const float* 
   __syncthreads();
   const int top = d.n_layers - 1;
   const int L = d.out[top];
-  const int64_t n_tiles = (n + kRows - 1) / kRows;
+  const int64_t n_tiles = (n + R - 1) / R;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int64_t row0 = tile * kRows;
-    const int rows = (int)(n - row0 < kRows ? n - row0 : kRows);
+    const int64_t row0 = tile * R;
+    const int rows = (int)(n - row0 < R ? n - row0 : R);
     const float* dtop = delta + top * delta_layer_stride;
     float* src = buf0;
     float* dst = buf1;
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(kRows) mlp_bwd_kernel(int64_t n, const float* 
       for (int ib = 0; ib < pi; ib += 8) {
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int j = 0; j < out; ++j) {
-          const float g = k == top ? (live ? g_row[j] : 0.0f) : src[j * kStride + t];
+          const float g = k == top ? (live ? g_row[j] : 0.0f) : src[j * (R + 1) + t];
           const float4 w0 = *reinterpret_cast<const float4*>(wk + j * pi + ib);
           const float4 w1 = *reinterpret_cast<const float4*>(wk + j * pi + ib + 4);
           acc[0] = fmaf(w0.x, g, acc[0]);
@@ -212,7 +218,7 @@ __global__ void __launch_bounds__(kRows) mlp_bwd_kernel(int64_t n, const float* 
             if (i < in) {
               const float a = live ? a_row[i] : 0.0f;
               const float dv = a > 0.0f ? acc[q] : d.slope * acc[q];
-              dst[i * kStride + t] = dv;
+              dst[i * (R + 1) + t] = dv;
               if (live) d_row[i] = dv;
             }
           }
@@ -232,21 +238,22 @@ __global__ void __launch_bounds__(kRows) mlp_bwd_kernel(int64_t n, const float* 
   }
 }
 
-// dW[j][i] += sum_b D[b][j] * A[b][i] over a 256-row chunk of the batch.
-constexpr int kWgTile = 32, kWgChunk = 256, kWgSub = 32;
+// dW[j][i] += sum_b D[b][j] * A[b][i] over a `chunk`-row slice of the batch
+// (a multiple of kWgSub), one 32 x 32 tile of dW per CTA.
+constexpr int kWgTile = 32, kWgSub = 32;
 
 __global__ void __launch_bounds__(256) weight_grad_kernel(const float* __restrict__ D, int ldd,
                                                           const float* __restrict__ A, int lda,
                                                           int64_t n, int n_out, int n_in,
-                                                          float* __restrict__ dW,
+                                                          int chunk, float* __restrict__ dW,
                                                           int32_t* status) {
   __shared__ float sD[kWgSub][kWgTile + 1];
   __shared__ float sA[kWgSub][kWgTile + 1];
   const int j0 = blockIdx.x * kWgTile, i0 = blockIdx.y * kWgTile;
-  const int64_t b0 = (int64_t)blockIdx.z * kWgChunk;
+  const int64_t b0 = (int64_t)blockIdx.z * chunk;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float acc[2][2] = {{0, 0}, {0, 0}};
-  for (int sb = 0; sb < kWgChunk; sb += kWgSub) {
+  for (int sb = 0; sb < chunk && b0 + sb < n; sb += kWgSub) {
     for (int e = threadIdx.x; e < kWgSub * kWgTile; e += 256) {
       const int r = e / kWgTile, c = e - r * kWgTile;
       const int64_t b = b0 + sb + r;
@@ -277,10 +284,39 @@ __global__ void __launch_bounds__(256) weight_grad_kernel(const float* __restric
     }
 }
 
-int persistent_blocks(const nvc_handle* h, size_t smem, int64_t n_tiles) {
-  const int per_sm = blocks_per_sm((const void*)mlp_fwd_kernel, kRows, smem);
+int small_rows(const nvc_handle* h, int64_t n) { return (n + kRows - 1) / kRows < h->num_sms; }
+
+template <int R>
+cudaError_t launch_fwd(const nvc_handle* h, const MlpDims& d, const float* feat, int64_t n,
+                       float* out, bool sigmoid_out, float* act_store, cudaStream_t s) {
+  const size_t smem = smem_bytes(d, R);
+  cudaError_t e = cudaFuncSetAttribute(mlp_fwd_kernel<R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t n_tiles = (n + R - 1) / R;
+  const int per_sm = blocks_per_sm((const void*)mlp_fwd_kernel<R>, R, smem);
   const int64_t cap = (int64_t)per_sm * h->num_sms;
-  return (int)(n_tiles < cap ? n_tiles : cap);
+  const int blocks = (int)(n_tiles < cap ? n_tiles : cap);
+  mlp_fwd_kernel<R><<<blocks, R, smem, s>>>(feat, n, h->params, d, out, sigmoid_out ? 1 : 0,
+                                            act_store, (int64_t)h->B * h->width);
+  return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_bwd(const nvc_handle* h, const MlpDims& d, int64_t n, cudaStream_t s) {
+  const size_t smem = smem_bytes(d, R);
+  cudaError_t e = cudaFuncSetAttribute(mlp_bwd_kernel<R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t n_tiles = (n + R - 1) / R;
+  const int per_sm = blocks_per_sm((const void*)mlp_bwd_kernel<R>, R, smem);
+  const int64_t cap = (int64_t)per_sm * h->num_sms;
+  const int blocks = (int)(n_tiles < cap ? n_tiles : cap);
+  const int maxdim = h->width > h->L ? h->width : h->L;
+  mlp_bwd_kernel<R><<<blocks, R, smem, s>>>(n, h->params, d, h->t_act,
+                                            (int64_t)h->B * h->width, h->t_delta,
+                                            (int64_t)h->B * maxdim, h->t_dfeat);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -291,15 +327,8 @@ cudaError_t launch_mlp_fwd_fp32(const nvc_handle* h, const float* feat, int64_t 
                                 bool sigmoid_out, float* act_store, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const MlpDims d = make_dims(h, true);
-  const size_t smem = smem_bytes(d);
-  cudaError_t e = cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  const int64_t n_tiles = (n + kRows - 1) / kRows;
-  const int blocks = persistent_blocks(h, smem, n_tiles);
-  mlp_fwd_kernel<<<blocks, kRows, smem, s>>>(feat, n, h->params, d, out, sigmoid_out ? 1 : 0,
-                                             act_store, (int64_t)h->B * h->width);
-  return cudaGetLastError();
+  return small_rows(h, n) ? launch_fwd<kRowsSmall>(h, d, feat, n, out, sigmoid_out, act_store, s)
+                          : launch_fwd<kRows>(h, d, feat, n, out, sigmoid_out, act_store, s);
 }
 
 cudaError_t launch_mlp_bwd_fp32(const nvc_handle* h, int64_t n, const float* dlogits_unused,
@@ -307,29 +336,26 @@ cudaError_t launch_mlp_bwd_fp32(const nvc_handle* h, int64_t n, const float* dlo
   (void)dlogits_unused;
   if (n == 0) return cudaSuccess;
   const MlpDims d = make_dims(h, false);
-  const size_t smem = smem_bytes(d);
-  cudaError_t e = cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = small_rows(h, n) ? launch_bwd<kRowsSmall>(h, d, n, s) : launch_bwd<kRows>(h, d, n, s);
   if (e != cudaSuccess) return e;
-  const int64_t n_tiles = (n + kRows - 1) / kRows;
-  const int per_sm = blocks_per_sm((const void*)mlp_bwd_kernel, kRows, smem);
-  const int64_t cap = (int64_t)per_sm * h->num_sms;
-  const int blocks = (int)(n_tiles < cap ? n_tiles : cap);
   const int maxdim = h->width > h->L ? h->width : h->L;
   const int64_t act_stride = (int64_t)h->B * h->width;
   const int64_t delta_stride = (int64_t)h->B * maxdim;
-  mlp_bwd_kernel<<<blocks, kRows, smem, s>>>(n, h->params, d, h->t_act, act_stride, h->t_delta,
-                                             delta_stride, h->t_dfeat);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // weight gradients: layer k's input is t_feat (k = 0) or hidden activation k-1
   for (int k = 0; k < h->n_layers; ++k) {
     const float* D = h->t_delta + (int64_t)k * delta_stride;
     const float* A = k == 0 ? h->t_feat : h->t_act + (int64_t)(k - 1) * act_stride;
     const int lda = h->w_in[k];
-    dim3 grid((h->w_out[k] + kWgTile - 1) / kWgTile, (h->w_in[k] + kWgTile - 1) / kWgTile,
-              (unsigned)((n + kWgChunk - 1) / kWgChunk));
+    // split the batch so the layer's tiles give about two CTAs per SM: a
+    // small batch is otherwise a handful of CTAs walking it serially
+    const int tx = (h->w_out[k] + kWgTile - 1) / kWgTile, ty = (h->w_in[k] + kWgTile - 1) / kWgTile;
+    const int64_t want = 2 * (int64_t)h->num_sms;
+    int64_t chunk = (n * tx * ty + want - 1) / want;
+    chunk = (chunk + kWgSub - 1) / kWgSub * kWgSub;
+    if (chunk < kWgSub) chunk = kWgSub;
+    dim3 grid(tx, ty, (unsigned)((n + chunk - 1) / chunk));
     weight_grad_kernel<<<grid, 256, 0, s>>>(D, h->w_out[k], A, lda, n, h->w_out[k], h->w_in[k],
-                                            grad + h->w_off[k], status);
+                                            (int)chunk, grad + h->w_off[k], status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
