@@ -261,6 +261,17 @@ nvc_status nvc_calibrate(nvc_handle* h, const float* pos, int64_t n, void* strea
  * bits of wsum, pdf and radiance. */
 #define NVC_SHADE_VARIANTS 8
 
+/* Chooses the fused-kernel variant that nvc_infer runs (the variants give
+ * bit-identical visibilities; the fastest for exporting them need not be the
+ * fastest for shading): times each variant that supports the configuration,
+ * `reps` calls of nvc_infer on pos (device [n][3]) into vis (device [n][L],
+ * scratch), and keeps the fastest for this handle's nvc_infer.  ms_out (host,
+ * NVC_SHADE_VARIANTS doubles, may be NULL) receives each variant's time
+ * (-1 where skipped); chosen (host, may be NULL) the variant.  Synchronous.
+ * With FP32 inference there are no variants: chosen = -1. */
+nvc_status nvc_autotune_infer(nvc_handle* h, const float* pos, int64_t n, float* vis,
+                              int32_t reps, int32_t* chosen, double* ms_out, void* stream);
+
 /* Times every applicable variant on these pixels (CUDA events on `stream`,
  * a warm-up then `reps` launches each; synchronises) and keeps the fastest
  * for this handle.  Outputs as nvc_shade (any may be NULL).  chosen (host,

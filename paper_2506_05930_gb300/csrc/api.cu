@@ -472,8 +472,12 @@ nvc_status nvc_infer(nvc_handle* h, const float* pos, int64_t n, float* vis, voi
   if (h->cfg.precision != NVC_PREC_FP32) {
     std::string why;
     if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
-    NVC_CUDA(h, launch_shade_fused(h, nullptr, pos, nullptr, n, 0, 0, 0, 0, nullptr, nullptr,
-                                   nullptr, nullptr, vis, s));
+    const int keep = h->shade_variant;
+    if (h->infer_variant >= 0) h->shade_variant = h->infer_variant;
+    const cudaError_t e = launch_shade_fused(h, nullptr, pos, nullptr, n, 0, 0, 0, 0, nullptr,
+                                             nullptr, nullptr, nullptr, vis, s);
+    h->shade_variant = keep;
+    NVC_CUDA(h, e);
     count_launches(h, 1);
     return NVC_OK;
   }
@@ -647,6 +651,61 @@ nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant) {
   if (variant != kShadeMono && variant != kShadePair && h->L > 32)
     return fail(h, NVC_ERR_UNSUPPORTED, "variants 1-4, 6 and 7 need n_outputs <= 32");
   h->shade_variant = variant;
+  return NVC_OK;
+}
+
+nvc_status nvc_autotune_infer(nvc_handle* h, const float* pos, int64_t n, float* vis,
+                              int32_t reps, int32_t* chosen, double* ms_out, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (n <= 0 || reps < 1) return fail(h, NVC_ERR_INVALID_ARG, "need n > 0 and reps >= 1");
+  NVC_TRY(check_ptr(h, pos, "pos"));
+  NVC_TRY(check_ptr(h, vis, "vis"));
+  for (int v = 0; v < kShadeVariants; ++v)
+    if (ms_out) ms_out[v] = -1.0;
+  if (h->cfg.precision == NVC_PREC_FP32) {   // the float32 path has no variants
+    if (chosen) *chosen = -1;
+    return NVC_OK;
+  }
+  std::string why;
+  if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  NVC_CUDA(h, cudaEventCreate(&e0));
+  NVC_CUDA(h, cudaEventCreate(&e1));
+  const int keep = h->shade_variant;
+  int best = -1;
+  double best_ms = 0.0;
+  cudaError_t err = cudaSuccess;
+  for (int v = 0; v < kShadeVariants && err == cudaSuccess; ++v) {
+    if (v != kShadeMono && h->cfg.precision == NVC_PREC_FP8) continue;
+    if (v != kShadeMono && v != kShadePair && h->L > 32) continue;
+    h->shade_variant = v;
+    if (launch_shade_fused(h, nullptr, pos, nullptr, n, 0, 0, 0, 0, nullptr, nullptr, nullptr,
+                           nullptr, vis, s) != cudaSuccess) {
+      cudaGetLastError();
+      continue;                       // variant does not fit this configuration
+    }
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r)
+      launch_shade_fused(h, nullptr, pos, nullptr, n, 0, 0, 0, 0, nullptr, nullptr, nullptr,
+                         nullptr, vis, s);
+    cudaEventRecord(e1, s);
+    if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = (double)ms / reps;
+    if (ms_out) ms_out[v] = per;
+    if (best < 0 || per < best_ms) {
+      best = v;
+      best_ms = per;
+    }
+  }
+  h->shade_variant = keep;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(h, err, "autotune");
+  if (best >= 0) h->infer_variant = best;
+  if (chosen) *chosen = h->infer_variant;
   return NVC_OK;
 }
 

@@ -80,6 +80,27 @@ __device__ __forceinline__ float sigmoid_fast(float z) {
   return __fdividef(1.0f, 1.0f + __expf(-z));
 }
 
+// Exported visibilities: the sigmoid of N accumulator words (times mul)
+// into dst[0 .. min(n, N)).  A full, 16-byte aligned run goes out as N/4
+// 16-byte stores; otherwise one checked store per value.
+template <int N>
+__device__ __forceinline__ void store_sigmoid_row(float* dst, const uint32_t (&r)[N], int n,
+                                                  float mul) {
+  if (n >= N && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q)
+      reinterpret_cast<float4*>(dst)[q] =
+          make_float4(sigmoid_fast(__uint_as_float(r[4 * q]) * mul),
+                      sigmoid_fast(__uint_as_float(r[4 * q + 1]) * mul),
+                      sigmoid_fast(__uint_as_float(r[4 * q + 2]) * mul),
+                      sigmoid_fast(__uint_as_float(r[4 * q + 3]) * mul));
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (j < n) dst[j] = sigmoid_fast(__uint_as_float(r[j]) * mul);
+  }
+}
+
 // Unshadowed contribution of a point light (Lambertian, albedo 1):
 // (I/pi) * (n.d) / (|d| * max(|d|^2, 1e-6)) for n.d > 0, with a hardware
 // reciprocal square root.

@@ -206,11 +206,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
         for (int c0 = 0; c0 < L; c0 += 32) {
           uint32_t r[32];
           tmem_ld32(t_lane + (uint32_t)c0, r);
-          if (live) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (c0 + j < L) V.vis_out[row * L + c0 + j] = sigmoid_fast(__uint_as_float(r[j]) * outmul);
-          }
+          if (live) store_sigmoid_row<32>(V.vis_out + row * L + c0, r, L - c0, outmul);
         }
       } else {
         float nx = 0.f, ny = 0.f, nz = 0.f;
@@ -468,11 +464,7 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
         for (int c0 = lo; c0 < hi; c0 += 16) {
           uint32_t r[16];
           tmem_ld16(t_lane + (uint32_t)c0, r);
-          if (live) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (c0 + j < hi) V.vis_out[row * L + c0 + j] = sigmoid_fast(__uint_as_float(r[j]));
-          }
+          if (live) store_sigmoid_row<16>(V.vis_out + row * L + c0, r, hi - c0, 1.0f);
         }
       } else {
         float nx = 0.f, ny = 0.f, nz = 0.f;
@@ -809,11 +801,7 @@ __global__ void __launch_bounds__(kTileM + PW * 32, PW == 4 ? 2 : 1) fused_shade
         uint32_t r[32];
         tmem_ld32(t_lane, r);
         if (V.vis_out) {
-          if (live) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < L) V.vis_out[row * L + j] = sigmoid_fast(__uint_as_float(r[j]));
-          }
+          if (live) store_sigmoid_row<32>(V.vis_out + row * L, r, L, 1.0f);
         } else {
           const float* cr =
               reinterpret_cast<const float*>(smem + (b ? a.ws_c[1] : a.ws_c[0])) + t * CS;

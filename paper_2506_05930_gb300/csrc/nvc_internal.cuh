@@ -199,8 +199,10 @@ struct nvc_handle {
   float* s_feat = nullptr;    // [stage][din]
   float* s_vis = nullptr;     // [stage][L]
 
-  // fused shading kernel variant (nvc::ShadeVariant)
+  // fused shading kernel variant (nvc::ShadeVariant); nvc_infer's own
+  // variant (-1: the shading variant), set by nvc_autotune_infer
   int shade_variant = 0;
+  int infer_variant = -1;
   // world-space share of the training positions (nvc_set_training_placement;
   // -1: the default split, ceil(B / 2) world-space)
   int64_t n_world = -1;

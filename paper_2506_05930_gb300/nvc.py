@@ -227,6 +227,17 @@ def nvc_autotune_shade(h, scene: Scene, pos, nrm, idx=None, pdf=None, wsum=None,
     return int(chosen.value), list(ms)
 
 
+def nvc_autotune_infer(h, pos, vis, reps=5, stream=None):
+    """Times nvc_infer under each fused-kernel variant (vis is scratch) and
+    keeps the fastest for this handle's nvc_infer.  Returns (chosen variant,
+    [ms per call or -1])."""
+    chosen = ctypes.c_int32()
+    ms = (ctypes.c_double * SHADE_VARIANTS)()
+    check(lib.nvc_autotune_infer(h, _ptr(pos, name="pos"), pos.shape[0], _ptr(vis, name="vis"),
+                                 int(reps), ctypes.byref(chosen), ms, _stream(stream)), h)
+    return int(chosen.value), list(ms)
+
+
 def nvc_calibrate(h, pos, stream=None):
     """Per-tensor E4M3 activation scales from a float32 pass over pos."""
     check(lib.nvc_calibrate(h, _ptr(pos, name="pos"), pos.shape[0], _stream(stream)), h)

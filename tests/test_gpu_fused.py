@@ -338,3 +338,25 @@ def test_multiview_full_workload_in_one_graph_launch_sampled():
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
     nvc.nvc_frame(cache.handle, scene, views, 1, seed=1, frame=1, loss_out=loss, use_graph=True)
     assert cache.counters()["step"] == 1 and np.isfinite(host(loss)[0])
+
+
+@pytest.mark.parametrize("L", [37, 32])
+def test_infer_export_and_its_autotuner(L):
+    """Exported visibilities within the fp16 bound of the oracle, with an odd
+    light count too (rows alternate between 16-byte and checked scalar
+    stores); nvc_autotune_infer keeps the fastest variant and the
+    visibilities stay bit-identical."""
+    cfg = cfg_frame(precision="fp16", batch_positions=256, n_outputs=L)
+    cache, p = make(cfg, seed=2, table_scale=0.5)
+    lo, hi = np.array(cfg.bounds_min), np.array(cfg.bounds_max)
+    pos = np.random.default_rng(4).uniform(lo, hi, (997, 3)).astype(np.float32)
+    ref = O.infer(cfg, p, pos)
+    vis0 = host(cache.infer(dev(pos)))
+    assert np.max(np.abs(vis0 - ref)) <= FP16_TOL
+    chosen, ms = nvc.nvc_autotune_infer(cache.handle, dev(pos),
+                                        torch.empty((len(pos), L), device="cuda"), reps=2)
+    ran = [m for m in ms if m > 0]
+    assert 0 <= chosen < nvc.SHADE_VARIANTS and ms[chosen] == min(ran)
+    if L > 32:
+        assert all(ms[v] < 0 for v in range(nvc.SHADE_VARIANTS) if v not in (0, PAIR_VARIANT))
+    assert np.array_equal(host(cache.infer(dev(pos))), vis0)
