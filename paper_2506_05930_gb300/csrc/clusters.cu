@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
     const int32_t* __restrict__ mem, int k, const float* __restrict__ vis,
     const float* __restrict__ pos, const float* __restrict__ nrm, int64_t n,
     int64_t pixel_offset, uint32_t k0, uint32_t k1, uint32_t frame, uint32_t view,
-    int32_t* __restrict__ light_out, float* __restrict__ weight_out, float* __restrict__ estimate) {
+    int32_t* __restrict__ light_out, float* __restrict__ weight_out, float* __restrict__ estimate,
+    bool vis_vec4) {
   extern __shared__ float4 s_scene4[];
   const int n_lt_s = kSmemLights ? n_lights : 0;
   float4* s_lt = s_scene4;
@@ -181,30 +182,54 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
     // warps at different clusters share the instruction cache); the weights
     // stay in registers through compare-and-select writes.
     float w[kMaxClusters];
-#pragma unroll
-    for (int t = 0; t < kMaxClusters; ++t) w[t] = 0.0f;
     float wsum = 0.0f;
     const float* vrow = vis + p * k;
+    if (!kSum) {
+      // visibility weights: no member loop, so the row's loads are issued
+      // together (16-byte loads when the row allows) into the weights'
+      // registers, and the short cluster loop is unrolled
+      if (vis_vec4) {
+#pragma unroll
+        for (int g = 0; g < kMaxClusters / 4; ++g) {
+          float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if (4 * g < k) v = __ldg(reinterpret_cast<const float4*>(vrow) + g);
+          w[4 * g] = v.x;
+          w[4 * g + 1] = v.y;
+          w[4 * g + 2] = v.z;
+          w[4 * g + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < kMaxClusters; ++t) w[t] = t < k ? __ldg(vrow + t) : 0.0f;
+      }
+#pragma unroll
+      for (int t = 0; t < kMaxClusters; ++t) {
+        if (t < k) {
+          w[t] = s_off[t + 1] > s_off[t] ? fmaxf(w[t], bits_f(kVisClampBits)) : 0.0f;
+          wsum = __fadd_rn(wsum, w[t]);
+        } else {
+          w[t] = 0.0f;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < kMaxClusters; ++t) w[t] = 0.0f;
 #pragma unroll 1
-    for (int y = 0; y < k; ++y) {
-      const float v = __ldg(vrow + y);
-      const int begin = s_off[y], end = s_off[y + 1];
-      float wy;
-      if (kSum) {
+      for (int y = 0; y < k; ++y) {
+        const float v = __ldg(vrow + y);
+        const int begin = s_off[y], end = s_off[y + 1];
         float ch = 0.0f;
 #pragma unroll 4
         for (int i = begin; i < end; ++i) {
           const float4 l = kSmemLights ? s_lt[i] : light_at<false>(s_lt, lights, mem[i]);
           ch = __fadd_rn(ch, contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w));
         }
-        wy = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), ch);
-      } else {
-        wy = end > begin ? fmaxf(v, bits_f(kVisClampBits)) : 0.0f;
-      }
+        const float wy = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), ch);
 #pragma unroll
-      for (int t = 0; t < kMaxClusters; ++t)
-        if (t == y) w[t] = wy;
-      wsum = __fadd_rn(wsum, wy);
+        for (int t = 0; t < kMaxClusters; ++t)
+          if (t == y) w[t] = wy;
+        wsum = __fadd_rn(wsum, wy);
+      }
     }
     const int y = cluster_reservoir(w, k, pixel, frame, view, k0, k1);
     int sel_light = -1;
@@ -323,10 +348,13 @@ cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl,
   const int64_t want = (n + threads - 1) / threads;
   const int64_t cap = (int64_t)num_sms * (best / threads);
   const int grid = (int)(want < cap ? want : cap);
+  // 16-byte loads of a pixel's visibilities need rows of a multiple of 4
+  // floats on a 16-byte aligned base
+  const bool vis_vec4 = (cl->k & 3) == 0 && (reinterpret_cast<uintptr_t>(vis) & 15) == 0;
   kern<<<grid, threads, smem, s>>>(sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes,
                                    sc->n_boxes, cl->offsets, cl->members, cl->k, vis, pos, nrm, n,
                                    pixel_offset, (uint32_t)seed, (uint32_t)(seed >> 32), frame,
-                                   view, light, weight, estimate);
+                                   view, light, weight, estimate, vis_vec4);
   return cudaGetLastError();
 }
 
