@@ -151,6 +151,12 @@ int32_t nvc_level_resolution(const nvc_config* cfg, int32_t level);
 nvc_status nvc_set_state(nvc_handle* h, const float* params, const float* adam_m,
                          const float* adam_v, int32_t step, void* stream);
 
+/* Copies parameters (device [n_params]) into the handle and refreshes the
+ * low-precision weight copies, leaving the Adam moments, the step counter
+ * and the gradient as they are: for callers that optimise the parameters
+ * themselves (the torch.autograd bridge).  Asynchronous. */
+nvc_status nvc_set_params(nvc_handle* h, const float* params, void* stream);
+
 /* Copies parameters and moments out (device [n_params] each; any may be
  * NULL).  Asynchronous; the step count is read by nvc_sync_status. */
 nvc_status nvc_get_state(nvc_handle* h, float* params, float* adam_m, float* adam_v,

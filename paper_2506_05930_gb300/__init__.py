@@ -3,7 +3,8 @@
 
 The compute lives in libnvc.so (hand-written CUDA for sm_103a behind the C
 ABI of include/nvc.h); ``nvc`` is the Python binding with the same entry
-point names, ``autograd`` wraps the hand-written adjoint for torch.
+point names, ``autograd`` puts the hand-written adjoint behind a
+torch.autograd.Function, and ``examples`` holds runnable workloads.
 """
 from .build import build, LIB  # noqa: F401
 

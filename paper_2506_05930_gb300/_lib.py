@@ -95,6 +95,7 @@ PROTOTYPES = {
     "nvc_autotune_shade": (c_int32, [_vp, _scp, _vp, _vp, c_int64, _vp, _vp, _vp, _vp, c_int32,
                                      POINTER(c_int32), POINTER(c_double), _vp]),
     "nvc_set_shade_variant": (c_int32, [_vp, c_int32]),
+    "nvc_set_params": (c_int32, [_vp, _vp, _vp]),
     "nvc_autotune_infer": (c_int32, [_vp, _vp, c_int64, _vp, c_int32, _vp, _vp, _vp]),
     "nvc_calibrate": (c_int32, [_vp, _vp, c_int64, _vp]),
     "nvc_trace_visibility": (c_int32, [_scp, _vp, c_int64, _vp, _vp]),

@@ -427,6 +427,16 @@ nvc_status nvc_set_state(nvc_handle* h, const float* params, const float* adam_m
   return NVC_OK;
 }
 
+nvc_status nvc_set_params(nvc_handle* h, const float* params, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  NVC_TRY(check_ptr(h, params, "params"));
+  cudaStream_t s = (cudaStream_t)stream;
+  NVC_CUDA(h, cudaMemcpyAsync(h->params, params, sizeof(float) * (size_t)h->n_params,
+                              cudaMemcpyDeviceToDevice, s));
+  NVC_CUDA(h, launch_pack_mlp(h, s));
+  return NVC_OK;
+}
+
 nvc_status nvc_get_state(nvc_handle* h, float* params, float* adam_m, float* adam_v,
                          void* stream) {
   if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");

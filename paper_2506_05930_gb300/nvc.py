@@ -148,6 +148,10 @@ def nvc_set_state(h, params, adam_m=None, adam_v=None, step=0, stream=None):
                             _ptr(adam_v, name="adam_v"), int(step), _stream(stream)), h)
 
 
+def nvc_set_params(h, params, stream=None):
+    check(lib.nvc_set_params(h, _ptr(params, name="params"), _stream(stream)), h)
+
+
 def nvc_get_state(h, params=None, adam_m=None, adam_v=None, stream=None):
     check(lib.nvc_get_state(h, _ptr(params), _ptr(adam_m), _ptr(adam_v), _stream(stream)), h)
 
