@@ -371,8 +371,8 @@ nvc_status nvc_train_step_clustered(nvc_handle* h, const nvc_scene* scene,
                                     double* loss_out, void* stream);
 
 /* Training targets of a clustered cache for given positions (device [n][3])
- * into target (device [n][k]), sample ids 0..n-1: the data step of
- * nvc_train_step_clustered.  Asynchronous. */
+ * into target (device [n][k]), sample ids 0..n-1 (n <= 2^32): the data step
+ * of nvc_train_step_clustered.  Asynchronous. */
 nvc_status nvc_cluster_targets(const nvc_scene* scene, const nvc_clusters* clusters,
                                const float* pos, int64_t n, uint64_t seed, uint32_t frame,
                                float* target, void* stream);

@@ -975,7 +975,8 @@ nvc_status nvc_cluster_targets(const nvc_scene* scene, const nvc_clusters* clust
                                float* target, void* stream) {
   NVC_TRY(check_scene(nullptr, scene, 0, kAnyLights));
   NVC_TRY(check_clusters(nullptr, scene, clusters, 0));
-  if (n < 0) return fail(nullptr, NVC_ERR_INVALID_ARG, "n < 0");
+  // sample ids are 32-bit Philox counters
+  if (n < 0 || n > ((int64_t)1 << 32)) return fail(nullptr, NVC_ERR_INVALID_ARG, "n out of range");
   if (n == 0) return NVC_OK;
   NVC_TRY(check_ptr(nullptr, pos, "pos"));
   NVC_TRY(check_ptr(nullptr, target, "target"));
