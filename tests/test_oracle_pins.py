@@ -741,3 +741,22 @@ def test_sample_clustered_mean_estimate_converges_to_exact_di(mode):
     se = est.std(0) / np.sqrt(F)
     assert np.all(np.abs(est.mean(0) - exact) <= 5 * se + 1e-9 * exact + 1e-12)
     assert (exact > 0).mean() > 0.5
+
+
+def test_visibility_weights_with_equal_visibilities_pick_clusters_uniformly():
+    """With every cluster's visibility equal, the visibility-only first step
+    (Section 3.6) picks each non-empty cluster with probability 1/(number of
+    non-empty clusters) and never an empty one, whatever the contributions;
+    the summed-contribution weights do not (they follow the contributions)."""
+    sc = S.scene_heightfield(seed=2, n_lights=12, n_spheres=2, n_boxes=2)
+    assign = np.array([0, 0, 1, 1, 1, 3, 3, 3, 3, 4, 4, 4])      # cluster 2 empty
+    off, mem = O.cluster_table(assign, 5)
+    gb = S.gbuffer_heightfield(seed=2, width=5, height=4)
+    c32 = O.contributions(gb.pos, gb.nrm, sc.lights, np.float32)
+    vis = np.full((gb.n, 5), 0.37, np.float32)
+    law = O.selection_law(O.cluster_weights(vis, c32, off, mem, "visibility"))
+    want = np.array([0.25, 0.25, 0.0, 0.25, 0.25])
+    np.testing.assert_allclose(law, np.broadcast_to(want, law.shape), atol=1e-6)
+    law_sum = O.selection_law(O.cluster_weights(vis, c32, off, mem, "sum"))
+    assert np.abs(law_sum - want).max() > 0.05
+    assert np.all(law_sum[:, 2] == 0.0)
