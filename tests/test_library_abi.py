@@ -115,3 +115,30 @@ def test_host_kmeans_rejects_bad_arguments(lib):
         nvc.nvc_kmeans_lights(L, np.arange(41, dtype=np.int32), 3)    # k > n_lights
     with pytest.raises(_lib.NVCError):
         nvc.nvc_kmeans_lights(L, np.arange(4, dtype=np.int32), -1)
+
+
+def test_new_entry_points_reject_null_arguments_without_a_gpu(lib):
+    """The clustered, placement, parameter and autotuning entry points answer
+    argument errors on the host, before any CUDA call."""
+    from paper_2506_05930_gb300 import _lib
+    E = _lib.NVC_ERR_INVALID_ARG
+    assert lib.nvc_set_training_placement(None, 0) == E
+    assert lib.nvc_set_params(None, None, None) == E
+    assert lib.nvc_autotune_infer(None, None, 10, None, 1, None, None, None) == E
+    assert lib.nvc_training_positions_split(None, None, 0, 10, 5, 0, 0, None, None) == E
+    assert lib.nvc_train_step_clustered(None, None, None, None, 0, 0, 0, None, None) == E
+    assert lib.nvc_cluster_targets(None, None, None, 1, 0, 0, None, None) == E
+    assert lib.nvc_sample_clustered(None, None, None, None, None, 1, 0, 0, 0, 0, None, None, None,
+                                    None) == E
+    # a scene with lights but no cluster table, and a table with a bad weight mode
+    sc = _lib.NvcScene()
+    sc.n_lights = 4
+    sc.lights = 16                      # never dereferenced: the table check fails first
+    assert lib.nvc_cluster_targets(ctypes.byref(sc), None, None, 1, 0, 0, None, None) == E
+    cl = _lib.NvcClusters()
+    cl.k, cl.offsets, cl.members, cl.weights = 4, 16, 16, 7
+    assert lib.nvc_sample_clustered(ctypes.byref(sc), ctypes.byref(cl), None, None, None, 1, 0, 0,
+                                    0, 0, None, None, None, None) == E
+    cl.weights, cl.k = 0, 33
+    assert lib.nvc_cluster_targets(ctypes.byref(sc), ctypes.byref(cl), None, 1, 0, 0, None,
+                                   None) == E
