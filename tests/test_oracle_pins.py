@@ -760,3 +760,21 @@ def test_visibility_weights_with_equal_visibilities_pick_clusters_uniformly():
     law_sum = O.selection_law(O.cluster_weights(vis, c32, off, mem, "sum"))
     assert np.abs(law_sum - want).max() > 0.05
     assert np.all(law_sum[:, 2] == 0.0)
+
+
+def test_ris_weight_closed_forms():
+    """W = (sum_j c_j / M) / (p(x) c(x)), p(x) = (w_y / w_sum) / m_y
+    (Section 3.6).  Equal candidates give W = 1 / p(x); a pick whose
+    contribution is twice the others' halves W against picking one of the
+    others; and W scales with m_y and w_sum / w_y as 1/p does.  A swapped
+    argument (w_sum for w_y, or the mean for c(x)) breaks these."""
+    c = np.array([0.5, 0.5, 0.5, 0.5], np.float32)
+    for w_y, w_sum, m_y in ((0.25, 1.0, 8), (3.0, 4.0, 1), (0.125, 0.5, 64)):
+        W = float(O.ris_weight(c, np.int64(2), w_y, w_sum, m_y))
+        assert W == pytest.approx(m_y * w_sum / w_y, rel=1e-6)
+    c2 = np.array([1.0, 0.5, 0.5, 0.5], np.float32)
+    W0 = float(O.ris_weight(c2, np.int64(0), 0.5, 1.0, 4))
+    W1 = float(O.ris_weight(c2, np.int64(1), 0.5, 1.0, 4))
+    assert W1 == pytest.approx(2 * W0, rel=1e-6)
+    # mean 0.625, p = 0.125: W0 = 0.625 / (0.125 * 1.0)
+    assert W0 == pytest.approx(5.0, rel=1e-6)
