@@ -27,20 +27,23 @@ def rel_err(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def fp16_gradient_model(cfg, params, pos, y, loss_scale):
+def fp16_gradient_model(cfg, params, pos, y, loss_scale, quantise=True):
     """The training gradient with the roundings the tensor-core path makes:
     encoded features, weights, hidden activations and the scaled deltas
     rounded to fp16, every product and sum in float64.  The distance of
     this model from the float64 oracle is the error fp16 operands cause;
-    the CUDA path should sit on the model, not merely near the oracle."""
+    the CUDA path should sit on the model, not merely near the oracle.
+    quantise=False skips the roundings, which must give the oracle's
+    gradient (the model's structure is pinned that way)."""
     from oracle import nvc as O
 
     def q(x):
-        return np.asarray(x, np.float64).astype(np.float16).astype(np.float64)
+        x = np.asarray(x, np.float64)
+        return x.astype(np.float16).astype(np.float64) if quantise else x
 
     table, Ws = O.split_params(cfg, params)
     feat, aux = O.encode(cfg, table, pos, with_aux=True)
-    h = q(feat.astype(np.float32))
+    h = q(feat.astype(np.float32) if quantise else feat)
     Wq = [q(W) for W in Ws]
     acts = [h]
     for W in Wq[:-1]:
