@@ -60,14 +60,17 @@ def peaks():
 
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region:
-    sampled every 50 ms with nvidia-smi's own timestamps; `ready` waits for
-    the first sample, `begin` / `stop` bracket the region on the host clock
-    and only the samples inside it are kept."""
+    sampled every 10 ms with nvidia-smi's own timestamps; `ready` waits for
+    the first sample, `begin` / `stop` bracket the region on the host clock.
+    The samples inside the region are kept; a region shorter than the
+    sampling interval keeps the last sample before it and the first after
+    it instead (`window` says which)."""
     Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, gpu_index: int, interval_ms: int = 50):
+    def __init__(self, gpu_index: int, interval_ms: int = 10):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.t0 = self.t1 = None
         try:
@@ -87,11 +90,43 @@ class ClockSampler:
     def begin(self):
         self.t0 = time.time()
 
+    @classmethod
+    def parse(cls, text):
+        """(timestamp, sm MHz, max MHz, active reasons) per sample line."""
+        rows = []
+        for line in text.splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(c[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                sm, mx = float(c[2]), float(c[3])
+            except ValueError:
+                continue
+            reasons = {n for n, v in zip(cls.NAMES, c[6:10]) if v.lower().startswith("active")}
+            rows.append((ts, sm, mx, reasons))
+        return rows
+
+    @staticmethod
+    def summarise(rows, t0, t1):
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        window = "inside"
+        if not inside:
+            before = [r for r in rows if r[0] < t0]
+            after = [r for r in rows if r[0] > t1]
+            inside = before[-1:] + after[:1]
+            window = "edges"
+        if not inside:
+            return None
+        reasons = set().union(*(r[3] for r in inside))
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": inside[-1][2],
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
+
     def stop(self):
         self.t1 = time.time()
         if self.p is None:
             return None
-        time.sleep(0.06)                 # let the sample that covers the end land
+        time.sleep(0.05)                 # let the sample after the end land
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -99,31 +134,9 @@ class ClockSampler:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, mx, reasons = [], None, set()
-        for line in self.f.read().splitlines():
-            c = [x.strip() for x in line.split(",")]
-            if len(c) < 10:
-                continue
-            try:
-                ts = datetime.datetime.strptime(c[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-            except ValueError:
-                ts = None
-            if ts is not None and self.t0 is not None and not (self.t0 <= ts <= self.t1):
-                continue
-            try:
-                sm.append(float(c[2]))
-                mx = float(c[3])
-            except ValueError:
-                continue
-            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-            for n, v in zip(names, c[6:10]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
+        rows = self.parse(self.f.read())
         os.unlink(self.f.name)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return self.summarise(rows, self.t0, self.t1)
 
 
 # ------------------------------------------------------- multi-rank logic --
@@ -184,13 +197,13 @@ def workload_config(world, pixels_per_gpu, positions_per_frame):
 #   normalise: 3 x (sub, div, two clamps)                                12
 #   per level: cell 3 x (mul, floor, min, sub) 12; 1 - f 3; hash 2 mul +
 #     3 add + 8 x (2 xor + and) 29; corner weights 12; blend 8 F; 8
-#     addresses + 8 loads 16                                            72 + 8F
+#     addresses 8 (the 8 row loads are load/store-unit work, not counted) 64 + 8F
 #   per hidden value: leaky ReLU 2 + conversion to the operand type 0.5  2.5
 #   per light: sigmoid 4; contribution 15 (3 sub, two 3-term dots, rsqrt,
 #     4 mul, clamp); weight 2; max / sum / Neural DI 3; reservoir 8
 #     (quantise 3, running sum, mulhi, compare, 2 selects); Philox 10
 #     (10 rounds x 4 ops per block of 4 lights)                          42
-ALU_OPS = dict(normalise=12, level_base=72, level_per_feature=8, hidden_value=2.5, light=42)
+ALU_OPS = dict(normalise=12, level_base=64, level_per_feature=8, hidden_value=2.5, light=42)
 
 
 def algorithmic(cfg, n_pixels):
@@ -272,6 +285,86 @@ def measure_tiny(stream, use_graph):
     return {"workload": "tiny_fp32: 64x64 points, 4 lights, 4 spheres; training 1024 "
                         "positions x 4 lights; FP32", "us_per_frame": e0.elapsed_time(e1) / 200 * 1e3,
             "cuda_graph": use_graph}
+
+
+def measure_gather_peak(stream, table_mib=64, rows_per_thread=256, reps=7):
+    """The random-row gather rate from an L2-resident table: the encode's
+    roofline denominator (nvc_gather_bench: 8 independent row loads in
+    flight per thread, rows of 8 and 16 bytes at uniformly random places of
+    a 64 MiB float32 table, the size of the 1080p workload's master table).
+    Two untimed launches bring the table into L2; the best of `reps` timed
+    launches is reported, as useful bytes and as 32-byte L2 sectors."""
+    import torch
+    from paper_2506_05930_gb300 import nvc
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    table = torch.rand(table_mib * (1 << 20) // 4, device="cuda")
+    n_threads = sms * 2048
+    sink = torch.empty(n_threads, device="cuda")
+    out = {"table_mib": table_mib, "threads": n_threads, "rows_per_thread": rows_per_thread}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for rb in (8, 16):
+        for _ in range(2):
+            nvc.nvc_gather_bench(table, rb, n_threads, rows_per_thread, sink, seed=1, stream=stream)
+        best = None
+        for r in range(reps):
+            e0.record(stream)
+            nvc.nvc_gather_bench(table, rb, n_threads, rows_per_thread, sink, seed=2 + r,
+                                 stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        rows = n_threads * rows_per_thread
+        out[f"row{rb}"] = {"ms": best, "useful_gbs": rows * rb / (best * 1e-3) / 1e9,
+                           "sector_gbs": rows * 32 / (best * 1e-3) / 1e9,
+                           "grows_per_s": rows / (best * 1e-3) / 1e9}
+    del table
+    return out
+
+
+def measure_phases(cache, scene, pos, nrm, view, seed, frame, shade_ms, cfg, gather_peak,
+                   pk, sm_mhz):
+    """Where the fused shading kernel's time goes, by phase (nvc_shade_phases:
+    SM-clock stamps at the phase boundaries of every tile), and the two
+    per-phase rooflines this attributes: the encode's useful gather bytes
+    over its share of the kernel time against the measured random-gather
+    rate, and the MLP's flops over its share against the tensor peak.  The
+    time attribution charges phase p with share_p x kernel time, share_p =
+    the groups' summed cycles in p over their summed tile-loop cycles."""
+    from paper_2506_05930_gb300 import nvc
+    try:
+        cyc = nvc.nvc_shade_phases(cache.handle, scene, pos, nrm, seed, frame, view.idx, view.pdf,
+                                   view.wsum, view.radiance)
+    except Exception as e:          # the chosen variant is not a tile-stream kernel
+        return {"unavailable": str(e)}
+    alg = algorithmic(cfg, pos.shape[0])
+    total = cyc[3]
+    share = {k: cyc[i] / total for i, k in enumerate(("encode", "mlp", "sampler"))}
+    t = shade_ms * 1e-3
+    enc_gbs = alg["shade_gather_bytes"] / (share["encode"] * t) / 1e9
+    mlp_tf = alg["shade_flops"] / (share["mlp"] * t) / 1e12
+    g8 = gather_peak["row8"]["useful_gbs"] if gather_peak else None
+    # per-tile view of the MLP phase: a tile's tensor work at one SM's peak
+    # over the mean wall time a tile spends in its MLP phase
+    n_sms = 152
+    tiles = -(-pos.shape[0] // 128)
+    mlp_tile_s = cyc[1] / tiles / (sm_mhz * 1e6)
+    tile_tensor_s = alg["shade_flops"] / tiles / (pk["bf16_sustained"] * 1e12 / n_sms)
+    return {
+        "cycles": {"encode": cyc[0], "mlp": cyc[1], "sampler": cyc[2], "tile_loop": cyc[3]},
+        "share": share,
+        "encode": {"useful_gather_gbs": enc_gbs, "l2_gather_peak_gbs": g8,
+                   "frac_of_l2_gather": enc_gbs / g8 if g8 else None,
+                   "gather_bytes_per_px": alg["shade_gather_bytes"] / pos.shape[0]},
+        "mlp": {"tflops": mlp_tf, "peak_tflops": pk["bf16_sustained"],
+                "frac_of_tensor_peak": mlp_tf / pk["bf16_sustained"],
+                "per_tile_phase_us": mlp_tile_s * 1e6,
+                "per_tile_tensor_us_at_sm_peak": tile_tensor_s * 1e6,
+                "per_tile_frac": tile_tensor_s / mlp_tile_s},
+        "note": "phase p is charged share_p x the kernel time; per_tile_frac = a tile's MLP "
+                "flops at one SM's sustained tensor peak over the mean time a tile spends in "
+                "its MLP phase (other tile streams of the SM run meanwhile)"}
 
 
 CLUSTERED_LIGHTS = 1024
@@ -469,6 +562,15 @@ def run_ours(args):
     nvc.nvc_set_profiling(cache.handle, False)
     stage_ms = [m / args.steps for m in stage_ms]
 
+    # the encode's and the MLP's own rooflines: the random-gather rate of an
+    # L2-resident table, and the fused kernel's time split by phase
+    gather = measure_gather_peak(stream) if rank == 0 else None
+    phases = None
+    if rank == 0 and fused:
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        phases = measure_phases(cache, scene, pos, nrm, view, seed, f0 + args.steps, stage_ms[3],
+                                cfg, gather, peaks(), sm_mhz)
+
     # end to end through the public API with host buffers
     pin_pos = torch.from_numpy(gb.pos).pin_memory()
     pin_nrm = torch.from_numpy(gb.nrm).pin_memory()
@@ -587,6 +689,23 @@ def run_ours(args):
     for v in (shade_view, adam_view, tensor_view):
         if v.get("achieved") is not None:
             v["frac"] = v["achieved"] / v["peak"]
+    # the fused kernel's three views: ALU issue (the bound), the encode's
+    # gathers against the measured L2 random-gather rate, the MLP against the
+    # tensor peak (both over their phase's share of the kernel time)
+    shade_view["views"] = {"alu_whole_kernel": {"achieved": shade_view["achieved"],
+                                                "frac": shade_view.get("frac"),
+                                                "ops_per_px": alg["alu_ops_per_px"]},
+                           "tensor_whole_kernel": {"achieved": tensor_view["achieved"],
+                                                   "frac": tensor_view["frac"]}}
+    if phases and "share" in phases:
+        shade_view["views"]["encode_vs_l2_gather"] = {
+            "achieved_gbs": phases["encode"]["useful_gather_gbs"],
+            "peak_gbs": phases["encode"]["l2_gather_peak_gbs"],
+            "frac": phases["encode"]["frac_of_l2_gather"], "phase_share": phases["share"]["encode"]}
+        shade_view["views"]["mlp_vs_tensor"] = {
+            "achieved_tflops": phases["mlp"]["tflops"], "peak_tflops": pk["bf16_sustained"],
+            "frac": phases["mlp"]["frac_of_tensor_peak"], "phase_share": phases["share"]["mlp"],
+            "per_tile_frac": phases["mlp"]["per_tile_frac"]}
     roof = shade_view if stage_ms[3] >= stage_ms[2] else adam_view
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world,
@@ -611,6 +730,9 @@ def run_ours(args):
         "gpu_launches": launches,
         "autotune": tune,
         "clocks": clk,
+        "l2_gather_peak_gbs": gather["row8"]["useful_gbs"] if gather else None,
+        "gather_bench": gather,
+        "shade_phases": phases,
     }
     if base:
         line["fp32_unfused_baseline"] = base

@@ -288,6 +288,23 @@ nvc_status nvc_autotune_shade(nvc_handle* h, const nvc_scene* scene, const float
                               float* wsum, float* radiance, int32_t reps, int32_t* chosen,
                               double* ms_out, void* stream);
 
+/* Phase profile of the fused shading kernel: one nvc_shade (fused = 1)
+ * launch of the handle's variant, which must be 6 or 7 (the tile-stream
+ * kernels; NVC_ERR_UNSUPPORTED otherwise), in an instantiation whose first
+ * thread of every 128-pixel tile group reads the SM clock at the phase
+ * boundaries of each tile.  cycles_out (host [4]) receives the SM cycles
+ * summed over all groups and tiles of [0] the hash-grid encode into the
+ * operand tile (Section 3.3), [1] the MLP layers up to the output
+ * accumulator's read (Section 3.3), [2] the sigmoid, contributions,
+ * reservoir pick and Neural DI with the stores (Sections 3.1, 3.2), and
+ * [3] every group's whole tile loop; the shares [i] / [3] say where a
+ * group's time goes.  Outputs as nvc_shade (pixel ids 0..n-1, view 0).
+ * A measurement aid with no counterpart in the paper.  Synchronous. */
+nvc_status nvc_shade_phases(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                            const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
+                            int32_t* idx, float* pdf, float* wsum, float* radiance,
+                            double* cycles_out, void* stream);
+
 /* Selects the fused shading kernel variant (0 .. NVC_SHADE_VARIANTS-1). */
 nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant);
 
@@ -538,6 +555,22 @@ nvc_status nvc_infer_noalloc(const nvc_config* cfg, const float* params, const f
                              int64_t n, float* vis, void* stream);
 
 /* ---- profiling ---------------------------------------------------------- */
+
+/* Random-row gather microbenchmark: the roofline denominator of the
+ * hash-grid encode, which reads 8 rows of a level's table per position at
+ * hashed, effectively random rows (Section 3.3).  n_threads threads each
+ * load rows_per_thread (a multiple of 8) rows of row_bytes (4, 8 or 16)
+ * bytes from table (device, 16-byte aligned, table_bytes / row_bytes a
+ * power of two up to 2^31), eight independent loads in flight before they
+ * are summed, row indices from a per-thread linear congruential sequence
+ * started from `seed`; sink (device [n_threads]) receives each thread's
+ * sum so that no load is dead.  The caller times the launch on `stream`;
+ * rows gathered = n_threads * rows_per_thread.  A measurement aid with no
+ * counterpart in the paper.  Asynchronous. */
+nvc_status nvc_gather_bench(const void* table, int64_t table_bytes, int32_t row_bytes,
+                            int64_t n_threads, int32_t rows_per_thread, uint32_t seed,
+                            float* sink, void* stream);
+
 
 /* When enabled, the handle records CUDA events around each stage it
  * launches; nvc_stage_times (synchronising) returns the summed milliseconds

@@ -95,6 +95,9 @@ PROTOTYPES = {
     "nvc_autotune_shade": (c_int32, [_vp, _scp, _vp, _vp, c_int64, _vp, _vp, _vp, _vp, c_int32,
                                      POINTER(c_int32), POINTER(c_double), _vp]),
     "nvc_set_shade_variant": (c_int32, [_vp, c_int32]),
+    "nvc_shade_phases": (c_int32, [_vp, _scp, _vp, _vp, c_int64, c_uint64, c_uint32, _vp, _vp,
+                                   _vp, _vp, POINTER(c_double), _vp]),
+    "nvc_gather_bench": (c_int32, [_vp, c_int64, c_int32, c_int64, c_int32, c_uint32, _vp, _vp]),
     "nvc_set_params": (c_int32, [_vp, _vp, _vp]),
     "nvc_autotune_infer": (c_int32, [_vp, _vp, c_int64, _vp, c_int32, _vp, _vp, _vp]),
     "nvc_calibrate": (c_int32, [_vp, _vp, c_int64, _vp]),

@@ -196,6 +196,8 @@ namespace nvc {
 
 void record_error(const char* msg) { g_create_error = msg; }
 
+nvc_status validate_config(const nvc_config* c, std::string* why) { return check_config(c, why); }
+
 int blocks_per_sm(const void* func, int block, size_t dyn_smem) {
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) return 1;
@@ -300,7 +302,8 @@ nvc_status nvc_create(const nvc_config* cfg, nvc_handle** out) {
       (e = dalloc(&h->t_logits, B * h->L)) ||
       (e = dalloc(&h->t_delta, (size_t)h->n_layers * B * maxdim)) ||
       (e = dalloc(&h->t_dfeat, B * h->din)) || (e = dalloc(&h->loss_partials, 256)) ||
-      (e = dalloc(&h->status, kStWords)) || (e = dalloc(&h->adam_scalars, 1)))
+      (e = dalloc(&h->status, kStWords)) || (e = dalloc(&h->adam_scalars, 1)) ||
+      (e = dalloc(&h->phase_cycles, 4)))
     return cleanup_fail(e, "cudaMalloc");
   h->n_loss_partials = 256;
   {
@@ -361,6 +364,7 @@ void nvc_destroy(nvc_handle* h) {
   cudaFree(h->t_dfeat);
   cudaFree(h->loss_partials);
   cudaFree(h->status);
+  cudaFree(h->phase_cycles);
   cudaFree(h->adam_scalars);
   cudaFree(h->fp8_scales);
   cudaFree(h->s_feat);
@@ -649,6 +653,30 @@ nvc_status nvc_calibrate(nvc_handle* h, const float* pos, int64_t n, void* strea
                                                         n * h->width, h->fp8_scales);
   NVC_CUDA(h, cudaGetLastError());
   h->fp8_calibrated = true;
+  return NVC_OK;
+}
+
+nvc_status nvc_shade_phases(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                            const float* nrm, int64_t n, uint64_t seed, uint32_t frame,
+                            int32_t* idx, float* pdf, float* wsum, float* radiance,
+                            double* cycles_out, void* stream) {
+  NVC_TRY(shade_checks(h, scene, pos, nrm, n, 0));
+  if (n == 0) return fail(h, NVC_ERR_INVALID_ARG, "need n > 0");
+  if (!cycles_out) return fail(h, NVC_ERR_INVALID_ARG, "cycles_out is NULL");
+  std::string why;
+  if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
+  if ((h->shade_variant != kShadeMulti2 && h->shade_variant != kShadeMulti4) || h->L > 32)
+    return fail(h, NVC_ERR_UNSUPPORTED,
+                "the phase profile instruments the tile-stream variants (6, 7) only");
+  cudaStream_t s = (cudaStream_t)stream;
+  NVC_CUDA(h, cudaMemsetAsync(h->phase_cycles, 0, 4 * sizeof(unsigned long long), s));
+  FusedView v{pos, nrm, n, 0, 0, idx, pdf, wsum, radiance, nullptr, nullptr};
+  NVC_CUDA(h, launch_shade_fused_views(h, scene, &v, 1, seed, frame, s, h->phase_cycles));
+  unsigned long long c[4];
+  NVC_CUDA(h, cudaMemcpyAsync(c, h->phase_cycles, sizeof(c), cudaMemcpyDeviceToHost, s));
+  NVC_CUDA(h, cudaStreamSynchronize(s));
+  for (int i = 0; i < 4; ++i) cycles_out[i] = (double)c[i];
+  count_launches(h, 1);
   return NVC_OK;
 }
 

@@ -69,6 +69,10 @@ struct FusedArgs {
   // several-tiles-per-CTA kernel: first activation tile, tile stride, light
   // table, mbarriers; TMEM columns per group
   int multi_a, multi_stride, multi_l, multi_bar, multi_cols;
+  // phase profile of the several-tiles-per-CTA kernel (nvc_shade_phases):
+  // summed SM cycles of [0] encode, [1] MLP, [2] sampler, [3] whole tile
+  // loop, over every group; NULL in ordinary launches
+  unsigned long long* phase_cycles;
 };
 
 // ---- the sampler's arithmetic ----------------------------------------------

@@ -53,7 +53,12 @@ __device__ __forceinline__ bool group_sync_or(int g, bool v) {
   return r != 0;
 }
 
-template <int F, int PREC, int TPC, bool FULL>
+// STAMP: the phase-profile instantiation (nvc_shade_phases).  Thread 0 of
+// each group reads the SM clock at four points of every tile -- tile start,
+// the encoded A tile complete, the output layer's accumulator read, the end
+// of the tile's sampler -- and adds the phases' cycles to a.phase_cycles
+// once at exit; outputs are the same as the plain instantiation's.
+template <int F, int PREC, int TPC, bool FULL, bool STAMP>
 __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
     fused_shade_multi_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int kThreads = kTileM * TPC;
@@ -106,9 +111,13 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
   // FULL: exactly 32 lights, so the light tests fold away, and every level's
   // N_l + 1 < T (checked by the launcher), so the hash's x terms need no mask
   const int L = FULL ? 32 : a.L;
+  unsigned long long cyc[3] = {0ull, 0ull, 0ull};
+  long long c_tile = 0, c_mark = 0;
+  const long long c_loop = STAMP ? clock64() : 0;
 
   for (int64_t tile = (int64_t)blockIdx.x * TPC + g; tile < n_tiles && !failed;
        tile += (int64_t)gridDim.x * TPC) {
+    if constexpr (STAMP) c_tile = clock64();
     const ViewDesc& V = a.v[view_of(a, tile)];
     const int64_t row = (tile - V.tile_start) * kTileM + rw;
     const bool live = row < V.n;
@@ -146,6 +155,10 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
     fence_async_smem();
     tc_fence_before();
     group_sync(g);
+    if constexpr (STAMP) {
+      c_mark = clock64();
+      cyc[0] += (unsigned long long)(c_mark - c_tile);
+    }
 
     // ---- the MLP -------------------------------------------------------------
     for (int k = 0; k < a.n_layers && !failed; ++k) {
@@ -186,6 +199,11 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
       // ---- output layer (the MMA that read this tile's A has completed) ------
       uint32_t r[32];
       tmem_ld32(t_lane, r);
+      if constexpr (STAMP) {
+        const long long c = clock64();
+        cyc[1] += (unsigned long long)(c - c_mark);
+        c_mark = c;
+      }
       if (V.vis_out) {
         if (live) {
 #pragma unroll
@@ -272,6 +290,15 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
       // also keeps the next tile's encode from overwriting weights that a
       // slower thread of the group still reads
       failed = group_sync_or(g, !ok);
+      if constexpr (STAMP) cyc[2] += (unsigned long long)(clock64() - c_mark);
+    }
+  }
+  if constexpr (STAMP) {
+    if (rw == 0 && a.phase_cycles) {
+      atomicAdd(a.phase_cycles + 0, cyc[0]);
+      atomicAdd(a.phase_cycles + 1, cyc[1]);
+      atomicAdd(a.phase_cycles + 2, cyc[2]);
+      atomicAdd(a.phase_cycles + 3, (unsigned long long)(clock64() - c_loop));
     }
   }
   if (failed && rw == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
@@ -314,8 +341,11 @@ cudaError_t launch_multi_typed(FusedArgs a, size_t smem_needed, int num_sms, cud
   int rmax = 0;
   for (int l = 0; l < a.ep.n_levels; ++l) rmax = a.ep.res[l] > rmax ? a.ep.res[l] : rmax;
   const bool full = a.L == 32 && (int64_t)rmax + 1 < ((int64_t)1 << a.ep.log2_table);
-  auto kern = full ? fused_shade_multi_kernel<F, PREC, TPC, true>
-                   : fused_shade_multi_kernel<F, PREC, TPC, false>;
+  auto kern = full ? fused_shade_multi_kernel<F, PREC, TPC, true, false>
+                   : fused_shade_multi_kernel<F, PREC, TPC, false, false>;
+  if (a.phase_cycles)
+    kern = full ? fused_shade_multi_kernel<F, PREC, TPC, true, true>
+                : fused_shade_multi_kernel<F, PREC, TPC, false, true>;
   a.multi_cols = (int)a.tmem_cols;              // per group
   a.tmem_cols = a.tmem_cols * (uint32_t)TPC;    // per CTA (a power of two)
   if (a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;

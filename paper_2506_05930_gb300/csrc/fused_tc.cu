@@ -1167,12 +1167,14 @@ bool fused_supported(const nvc_handle* h, std::string* why) {
 
 cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
                                      const FusedView* views, int n_views, uint64_t seed,
-                                     uint32_t frame, cudaStream_t s) {
+                                     uint32_t frame, cudaStream_t s,
+                                     unsigned long long* phase_cycles) {
   // views beyond one launch's table go to further launches
   if (n_views > kMaxViews) {
-    cudaError_t e = launch_shade_fused_views(h, sc, views, kMaxViews, seed, frame, s);
+    cudaError_t e = launch_shade_fused_views(h, sc, views, kMaxViews, seed, frame, s, phase_cycles);
     if (e != cudaSuccess) return e;
-    return launch_shade_fused_views(h, sc, views + kMaxViews, n_views - kMaxViews, seed, frame, s);
+    return launch_shade_fused_views(h, sc, views + kMaxViews, n_views - kMaxViews, seed, frame, s,
+                                    phase_cycles);
   }
   PackArgs p{};
   layer_geometry(h, p);
@@ -1225,6 +1227,7 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
   a.frame = frame;
   a.status = h->status;
   a.fp8_scales = h->fp8_scales;
+  a.phase_cycles = phase_cycles;
   if (h->cfg.precision == NVC_PREC_FP8) {
     const size_t smem8 = fused_smem(h, p, &a);
     switch (h->F) {

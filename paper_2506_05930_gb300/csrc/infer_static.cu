@@ -12,8 +12,10 @@
 //
 // It runs the float32 separate-kernel path: encode into that array, then
 // the float32 MLP with the sigmoid writing the caller's output.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <string>
 
 #include "nvc_internal.cuh"
 
@@ -26,17 +28,20 @@ static __device__ __align__(256) float g_feat_scratch[kScratchFloats];
 
 // Device address of g_feat_scratch per device, found once per device with
 // that device current.  In host code the array's name is only a host-side
-// stand-in, never a device address.
+// stand-in, never a device address.  Atomic slots: host threads making
+// their first call on a device at the same time each look the address up
+// and store the same value.
 constexpr int kMaxDevices = 64;
-float* g_scratch_addr[kMaxDevices] = {};
+std::atomic<float*> g_scratch_addr[kMaxDevices] = {};
 
 }  // namespace
 
 extern "C" nvc_status nvc_infer_noalloc(const nvc_config* cfg, const float* params,
                                         const float* pos, int64_t n, float* vis, void* stream) {
   using namespace nvc;
-  if (nvc_param_count(cfg) < 0) {
-    record_error("nvc_infer_noalloc: invalid configuration");
+  std::string why;
+  if (validate_config(cfg, &why) != NVC_OK) {
+    record_error(("nvc_infer_noalloc: " + why).c_str());
     return NVC_ERR_INVALID_ARG;
   }
   if (n < 0) {
@@ -67,16 +72,17 @@ extern "C" nvc_status nvc_infer_noalloc(const nvc_config* cfg, const float* para
     record_error("nvc_infer_noalloc: no usable current device");
     return NVC_ERR_CUDA;
   }
-  if (!g_scratch_addr[dev]) {
+  float* scratch = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!scratch) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_feat_scratch);
     if (e != cudaSuccess || !p) {
       record_error("nvc_infer_noalloc: cudaGetSymbolAddress of the scratch array failed");
       return NVC_ERR_CUDA;
     }
-    g_scratch_addr[dev] = static_cast<float*>(p);
+    scratch = static_cast<float*>(p);
+    g_scratch_addr[dev].store(scratch, std::memory_order_release);
   }
-  float* scratch = g_scratch_addr[dev];
 
   // A read-only view of the configuration in the handle's form; nothing in
   // it owns memory.

@@ -192,6 +192,7 @@ struct nvc_handle {
   int n_loss_partials = 0;
   int loss_blocks = 0;                  // partials written by the last training pass
   int32_t* status = nullptr;            // nvc::kStWords
+  unsigned long long* phase_cycles = nullptr;   // [4], nvc_shade_phases
   nvc::AdamScalars* adam_scalars = nullptr;
 
   // staging of the unfused shading path
@@ -228,6 +229,10 @@ namespace nvc {
 
 // Records the message nvc_last_error(NULL) returns on this thread.
 void record_error(const char* msg);
+
+// The configuration checks of nvc_create: NVC_OK, or NVC_ERR_INVALID_ARG
+// with the reason in *why.
+nvc_status validate_config(const nvc_config* c, std::string* why);
 
 // Resident blocks per SM of `func` with `block` threads and `dyn_smem`
 // dynamic shared memory, from the function's register and shared-memory
@@ -299,9 +304,12 @@ struct FusedView {
   float* vis_out;
   float* w_out;
 };
+// phase_cycles (device [4] uint64, may be NULL): the several-tiles-per-CTA
+// variants add their per-phase SM cycles there (nvc_shade_phases).
 cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
                                      const FusedView* views, int n_views, uint64_t seed,
-                                     uint32_t frame, cudaStream_t s);
+                                     uint32_t frame, cudaStream_t s,
+                                     unsigned long long* phase_cycles = nullptr);
 
 // train_tc.cu
 bool train_tc_supported(const nvc_handle* h, std::string* why);

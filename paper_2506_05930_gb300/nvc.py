@@ -251,6 +251,30 @@ def nvc_set_shade_variant(h, variant: int):
     check(lib.nvc_set_shade_variant(h, int(variant)), h)
 
 
+def nvc_shade_phases(h, scene: Scene, pos, nrm, seed=0, frame=0, idx=None, pdf=None, wsum=None,
+                     radiance=None, stream=None):
+    """One instrumented fused shading launch (variants 6 and 7): returns the
+    summed SM cycles of [encode, MLP, sampler, whole tile loop]."""
+    cyc = (ctypes.c_double * 4)()
+    check(lib.nvc_shade_phases(h, scene.ref, _ptr(pos, name="pos"), _ptr(nrm, name="nrm"),
+                               pos.shape[0], int(seed), int(frame),
+                               _ptr(idx, torch.int32, "idx"), _ptr(pdf), _ptr(wsum),
+                               _ptr(radiance), cyc, _stream(stream)), h)
+    return list(cyc)
+
+
+def nvc_gather_bench(table, row_bytes, n_threads, rows_per_thread, sink, seed=0, stream=None):
+    """Queues the random-row gather microbenchmark over `table` (a CUDA
+    tensor of a power-of-two byte size); the caller times it."""
+    if not isinstance(table, torch.Tensor) or not table.is_cuda or not table.is_contiguous():
+        raise ValueError("table must be a contiguous CUDA tensor")
+    if sink.numel() < n_threads:
+        raise ValueError("sink must hold n_threads floats")
+    check(lib.nvc_gather_bench(table.data_ptr(), table.numel() * table.element_size(),
+                               int(row_bytes), int(n_threads), int(rows_per_thread), int(seed),
+                               _ptr(sink, name="sink"), _stream(stream)))
+
+
 def nvc_trace_visibility(scene: Scene, pos, vis, stream=None):
     check(lib.nvc_trace_visibility(scene.ref, _ptr(pos), pos.shape[0], _ptr(vis),
                                    _stream(stream)))
@@ -450,10 +474,30 @@ def nvc_sample_clustered(scene: Scene, clusters: Clusters, vis, pos, nrm, seed, 
 def nvc_infer_noalloc(cfg: NvcConfig, params, pos, vis, stream=None):
     """nvc_infer for callers that cannot allocate GPU memory: parameters come
     from the caller, the library's fixed scratch array holds the encoded
-    features (at most 2^21 floats per call)."""
-    check(lib.nvc_infer_noalloc(ctypes.byref(cfg), _ptr(params, name="params"),
-                                _ptr(pos, name="pos"), pos.shape[0], _ptr(vis, name="vis"),
-                                _stream(stream)))
+    features (at most 2^21 floats per call).
+
+    The C entry point cannot see tensor sizes, so the shapes are checked
+    here against the configuration before anything is launched: params must
+    hold exactly nvc_param_count(cfg) floats, pos be [n, 3] and vis
+    [n, n_outputs], all three on one CUDA device; the call is made with that
+    device current, so the library uses that device's scratch array."""
+    n_params = nvc_param_count(cfg)
+    if n_params < 0:
+        raise NVCError(_lib.NVC_ERR_INVALID_ARG, "invalid configuration")
+    for t, name in ((params, "params"), (pos, "pos"), (vis, "vis")):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
+    if params.numel() != n_params:
+        raise ValueError(f"params holds {params.numel()} floats, the configuration needs {n_params}")
+    if pos.dim() != 2 or pos.shape[1] != 3:
+        raise ValueError(f"pos must be [n, 3], got {tuple(pos.shape)}")
+    if tuple(vis.shape) != (pos.shape[0], cfg.n_outputs):
+        raise ValueError(f"vis must be [{pos.shape[0]}, {cfg.n_outputs}], got {tuple(vis.shape)}")
+    if not (params.device == pos.device == vis.device):
+        raise ValueError("params, pos and vis must be on one device")
+    pp, px, pv = _ptr(params, name="params"), _ptr(pos, name="pos"), _ptr(vis, name="vis")
+    with torch.cuda.device(params.device):
+        check(lib.nvc_infer_noalloc(ctypes.byref(cfg), pp, px, pos.shape[0], pv, _stream(stream)))
 
 
 def nvc_set_profiling(h, enable: bool):

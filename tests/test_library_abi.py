@@ -142,3 +142,45 @@ def test_new_entry_points_reject_null_arguments_without_a_gpu(lib):
     cl.weights, cl.k = 0, 33
     assert lib.nvc_cluster_targets(ctypes.byref(sc), ctypes.byref(cl), None, 1, 0, 0, None,
                                    None) == E
+
+
+def test_measurement_entry_points_reject_bad_arguments_without_a_gpu(lib):
+    """The gather microbenchmark and the phase profile check their arguments
+    on the host: nothing is launched for a bad row size, a table whose row
+    count is not a power of two, a row count per thread that is not a
+    multiple of 8, or a missing handle."""
+    from paper_2506_05930_gb300 import _lib
+    E = _lib.NVC_ERR_INVALID_ARG
+    fake = 1 << 20            # an aligned address that is never dereferenced
+    assert lib.nvc_gather_bench(fake, 1 << 20, 12, 100, 8, 0, fake, None) == E
+    assert lib.nvc_gather_bench(fake, 3 << 20, 8, 100, 8, 0, fake, None) == E
+    assert lib.nvc_gather_bench(fake, 1 << 20, 8, 100, 12, 0, fake, None) == E
+    assert lib.nvc_gather_bench(fake, 1 << 20, 8, 0, 8, 0, fake, None) == E
+    assert lib.nvc_gather_bench(fake + 4, 1 << 20, 8, 100, 8, 0, fake, None) == E
+    assert lib.nvc_gather_bench(None, 1 << 20, 8, 100, 8, 0, fake, None) == E
+    cyc = (ctypes.c_double * 4)()
+    assert lib.nvc_shade_phases(None, None, None, None, 10, 0, 0, None, None, None, None, cyc,
+                                None) == E
+
+
+def test_noalloc_wrapper_checks_shapes_before_launching(lib):
+    """nvc_infer_noalloc cannot see tensor sizes, so the binding checks them
+    against the configuration first: a short parameter vector, a position
+    array of the wrong width or an output of the wrong shape is refused with
+    ValueError before any pointer reaches the library (CPU tensors here, so
+    a launch could not even be attempted)."""
+    import torch
+    import paper_2506_05930_gb300.nvc as nvc
+    cfg = S.config_by_name("tiny_fp32")
+    c = nvc.make_config(cfg)
+    n_params = nvc.nvc_param_count(c)
+    good = dict(params=torch.zeros(n_params), pos=torch.zeros((8, 3)),
+                vis=torch.zeros((8, cfg.n_outputs)))
+    for key, bad in (("params", torch.zeros(n_params - 1)), ("pos", torch.zeros((8, 2))),
+                     ("vis", torch.zeros((8, cfg.n_outputs + 1))), ("vis", torch.zeros((7, 4)))):
+        args = dict(good, **{key: bad})
+        with pytest.raises(ValueError):
+            nvc.nvc_infer_noalloc(c, args["params"], args["pos"], args["vis"])
+    # right shapes but host tensors: refused as not CUDA, still before the call
+    with pytest.raises(ValueError):
+        nvc.nvc_infer_noalloc(c, good["params"], good["pos"], good["vis"])
