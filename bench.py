@@ -244,7 +244,7 @@ def clustered_alu_ops(n_lights, k, n_pixels):
 
 # Per-launch DRAM traffic of the dominant kernel from the ncu capture named in
 # profiles/ (None once the kernel has changed since that capture).
-KERNEL_TRAFFIC = {"fused_shade": 109.98e6, "adam": 428.34e6,
+KERNEL_TRAFFIC = {"fused_shade": None, "adam": 428.34e6,
                   # 1080p launch with the shadow ray (light, W and estimate written)
                   "sample_clustered": 336.47e6}
 
@@ -365,6 +365,162 @@ def measure_phases(cache, scene, pos, nrm, view, seed, frame, shade_ms, cfg, gat
         "note": "phase p is charged share_p x the kernel time; per_tile_frac = a tile's MLP "
                 "flops at one SM's sustained tensor peak over the mean time a tile spends in "
                 "its MLP phase (other tile streams of the SM run meanwhile)"}
+
+
+def _timed(stream, fn, n, warm=3):
+    """Mean milliseconds of fn(k) over n calls on `stream` (CUDA events),
+    after `warm` untimed calls."""
+    import torch
+    for w in range(warm):
+        fn(w)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(n):
+        fn(warm + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def shade_views(cfg, n_pixels, seconds):
+    """The fused shading kernel's ALU roofline view for `n_pixels` pixels of
+    configuration `cfg` shaded in `seconds`."""
+    alg = algorithmic(cfg, n_pixels)
+    pk = peaks()
+    return {"alu_frac": alg["shade_alu_ops"] / seconds / alu_peak_ops(),
+            "tensor_frac_of_sustained": alg["shade_flops"] / seconds / 1e12 / pk["bf16_sustained"],
+            "alu_ops_per_px": alg["alu_ops_per_px"], "mlp_flop_per_px": 2 * alg["macs_per_px"]}
+
+
+def measure_multiview(stream):
+    """The batched multi-view workload: four views of the unit-cube scene at
+    1280x720, 1920x1080, 2560x1440 and 3840x2160 (14,976,000 pixels), 128
+    lights, MLP 32-64-64-64-128, every view shaded by one persistent launch
+    of the variant the project's autotuner picks; the frame (a training step
+    on 8,192 positions x 128 lights, then the shading) replayed as one CUDA
+    graph, and the shading alone.  10 frames after 3 warm-up."""
+    import torch
+    from paper_2506_05930_gb300 import nvc
+    import nvc_synth as S
+    cfg = S.config_by_name("multiview")
+    sc = S.scene_unit_cube(seed=0, n_lights=128)
+    gbs = S.multiview_gbuffers(seed=0)
+    P = sum(g.n for g in gbs)
+    cache = nvc.VisibilityCache(cfg)
+    cache.set_params(S.init_params(cfg, seed=0))
+    scene = nvc.Scene.from_synth(sc)
+    views = []
+    for v, gb in enumerate(gbs):
+        n = gb.n
+        views.append(nvc.View(torch.from_numpy(gb.pos).cuda(), torch.from_numpy(gb.nrm).cuda(), v,
+                              torch.empty(n, dtype=torch.int32, device="cuda"),
+                              torch.empty(n, device="cuda"), torch.empty(n, device="cuda"),
+                              torch.empty(n, device="cuda")))
+    big = views[-1]
+    chosen, ms = nvc.nvc_autotune_shade(cache.handle, scene, big.pos, big.nrm, big.idx, big.pdf,
+                                        big.wsum, big.radiance, reps=3)
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    s = stream.cuda_stream
+    frame_ms = _timed(stream, lambda f: nvc.nvc_frame(cache.handle, scene, views, 1, 11, f, loss,
+                                                      use_graph=True, stream=s), 10)
+    shade_ms = _timed(stream, lambda f: nvc.nvc_frame(cache.handle, scene, views, nvc.NO_TRAINING,
+                                                      11, 100 + f, use_graph=True, stream=s), 10)
+    cache.close()
+    return {"workload": "multiview: 1280x720 + 1920x1080 + 2560x1440 + 3840x2160 views "
+                        "(14,976,000 pixels), 128 lights, MLP 32-64-64-64-128, one launch",
+            "pixels": P, "frame_ms": frame_ms, "value": P / (frame_ms * 1e-3) / 1e6,
+            "unit": "Mpixels/s", "shade_ms": shade_ms,
+            "shade_mpixels_s": P / (shade_ms * 1e-3) / 1e6,
+            "autotune": {"chosen_variant": chosen, "variant_ms_4k_view": [round(m, 4) for m in ms]},
+            "roofline": shade_views(cfg, P, shade_ms * 1e-3)}
+
+
+def measure_online_training(stream):
+    """The online-training workload: the tiny scene seen along its camera
+    path, 16,384 positions x 4 lights = 65,536 shadow-ray samples per frame,
+    BCE, FP16 tensor-core forward/backward, loss scale 128, Adam; one frame =
+    the training step + inference, WRS and Neural DI of the 64x64 view, as a
+    CUDA graph.  100 frames of the path after 5 warm-up (their G-buffers made
+    on the host beforehand and uploaded once)."""
+    import torch
+    from paper_2506_05930_gb300 import nvc
+    import nvc_synth as S
+    cfg = S.config_by_name("online_train")
+    sc = S.scene_unit_cube(seed=0)
+    cache = nvc.VisibilityCache(cfg)
+    cache.set_params(S.init_params(cfg, seed=0))
+    scene = nvc.Scene.from_synth(sc)
+    n_frames = 105
+    gbs = [S.gbuffer_camera_path(seed=0, frame=f) for f in range(n_frames)]
+    n = gbs[0].n
+    views = [nvc.View(torch.from_numpy(g.pos).cuda(), torch.from_numpy(g.nrm).cuda(), 0,
+                      torch.empty(n, dtype=torch.int32, device="cuda"),
+                      torch.empty(n, device="cuda"), torch.empty(n, device="cuda"),
+                      torch.empty(n, device="cuda")) for g in gbs]
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    s = stream.cuda_stream
+    frame_ms = _timed(stream, lambda f: nvc.nvc_frame(cache.handle, scene, [views[f]], 0, 2, f,
+                                                      loss, use_graph=True, stream=s), 100, warm=5)
+    train_ms = _timed(stream, lambda f: nvc.nvc_train_step(cache.handle, scene, views[f % n_frames].pos,
+                                                           2, 1000 + f, loss, stream=s), 100, warm=5)
+    samples = cfg.batch_positions * cfg.n_outputs
+    cache.close()
+    return {"workload": "online_train: unit-cube scene, 64x64 view on the camera path, 16,384 "
+                        "positions x 4 lights per frame, FP16 training with loss scale 128",
+            "us_per_frame": frame_ms * 1e3, "train_step_us": train_ms * 1e3,
+            "training_samples_per_s": samples / (train_ms * 1e-3),
+            "training_positions_per_s": cfg.batch_positions / (train_ms * 1e-3),
+            "note": "a launch-latency-bound workload; frame = training step + shading in one graph"}
+
+
+def measure_precisions(stream):
+    """The 4K precision workload: 3840x2160 pixels of the heightfield scene
+    with 256 lights and 256 occluders, T = 2^21 with half-precision table
+    features for the tensor-core paths; inference + WRS + Neural DI per
+    MLP precision (FP32 on the CUDA cores with the float32 table, FP16, BF16
+    and E4M3 on the tensor cores), each with the variant the autotuner
+    picks.  5 launches after 2 warm-up per precision."""
+    import torch
+    from paper_2506_05930_gb300 import nvc
+    import nvc_synth as S
+    base = S.config_by_name("precision_4k")
+    sc = S.scene_heightfield(seed=5, n_lights=256, n_spheres=128, n_boxes=128)
+    gb = S.gbuffer_heightfield(seed=5, width=3840, height=2160)
+    scene = nvc.Scene.from_synth(sc)
+    pos = torch.from_numpy(gb.pos).cuda()
+    nrm = torch.from_numpy(gb.nrm).cuda()
+    P = gb.n
+    p = S.init_params(base, seed=0)
+    out = dict(idx=torch.empty(P, dtype=torch.int32, device="cuda"),
+               pdf=torch.empty(P, device="cuda"), wsum=torch.empty(P, device="cuda"),
+               radiance=torch.empty(P, device="cuda"))
+    s = stream.cuda_stream
+    res = {}
+    for prec in ("fp32", "fp16", "bf16", "fp8"):
+        cfg = base.with_(precision=prec, train_precision="fp32",
+                         table_precision="fp32" if prec == "fp32" else "fp16")
+        cache = nvc.VisibilityCache(cfg)
+        cache.set_params(p)
+        fused = prec != "fp32"
+        chosen = None
+        if prec == "fp8":
+            nvc.nvc_calibrate(cache.handle, pos[::4096][:1024].contiguous())
+        if not fused:
+            nvc.nvc_set_staging(cache.handle, P)
+        elif prec != "fp8":
+            chosen, _ = nvc.nvc_autotune_shade(cache.handle, scene, pos, nrm, reps=2, **out)
+        ms = _timed(stream, lambda f: nvc.nvc_shade(cache.handle, scene, pos, nrm, 3, f, 0, 0,
+                                                    fused=fused, stream=s, **out), 5, warm=2)
+        r = {"ms": ms, "mpixels_s": P / (ms * 1e-3) / 1e6, "variant": chosen}
+        if fused:
+            r["roofline"] = shade_views(cfg, P, ms * 1e-3)
+        res[prec] = r
+        cache.close()
+    return {"workload": "precision_4k: 3840x2160 heightfield view, 256 lights, 256 occluders, "
+                        "T = 2^21, MLP 32-64-64-64-256; inference + WRS + Neural DI",
+            "precisions": res}
 
 
 CLUSTERED_LIGHTS = 1024
@@ -660,6 +816,9 @@ def run_ours(args):
 
     clustered = measure_clustered(args, gb, stream) if rank == 0 else None
     tiny = measure_tiny(stream, use_graph) if rank == 0 else None
+    multiview = measure_multiview(stream) if rank == 0 else None
+    online = measure_online_training(stream) if rank == 0 else None
+    precisions = measure_precisions(stream) if rank == 0 else None
 
     if rank != 0:
         if world > 1:
@@ -742,10 +901,15 @@ def run_ours(args):
         line["clustered"] = clustered
     if tiny:
         line["tiny_frame"] = tiny
+    if multiview:
+        line["multiview"] = multiview
+    if online:
+        line["online_training"] = online
+    if precisions:
+        line["precision_4k"] = precisions
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(seconds_target=15.0)
-        line["cpu_baseline_all_cores"] = cpu_baseline(seconds_target=15.0,
-                                                      threads=oracle_processes())
+        line["cpu_baseline"] = cpu_baseline(threads=1, parts=4)
+        line["cpu_baseline_all_cores"] = cpu_baseline(threads=oracle_processes())
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -827,35 +991,98 @@ def oracle_processes(per_process_bytes=2e9):
     return max(1, min(cores, int(0.5 * free // per_process_bytes)))
 
 
-def cpu_baseline(seconds_target=15.0, threads=1):
-    """The oracle's frame rate on the host.  `threads` single-threaded oracle
-    processes run at once, each timing the same sample of an independent
-    frame (one BLAS thread each); the rate is the sum of theirs, so `cores`
-    is the number of processes that actually ran."""
+def oracle_frame_part(k, n_parts, chunk=32768):
+    """Part k of n_parts of one 1080p frame on the oracle, timed directly:
+    inference + WRS + Neural DI of pixels [k P / n, (k + 1) P / n), the
+    training forward/backward on positions [k B / n, (k + 1) B / n) of the
+    frame's batch, and the Adam update of parameters [k N / n, (k + 1) N / n).
+    Returns the part's pixel count; the caller times it."""
+    import numpy as np
+    from oracle import nvc as O
+    import nvc_synth as S
+    cfg, sc, gb = workload()
+    if "oracle_state" not in _WORKLOAD_CACHE:
+        p0 = S.init_params(cfg, seed=0)
+        _WORKLOAD_CACHE["oracle_state"] = (p0, O.TrainState.fresh(p0))
+    p, st = _WORKLOAD_CACHE["oracle_state"]
+
+    def span(total):
+        return total * k // n_parts, total * (k + 1) // n_parts
+
+    def work():
+        a, b = span(gb.n)
+        for c in range(a, b, chunk):
+            e = min(c + chunk, b)
+            O.shade(cfg, p, gb.pos[c:e], gb.nrm[c:e], sc.lights, seed=1, frame=0,
+                    pixel_offset=c)
+        pos = O.training_positions(cfg.batch_positions, sc.world_min, sc.world_max, gb.pos, 1, 0)
+        a2, b2 = span(cfg.batch_positions)
+        y = O.visibility(pos[a2:b2], sc.lights, sc.spheres, sc.boxes, np.float32)
+        _, g = O.gradients(cfg, p, pos[a2:b2], y)
+        a3, b3 = span(len(p))
+        O.adam_update(st.params[a3:b3], g[a3:b3], st.m[a3:b3], st.v[a3:b3], 1, cfg.lr, cfg.beta1,
+                      cfg.beta2, cfg.eps)
+        return b - a
+    return work
+
+
+def cpu_baseline(threads=1, parts=None):
+    """The oracle's 1080p frame on the host, timed directly: the frame is
+    split into `parts` disjoint parts (oracle_frame_part; default one per
+    process) and `threads` single-threaded oracle processes (one BLAS
+    thread each) run parts 0 .. threads - 1.  Each sets up, reports ready
+    and waits; all start together on one signal, and the time is the span
+    from the earliest start to the latest end.  With parts > threads only
+    that share of the frame runs, and the frame time is the span times
+    parts / threads (every part holds the same share of pixels, positions
+    and parameters).  The training step's partial gradients are not summed
+    across processes (each updates its own slice of the parameters)."""
+    n = max(int(threads), 1)
+    parts = max(int(parts or n), n)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "fx = bench.oracle_fixed_costs(); "
-            "f, w, P = bench.oracle_frame_sample(131072, 4096, fixed=fx); print(json.dumps([f, w, P]))" % ROOT)
-    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
-                              stderr=subprocess.PIPE, text=True, env=env)
-             for _ in range(max(int(threads), 1))]
+    code = ("import json, sys, time; sys.path.insert(0, %r); import bench; "
+            "work = bench.oracle_frame_part(int(sys.argv[1]), int(sys.argv[2])); "
+            "print('ready', flush=True); sys.stdin.readline(); "
+            "t0 = time.time(); px = work(); t1 = time.time(); "
+            "print(json.dumps([t0, t1, px]), flush=True)" % ROOT)
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(k), str(parts)], stdin=subprocess.PIPE,
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+             for k in range(n)]
+
+    def abandon(msg):
+        for q in procs:
+            if q.poll() is None:
+                q.kill()
+            q.wait()
+        return {"error": msg[-300:]}
+
+    for pr in procs:
+        if pr.stdout.readline().strip() != "ready":
+            return abandon(pr.stderr.read() if pr.poll() is not None else "no ready line")
+    for pr in procs:
+        pr.stdin.write("go\n")
+        pr.stdin.flush()
     results = []
     for pr in procs:
         out, err = pr.communicate()
         if pr.returncode != 0:
-            return {"error": err[-300:]}
+            return abandon(err)
         results.append(json.loads(out.strip().splitlines()[-1]))
-    rate = sum(P / f for f, _, P in results)
-    frame_s = sum(f for f, _, _ in results) / len(results)
-    wall = max(w for _, w, _ in results)
-    P = results[0][2]
-    return {"value": rate / 1e6, "unit": "Mpixels/s", "cores": len(results),
-            "kind": "oracle", "ms_per_frame": frame_s * 1e3, "wall_s": wall,
-            "sample": ("%d concurrent single-threaded oracle processes, each: " % len(results))
-                      + "131,072 random pixels of the 1080p frame shaded (inference+WRS+DI), "
-                      "training forward/backward on 4,096 of the 8,192 positions, one dense Adam "
-                      "update of all parameters; each part extrapolated to the full frame as a "
-                      "fixed per-call cost (timed on one pixel / one position) plus a linear rest"}
+    t0 = min(r[0] for r in results)
+    t1 = max(r[1] for r in results)
+    span = t1 - t0
+    frame_s = span * parts / n
+    P = sum(r[2] for r in results) * parts // n
+    share = "the whole 1080p frame" if parts == n else "%d/%d of the 1080p frame" % (n, parts)
+    return {"value": P / frame_s / 1e6, "unit": "Mpixels/s", "cores": n, "kind": "oracle",
+            "ms_per_frame": frame_s * 1e3, "wall_s": span,
+            "sample": ("%s timed directly: %d disjoint equal parts run by %d concurrent "
+                       "single-threaded oracle processes started together: inference + WRS + "
+                       "Neural DI of the part's pixels, the training forward/backward on its "
+                       "share of the 8,192 positions and the Adam update of its share of the "
+                       "parameters (partial gradients not summed across processes)%s"
+                       % (share, n, n, "" if parts == n else
+                          "; frame time = the span x %d/%d" % (parts, n)))}
 
 
 def run_reference(args):

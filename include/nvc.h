@@ -157,6 +157,19 @@ nvc_status nvc_set_state(nvc_handle* h, const float* params, const float* adam_m
  * themselves (the torch.autograd bridge).  Asynchronous. */
 nvc_status nvc_set_params(nvc_handle* h, const float* params, void* stream);
 
+/* Precision of the hash-table features the fused inference kernels read
+ * (the tables of Section 3.3): NVC_PREC_FP32 (the default) reads the float32
+ * master parameters; NVC_PREC_FP16 keeps a half-precision copy (levels x T
+ * x F halves, round to nearest even), written now and refreshed after every
+ * parameter change -- nvc_set_state, nvc_set_params and every Adam step of
+ * nvc_train_step / nvc_frame -- and the fused kernels (nvc_shade fused = 1,
+ * nvc_infer, nvc_sampler_weights and the frames in FP16, BF16 or FP8
+ * precision) read it instead.  Training always reads and updates the
+ * float32 master; the float32 inference path always reads the master.
+ * Synchronous (waits for `stream`); allocates the copy, or frees it when
+ * going back to NVC_PREC_FP32.  NVC_ERR_INVALID_ARG for other precisions. */
+nvc_status nvc_set_table_precision(nvc_handle* h, int32_t precision, void* stream);
+
 /* Copies parameters and moments out (device [n_params] each; any may be
  * NULL).  Asynchronous; the step count is read by nvc_sync_status. */
 nvc_status nvc_get_state(nvc_handle* h, float* params, float* adam_m, float* adam_v,

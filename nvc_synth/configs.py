@@ -43,6 +43,9 @@ class NVCConfig:
     # precision of the inference MLP and of the training forward/backward
     precision: str = "fp32"           # fp32 | fp16 | bf16 | fp8
     train_precision: str = "fp32"     # fp32 | fp16
+    # hash-table features the fused inference kernels read: the float32
+    # master or a half-precision copy of it
+    table_precision: str = "fp32"     # fp32 | fp16
     # encoding domain (positions are normalised into [0,1]^3 by these)
     bounds_min: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     bounds_max: Tuple[float, float, float] = (1.0, 1.0, 1.0)
@@ -88,9 +91,10 @@ ONLINE_TRAIN = TINY_FP32.with_(
 MULTIVIEW = FRAME_1080P.with_(
     name="multiview", n_outputs=128, bounds_max=(1.0, 1.0, 1.0))
 
-# Precision sweep at 4K: 256 lights, 256 occluders, T = 2^21.
+# Precision sweep at 4K: 256 lights, 256 occluders, T = 2^21, FP16
+# hash-table features.
 PRECISION_4K = FRAME_1080P.with_(
-    name="precision_4k", log2_table_size=21, n_outputs=256)
+    name="precision_4k", log2_table_size=21, n_outputs=256, table_precision="fp16")
 
 # Clustered cache on the 1080p workload (Section 3.6): k = 32 cluster
 # outputs over the 16-room scene with 1024 lights, 8 levels with base resolution 2 (the

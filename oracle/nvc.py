@@ -191,10 +191,20 @@ def sigmoid(x):
     return 1.0 / (1.0 + np.exp(-np.asarray(x, np.float64)))
 
 
+def inference_table(cfg, table: np.ndarray) -> np.ndarray:
+    """The feature table inference reads: the float32 master itself, or, for
+    a cache whose tables hold half-precision features (the 4K workload's
+    FP16 features), every entry rounded to the nearest float16 (ties to
+    even) and then used exactly."""
+    if getattr(cfg, "table_precision", "fp32") == "fp16":
+        return np.asarray(table, np.float64).astype(np.float16).astype(np.float64)
+    return table
+
+
 def infer(cfg, params: np.ndarray, pos: np.ndarray) -> np.ndarray:
     """Predicted visibility of every light, float64 [n, L]."""
     table, Ws = split_params(cfg, params)
-    logits, _, _ = mlp_forward(Ws, encode(cfg, table, pos), cfg.leaky_slope)
+    logits, _, _ = mlp_forward(Ws, encode(cfg, inference_table(cfg, table), pos), cfg.leaky_slope)
     return sigmoid(logits)
 
 

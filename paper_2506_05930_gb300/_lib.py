@@ -99,6 +99,7 @@ PROTOTYPES = {
                                    _vp, _vp, POINTER(c_double), _vp]),
     "nvc_gather_bench": (c_int32, [_vp, c_int64, c_int32, c_int64, c_int32, c_uint32, _vp, _vp]),
     "nvc_set_params": (c_int32, [_vp, _vp, _vp]),
+    "nvc_set_table_precision": (c_int32, [_vp, c_int32, _vp]),
     "nvc_autotune_infer": (c_int32, [_vp, _vp, c_int64, _vp, c_int32, _vp, _vp, _vp]),
     "nvc_calibrate": (c_int32, [_vp, _vp, c_int64, _vp]),
     "nvc_trace_visibility": (c_int32, [_scp, _vp, c_int64, _vp, _vp]),

@@ -355,6 +355,7 @@ void nvc_destroy(nvc_handle* h) {
   cudaFree(h->adam_m);
   cudaFree(h->adam_v);
   cudaFree(h->mlp_packed);
+  cudaFree(h->table16);
   cudaFree(h->t_pos);
   cudaFree(h->t_target);
   cudaFree(h->t_feat);
@@ -428,6 +429,7 @@ nvc_status nvc_set_state(nvc_handle* h, const float* params, const float* adam_m
   set_status_kernel<<<1, 1, 0, s>>>(h->status, step);
   NVC_CUDA(h, cudaGetLastError());
   NVC_CUDA(h, launch_pack_mlp(h, s));
+  NVC_CUDA(h, launch_pack_table(h, s));
   return NVC_OK;
 }
 
@@ -438,6 +440,29 @@ nvc_status nvc_set_params(nvc_handle* h, const float* params, void* stream) {
   NVC_CUDA(h, cudaMemcpyAsync(h->params, params, sizeof(float) * (size_t)h->n_params,
                               cudaMemcpyDeviceToDevice, s));
   NVC_CUDA(h, launch_pack_mlp(h, s));
+  NVC_CUDA(h, launch_pack_table(h, s));
+  return NVC_OK;
+}
+
+nvc_status nvc_set_table_precision(nvc_handle* h, int32_t precision, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (precision != NVC_PREC_FP32 && precision != NVC_PREC_FP16)
+    return fail(h, NVC_ERR_INVALID_ARG, "table precision must be NVC_PREC_FP32 or NVC_PREC_FP16");
+  cudaStream_t s = (cudaStream_t)stream;
+  NVC_CUDA(h, cudaStreamSynchronize(s));
+  if (precision == NVC_PREC_FP32) {
+    NVC_CUDA(h, cudaDeviceSynchronize());
+    cudaFree(h->table16);
+    h->table16 = nullptr;
+    return NVC_OK;
+  }
+  if (!h->table16) {
+    void* p = nullptr;
+    NVC_CUDA(h, cudaMalloc(&p, sizeof(__half) * (size_t)h->n_table));
+    h->table16 = static_cast<__half*>(p);
+  }
+  NVC_CUDA(h, launch_pack_table(h, s));
+  NVC_CUDA(h, cudaStreamSynchronize(s));
   return NVC_OK;
 }
 

@@ -46,6 +46,7 @@ struct FusedArgs {
   int64_t n_tiles;
   ViewDesc v[kMaxViews];
   const float* table;
+  const __half* table16;     // half-precision copy read instead of `table` (may be NULL)
   EncodeParams ep;
   int F;
   const uint4* wimg;
@@ -74,6 +75,33 @@ struct FusedArgs {
   // loop, over every group; NULL in ordinary launches
   unsigned long long* phase_cycles;
 };
+
+// ---- the encode's chunks of CH features -------------------------------------
+// Chunk c of a pixel's layer-0 input (one 16-byte core-matrix row: 8
+// 16-bit or 16 E4M3 operands): levels c LPC .. c LPC + LPC - 1 (F divides
+// CH), zero beyond the real inputs or for a dead pixel.  TT is the table's
+// element type (float32 master or half-precision copy); the fused kernels
+// branch on it once per tile, not per level.
+template <int F, bool XSMALL, int CH, typename TT>
+__device__ __forceinline__ void encode_chunk(const EncodeParams& ep, const TT* table, int c,
+                                             int din, float x, float y, float z, bool live,
+                                             float (&fv)[CH]) {
+  constexpr int LPC = F >= CH ? 1 : CH / F;
+#pragma unroll
+  for (int s = 0; s < CH; ++s) fv[s] = 0.0f;
+  if (live) {
+#pragma unroll
+    for (int q = 0; q < LPC; ++q) {
+      const int l = c * LPC + q;
+      if (l * F < din) {
+        float acc[F];
+        encode_level<F, XSMALL, true, TT>(ep, table, l, x, y, z, acc);
+#pragma unroll
+        for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
+      }
+    }
+  }
+}
 
 // ---- the sampler's arithmetic ----------------------------------------------
 // The two-threads-per-pixel kernel gives lights [0, H) to one thread and

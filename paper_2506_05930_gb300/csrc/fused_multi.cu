@@ -79,10 +79,17 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
   for (int e = t; e < a.wimg_bytes / 16; e += kThreads)
     reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
   if (a.lights) {
-    for (int e = t; e < a.L; e += kThreads) {
-      float4 l = reinterpret_cast<const float4*>(a.lights)[e];
+    // lights in pairs, coordinate-major: {x_j, x_j+1, y_j, y_j+1},
+    // {z_j, z_j+1, I_j/pi, I_j+1/pi}; an odd count's last slot is zero
+    const int Lp = (a.L + 1) & ~1;
+    for (int e = t; e < Lp; e += kThreads) {
+      float4 l = e < a.L ? reinterpret_cast<const float4*>(a.lights)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
       l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
-      s_l[e] = l;
+      float* q = reinterpret_cast<float*>(s_l) + (e >> 1) * 8 + (e & 1);
+      q[0] = l.x;
+      q[2] = l.y;
+      q[4] = l.z;
+      q[6] = l.w;
     }
   }
   if (t == 0) {
@@ -132,25 +139,17 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
       const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
       const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
       const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
-      constexpr int LPC = F >= CH ? 1 : CH / F;
-      for (int c = 0; c < K0 / CH; ++c) {
-        float fv[CH];
-#pragma unroll
-        for (int s = 0; s < CH; ++s) fv[s] = 0.0f;
-        if (live) {
-#pragma unroll
-          for (int q = 0; q < LPC; ++q) {
-            const int l = c * LPC + q;
-            if (l * F < din) {
-              float acc[F];
-              encode_level<F, FULL>(a.ep, a.table, l, x, y, z, acc);
-#pragma unroll
-              for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
-            }
-          }
+      auto encode_all = [&](const auto* tab) {
+        for (int c = 0; c < K0 / CH; ++c) {
+          float fv[CH];
+          encode_chunk<F, FULL, CH>(a.ep, tab, c, din, x, y, z, live, fv);
+          *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, 2)) = pack_chunk<PREC, CH>(fv, 1.0f);
         }
-        *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, 2)) = pack_chunk<PREC, CH>(fv, 1.0f);
-      }
+      };
+      if (a.table16)
+        encode_all(a.table16);
+      else
+        encode_all(a.table);
     }
     fence_async_smem();
     tc_fence_before();
@@ -218,22 +217,45 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
           nz = __ldg(V.nrm + 3 * row + 2);
         }
         float wmax = 0.0f, sum = 0.0f, di = 0.0f;
+        const float2 npx = make_float2(-px, -px), npy = make_float2(-py, -py),
+                     npz = make_float2(-pz, -pz);
+        const float2 nx2 = make_float2(nx, nx), ny2 = make_float2(ny, ny), nz2 = make_float2(nz, nz);
 #pragma unroll
         for (int q4 = 0; q4 < 8; ++q4) {
           float w4[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int j = q4 * 4 + u;
-            float w = 0.0f;
+          for (int up = 0; up < 2; ++up) {
+            const int j = q4 * 4 + up * 2;
+            w4[up * 2] = 0.0f;
+            w4[up * 2 + 1] = 0.0f;
             if (j < L) {
-              const float v = sigmoid_fast(__uint_as_float(r[j]));
-              const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
-              w = fmaxf(v, bits_f(kVisClampBits)) * c;
-              wmax = fmaxf(wmax, w);
-              sum += w;
-              di = fmaf(v, c, di);
+              const float4 A = s_l[j], B = s_l[j + 1];   // pair j/2: {x, y}, {z, I/pi}
+              const float2 dx = __fadd2_rn(make_float2(A.x, A.y), npx);
+              const float2 dy = __fadd2_rn(make_float2(A.z, A.w), npy);
+              const float2 dz = __fadd2_rn(make_float2(B.x, B.y), npz);
+              const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+              const float2 ndl = __ffma2_rn(nx2, dx, __ffma2_rn(ny2, dy, __fmul2_rn(nz2, dz)));
+              const float2 rq = make_float2(rsqrtf(fmaxf(d2.x, 1e-30f)), rsqrtf(fmaxf(d2.y, 1e-30f)));
+              const float2 rr = __fmul2_rn(rq, rq);
+              const float2 inv = make_float2(d2.x >= 1e-6f ? rr.x : 1e6f, d2.y >= 1e-6f ? rr.y : 1e6f);
+              float2 c = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(B.z, B.w), ndl), rq), inv);
+              c.x = fmaxf(c.x, 0.0f);
+              c.y = fmaxf(c.y, 0.0f);
+              const float v0 = sigmoid_fast(__uint_as_float(r[j]));
+              const float v1 = sigmoid_fast(__uint_as_float(r[j + 1]));
+              const float2 w2 = __fmul2_rn(make_float2(fmaxf(v0, bits_f(kVisClampBits)),
+                                                       fmaxf(v1, bits_f(kVisClampBits))), c);
+              wmax = fmaxf(wmax, w2.x);
+              sum += w2.x;
+              di = fmaf(v0, c.x, di);
+              w4[up * 2] = w2.x;
+              if (j + 1 < L) {
+                wmax = fmaxf(wmax, w2.y);
+                sum += w2.y;
+                di = fmaf(v1, c.y, di);
+                w4[up * 2 + 1] = w2.y;
+              }
             }
-            w4[u] = w;
           }
           if (q4 * 4 < L) s_wst4[q4] = make_float4(w4[0], w4[1], w4[2], w4[3]);
         }
@@ -323,7 +345,7 @@ size_t multi_smem(const nvc_handle* h, const PackArgs& p, int tpc, FusedArgs* a 
   stride = (stride + 127) & ~(size_t)127;
   off += (size_t)tpc * stride;
   const size_t l_off = off;
-  off += 16 * (size_t)(h->L > 0 ? h->L : 1);
+  off += 16 * (size_t)(h->L > 0 ? ((h->L + 1) & ~1) : 2);
   off = (off + 7) & ~(size_t)7;
   const size_t bar_off = off;
   off += 8 * (size_t)tpc + 8;

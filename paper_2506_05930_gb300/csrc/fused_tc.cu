@@ -113,26 +113,18 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
       const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
       const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
       const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
-      constexpr int LPC = F >= CH ? 1 : CH / F;   // levels per chunk
-      for (int c = 0; c < K0 / CH; ++c) {
-        float fv[CH];
-#pragma unroll
-        for (int s = 0; s < CH; ++s) fv[s] = 0.0f;
-        if (live) {
-#pragma unroll
-          for (int q = 0; q < LPC; ++q) {
-            const int l = c * LPC + q;   // F divides CH: chunk c holds levels c LPC ..
-            if (l * F < din) {
-              float acc[F];
-              encode_level<F>(a.ep, a.table, l, x, y, z, acc);
-#pragma unroll
-              for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
-            }
-          }
+      auto encode_all = [&](const auto* tab) {
+        for (int c = 0; c < K0 / CH; ++c) {
+          float fv[CH];
+          encode_chunk<F, false, CH>(a.ep, tab, c, din, x, y, z, live, fv);
+          *reinterpret_cast<uint4*>(s_a + cm_offset(t, c * CH, K0, ES)) =
+              pack_chunk<PREC, CH>(fv, s_in0);
         }
-        *reinterpret_cast<uint4*>(s_a + cm_offset(t, c * CH, K0, ES)) =
-            pack_chunk<PREC, CH>(fv, s_in0);
-      }
+      };
+      if (a.table16)
+        encode_all(a.table16);
+      else
+        encode_all(a.table);
     }
     fence_async_smem();
     tc_fence_before();
@@ -227,7 +219,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
             if (i < L) {
               const float v = sigmoid_fast(__uint_as_float(r[j]) * outmul);
               const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
-              w = fmaxf(v, bits_f(kVisClampBits)) * c;
+              w = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), c);
               wmax = fmaxf(wmax, w);
               sum += w;
               di = fmaf(v, c, di);
@@ -399,25 +391,17 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
       const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
       const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
       const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
-      constexpr int LPC = F >= CH ? 1 : CH / F;
-      for (int c = half; c < K0 / CH; c += 2) {
-        float fv[CH];
-#pragma unroll
-        for (int s = 0; s < CH; ++s) fv[s] = 0.0f;
-        if (live) {
-#pragma unroll
-          for (int q = 0; q < LPC; ++q) {
-            const int l = c * LPC + q;
-            if (l * F < din) {
-              float acc[F];
-              encode_level<F>(a.ep, a.table, l, x, y, z, acc);
-#pragma unroll
-              for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
-            }
-          }
+      auto encode_half = [&](const auto* tab) {
+        for (int c = half; c < K0 / CH; c += 2) {
+          float fv[CH];
+          encode_chunk<F, false, CH>(a.ep, tab, c, din, x, y, z, live, fv);
+          *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, 2)) = pack_chunk<PREC, CH>(fv, 1.0f);
         }
-        *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, 2)) = pack_chunk<PREC, CH>(fv, 1.0f);
-      }
+      };
+      if (a.table16)
+        encode_half(a.table16);
+      else
+        encode_half(a.table);
     }
     fence_async_smem();
     tc_fence_before();
@@ -485,7 +469,7 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
             if (i < hi) {
               const float v = sigmoid_fast(__uint_as_float(r[j]));
               const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
-              w = fmaxf(v, bits_f(kVisClampBits)) * c;
+              w = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), c);
               wmax = fmaxf(wmax, w);
               sum += w;
               di = fmaf(v, c, di);
@@ -698,30 +682,22 @@ __global__ void __launch_bounds__(kTileM + PW * 32, PW == 4 ? 2 : 1) fused_shade
         const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
         const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
         const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
-        constexpr int LPC = F >= 8 ? 1 : 8 / F;
-        for (int c = part; c < K0 / 8; c += kParts) {
-          float f8[8];
-#pragma unroll
-          for (int s = 0; s < 8; ++s) f8[s] = 0.0f;
-          if (live) {
-#pragma unroll
-            for (int q = 0; q < LPC; ++q) {
-              const int l = c * LPC + q;   // F divides 8: chunk c holds levels c LPC ..
-              if (l * F < din) {
-                float acc[F];
-                encode_level<F>(a.ep, a.table, l, x, y, z, acc);
-#pragma unroll
-                for (int f = 0; f < F; ++f) f8[q * F + f] = acc[f];
-              }
-            }
+        auto encode_part = [&](const auto* tab) {
+          for (int c = part; c < K0 / 8; c += kParts) {
+            float f8[8];
+            encode_chunk<F, false, 8>(a.ep, tab, c, din, x, y, z, live, f8);
+            uint4 pk;
+            pk.x = pack2<PREC>(f8[0], f8[1]);
+            pk.y = pack2<PREC>(f8[2], f8[3]);
+            pk.z = pack2<PREC>(f8[4], f8[5]);
+            pk.w = pack2<PREC>(f8[6], f8[7]);
+            *reinterpret_cast<uint4*>(a0 + cm_offset(p, c * 8, K0, 2)) = pk;
           }
-          uint4 pk;
-          pk.x = pack2<PREC>(f8[0], f8[1]);
-          pk.y = pack2<PREC>(f8[2], f8[3]);
-          pk.z = pack2<PREC>(f8[4], f8[5]);
-          pk.w = pack2<PREC>(f8[6], f8[7]);
-          *reinterpret_cast<uint4*>(a0 + cm_offset(p, c * 8, K0, 2)) = pk;
-        }
+        };
+        if (a.table16)
+          encode_part(a.table16);
+        else
+          encode_part(a.table);
       }
       if (PRE_C && a.lights) {
         float nx = 0.f, ny = 0.f, nz = 0.f;
@@ -823,7 +799,7 @@ __global__ void __launch_bounds__(kTileM + PW * 32, PW == 4 ? 2 : 1) fused_shade
               const float v = sigmoid_fast(__uint_as_float(r[j]));
               const float c =
                   PRE_C ? cr[j] : contribution_fast(px, py, pz, nx, ny, nz, s_l[j]);
-              w = fmaxf(v, bits_f(kVisClampBits)) * c;
+              w = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), c);
               wmax = fmaxf(wmax, w);
               sum += w;
               di = fmaf(v, c, di);
@@ -1142,6 +1118,27 @@ cudaError_t launch_pack_mlp(nvc_handle* h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The half-precision copy of the hash table (nvc_set_table_precision):
+// table16[i] = fp16(params[i]) for i < n_table, round to nearest even.
+__global__ void pack_table_kernel(const float4* __restrict__ params, uint2* __restrict__ table16,
+                                  int64_t n4) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = params[e];
+    const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    table16[e] = make_uint2(*reinterpret_cast<const uint32_t*>(&a),
+                            *reinterpret_cast<const uint32_t*>(&b));
+  }
+}
+
+cudaError_t launch_pack_table(nvc_handle* h, cudaStream_t s) {
+  if (!h->table16) return cudaSuccess;
+  pack_table_kernel<<<h->num_sms * 8, 256, 0, s>>>(reinterpret_cast<const float4*>(h->params),
+                                                    reinterpret_cast<uint2*>(h->table16),
+                                                    h->n_table / 4);
+  return cudaGetLastError();
+}
+
 bool fused_supported(const nvc_handle* h, std::string* why) {
   if (!tc_precision(h->cfg.precision)) {
     *why = "the fused tensor-core kernel runs in FP16, BF16 or FP8 precision";
@@ -1201,6 +1198,7 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
   if (tiles == 0) return cudaSuccess;
   a.n_tiles = tiles;
   a.table = h->params;
+  a.table16 = h->table16;
   a.ep = encode_params(h);
   a.F = h->F;
   a.wimg = reinterpret_cast<const uint4*>(h->mlp_packed);

@@ -163,6 +163,9 @@ struct nvc_handle {
   float* grad = nullptr;
   float* adam_m = nullptr;
   float* adam_v = nullptr;
+  // half-precision copy of the hash table read by the fused inference
+  // kernels (nvc_set_table_precision; NULL: they read `params`)
+  __half* table16 = nullptr;
   // tensor-core copies of the MLP weights, packed for the fused kernel
   void* mlp_packed = nullptr;
   size_t mlp_packed_bytes = 0;
@@ -283,6 +286,8 @@ cudaError_t launch_finish_gradient(nvc_handle* h, float* grad_out, double* loss_
 
 // fused_tc.cu
 cudaError_t launch_pack_mlp(nvc_handle* h, cudaStream_t s);
+// Refreshes the half-precision table copy from the master (no-op without one).
+cudaError_t launch_pack_table(nvc_handle* h, cudaStream_t s);
 bool fused_supported(const nvc_handle* h, std::string* why);
 cudaError_t launch_shade_fused(const nvc_handle* h, const nvc_scene* sc, const float* pos,
                                const float* nrm, int64_t n, uint64_t seed, uint32_t frame,

@@ -206,12 +206,15 @@ __device__ __forceinline__ bool nonzero4(float4 g) {
   return g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f;
 }
 
+// table16 (may be NULL): the half-precision copy of the first 4 n_table4
+// parameters (the hash table), rewritten from the updated values.
 __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
                                                    float* __restrict__ grad,
                                                    float* __restrict__ m, float* __restrict__ v,
                                                    int64_t n4, int64_t n, float beta1,
                                                    float beta2, float eps,
-                                                   const AdamScalars* __restrict__ scp) {
+                                                   const AdamScalars* __restrict__ scp,
+                                                   uint2* __restrict__ table16, int64_t n_table4) {
   const AdamScalars sc = *scp;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -249,6 +252,12 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
       adam_scalar(th[u].w, g[u].w, mm[u].w, vv[u].w, sc, beta1, beta2, eps);
       const int64_t ee = u == 0 ? e : e1;
       th4[ee] = th[u];
+      if (table16 != nullptr && ee < n_table4) {
+        const __half2 a = __floats2half2_rn(th[u].x, th[u].y);
+        const __half2 b = __floats2half2_rn(th[u].z, th[u].w);
+        table16[ee] = make_uint2(*reinterpret_cast<const uint32_t*>(&a),
+                                 *reinterpret_cast<const uint32_t*>(&b));
+      }
       __stcs(m4 + ee, mm[u]);
       __stcs(v4 + ee, vv[u]);
       if (nonzero4(g[u])) __stcs(g4 + ee, zero);
@@ -350,7 +359,8 @@ cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_
   const int64_t n4 = h->n_params / 4;
   const int blocks = h->num_sms * 8;
   adam_kernel<<<blocks, 256, 0, s>>>(h->params, h->grad, h->adam_m, h->adam_v, n4, h->n_params,
-                                     c.beta1, c.beta2, c.eps, h->adam_scalars);
+                                     c.beta1, c.beta2, c.eps, h->adam_scalars,
+                                     reinterpret_cast<uint2*>(h->table16), h->n_table / 4);
   return cudaGetLastError();
 }
 

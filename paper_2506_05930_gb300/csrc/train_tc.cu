@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_c
             const int l = c * LPC + q;   // F divides 8: chunk c holds levels c LPC ..
             if (l * F < din) {
               float acc[F];
-              encode_level<F>(a.ep, a.table, l, x, y, z, acc);
+              encode_level<F, false, false>(a.ep, a.table, l, x, y, z, acc);
 #pragma unroll
               for (int f = 0; f < F; ++f) f8[q * F + f] = acc[f];
             }

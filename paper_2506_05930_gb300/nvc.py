@@ -247,6 +247,12 @@ def nvc_calibrate(h, pos, stream=None):
     check(lib.nvc_calibrate(h, _ptr(pos, name="pos"), pos.shape[0], _stream(stream)), h)
 
 
+def nvc_set_table_precision(h, precision: str, stream=None):
+    """"fp16": the fused inference kernels read a half-precision copy of the
+    hash table, refreshed after every parameter change; "fp32": the master."""
+    check(lib.nvc_set_table_precision(h, _lib.PRECISIONS[precision], _stream(stream)), h)
+
+
 def nvc_set_shade_variant(h, variant: int):
     check(lib.nvc_set_shade_variant(h, int(variant)), h)
 
@@ -524,6 +530,9 @@ class VisibilityCache:
         self.handle = nvc_create(self.cfg)
         self.L = self.cfg.n_outputs
         self.din = self.cfg.n_levels * self.cfg.n_features
+        table_precision = kw.get("table_precision", getattr(cfg, "table_precision", "fp32"))
+        if table_precision != "fp32":
+            nvc_set_table_precision(self.handle, table_precision)
 
     def close(self):
         if self.handle is not None:

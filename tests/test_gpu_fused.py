@@ -38,12 +38,33 @@ def make(cfg, seed=0, table_scale=1.0):
 
 FP16_TOL = 2e-3
 
+# The fused kernel's light contribution, c = (I/pi) (n.d) r inv with
+# d = l - x, d.d and n.d by fused multiply-adds, r = rsqrtf(d.d) (at most 2
+# ulp, 4u relative with u = 2^-24) and inv = r r (1e6 below d.d = 1e-6),
+# against the float64 definition: d carries u; d.d 5u; r 4u + 2.5u; inv
+# 2 x 6.5u + u = 14u; I rounded with 1/pi 2u and three products 3u: 25.5u
+# relative in all.  n.d cancels at grazing angles: its absolute error,
+# <= 4u |n| |d|, reaches c as <= 4u S (1 + 26u), S = I / (pi max(d.d, 1e-6))
+# the normal-incidence value.  So |c_fused - c| <= 25.5u c + 4.1u S, and as
+# c <= S, <= 30u S.  A weight max(v, 0.001) c adds one rounding and the
+# visibility's error: |w - w64| <= FP16_TOL c + 31u S.  Neural DI, summed
+# by L fused multiply-adds over positive terms, adds (L - 1) u sum v c.
+U = 2.0 ** -24
+C_TOL = 31 * U
+
 
 def c_scale(pos, lights):
     """Normal-incidence contribution I / (pi d^2) of every light: the scale
     of the float32 rounding error of a contribution."""
     d2 = np.sum((lights[None, :, :3].astype(np.float64) - pos[:, None, :]) ** 2, -1)
     return lights[None, :, 3] / (np.pi * np.maximum(d2, 1e-6))
+
+
+def di_bound(c64, cs):
+    """Neural DI bound per pixel from the per-light contribution bound:
+    visibility error x sum c, contribution error x sum S, summation error."""
+    L = c64.shape[1]
+    return (FP16_TOL + L * U) * c64.sum(1) + C_TOL * cs.sum(1)
 
 
 @pytest.mark.parametrize("n", [1, 127, 129, 1000, 4096])
@@ -113,11 +134,38 @@ def test_fused_shade_pick_bitexact_on_its_weights(L):
     w64 = np.maximum(v64, 0.001) * c64
     # float32 error of c_i scales with I / (pi d^2) (n.d cancels at grazing angles)
     cs = c_scale(gb.pos, sc.lights)
-    assert np.all(np.abs(w - w64) <= FP16_TOL * c64 + 2e-6 * cs + 1e-30)
+    assert np.all(np.abs(w - w64) <= FP16_TOL * c64 + C_TOL * cs + 1e-30)
     # Neural DI
     di = host(out["radiance"])
     ref_di = O.neural_di(v64, c64)
-    assert np.all(np.abs(di - ref_di) <= FP16_TOL * c64.sum(1) + 2e-6 * cs.sum(1) + 1e-30)
+    assert np.all(np.abs(di - ref_di) <= di_bound(c64, cs) + 1e-30)
+
+
+@pytest.mark.parametrize("L", [32, 256])
+def test_fused_contribution_within_its_derived_bound(L):
+    """The contribution the fused kernel computes (fused multiply-add dot
+    products, hardware reciprocal square root), recovered from its exported
+    weights w = max(v, 0.001) c as w / max(v, 0.001) with v its own exported
+    visibility (one more rounding), against the float64 definition:
+    |c - c64| <= 26.5u c64 + 4.1u S, checked as 27u c64 + 5u S."""
+    base = {32: "frame_1080p", 256: "precision_4k"}[L]
+    cfg = S.config_by_name(base).with_(precision="fp16", batch_positions=256)
+    sc = S.scene_heightfield(seed=7, n_lights=L, n_spheres=4, n_boxes=4)
+    gb = S.gbuffer_heightfield(seed=7, width=97, height=61)
+    cache, p = make(cfg, seed=3, table_scale=0.5)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    w = torch.empty((gb.n, L), device="cuda")
+    nvc.nvc_sampler_weights(cache.handle, scene, pos, nrm, w)
+    v = host(cache.infer(pos)).astype(np.float32)
+    c_est = host(w).astype(np.float64) / np.maximum(v, np.float32(0.001)).astype(np.float64)
+    c64 = O.contributions(gb.pos, gb.nrm, sc.lights)
+    cs = c_scale(gb.pos, sc.lights)
+    bound = 27 * U * c64 + 5 * U * cs
+    err = np.abs(c_est - c64)
+    worst = np.unravel_index(np.argmax(err / bound), err.shape)
+    assert np.all(err <= bound), (worst, err[worst] / bound[worst])
+    cache.close()
 
 
 def test_fused_shade_shard_invariance_and_zero_size():
@@ -171,8 +219,8 @@ def test_fused_full_1080p_frame_sampled():
     c64 = O.contributions(gb.pos[pick], gb.nrm[pick], sc.lights)
     ref_di = O.neural_di(v64, c64)
     di = host(out["radiance"])[pick]
-    cs = c_scale(gb.pos[pick], sc.lights).sum(1)
-    assert np.all(np.abs(di - ref_di) <= FP16_TOL * c64.sum(1) + 2e-6 * cs + 1e-30)
+    cs = c_scale(gb.pos[pick], sc.lights)
+    assert np.all(np.abs(di - ref_di) <= di_bound(c64, cs) + 1e-30)
     assert (host(out["idx"]) >= 0).mean() > 0.5
 
 
@@ -332,8 +380,8 @@ def test_multiview_full_workload_in_one_graph_launch_sampled():
         v64 = O.infer(cfg, p, gb.pos[pick])
         c64 = O.contributions(gb.pos[pick], gb.nrm[pick], sc.lights)
         ref_di = O.neural_di(v64, c64)
-        cs = c_scale(gb.pos[pick], sc.lights).sum(1)
-        assert np.all(np.abs(host(v.radiance)[pick] - ref_di) <= FP16_TOL * c64.sum(1) + 2e-6 * cs)
+        cs = c_scale(gb.pos[pick], sc.lights)
+        assert np.all(np.abs(host(v.radiance)[pick] - ref_di) <= di_bound(c64, cs))
     # and a training frame over the same views runs and counts
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
     nvc.nvc_frame(cache.handle, scene, views, 1, seed=1, frame=1, loss_out=loss, use_graph=True)
@@ -360,3 +408,32 @@ def test_infer_export_and_its_autotuner(L):
     if L > 32:
         assert all(ms[v] < 0 for v in range(nvc.SHADE_VARIANTS) if v not in (0, PAIR_VARIANT))
     assert np.array_equal(host(cache.infer(dev(pos))), vis0)
+
+
+def test_fp16_table_copy_follows_the_master():
+    """Half-precision table features: inference within the FP16 bound of the
+    oracle run on the float16-rounded table; the copy an Adam step refreshes
+    equals the copy nvc_set_params writes from the same master (bitwise equal
+    visibilities); going back to float32 features reads the master again."""
+    cfg = cfg_frame(precision="fp16", batch_positions=512, table_precision="fp16")
+    cache, p = make(cfg, seed=2, table_scale=0.5)
+    pos_np = np.random.default_rng(3).uniform(0, 10, (3000, 3)).astype(np.float32)
+    pos = dev(pos_np)
+    assert np.max(np.abs(host(cache.infer(pos)) - O.infer(cfg, p, pos_np))) <= FP16_TOL
+    sc = S.scene_heightfield(seed=1, n_lights=32, n_spheres=32, n_boxes=32)
+    gb = S.gbuffer_heightfield(seed=1, width=64, height=36)
+    cache.train_step(nvc.Scene.from_synth(sc), dev(gb.pos), seed=1, frame=0)
+    theta = cache.state()[0]
+    vis_trained = host(cache.infer(pos))
+    assert np.max(np.abs(vis_trained - O.infer(cfg, host(theta), pos_np))) <= FP16_TOL
+    fresh = nvc.VisibilityCache(cfg)
+    fresh.set_params(theta)
+    assert np.array_equal(host(fresh.infer(pos)), vis_trained)
+    # float32 features: the same as a cache that never had the copy
+    nvc.nvc_set_table_precision(cache.handle, "fp32")
+    plain = nvc.VisibilityCache(cfg.with_(table_precision="fp32"))
+    plain.set_params(theta)
+    assert np.array_equal(host(cache.infer(pos)), host(plain.infer(pos)))
+    assert not np.array_equal(host(plain.infer(pos)), vis_trained)
+    for c in (cache, fresh, plain):
+        c.close()

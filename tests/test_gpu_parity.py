@@ -424,9 +424,10 @@ def test_train_gradient_fp16_tensor_cores_matches_oracle(name, loss, batch):
     """FP16 operands, FP32 accumulation, loss scale 128.  The gradient sits
     on the fp16 rounding model (features, weights, activations and deltas
     rounded to fp16, everything else exact) within 5e-4, and is as close to
-    the float64 oracle as that model is (fp16 rounds each operand to 2^-11;
-    through three backward layers with cancelling sums that reaches 1e-2 on
-    the first layer's weights)."""
+    the float64 oracle as that model is.  On the whole-vector norm that is
+    the 2e-3 budget for the tiny network; on the 1080p network fp16
+    operand rounding alone is 3.2e-3 from the oracle (2e-2 on the table's
+    part), so there the bound is the model's own distance plus 5e-4."""
     from helpers import fp16_gradient_model
     cfg = S.config_by_name(name).with_(train_precision="fp16", loss=loss, loss_scale=128.0,
                                        leaky_slope=0.01, batch_positions=batch)
@@ -453,7 +454,10 @@ def test_train_gradient_fp16_tensor_cores_matches_oracle(name, loss, batch):
         assert rel_err(g[lo:hi], g_model[lo:hi]) <= 5e-4, (lo, rel_err(g[lo:hi], g_model[lo:hi]))
         bound = 1.1 * rel_err(g_model[lo:hi], g_ref[lo:hi]) + 5e-4
         assert rel_err(g[lo:hi], g_ref[lo:hi]) <= bound
-    assert rel_err(g, g_ref) <= 5e-3
+    if name == "tiny_fp32":
+        assert rel_err(g, g_ref) <= 2e-3
+    else:
+        assert rel_err(g, g_ref) <= rel_err(g_model, g_ref) + 5e-4
 
 
 def test_online_training_fp16_follows_oracle_and_learns():

@@ -1,9 +1,12 @@
 """Precision sweep of the inference path: FP32 (CUDA cores) and FP16, BF16,
 FP8-E4M3 (tensor cores, FP32 accumulation, per-tensor scales for E4M3) on
-the 4K workload: 3840x2160 pixels, 256 lights, a 2^21-entry table.  For each
-precision: visibility error against the float64 oracle on a seeded
-65,536-pixel subset, WRS light-index agreement with the FP32 path on every
-pixel (same random streams), and the Neural-DI relative error."""
+the 4K workload: 3840x2160 pixels, 256 lights, a 2^21-entry table whose
+features the tensor-core paths read in half precision.  For each precision:
+visibility error against the float64 oracle of the same features (the
+float32 master for the FP32 path, the table rounded to float16 for the
+others) on a seeded 65,536-pixel subset, WRS light-index agreement with the
+FP32 path on every pixel (same random streams), and the Neural-DI relative
+error."""
 import json
 
 import numpy as np
@@ -25,9 +28,14 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-# per precision: (max |vis - oracle|, mean |vis - oracle|, min index agreement, mean DI rel. error)
-BOUNDS = {"fp32": (1e-5, 1e-6, 1.0, 1e-5), "fp16": (2e-3, 2e-4, 0.99, 1e-3),
-          "bf16": (2e-2, 2e-3, 0.95, 5e-3), "fp8": (0.2, 2e-2, 0.7, 5e-2)}
+# per precision: (max |vis - oracle|, mean |vis - oracle|, min index agreement, mean DI rel.
+# error).  Each is 3x the value measured on GB300 (max / mean / DI error; for the
+# agreement, 3x the disagreement): fp32 8.0e-8 / 1.9e-8 / 1 / 1.9e-7; fp16 3.3e-5 /
+# 3.0e-6 / 1 - 5.5e-6 / 6.9e-7; bf16 2.4e-4 / 2.4e-5 / 1 - 4.3e-5 / 5.9e-6; fp8 4.0e-3 /
+# 3.9e-4 / 1 - 7.4e-4 / 8.6e-5.  They guard against regressions; the stated
+# tolerances (1e-5 float32, 2e-3 fp16) are far looser.
+BOUNDS = {"fp32": (2.5e-7, 6e-8, 1.0, 6e-7), "fp16": (1e-4, 1e-5, 1 - 1.7e-5, 2.1e-6),
+          "bf16": (7.2e-4, 7.4e-5, 1 - 1.3e-4, 1.8e-5), "fp8": (1.2e-2, 1.2e-3, 1 - 2.2e-3, 2.6e-4)}
 
 
 def test_fp8_small_network_close_to_oracle():
@@ -41,6 +49,7 @@ def test_fp8_small_network_close_to_oracle():
         cache.infer(pos)                      # scales not calibrated yet
     nvc.nvc_calibrate(cache.handle, pos[:2048])
     err = np.abs(host(cache.infer(pos)) - O.infer(cfg, p, gb.pos))
+    print("fp8 small network: mean", err.mean(), "max", err.max())
     assert err.mean() < 2e-2 and err.max() < 0.2, (err.mean(), err.max())
 
 
@@ -51,15 +60,21 @@ def test_precision_sweep_4k_256_lights():
     scene = nvc.Scene.from_synth(sc)
     pos = torch.from_numpy(gb.pos).cuda()
     nrm = torch.from_numpy(gb.nrm).cuda()
+    assert base.table_precision == "fp16"
     p = scaled_params(base, seed=6, table_scale=0.5)
     pick = np.sort(np.random.default_rng(7).choice(gb.n, 65536, replace=False))
-    v64 = O.infer(base, p, gb.pos[pick])
-    di64 = O.neural_di(v64, O.contributions(gb.pos[pick], gb.nrm[pick], sc.lights))
-    lit = di64 > 1e-3 * di64.max()
+    c64 = O.contributions(gb.pos[pick], gb.nrm[pick], sc.lights)
+    ref = {}
+    for tp in ("fp32", "fp16"):
+        v = O.infer(base.with_(table_precision=tp), p, gb.pos[pick])
+        ref[tp] = (v, O.neural_di(v, c64))
+    lit = ref["fp32"][1] > 1e-3 * ref["fp32"][1].max()
     pt = torch.from_numpy(pick).cuda()
     results, ref_idx = {}, None
     for prec in ("fp32", "fp16", "bf16", "fp8"):
-        cfg = base.with_(precision=prec)
+        # the float32 path reads the float32 master table
+        cfg = base.with_(precision=prec, table_precision="fp32" if prec == "fp32" else "fp16")
+        v64, di64 = ref[cfg.table_precision]
         cache = nvc.VisibilityCache(cfg)
         cache.set_params(p)
         if prec == "fp8":

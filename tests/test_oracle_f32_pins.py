@@ -317,3 +317,26 @@ def test_fp16_operand_rounding_alone_sets_the_training_gradient_error():
         _, g_ref = O.gradients(cfg, p, pos, y)
         dist[name] = rel_err(fp16_gradient_model(cfg, p, pos, y, 128.0), g_ref)
     assert dist["tiny_fp32"] < 2e-3 < dist["frame_1080p"], dist
+
+
+# ------------------------------------------------- FP16 hash-table features --
+
+def test_fp16_table_features_are_the_rounded_table_used_exactly():
+    """A cache with half-precision table features infers from every table
+    entry rounded to the nearest float16 (ties to even), then exactly: the
+    same result as the float32-feature oracle run on a table already holding
+    those rounded values, and a different one from the unrounded table."""
+    from helpers import scaled_params
+    cfg = S.config_by_name("tiny_fp32").with_(table_precision="fp16")
+    p = scaled_params(cfg, seed=4, table_scale=0.3)
+    tn = cfg.n_levels * cfg.table_size * cfg.n_features
+    q = p.copy()
+    q[:tn] = p[:tn].astype(np.float16).astype(np.float32)
+    # float16 rounding of float32 values: ties go to the even neighbour
+    assert np.float32(1 + 2 ** -11).astype(np.float16) == np.float16(1.0)
+    assert np.float32(1 + 3 * 2 ** -11).astype(np.float16) == np.float16(1 + 2 ** -9)
+    pos = np.random.default_rng(0).uniform(0, 1, (500, 3))
+    v16 = O.infer(cfg, p, pos)
+    assert np.array_equal(v16, O.infer(cfg.with_(table_precision="fp32"), q, pos))
+    v32 = O.infer(cfg.with_(table_precision="fp32"), p, pos)
+    assert 0 < np.max(np.abs(v16 - v32)) < 1e-2
