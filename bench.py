@@ -244,7 +244,7 @@ def clustered_alu_ops(n_lights, k, n_pixels):
 
 # Per-launch DRAM traffic of the dominant kernel from the ncu capture named in
 # profiles/ (None once the kernel has changed since that capture).
-KERNEL_TRAFFIC = {"fused_shade": None, "adam": 428.34e6,
+KERNEL_TRAFFIC = {"fused_shade": 109.36e6, "adam": 428.34e6,
                   # 1080p launch with the shadow ray (light, W and estimate written)
                   "sample_clustered": 336.47e6}
 
@@ -392,6 +392,29 @@ def shade_views(cfg, n_pixels, seconds):
     return {"alu_frac": alg["shade_alu_ops"] / seconds / alu_peak_ops(),
             "tensor_frac_of_sustained": alg["shade_flops"] / seconds / 1e12 / pk["bf16_sustained"],
             "alu_ops_per_px": alg["alu_ops_per_px"], "mlp_flop_per_px": 2 * alg["macs_per_px"]}
+
+
+def measure_training_data_fusion(cache, scene, screen, seed, frame0, stream, n=20):
+    """The 1080p training step with its batch made by a launch of its own
+    and made inside the tensor-core training kernel (Section 4.4 fuses
+    them): milliseconds per step (positions + shadow-ray targets, forward,
+    loss, backward, Adam) for each, on the bench's own cache; the handle's
+    setting is restored afterwards."""
+    from paper_2506_05930_gb300 import nvc
+    import torch
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    s = stream.cuda_stream
+    out = {}
+    for fused in (False, True):
+        nvc.nvc_set_training_data_fused(cache.handle, fused)
+        out["fused_ms" if fused else "separate_ms"] = _timed(
+            stream, lambda f: nvc.nvc_train_step(cache.handle, scene, screen, seed, frame0 + f, loss,
+                                                 stream=s), n)
+    nvc.nvc_set_training_data_fused(cache.handle, False)
+    out["note"] = ("training step incl. Adam; separate: positions + targets in their own "
+                   "launch over all SMs; fused: inside the 64 training CTAs, traced while the "
+                   "forward MMAs run")
+    return out
 
 
 def measure_multiview(stream):
@@ -814,6 +837,8 @@ def run_ours(args):
                    "note": "shade pass: one shadow ray per pixel to the sampled light, V c / p, "
                            "running mean; exact DI: a shadow ray to every light from every pixel"}
 
+    fusion = (measure_training_data_fusion(cache, scene, pos, seed, 10_000, stream)
+              if rank == 0 and cfg.train_precision == "fp16" else None)
     clustered = measure_clustered(args, gb, stream) if rank == 0 else None
     tiny = measure_tiny(stream, use_graph) if rank == 0 else None
     multiview = measure_multiview(stream) if rank == 0 else None
@@ -901,6 +926,8 @@ def run_ours(args):
         line["clustered"] = clustered
     if tiny:
         line["tiny_frame"] = tiny
+    if fusion:
+        line["training_data_fusion"] = fusion
     if multiview:
         line["multiview"] = multiview
     if online:

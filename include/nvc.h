@@ -465,6 +465,25 @@ nvc_status nvc_training_positions_split(const nvc_scene* scene, const float* scr
  * step, including captured frame graphs (they are recaptured per frame). */
 nvc_status nvc_set_training_placement(nvc_handle* h, int64_t n_world);
 
+/* Where an FP16 (tensor-core) training step makes its batch (Section 4.4
+ * runs data generation fused into the training pass): fused = 0 (the
+ * default) makes the positions and their shadow-ray targets in a launch of
+ * their own over all SMs before the training kernel; fused != 0 makes them
+ * inside the training kernel, each CTA its own 128-position tiles, the rays
+ * traced slice by slice while the forward layers' MMAs run.  Both give the
+ * same positions and targets bit for bit (nvc_training_positions /
+ * nvc_trace_visibility arithmetic) and so the same loss.  Per-light steps
+ * only (clustered steps keep their own targets); the fused form falls back
+ * to the separate one when the scene's occluders and lights do not fit in
+ * shared memory beside the training tiles.  Host only.
+ * NVC_ERR_UNSUPPORTED with FP32 training. */
+nvc_status nvc_set_training_data_fused(nvc_handle* h, int32_t fused);
+
+/* The batch of the last training step: positions (device [batch_positions]
+ * [3], may be NULL) and binary targets (device [batch_positions][n_outputs],
+ * may be NULL) as the step made them.  Asynchronous copies on `stream`. */
+nvc_status nvc_training_batch(nvc_handle* h, float* pos, float* target, void* stream);
+
 /* One online training step: batch_positions positions (as
  * nvc_training_positions), shadow-ray targets, forward, loss (L2 or BCE,
  * mean over positions x lights), hand-written backward, Adam (bias

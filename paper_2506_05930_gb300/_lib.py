@@ -108,6 +108,8 @@ PROTOTYPES = {
     "nvc_training_positions_split": (c_int32, [_scp, _vp, c_int64, c_int64, c_int64, c_uint64,
                                                c_uint32, _vp, _vp]),
     "nvc_set_training_placement": (c_int32, [_vp, c_int64]),
+    "nvc_set_training_data_fused": (c_int32, [_vp, c_int32]),
+    "nvc_training_batch": (c_int32, [_vp, _vp, _vp, _vp]),
     "nvc_train_step": (c_int32, [_vp, _scp, _vp, c_int64, c_uint64, c_uint32, _vp, _vp]),
     "nvc_train_gradient": (c_int32, [_vp, _scp, _vp, c_int64, c_uint64, c_uint32, _vp, _vp,
                                      _vp]),

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "nvc_internal.cuh"
+#include "shadow.cuh"
 
 using namespace nvc;
 
@@ -902,6 +903,30 @@ nvc_status nvc_training_positions(const nvc_scene* scene, const float* screen_po
                                       stream);
 }
 
+nvc_status nvc_set_training_data_fused(nvc_handle* h, int32_t fused) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (fused && h->cfg.train_precision != NVC_PREC_FP16)
+    return fail(h, NVC_ERR_UNSUPPORTED, "the fused training data needs FP16 training");
+  h->fused_training_data = fused != 0;
+  return NVC_OK;
+}
+
+nvc_status nvc_training_batch(nvc_handle* h, float* pos, float* target, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (pos) {
+    NVC_TRY(check_ptr(h, pos, "pos"));
+    NVC_CUDA(h, cudaMemcpyAsync(pos, h->t_pos, sizeof(float) * 3 * (size_t)h->B,
+                                cudaMemcpyDeviceToDevice, s));
+  }
+  if (target) {
+    NVC_TRY(check_ptr(h, target, "target"));
+    NVC_CUDA(h, cudaMemcpyAsync(target, h->t_target, sizeof(float) * (size_t)h->B * h->L,
+                                cudaMemcpyDeviceToDevice, s));
+  }
+  return NVC_OK;
+}
+
 nvc_status nvc_set_training_placement(nvc_handle* h, int64_t n_world) {
   if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
   if (n_world < -1 || n_world > h->B)
@@ -917,6 +942,18 @@ static nvc_status train_forward_backward(nvc_handle* h, const nvc_scene* scene,
                                          uint64_t seed, uint32_t frame, cudaStream_t s,
                                          const nvc_clusters* clusters = nullptr) {
   const int64_t B = h->B;
+  if (!clusters && h->fused_training_data && h->cfg.train_precision == NVC_PREC_FP16 &&
+      train_tc_gen_supported(h, scene)) {
+    // positions, shadow-ray targets, forward, loss, backward and the hash
+    // scatter in one tensor-core launch
+    StageScope sc(h, s, 1);
+    const PosGen g = pos_gen(scene, screen_pos, n_screen, B, seed, frame, h->n_world);
+    int blocks = 0;
+    NVC_CUDA(h, launch_train_tc(h, B, &blocks, s, scene, &g));
+    h->loss_blocks = blocks;
+    count_launches(h, 1);
+    return NVC_OK;
+  }
   {
     StageScope sc(h, s, 0);
     if (clusters) {

@@ -2,6 +2,7 @@
 // kernel argument block, the weight-image geometry and the sampler's device
 // arithmetic.
 #pragma once
+#include <type_traits>
 #include "nvc_internal.cuh"
 #include "hashgrid.cuh"
 #include "tc_common.cuh"
@@ -89,6 +90,27 @@ __device__ __forceinline__ void encode_chunk(const EncodeParams& ep, const TT* t
   constexpr int LPC = F >= CH ? 1 : CH / F;
 #pragma unroll
   for (int s = 0; s < CH; ++s) fv[s] = 0.0f;
+  if constexpr (F == 2 && LPC % 2 == 0 && std::is_same<TT, __half>::value) {
+    // half-precision rows: two levels' loads in flight at once
+    if (live) {
+#pragma unroll
+      for (int q = 0; q < LPC; q += 2) {
+        const int l = c * LPC + q;
+        if ((l + 1) * F < din) {
+          float acc[4];
+          encode_two_levels_h2<XSMALL>(ep, table, l, x, y, z, acc);
+#pragma unroll
+          for (int f = 0; f < 4; ++f) fv[q * F + f] = acc[f];
+        } else if (l * F < din) {
+          float acc[F];
+          encode_level<F, XSMALL, true, TT>(ep, table, l, x, y, z, acc);
+#pragma unroll
+          for (int f = 0; f < F; ++f) fv[q * F + f] = acc[f];
+        }
+      }
+    }
+    return;
+  }
   if (live) {
 #pragma unroll
     for (int q = 0; q < LPC; ++q) {

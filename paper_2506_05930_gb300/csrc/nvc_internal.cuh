@@ -210,6 +210,9 @@ struct nvc_handle {
   // world-space share of the training positions (nvc_set_training_placement;
   // -1: the default split, ceil(B / 2) world-space)
   int64_t n_world = -1;
+  // FP16 training makes its positions and targets inside the tensor-core
+  // training kernel instead of a separate launch (nvc_set_training_data_fused)
+  bool fused_training_data = false;
   // E4M3 per-tensor scales: [0, 9) activations (set by nvc_calibrate),
   // [9, 18) weights (set by the weight packing)
   float* fp8_scales = nullptr;
@@ -343,6 +346,11 @@ void kmeans_host(const float* lights, int n, const int32_t* init, int k, int ite
 cudaError_t launch_training_data(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,
                                  int64_t batch, uint64_t seed, uint32_t frame, float* pos,
                                  float* vis, cudaStream_t s, int64_t n_world = -1);
-cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStream_t s);
+// gen (with gen_scene): the fused-data variant, which makes the batch's
+// positions and shadow-ray targets itself (into t_pos / t_target).
+struct PosGen;
+cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStream_t s,
+                            const nvc_scene* gen_scene = nullptr, const PosGen* gen = nullptr);
+bool train_tc_gen_supported(const nvc_handle* h, const nvc_scene* sc);
 
 }  // namespace nvc

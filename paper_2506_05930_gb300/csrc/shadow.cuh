@@ -68,4 +68,33 @@ __device__ __forceinline__ bool segment_blocked(float px, float py, float pz, fl
   return occ;
 }
 
+// ---- training positions (Section 3.4) ------------------------------------------
+// Samples [0, n_world) are uniform in the world box (stream tag 1); the rest
+// copy G-buffer pixel floor(r * n_screen / 2^32) (stream tag 2).
+struct PosGen {
+  float3 lo, ext;
+  const float* screen;
+  int64_t n_screen, n_world;
+  uint32_t k0, k1, frame;
+};
+
+__device__ __forceinline__ float3 training_position(int64_t j, const PosGen& g) {
+  if (j < g.n_world) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)j, g.frame, 0u, kTagWorld), g.k0, g.k1);
+    return make_float3(__fadd_rn(g.lo.x, __fmul_rn(uniform24(r.x), g.ext.x)),
+                       __fadd_rn(g.lo.y, __fmul_rn(uniform24(r.y), g.ext.y)),
+                       __fadd_rn(g.lo.z, __fmul_rn(uniform24(r.z), g.ext.z)));
+  }
+  const uint32_t s = (uint32_t)(j - g.n_world);
+  const uint4 r = philox4x32_10(make_uint4(s, g.frame, 0u, kTagScreen), g.k0, g.k1);
+  const int64_t pix = (int64_t)(((uint64_t)r.x * (uint64_t)g.n_screen) >> 32);
+  return make_float3(g.screen[3 * pix], g.screen[3 * pix + 1], g.screen[3 * pix + 2]);
+}
+
+// The generator of a training batch (train.cu): n_world = -1 for the
+// default split ceil(batch / 2); every position is world space without
+// screen positions.
+PosGen pos_gen(const nvc_scene* sc, const float* screen_pos, int64_t n_screen, int64_t batch,
+               uint64_t seed, uint32_t frame, int64_t n_world);
+
 }  // namespace nvc

@@ -234,9 +234,19 @@ __device__ __forceinline__ FeatVec<F> load_row(const float* p) {
 //     two features per packed float32x2 operation -- 14 instructions for 8
 //     corners instead of 12 weight products and 16 fused multiply-adds;
 //     equal to the weighted sum up to rounding.
-template <int F, bool XSMALL = false, bool LERP = true, typename TT = float>
-__device__ __forceinline__ void encode_level(const EncodeParams& ep, const TT* __restrict__ table,
-                                             int l, float x, float y, float z, float (&acc)[F]) {
+// The cell of x_hat at level l: the 8 corner rows (within the level's table)
+// and the fractions.  (a ^ b ^ c) & m = (a & m) ^ (b & m) ^ (c & m): masking
+// the six axis terms leaves one three-input XOR per corner.  XSMALL: the
+// caller knows every level's N_l + 1 < T, so the x terms need no mask.
+struct LevelCell {
+  uint32_t row[8];
+  float fx, fy, fz;
+};
+
+template <bool XSMALL>
+__device__ __forceinline__ LevelCell level_cell(const EncodeParams& ep, int l, float x, float y,
+                                                float z) {
+  LevelCell c;
   const int n = ep.res[l];
   const float nf = (float)n;
   int cx = __float2int_rd(__fmul_rn(x, nf)), cy = __float2int_rd(__fmul_rn(y, nf)),
@@ -244,44 +254,53 @@ __device__ __forceinline__ void encode_level(const EncodeParams& ep, const TT* _
   cx = min(cx, n - 1);
   cy = min(cy, n - 1);
   cz = min(cz, n - 1);
-  const float fx = __fsub_rn(__fmul_rn(x, nf), (float)cx);
-  const float fy = __fsub_rn(__fmul_rn(y, nf), (float)cy);
-  const float fz = __fsub_rn(__fmul_rn(z, nf), (float)cz);
+  c.fx = __fsub_rn(__fmul_rn(x, nf), (float)cx);
+  c.fy = __fsub_rn(__fmul_rn(y, nf), (float)cy);
+  c.fz = __fsub_rn(__fmul_rn(z, nf), (float)cz);
   const uint32_t mask = (1u << ep.log2_table) - 1u;
-  // (a ^ b ^ c) & m = (a & m) ^ (b & m) ^ (c & m): masking the six axis
-  // terms leaves one three-input XOR per corner.  XSMALL: the caller knows
-  // every level's N_l + 1 < T, so the x terms need no mask.
   const uint32_t hx[2] = {XSMALL ? (uint32_t)cx : (uint32_t)cx & mask,
                           XSMALL ? (uint32_t)cx + 1u : ((uint32_t)cx + 1u) & mask};
   const uint32_t hy0 = (uint32_t)cy * kPrime1, hz0 = (uint32_t)cz * kPrime2;
   const uint32_t hy[2] = {hy0 & mask, (hy0 + kPrime1) & mask};
   const uint32_t hz[2] = {hz0 & mask, (hz0 + kPrime2) & mask};
-  const TT* tab = table + ((size_t)l << ep.log2_table) * F;
-  uint32_t row[8];
 #pragma unroll
-  for (int d = 0; d < 8; ++d) row[d] = hx[d & 1] ^ hy[(d >> 1) & 1] ^ hz[d >> 2];
+  for (int d = 0; d < 8; ++d) c.row[d] = hx[d & 1] ^ hy[(d >> 1) & 1] ^ hz[d >> 2];
+  return c;
+}
+
+// Packed linear interpolation of 8 corners' feature pairs (f, f + 1):
+// v0 + f (v1 - v0) along x, then y, then z.
+__device__ __forceinline__ float2 lerp_corners(const float2 (&v)[8], float fx, float fy, float fz) {
+  const float2 fx2 = make_float2(fx, fx), fy2 = make_float2(fy, fy), fz2 = make_float2(fz, fz);
+  float2 e[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) e[k] = __ffma2_rn(fx2, fsub2(v[2 * k + 1], v[2 * k]), v[2 * k]);
+  const float2 e0 = __ffma2_rn(fy2, fsub2(e[1], e[0]), e[0]);
+  const float2 e1 = __ffma2_rn(fy2, fsub2(e[3], e[2]), e[2]);
+  return __ffma2_rn(fz2, fsub2(e1, e0), e0);
+}
+
+template <int F, bool XSMALL = false, bool LERP = true, typename TT = float>
+__device__ __forceinline__ void encode_level(const EncodeParams& ep, const TT* __restrict__ table,
+                                             int l, float x, float y, float z, float (&acc)[F]) {
+  const LevelCell c = level_cell<XSMALL>(ep, l, x, y, z);
+  const TT* tab = table + ((size_t)l << ep.log2_table) * F;
   FeatVec<F> v[8];
 #pragma unroll
-  for (int d = 0; d < 8; ++d) v[d] = load_row<F>(tab + (size_t)row[d] * F);
+  for (int d = 0; d < 8; ++d) v[d] = load_row<F>(tab + (size_t)c.row[d] * F);
   if constexpr (LERP && F % 2 == 0) {
-    const float2 fx2 = make_float2(fx, fx), fy2 = make_float2(fy, fy), fz2 = make_float2(fz, fz);
 #pragma unroll
     for (int f = 0; f < F; f += 2) {
-      float2 e[4];
+      float2 vv[8];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float2 v0 = make_float2(v[2 * k].v[f], v[2 * k].v[f + 1]);
-        const float2 v1 = make_float2(v[2 * k + 1].v[f], v[2 * k + 1].v[f + 1]);
-        e[k] = __ffma2_rn(fx2, fsub2(v1, v0), v0);
-      }
-      const float2 e0 = __ffma2_rn(fy2, fsub2(e[1], e[0]), e[0]);
-      const float2 e1 = __ffma2_rn(fy2, fsub2(e[3], e[2]), e[2]);
-      const float2 r = __ffma2_rn(fz2, fsub2(e1, e0), e0);
+      for (int d = 0; d < 8; ++d) vv[d] = make_float2(v[d].v[f], v[d].v[f + 1]);
+      const float2 r = lerp_corners(vv, c.fx, c.fy, c.fz);
       acc[f] = r.x;
       acc[f + 1] = r.y;
     }
   } else {
-    const float gx[2] = {1.0f - fx, fx}, gy[2] = {1.0f - fy, fy}, gz[2] = {1.0f - fz, fz};
+    const float gx[2] = {1.0f - c.fx, c.fx}, gy[2] = {1.0f - c.fy, c.fy},
+                gz[2] = {1.0f - c.fz, c.fz};
 #pragma unroll
     for (int f = 0; f < F; ++f) acc[f] = 0.0f;
 #pragma unroll
@@ -291,6 +310,37 @@ __device__ __forceinline__ void encode_level(const EncodeParams& ep, const TT* _
       for (int f = 0; f < F; ++f) acc[f] = fmaf(w, v[d].v[f], acc[f]);
     }
   }
+}
+
+// Two levels of a half-precision, two-feature table at once: both cells'
+// 16 rows are requested before either is blended, so twice as many row
+// loads are in flight.  The rows stay packed half2 words (one register a
+// corner) until the blend widens them.  Same results as two encode_level
+// calls.
+template <bool XSMALL>
+__device__ __forceinline__ void encode_two_levels_h2(const EncodeParams& ep,
+                                                     const __half* __restrict__ table, int la,
+                                                     float x, float y, float z, float (&acc)[4]) {
+  const LevelCell ca = level_cell<XSMALL>(ep, la, x, y, z);
+  const LevelCell cb = level_cell<XSMALL>(ep, la + 1, x, y, z);
+  const unsigned int* ta = reinterpret_cast<const unsigned int*>(table) + ((size_t)la << ep.log2_table);
+  const unsigned int* tb = ta + ((size_t)1 << ep.log2_table);
+  uint32_t ua[8], ub[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) ua[d] = __ldg(ta + ca.row[d]);
+#pragma unroll
+  for (int d = 0; d < 8; ++d) ub[d] = __ldg(tb + cb.row[d]);
+  float2 va[8], vb[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) va[d] = h2f2(ua[d]);
+  const float2 ra = lerp_corners(va, ca.fx, ca.fy, ca.fz);
+#pragma unroll
+  for (int d = 0; d < 8; ++d) vb[d] = h2f2(ub[d]);
+  const float2 rb = lerp_corners(vb, cb.fx, cb.fy, cb.fz);
+  acc[0] = ra.x;
+  acc[1] = ra.y;
+  acc[2] = rb.x;
+  acc[3] = rb.y;
 }
 
 }  // namespace tc

@@ -7,29 +7,7 @@ namespace nvc {
 
 namespace {
 
-// ---- training positions ---------------------------------------------------
-// Samples [0, n_world) are uniform in the world box (stream tag 1); the rest
-// copy G-buffer pixel floor(r * n_screen / 2^32) (stream tag 2).
-struct PosGen {
-  float3 lo, ext;
-  const float* screen;
-  int64_t n_screen, n_world;
-  uint32_t k0, k1, frame;
-};
-
-__device__ __forceinline__ float3 training_position(int64_t j, const PosGen& g) {
-  if (j < g.n_world) {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)j, g.frame, 0u, kTagWorld), g.k0, g.k1);
-    return make_float3(__fadd_rn(g.lo.x, __fmul_rn(uniform24(r.x), g.ext.x)),
-                       __fadd_rn(g.lo.y, __fmul_rn(uniform24(r.y), g.ext.y)),
-                       __fadd_rn(g.lo.z, __fmul_rn(uniform24(r.z), g.ext.z)));
-  }
-  const uint32_t s = (uint32_t)(j - g.n_world);
-  const uint4 r = philox4x32_10(make_uint4(s, g.frame, 0u, kTagScreen), g.k0, g.k1);
-  const int64_t pix = (int64_t)(((uint64_t)r.x * (uint64_t)g.n_screen) >> 32);
-  return make_float3(g.screen[3 * pix], g.screen[3 * pix + 1], g.screen[3 * pix + 2]);
-}
-
+// ---- training positions (training_position in shadow.cuh) -----------------
 __global__ void training_positions_kernel(PosGen g, int64_t batch, float* __restrict__ pos) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= batch) return;
@@ -282,8 +260,8 @@ __global__ void take_gradient_kernel(float* __restrict__ grad, float* __restrict
 
 }  // namespace
 
-static PosGen pos_gen(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,
-                      int64_t batch, uint64_t seed, uint32_t frame, int64_t n_world) {
+PosGen pos_gen(const nvc_scene* sc, const float* screen_pos, int64_t n_screen,
+               int64_t batch, uint64_t seed, uint32_t frame, int64_t n_world) {
   const bool have_screen = screen_pos != nullptr && n_screen > 0;
   PosGen g;
   g.lo = make_float3(sc->world_min[0], sc->world_min[1], sc->world_min[2]);

@@ -25,8 +25,18 @@
 // matrices (stride-byte offset 128, leading-byte offset 16 * row length).
 // At the end each CTA adds its dW (times 1/(B*L)) into the gradient with
 // fp32 atomics and writes its loss partial.
+//
+// GEN (the fused training data of Section 4.4): the kernel also makes the
+// tile's training positions (training_position, as the separate data
+// kernel) and traces their shadow rays to every light against the
+// occluders staged in shared memory.  The rays of a tile are split into one
+// slice per hidden layer, each traced by all threads between the layer's
+// MMA issue and its wait, so the ray tests run while the tensor core works;
+// the targets stay in shared memory for the loss (and are also written out
+// with the positions, the batch nvc_training_batch reads back).
 #include "nvc_internal.cuh"
 #include "hashgrid.cuh"
+#include "shadow.cuh"
 #include "tc_common.cuh"
 
 namespace nvc {
@@ -69,7 +79,36 @@ struct TrainTcArgs {
   float* grad;
   double* partials;
   int32_t* status;
+  // GEN only: the batch generator, the scene and where the batch goes
+  PosGen pg;
+  const float* lights;
+  const float* spheres;
+  const float* boxes;
+  int n_sph, n_box;
+  float* pos_out;             // [n][3]
+  float* target_out;          // [n][L]
+  int occ_off;                // smem: spheres (float4), boxes (6 floats), lights (float4)
+  int tgt_off;                // smem: the tile's targets, 128 x L bytes
 };
+
+// Rays [r0, r1) of a tile's 128 x L (row-major by sample): the segment from
+// the row's position to light i against every staged occluder; the binary
+// target goes to shared memory and, for live rows, to target_out.
+__device__ __forceinline__ void trace_slice(const TrainTcArgs& a, const float* s_pos,
+                                            const float4* s_sph, const float* s_box,
+                                            const float4* s_lt, uint8_t* s_tgt, int64_t tile,
+                                            int r0, int r1, int t, int n_threads) {
+  for (int r = r0 + t; r < r1; r += n_threads) {
+    const int row = r / a.L, i = r - row * a.L;
+    const int64_t sample = tile * 128 + row;
+    if (sample >= a.n) continue;
+    const float4 lt = s_lt[i];
+    const bool occ = segment_blocked(s_pos[3 * row], s_pos[3 * row + 1], s_pos[3 * row + 2], lt.x,
+                                     lt.y, lt.z, s_sph, a.n_sph, s_box, a.n_box);
+    s_tgt[r] = occ ? 0 : 1;
+    a.target_out[sample * a.L + i] = occ ? 0.0f : 1.0f;
+  }
+}
 
 template <int PREC>
 __device__ __forceinline__ void unpack2(uint32_t u, float& a, float& b) {
@@ -114,11 +153,27 @@ __device__ __forceinline__ void store_row16(uint8_t* tile, int row, int c0, int 
 // parallel instead of one after another in a single thread.
 constexpr int kGroups = 4;
 
-template <int F, int PREC, int NG>
+template <int F, int PREC, int NG, bool GEN>
 __global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_constant__ TrainTcArgs a) {
   constexpr int kThreads = kTileM * NG;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ double s_red[kThreads / 32];
+  __shared__ float s_pos[GEN ? 3 * kTileM : 1];
+  const float4* s_sph = reinterpret_cast<const float4*>(smem + a.occ_off);
+  const float* s_box = reinterpret_cast<const float*>(smem + a.occ_off) + 4 * a.n_sph;
+  const float4* s_lt = reinterpret_cast<const float4*>(smem + a.occ_off + 16 * a.n_sph +
+                                                       ((24 * a.n_box + 15) & ~15));
+  uint8_t* s_tgt = smem + a.tgt_off;
+  if constexpr (GEN) {
+    float4* sph = const_cast<float4*>(s_sph);
+    float* box = const_cast<float*>(s_box);
+    float4* lt = const_cast<float4*>(s_lt);
+    for (int e = threadIdx.x; e < a.n_sph; e += kThreads)
+      sph[e] = reinterpret_cast<const float4*>(a.spheres)[e];
+    for (int e = threadIdx.x; e < 6 * a.n_box; e += kThreads) box[e] = a.boxes[e];
+    for (int e = threadIdx.x; e < a.L; e += kThreads)
+      lt[e] = reinterpret_cast<const float4*>(a.lights)[e];
+  }
   uint8_t* s_w = smem;
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.bar_off);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 1);
@@ -158,9 +213,30 @@ __global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_c
     const bool live = row < a.n;
     float x = 0.f, y = 0.f, z = 0.f;
     if (live) {
-      x = normalise(__ldg(a.pos + 3 * row), a.ep.lo[0], a.ep.ext[0]);
-      y = normalise(__ldg(a.pos + 3 * row + 1), a.ep.lo[1], a.ep.ext[1]);
-      z = normalise(__ldg(a.pos + 3 * row + 2), a.ep.lo[2], a.ep.ext[2]);
+      float px, py, pz;
+      if constexpr (GEN) {
+        // every warpgroup makes its row's position (a cheaper way to share
+        // it than a barrier); the first also stages and stores it
+        const float3 q = training_position(row, a.pg);
+        px = q.x;
+        py = q.y;
+        pz = q.z;
+        if (wg == 0) {
+          s_pos[3 * rw] = px;
+          s_pos[3 * rw + 1] = py;
+          s_pos[3 * rw + 2] = pz;
+          a.pos_out[3 * row] = px;
+          a.pos_out[3 * row + 1] = py;
+          a.pos_out[3 * row + 2] = pz;
+        }
+      } else {
+        px = __ldg(a.pos + 3 * row);
+        py = __ldg(a.pos + 3 * row + 1);
+        pz = __ldg(a.pos + 3 * row + 2);
+      }
+      x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
+      y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
+      z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
     }
     // ---- encode into act_0 (this warpgroup's 8-feature chunks) ------------
     {
@@ -207,6 +283,15 @@ __global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_c
                   a.idesc_fwd[k], kk > 0 ? 1u : 0u);
         mma_commit(bar);
       }
+      if constexpr (GEN) {
+        // slice k of the tile's shadow rays while layer k's MMAs run; the
+        // loss (layer `last`) reads them after this layer's barrier
+        if (k < last) {
+          const int R = kTileM * a.L;
+          trace_slice(a, s_pos, s_sph, s_box, s_lt, s_tgt, tile, R * k / last, R * (k + 1) / last, t,
+                      kThreads);
+        }
+      }
       const bool ok = mbar_wait_bounded(bar, phase);
       phase ^= 1u;
       tc_fence_after();
@@ -237,7 +322,7 @@ __global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_c
             float g = 0.0f;
             if (live && i < a.L) {
               const float zz = __uint_as_float(r[j]);
-              const float yy = __ldg(yrow + i);
+              const float yy = GEN ? (float)s_tgt[rw * a.L + i] : __ldg(yrow + i);
               const float s = 1.0f / (1.0f + expf(-zz));
               if (a.loss == NVC_LOSS_BCE) {
                 loss_acc += (double)(fmaxf(zz, 0.0f) + log1pf(expf(-fabsf(zz))) - yy * zz);
@@ -434,7 +519,10 @@ uint32_t idesc(int M, int N, int prec, bool a_mn, bool b_mn) {
 
 // Shared-memory and TMEM plan; returns false with a reason when the network
 // does not fit.
-bool plan(const nvc_handle* h, TrainTcArgs& a, size_t* smem, std::string* why) {
+// gen (may be NULL): the scene of the fused-data variant, whose occluders,
+// lights and targets then take shared memory too.
+bool plan(const nvc_handle* h, TrainTcArgs& a, size_t* smem, std::string* why,
+          const nvc_scene* gen = nullptr) {
   const int nl = h->n_layers;
   a.n_layers = nl;
   int wbytes = 0, work = 32;
@@ -469,6 +557,12 @@ bool plan(const nvc_handle* h, TrainTcArgs& a, size_t* smem, std::string* why) {
   off += kGuardBytes;
   a.bar_off = off;
   off += 64;
+  if (gen) {
+    a.occ_off = off;
+    off += 16 * gen->n_spheres + ((24 * gen->n_boxes + 15) & ~15) + 16 * h->L;
+    a.tgt_off = off;
+    off += (kTileM * h->L + 15) & ~15;
+  }
   uint32_t col = (uint32_t)((work + 31) & ~31);
   for (int k = 0; k < nl; ++k) {
     a.dw_col[k] = col;
@@ -506,11 +600,38 @@ bool train_tc_supported(const nvc_handle* h, std::string* why) {
   return plan(h, a, &smem, why);
 }
 
-cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStream_t s) {
+template <int F, int PREC, bool GEN>
+cudaError_t launch_train_kernel(const TrainTcArgs& a, int grid, size_t smem, cudaStream_t s) {
+  auto kern = train_tc_kernel<F, PREC, kGroups, GEN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kTileM * kGroups, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+bool train_tc_gen_supported(const nvc_handle* h, const nvc_scene* sc) {
   TrainTcArgs a{};
   size_t smem = 0;
   std::string why;
-  if (!plan(h, a, &smem, &why)) return cudaErrorNotSupported;
+  return h->mlp_packed && sc && sc->n_lights == h->L && plan(h, a, &smem, &why, sc);
+}
+
+cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStream_t s,
+                            const nvc_scene* gen_scene, const PosGen* gen) {
+  TrainTcArgs a{};
+  size_t smem = 0;
+  std::string why;
+  if (!plan(h, a, &smem, &why, gen ? gen_scene : nullptr)) return cudaErrorNotSupported;
+  if (gen) {
+    a.pg = *gen;
+    a.lights = gen_scene->lights;
+    a.spheres = gen_scene->spheres;
+    a.boxes = gen_scene->boxes;
+    a.n_sph = gen_scene->n_spheres;
+    a.n_box = gen_scene->n_boxes;
+    a.pos_out = h->t_pos;
+    a.target_out = h->t_target;
+  }
   const int prec = h->cfg.precision == NVC_PREC_BF16 ? NVC_PREC_BF16 : NVC_PREC_FP16;
   a.pos = h->t_pos;
   a.target = h->t_target;
@@ -535,16 +656,12 @@ cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStre
   int grid = (int)(n_tiles < h->num_sms ? n_tiles : h->num_sms);
   if (grid > h->n_loss_partials) grid = h->n_loss_partials;
   *blocks_used = grid;
-  cudaError_t e;
   if (prec == NVC_PREC_BF16) {
     switch (h->F) {
 #define NVC_TRAIN_CASE(FF)                                                                      \
   case FF:                                                                                      \
-    e = cudaFuncSetAttribute(train_tc_kernel<FF, NVC_PREC_BF16, kGroups>,                           \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
-    if (e != cudaSuccess) return e;                                                             \
-    train_tc_kernel<FF, NVC_PREC_BF16, kGroups><<<grid, kTileM * kGroups, smem, s>>>(a);            \
-    return cudaGetLastError();
+    return gen ? launch_train_kernel<FF, NVC_PREC_BF16, true>(a, grid, smem, s)                   \
+               : launch_train_kernel<FF, NVC_PREC_BF16, false>(a, grid, smem, s);
       NVC_TRAIN_CASE(1) NVC_TRAIN_CASE(2) NVC_TRAIN_CASE(4) NVC_TRAIN_CASE(8)
 #undef NVC_TRAIN_CASE
     }
@@ -552,11 +669,8 @@ cudaError_t launch_train_tc(nvc_handle* h, int64_t n, int* blocks_used, cudaStre
     switch (h->F) {
 #define NVC_TRAIN_CASE(FF)                                                                      \
   case FF:                                                                                      \
-    e = cudaFuncSetAttribute(train_tc_kernel<FF, NVC_PREC_FP16, kGroups>,                           \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
-    if (e != cudaSuccess) return e;                                                             \
-    train_tc_kernel<FF, NVC_PREC_FP16, kGroups><<<grid, kTileM * kGroups, smem, s>>>(a);            \
-    return cudaGetLastError();
+    return gen ? launch_train_kernel<FF, NVC_PREC_FP16, true>(a, grid, smem, s)                   \
+               : launch_train_kernel<FF, NVC_PREC_FP16, false>(a, grid, smem, s);
       NVC_TRAIN_CASE(1) NVC_TRAIN_CASE(2) NVC_TRAIN_CASE(4) NVC_TRAIN_CASE(8)
 #undef NVC_TRAIN_CASE
     }

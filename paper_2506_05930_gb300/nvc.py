@@ -300,6 +300,18 @@ def nvc_training_positions_split(scene: Scene, screen_pos, batch, n_world, seed,
                                            _stream(stream)))
 
 
+def nvc_set_training_data_fused(h, fused: bool):
+    """FP16 training makes its positions and shadow-ray targets inside the
+    tensor-core training kernel (True) or in a launch of their own (False)."""
+    check(lib.nvc_set_training_data_fused(h, 1 if fused else 0), h)
+
+
+def nvc_training_batch(h, pos=None, target=None, stream=None):
+    """Copies the last training step's positions [B, 3] and targets [B, L] out."""
+    check(lib.nvc_training_batch(h, _ptr(pos, name="pos"), _ptr(target, name="target"),
+                                 _stream(stream)), h)
+
+
 def nvc_set_training_placement(h, n_world: int):
     check(lib.nvc_set_training_placement(h, int(n_world)), h)
 

@@ -175,3 +175,74 @@ def test_adaptation_after_an_abrupt_scene_change(capsys):
     assert one[0] > 2 * one[32]                 # the jump is visible, and training recovers
     assert one[16] < 0.5 * one[0]               # within 16 frames the error at least halves
     assert two[8] < one[8]                      # two steps per frame adapt faster
+
+
+@pytest.mark.parametrize("name,batch", [("frame_1080p", 8192), ("frame_1080p", 1000),
+                                        ("tiny_fp32", 1024)])
+def test_fused_training_data_equals_the_separate_launch(name, batch):
+    """Training data made inside the tensor-core training kernel (Section
+    4.4's fused data generation): the positions and shadow-ray targets are
+    the oracle's bit for bit -- the same as the separate launch's -- so the
+    loss is the same double-precision sum, and the gradient differs only by
+    the order of the float atomics that collect it.  A batch that is not a
+    multiple of the 128-sample tile is included."""
+    cfg = S.config_by_name(name).with_(train_precision="fp16", loss="bce", loss_scale=128.0,
+                                       leaky_slope=0.01, batch_positions=batch)
+    if name == "tiny_fp32":
+        sc, gb = S.scene_unit_cube(seed=0), S.gbuffer_points(0, 64, 64)
+    else:
+        sc = S.scene_heightfield(seed=1, n_lights=32, n_spheres=32, n_boxes=32)
+        gb = S.gbuffer_heightfield(seed=1, width=96, height=54)
+    p = scaled_params(cfg, seed=2, table_scale=0.5)
+    scene = nvc.Scene.from_synth(sc)
+    screen = dev(gb.pos)
+    out = {}
+    for fused in (False, True):
+        cache = nvc.VisibilityCache(cfg)
+        cache.set_params(p)
+        nvc.nvc_set_training_data_fused(cache.handle, fused)
+        g, loss = cache.train_gradient(scene, screen, seed=5, frame=3)
+        pos = torch.empty((batch, 3), device="cuda")
+        tgt = torch.empty((batch, cfg.n_outputs), device="cuda")
+        nvc.nvc_training_batch(cache.handle, pos, tgt)
+        out[fused] = (host(g), host(loss)[0], host(pos), host(tgt))
+        cache.close()
+    ref_pos = O.training_positions(batch, sc.world_min, sc.world_max, gb.pos, 5, 3)
+    ref_tgt = O.visibility(ref_pos, sc.lights, sc.spheres, sc.boxes, np.float32)
+    for fused in (False, True):
+        assert np.array_equal(out[fused][2], ref_pos), fused
+        assert np.array_equal(out[fused][3], ref_tgt), fused
+    assert 0.05 < ref_tgt.mean() < 0.95
+    assert out[True][1] == out[False][1]
+    assert rel_err(out[True][0], out[False][0]) <= 1e-5
+
+
+def test_fused_training_data_steps_and_frames_train():
+    """Whole training steps and graph-captured frames with the fused data:
+    the loss follows the separate-launch path step for step, to the
+    atomics-order difference the gradients carry into Adam."""
+    cfg = S.config_by_name("frame_1080p").with_(batch_positions=2048)
+    sc = S.scene_heightfield(seed=1, n_lights=32, n_spheres=32, n_boxes=32)
+    gb = S.gbuffer_heightfield(seed=1, width=128, height=72)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    p = scaled_params(cfg, seed=2, table_scale=0.5)
+    losses = {}
+    for fused in (False, True):
+        cache = nvc.VisibilityCache(cfg)
+        cache.set_params(p)
+        nvc.nvc_set_training_data_fused(cache.handle, fused)
+        n = gb.n
+        view = nvc.View(pos, nrm, 0, torch.empty(n, dtype=torch.int32, device="cuda"),
+                        torch.empty(n, device="cuda"), torch.empty(n, device="cuda"),
+                        torch.empty(n, device="cuda"))
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        ls = []
+        for f in range(12):
+            nvc.nvc_frame(cache.handle, scene, [view], 0, 3, f, loss, use_graph=f % 2 == 1)
+            ls.append(host(loss)[0])
+        losses[fused] = np.array(ls)
+        assert cache.counters()["step"] == 12
+        cache.close()
+    np.testing.assert_allclose(losses[True], losses[False], rtol=1e-3)
+    assert losses[True][-1] < losses[True][0]

@@ -161,6 +161,9 @@ def test_measurement_entry_points_reject_bad_arguments_without_a_gpu(lib):
     cyc = (ctypes.c_double * 4)()
     assert lib.nvc_shade_phases(None, None, None, None, 10, 0, 0, None, None, None, None, cyc,
                                 None) == E
+    assert lib.nvc_set_training_data_fused(None, 1) == E
+    assert lib.nvc_training_batch(None, None, None, None) == E
+    assert lib.nvc_set_table_precision(None, 1, None) == E
 
 
 def test_noalloc_wrapper_checks_shapes_before_launching(lib):
