@@ -184,8 +184,9 @@ def workload(precision=None):
 def workload_config(world, pixels_per_gpu, positions_per_frame):
     """The bench line's `config`, the same for both arms."""
     return {"workload": "frame_1080p: 1920x1080 heightfield+boxes view, 32 point lights, "
-                        "32 spheres + 32 boxes; hash grid 16 levels x 2 features x 2^19, "
-                        "MLP 32-64-64-64-32; training 8192 positions x 32 lights per frame",
+                        "32 spheres + 32 boxes; hash grid 16 levels x 2 features x 2^19 (FP32 "
+                        "master, FP16 copy for inference), MLP 32-64-64-64-32; training 8192 "
+                        "positions x 32 lights per frame",
             "global_batch": world * pixels_per_gpu, "pixels_per_gpu": pixels_per_gpu,
             "train_positions_per_frame": positions_per_frame, "parallelism": f"replica{world}",
             "l2": "no flush: per-frame working set (G-buffer 50 MB, table+Adam state 270 MB) "
@@ -442,8 +443,8 @@ def measure_multiview(stream):
                               torch.empty(n, device="cuda"), torch.empty(n, device="cuda"),
                               torch.empty(n, device="cuda")))
     big = views[-1]
-    chosen, ms = nvc.nvc_autotune_shade(cache.handle, scene, big.pos, big.nrm, big.idx, big.pdf,
-                                        big.wsum, big.radiance, reps=3)
+    chosen, tried = nvc.nvc_autotune_shade_plan(cache.handle, scene, big.pos, big.nrm, big.idx,
+                                                big.pdf, big.wsum, big.radiance, reps=3)
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
     s = stream.cuda_stream
     frame_ms = _timed(stream, lambda f: nvc.nvc_frame(cache.handle, scene, views, 1, 11, f, loss,
@@ -456,7 +457,8 @@ def measure_multiview(stream):
             "pixels": P, "frame_ms": frame_ms, "value": P / (frame_ms * 1e-3) / 1e6,
             "unit": "Mpixels/s", "shade_ms": shade_ms,
             "shade_mpixels_s": P / (shade_ms * 1e-3) / 1e6,
-            "autotune": {"chosen_variant": chosen, "variant_ms_4k_view": [round(m, 4) for m in ms]},
+            "autotune": {"chosen": {"variant": chosen[0], "ctas_per_sm": chosen[1]},
+                         "points_ms_4k_view": {f"{v}/{c}": round(m, 4) for (v, c), m in tried}},
             "roofline": shade_views(cfg, P, shade_ms * 1e-3)}
 
 
@@ -533,7 +535,7 @@ def measure_precisions(stream):
         if not fused:
             nvc.nvc_set_staging(cache.handle, P)
         elif prec != "fp8":
-            chosen, _ = nvc.nvc_autotune_shade(cache.handle, scene, pos, nrm, reps=2, **out)
+            chosen, _ = nvc.nvc_autotune_shade_plan(cache.handle, scene, pos, nrm, reps=2, **out)
         ms = _timed(stream, lambda f: nvc.nvc_shade(cache.handle, scene, pos, nrm, 3, f, 0, 0,
                                                     fused=fused, stream=s, **out), 5, warm=2)
         r = {"ms": ms, "mpixels_s": P / (ms * 1e-3) / 1e6, "variant": chosen}
@@ -624,6 +626,10 @@ def measure_clustered(args, gb, stream):
     scene_v = nvc.Scene.from_synth(sc_big)
     cl_v = nvc.Clusters(assign_big, k, weights="visibility")
     sample_vis_big_ms = timed(("sample_vis",))
+    # the summed-contribution weights at the same scale: one contribution per
+    # light and pixel, the lights staged through shared memory in tiles
+    cl_v = nvc.Clusters(assign_big, k, weights="sum")
+    sample_sum_big_ms = timed(("sample_vis",), n=3)
     cache.close()
     ops = clustered_alu_ops(CLUSTERED_LIGHTS, k, P)
     peak = alu_peak_ops()
@@ -633,6 +639,7 @@ def measure_clustered(args, gb, stream):
         "value": P / (frame_ms * 1e-3) / 1e6, "unit": "Mpixels/s", "frame_ms": frame_ms,
         "train_ms": train_ms, "infer_ms": infer_ms, "infer_variant": infer_variant,
         "sample_with_shadow_ray_ms": sample_ms,
+        f"sample_with_shadow_ray_ms_at_{PAPER_SCALE_LIGHTS}_lights": sample_sum_big_ms,
         "sampler_ms": sampler_ms,
         "visibility_weights": {
             "frame_ms": frame_vis_ms, "value": P / (frame_vis_ms * 1e-3) / 1e6,
@@ -683,10 +690,13 @@ def run_ours(args):
                     torch.empty(P, device="cuda"))
     tune = None
     if fused:
-        # the project's autotuner picks the fused kernel variant for this frame (untimed)
-        chosen, ms = nvc.nvc_autotune_shade(cache.handle, scene, pos, nrm, view.idx, view.pdf,
-                                            view.wsum, view.radiance, reps=5)
-        tune = {"chosen_variant": chosen, "variant_ms": [round(m, 4) for m in ms]}
+        # the project's autotuner picks the fused kernel's point -- layout
+        # (tile streams per CTA, levels split across threads, warp
+        # specialisation) x resident CTAs per SM -- for this frame (untimed)
+        chosen, tried = nvc.nvc_autotune_shade_plan(cache.handle, scene, pos, nrm, view.idx,
+                                                    view.pdf, view.wsum, view.radiance, reps=5)
+        tune = {"chosen": {"variant": chosen[0], "ctas_per_sm": chosen[1]},
+                "points_ms": {f"{v}/{c}": round(m, 4) for (v, c), m in tried}}
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
     use_graph = not args.no_graph
     # pretraining (untimed): 500 frames of online training on this view

@@ -318,6 +318,41 @@ nvc_status nvc_shade_phases(nvc_handle* h, const nvc_scene* scene, const float* 
                             int32_t* idx, float* pdf, float* wsum, float* radiance,
                             double* cycles_out, void* stream);
 
+/* A point of the fused shading kernel's tuning space (nvc_autotune_shade_plan):
+ *   variant      the kernel layout, 0 .. NVC_SHADE_VARIANTS-1: tile streams
+ *                per CTA (1, 2 or 4 -- 128, 256 or 512 pixels in flight per
+ *                CTA: variants 0, 6, 7), the levels of a pixel encoded by one
+ *                thread or split between two (variant 5, and variants 3, 4
+ *                with producer warps), producer/consumer warp specialisation
+ *                (1-4);
+ *   ctas_per_sm  how many CTAs of that layout an SM holds at once (the grid
+ *                is ctas_per_sm x SMs persistent CTAs); 0 = as many as its
+ *                registers, shared memory and TMEM allow.
+ * Every point shades identically (the same picks from the same weights;
+ * variant 5's sums as stated above). */
+typedef struct nvc_shade_plan {
+  int32_t variant;
+  int32_t ctas_per_sm;
+} nvc_shade_plan;
+
+/* Sets the handle's shading point (variant as nvc_set_shade_variant;
+ * ctas_per_sm >= 0). */
+nvc_status nvc_set_shade_plan(nvc_handle* h, const nvc_shade_plan* plan);
+
+/* The autotuner over the whole tuning space: every applicable variant at
+ * ctas_per_sm 0 (all that fit), 1, 2 and 3, each timed as
+ * nvc_autotune_shade times a variant (CUDA events on `stream`, a warm-up
+ * then `reps` launches; synchronises); keeps the fastest point for the
+ * handle.  chosen (host, may be NULL) receives it; points (host
+ * [max_points], may be NULL) and ms (host [max_points], may be NULL) every
+ * point tried and its mean milliseconds per launch, *n_points (may be
+ * NULL) their number.  Outputs as nvc_shade. */
+nvc_status nvc_autotune_shade_plan(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                                   const float* nrm, int64_t n, int32_t* idx, float* pdf,
+                                   float* wsum, float* radiance, int32_t reps,
+                                   nvc_shade_plan* chosen, nvc_shade_plan* points, double* ms,
+                                   int32_t max_points, int32_t* n_points, void* stream);
+
 /* Selects the fused shading kernel variant (0 .. NVC_SHADE_VARIANTS-1). */
 nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant);
 
@@ -428,6 +463,36 @@ nvc_status nvc_sample_clustered(const nvc_scene* scene, const nvc_clusters* clus
                                 int64_t pixel_offset, uint64_t seed, uint32_t frame,
                                 uint32_t view, int32_t* light, float* weight, float* estimate,
                                 void* stream);
+
+/* ---- the cache as ReSTIR's initial-candidate generator (Sections 3.1, 4.2)
+ *
+ * Temporal resampling of one reservoir per pixel: the frame's
+ * initial-candidate reservoir, made by the cache's sampler (cur_light with
+ * its unbiased contribution weight cur_W: 1 / pdf from nvc_wrs_sample /
+ * nvc_shade, or W from nvc_sample_clustered), counts M_c = 1 candidate and
+ * needs no shadow ray of its own (the cache already weighs visibility);
+ * the previous frame's reservoir at the same pixel (prev_light, prev_W,
+ * prev_M; prev_M = 0 where the pixel is disoccluded, so the cache's
+ * candidate stands alone) counts M_p' = min(prev_M, 20) (the previous
+ * reservoir counts at most 20x the new one).  With the target p_hat(y) =
+ * c_y, the float32 contribution of nvc_light_weights:
+ *     w_c = (1 * p_hat(y_c)) * W_c,   w_p = (M_p' * p_hat(y_p)) * W_p,
+ * the integer reservoir of nvc_wrs_sample picks y from (y_c, y_p) with
+ * words 0, 1 of the Philox stream (pixel_offset + p, frame, view, 6), and
+ *     M = 1 + M_p',   W = (w_c + w_p) / (M * p_hat(y))
+ * (float32, each operation correctly rounded in that order; y = -1, W = 0
+ * when both weights are 0; a light index outside [0, n_lights) counts as
+ * no sample).  Outputs (device [n], any may be NULL, not all): light, W,
+ * M and estimate = V(y) p_hat(y) W with one shadow ray (0 when blocked or
+ * empty).  The output reservoir is next frame's previous reservoir.
+ * prev_* (device [n]) may all be NULL: every pixel disoccluded.  Any
+ * number of lights.  Asynchronous. */
+nvc_status nvc_temporal_merge(const nvc_scene* scene, const float* pos, const float* nrm,
+                              int64_t n, int64_t pixel_offset, uint64_t seed, uint32_t frame,
+                              uint32_t view, const int32_t* cur_light, const float* cur_W,
+                              const int32_t* prev_light, const float* prev_W,
+                              const int32_t* prev_M, int32_t* light, float* W, int32_t* M,
+                              float* estimate, void* stream);
 
 /* ---- training (Section 3.4) -------------------------------------------- */
 

@@ -193,10 +193,11 @@ def sigmoid(x):
 
 def inference_table(cfg, table: np.ndarray) -> np.ndarray:
     """The feature table inference reads: the float32 master itself, or, for
-    a cache whose tables hold half-precision features (the 4K workload's
-    FP16 features), every entry rounded to the nearest float16 (ties to
-    even) and then used exactly."""
-    if getattr(cfg, "table_precision", "fp32") == "fp16":
+    a cache whose tensor-core inference reads half-precision features (the
+    1080p and 4K workloads' FP16 feature copy), every entry rounded to the
+    nearest float16 (ties to even) and then used exactly.  Float32 inference
+    always reads the master."""
+    if getattr(cfg, "table_precision", "fp32") == "fp16" and cfg.precision != "fp32":
         return np.asarray(table, np.float64).astype(np.float16).astype(np.float64)
     return table
 
@@ -656,6 +657,76 @@ def sample_clustered(vis, pos, nrm, lights, offsets, members, pixel_ids, seed: i
         light[p] = cand[j]
         W[p] = ris_weight(cc, np.int64(j), w[p, yy], wsum[p], m_y)
     return light, W
+
+
+# ----------------------------------------------------------------------------
+# The cache as ReSTIR's initial-candidate generator (Sections 3.1 and 4.2)
+# ----------------------------------------------------------------------------
+
+TEMPORAL_M_CAP = 20   # the previous reservoir counts at most 20x the new one
+
+
+def integer_pick(w32: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """The integer streaming reservoir of ``wrs_select`` over the columns of
+    w32 [n, m] with the words r [n, m]: index of the kept candidate, -1 when
+    every weight is 0."""
+    q = quantize_weights(np.asarray(w32, np.float32))
+    r = np.asarray(r).astype(np.uint64)
+    sel = np.full(q.shape[0], -1, np.int64)
+    Q = np.zeros(q.shape[0], np.uint64)
+    for i in range(q.shape[1]):
+        Q = Q + q[:, i]
+        take = (q[:, i] > 0) & (r[:, i] * Q < q[:, i] * np.uint64(1 << 32))
+        sel = np.where(take, i, sel)
+    return sel
+
+
+def target_at(c32: np.ndarray, light: np.ndarray) -> np.ndarray:
+    """The resampling target p_hat(y) = c_y, the float32 unshadowed
+    contribution of light y at each pixel (0 for y = -1)."""
+    light = np.asarray(light, np.int64)
+    t = np.take_along_axis(np.asarray(c32, np.float32), np.maximum(light, 0)[:, None], 1)[:, 0]
+    return np.where(light >= 0, t, np.float32(0)).astype(np.float32)
+
+
+def temporal_merge(c32, cur_light, cur_W, prev_light, prev_W, prev_M, pixel_ids, seed: int,
+                   frame: int, view: int):
+    """Temporal resampling of a pixel's reservoirs (the ReSTIR combination
+    the paper feeds with the cache's samples: Section 3.1, last paragraph,
+    and Section 4.2).
+
+    The frame's initial-candidate reservoir (y_c, W_c), made by the cache's
+    sampler, counts M_c = 1 candidate; the previous frame's reservoir at the
+    same pixel (y_p, W_p, M_p) counts M_p' = min(M_p, 20 M_c) (M_p = 0 where
+    the pixel is disoccluded: the cache's candidate alone).  With the target
+    p_hat(y) = c_y (float32 contributions c32 [n, L]):
+        w_c = (M_c p_hat(y_c)) W_c,   w_p = (M_p' p_hat(y_p)) W_p,
+    the integer reservoir picks y between [y_c, y_p] with words 0, 1 of
+    stream (pixel, frame, view, TAG_TEMPORAL), and
+        M = M_c + M_p',   W = (w_c + w_p) / (M p_hat(y)),
+    every product, sum and quotient a float32 rounding in that order;
+    y = -1 and W = 0 when both weights are 0.  Returns (light int32, W
+    float32, M int32), each [n]."""
+    n = len(cur_light)
+    Mc = np.ones(n, np.int64)
+    Mp = np.minimum(np.asarray(prev_M, np.int64), TEMPORAL_M_CAP * Mc)
+    pc = target_at(c32, cur_light)
+    pp = target_at(c32, prev_light)
+    f32 = np.float32
+    wc = ((Mc.astype(f32) * pc).astype(f32) * np.asarray(cur_W, f32)).astype(f32)
+    wp = ((Mp.astype(f32) * pp).astype(f32) * np.asarray(prev_W, f32)).astype(f32)
+    wc = np.where(np.asarray(cur_light) >= 0, wc, f32(0))
+    wp = np.where((np.asarray(prev_light) >= 0) & (Mp > 0), wp, f32(0))
+    r = _ph.stream_words(pixel_ids, frame, view, _ph.TAG_TEMPORAL, 2, seed)
+    pick = integer_pick(np.stack([wc, wp], 1), r)
+    light = np.where(pick == 0, cur_light, np.where(pick == 1, prev_light, -1)).astype(np.int32)
+    M = (Mc + Mp).astype(np.int32)
+    py = target_at(c32, light)
+    s = (wc + wp).astype(f32)
+    den = (M.astype(f32) * py).astype(f32)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        W = np.where(light >= 0, (s / np.where(light >= 0, den, f32(1))).astype(f32), f32(0))
+    return light, W.astype(np.float32), M
 
 
 # ----------------------------------------------------------------------------

@@ -80,6 +80,7 @@ TAG_SCREEN = 2
 TAG_SHADE = 3
 TAG_RIS = 4        # clustered sampling: candidates in a cluster and their pick
 TAG_CLUSTER = 5    # clustered training targets: a member light per cluster
+TAG_TEMPORAL = 6   # temporal resampling: the pick between the current and previous reservoir
 
 
 def stream_words(ids: np.ndarray, frame: int, view: int, tag: int,

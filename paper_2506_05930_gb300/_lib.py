@@ -55,6 +55,10 @@ class NvcClusters(Structure):
                 ("weights", c_int32)]
 
 
+class NvcShadePlan(Structure):
+    _fields_ = [("variant", c_int32), ("ctas_per_sm", c_int32)]
+
+
 class NvcCounters(Structure):
     _fields_ = [("step", c_int32), ("skipped", c_int32), ("error_flags", c_int32),
                 ("frames", c_int32)]
@@ -95,6 +99,10 @@ PROTOTYPES = {
     "nvc_autotune_shade": (c_int32, [_vp, _scp, _vp, _vp, c_int64, _vp, _vp, _vp, _vp, c_int32,
                                      POINTER(c_int32), POINTER(c_double), _vp]),
     "nvc_set_shade_variant": (c_int32, [_vp, c_int32]),
+    "nvc_set_shade_plan": (c_int32, [_vp, POINTER(NvcShadePlan)]),
+    "nvc_autotune_shade_plan": (c_int32, [_vp, _scp, _vp, _vp, c_int64, _vp, _vp, _vp, _vp, c_int32,
+                                          POINTER(NvcShadePlan), POINTER(NvcShadePlan),
+                                          POINTER(c_double), c_int32, POINTER(c_int32), _vp]),
     "nvc_shade_phases": (c_int32, [_vp, _scp, _vp, _vp, c_int64, c_uint64, c_uint32, _vp, _vp,
                                    _vp, _vp, POINTER(c_double), _vp]),
     "nvc_gather_bench": (c_int32, [_vp, c_int64, c_int32, c_int64, c_int32, c_uint32, _vp, _vp]),
@@ -128,6 +136,8 @@ PROTOTYPES = {
     "nvc_cluster_targets": (c_int32, [_scp, _clp, _vp, c_int64, c_uint64, c_uint32, _vp, _vp]),
     "nvc_sample_clustered": (c_int32, [_scp, _clp, _vp, _vp, _vp, c_int64, c_int64, c_uint64,
                                        c_uint32, c_uint32, _vp, _vp, _vp, _vp]),
+    "nvc_temporal_merge": (c_int32, [_scp, _vp, _vp, c_int64, c_int64, c_uint64, c_uint32, c_uint32,
+                                     _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nvc_infer_noalloc": (c_int32, [_cfgp, _vp, _vp, c_int64, _vp, _vp]),
     "nvc_set_profiling": (c_int32, [_vp, c_int32]),
     "nvc_stage_times": (c_int32, [_vp, POINTER(c_double), c_int32, POINTER(c_int64)]),

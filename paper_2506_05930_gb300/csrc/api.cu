@@ -706,6 +706,91 @@ nvc_status nvc_shade_phases(nvc_handle* h, const nvc_scene* scene, const float* 
   return NVC_OK;
 }
 
+static nvc_status check_variant(nvc_handle* h, int32_t variant) {
+  if (variant < 0 || variant >= kShadeVariants)
+    return fail(h, NVC_ERR_INVALID_ARG, "variant out of range");
+  if (variant != kShadeMono && h->cfg.precision == NVC_PREC_FP8)
+    return fail(h, NVC_ERR_UNSUPPORTED, "E4M3 operands run the monolithic variant only");
+  if (variant != kShadeMono && variant != kShadePair && h->L > 32)
+    return fail(h, NVC_ERR_UNSUPPORTED, "variants 1-4, 6 and 7 need n_outputs <= 32");
+  return NVC_OK;
+}
+
+nvc_status nvc_set_shade_plan(nvc_handle* h, const nvc_shade_plan* plan) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (!plan) return fail(h, NVC_ERR_INVALID_ARG, "plan is NULL");
+  NVC_TRY(check_variant(h, plan->variant));
+  if (plan->ctas_per_sm < 0 || plan->ctas_per_sm > 64)
+    return fail(h, NVC_ERR_INVALID_ARG, "ctas_per_sm out of range");
+  h->shade_variant = plan->variant;
+  h->shade_ctas_per_sm = plan->ctas_per_sm;
+  return NVC_OK;
+}
+
+nvc_status nvc_autotune_shade_plan(nvc_handle* h, const nvc_scene* scene, const float* pos,
+                                   const float* nrm, int64_t n, int32_t* idx, float* pdf,
+                                   float* wsum, float* radiance, int32_t reps,
+                                   nvc_shade_plan* chosen, nvc_shade_plan* points, double* ms,
+                                   int32_t max_points, int32_t* n_points, void* stream) {
+  NVC_TRY(shade_checks(h, scene, pos, nrm, n, 0));
+  if (n == 0 || reps < 1) return fail(h, NVC_ERR_INVALID_ARG, "need n > 0 and reps >= 1");
+  if ((points || ms) && max_points < 1) return fail(h, NVC_ERR_INVALID_ARG, "max_points < 1");
+  std::string why;
+  if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  NVC_CUDA(h, cudaEventCreate(&e0));
+  NVC_CUDA(h, cudaEventCreate(&e1));
+  const int keep_v = h->shade_variant, keep_c = h->shade_ctas_per_sm;
+  nvc_shade_plan best{keep_v, keep_c};
+  double best_ms = -1.0;
+  int np = 0;
+  cudaError_t err = cudaSuccess;
+  static const int kCtas[] = {0, 1, 2, 3};
+  for (int v = 0; v < kShadeVariants && err == cudaSuccess; ++v) {
+    if (check_variant(h, v) != NVC_OK) continue;
+    for (int c : kCtas) {
+      h->shade_variant = v;
+      h->shade_ctas_per_sm = c;
+      if (launch_shade_fused(h, scene, pos, nrm, n, 1, 0, 0, 0, idx, pdf, wsum, radiance, nullptr,
+                             s) != cudaSuccess) {
+        cudaGetLastError();
+        break;                         // the layout does not fit this configuration
+      }
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r)
+        launch_shade_fused(h, scene, pos, nrm, n, 1, (uint32_t)r, 0, 0, idx, pdf, wsum, radiance,
+                           nullptr, s);
+      cudaEventRecord(e1, s);
+      if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      const double per = (double)t / reps;
+      if (np < max_points) {
+        if (points) points[np] = nvc_shade_plan{v, c};
+        if (ms) ms[np] = per;
+      }
+      ++np;
+      if (best_ms < 0.0 || per < best_ms) {
+        best_ms = per;
+        best = nvc_shade_plan{v, c};
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) {
+    h->shade_variant = keep_v;
+    h->shade_ctas_per_sm = keep_c;
+    return cuda_fail(h, err, "autotune");
+  }
+  h->shade_variant = best.variant;
+  h->shade_ctas_per_sm = best.ctas_per_sm;
+  if (chosen) *chosen = best;
+  if (n_points) *n_points = np;
+  return NVC_OK;
+}
+
 nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant) {
   if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
   if (variant < 0 || variant >= kShadeVariants)
@@ -1099,6 +1184,38 @@ nvc_status nvc_sample_clustered(const nvc_scene* scene, const nvc_clusters* clus
   NVC_CUDA(nullptr, launch_sample_clustered(scene, clusters, vis, pos, nrm, n, pixel_offset, seed,
                                             frame, view, light, weight, estimate, sms,
                                             (cudaStream_t)stream));
+  return NVC_OK;
+}
+
+nvc_status nvc_temporal_merge(const nvc_scene* scene, const float* pos, const float* nrm,
+                              int64_t n, int64_t pixel_offset, uint64_t seed, uint32_t frame,
+                              uint32_t view, const int32_t* cur_light, const float* cur_W,
+                              const int32_t* prev_light, const float* prev_W,
+                              const int32_t* prev_M, int32_t* light, float* W, int32_t* M,
+                              float* estimate, void* stream) {
+  NVC_TRY(check_scene(nullptr, scene, 0, kAnyLights));
+  if (n < 0 || pixel_offset < 0 || pixel_offset + n > ((int64_t)1 << 32))
+    return fail(nullptr, NVC_ERR_INVALID_ARG, "n or pixel ids out of range");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(nullptr, pos, "pos"));
+  NVC_TRY(check_ptr(nullptr, nrm, "nrm"));
+  NVC_TRY(check_ptr(nullptr, cur_light, "cur_light"));
+  NVC_TRY(check_ptr(nullptr, cur_W, "cur_W"));
+  if ((prev_light == nullptr) != (prev_W == nullptr) || (prev_light == nullptr) != (prev_M == nullptr))
+    return fail(nullptr, NVC_ERR_INVALID_ARG, "prev_light, prev_W and prev_M go together");
+  if (prev_light) {
+    NVC_TRY(check_ptr(nullptr, prev_light, "prev_light"));
+    NVC_TRY(check_ptr(nullptr, prev_W, "prev_W"));
+    NVC_TRY(check_ptr(nullptr, prev_M, "prev_M"));
+  }
+  if (!light && !W && !M && !estimate) return fail(nullptr, NVC_ERR_INVALID_ARG, "no output");
+  if (sizeof(float) * (4 * (size_t)scene->n_spheres + 6 * (size_t)scene->n_boxes) > 227 * 1024)
+    return fail(nullptr, NVC_ERR_UNSUPPORTED, "too many occluders for shared memory");
+  int sms = 0;
+  NVC_CUDA(nullptr, current_sms(&sms));
+  NVC_CUDA(nullptr, launch_temporal_merge(scene, pos, nrm, n, pixel_offset, seed, frame, view,
+                                          cur_light, cur_W, prev_light, prev_W, prev_M, light, W, M,
+                                          estimate, sms, (cudaStream_t)stream));
   return NVC_OK;
 }
 

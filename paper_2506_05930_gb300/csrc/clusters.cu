@@ -141,13 +141,21 @@ __device__ __forceinline__ int cluster_reservoir(const float (&w)[kMaxClusters],
   return sel;
 }
 
+// Lights per shared-memory tile of the tiled step 1 (16 KB).
+constexpr int kLightTile = 1024;
+
 // Shared-memory layout: [the lights in cluster-table order, I / pi in .w
-// (kSmemLights only)] [spheres] [offsets k + 1, as float4 slots] [boxes].
-// With the lights in table order the members of cluster y are the
-// contiguous slots offsets[y] .. offsets[y + 1] - 1.
+// (kSmemLights: all of them; kTiled: one tile of kLightTile)] [spheres]
+// [offsets k + 1, as float4 slots] [boxes].  With the lights in table order
+// the members of cluster y are the contiguous slots offsets[y] ..
+// offsets[y + 1] - 1.
 // kSum: first-step weights max(v, 0.001) * c_hat (else max(v, 0.001) alone,
 // and no light loop).
-template <bool kSmemLights, bool kSum>
+// kTiled (with kSum, for light sets too large to stage whole): the CTA's
+// threads walk the table in tiles of kLightTile lights staged together in
+// shared memory, each thread carrying its pixel's running cluster sum across
+// tiles -- the same additions in the same order as the whole-set loop.
+template <bool kSmemLights, bool kSum, bool kTiled = false>
 __global__ void __launch_bounds__(1024) sample_clustered_kernel(
     const float* __restrict__ lights, int n_lights, const float* __restrict__ spheres, int n_sph,
     const float* __restrict__ boxes, int n_box, const int32_t* __restrict__ off,
@@ -157,25 +165,33 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
     int32_t* __restrict__ light_out, float* __restrict__ weight_out, float* __restrict__ estimate,
     bool vis_vec4) {
   extern __shared__ float4 s_scene4[];
-  const int n_lt_s = kSmemLights ? n_lights : 0;
+  const int n_lt_s = kSmemLights ? n_lights : kTiled ? kLightTile : 0;
   float4* s_lt = s_scene4;
   float4* s_sph = s_lt + n_lt_s;
   int32_t* s_off = reinterpret_cast<int32_t*>(s_sph + n_sph);
   float* s_box = reinterpret_cast<float*>(s_sph + n_sph + (kMaxClusters + 4) / 4);
-  for (int e = threadIdx.x; e < n_lt_s; e += blockDim.x) {
-    float4 l = reinterpret_cast<const float4*>(lights)[mem[e]];
-    l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
-    s_lt[e] = l;
+  if (kSmemLights) {
+    for (int e = threadIdx.x; e < n_lt_s; e += blockDim.x) {
+      float4 l = reinterpret_cast<const float4*>(lights)[mem[e]];
+      l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+      s_lt[e] = l;
+    }
   }
   for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
     s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
   for (int e = threadIdx.x; e <= k; e += blockDim.x) s_off[e] = off[e];
   for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
   __syncthreads();
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
-    const float nx = nrm[3 * p], ny = nrm[3 * p + 1], nz = nrm[3 * p + 2];
+  // the CTA walks its pixel batches together (the tiled step 1 has block
+  // barriers); a thread past the end takes part in them and writes nothing
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = base + threadIdx.x;
+    const bool live = p < n;
+    if (!kTiled && !live) continue;
+    const int64_t pl = live ? p : 0;
+    const float px = pos[3 * pl], py = pos[3 * pl + 1], pz = pos[3 * pl + 2];
+    const float nx = nrm[3 * pl], ny = nrm[3 * pl + 1], nz = nrm[3 * pl + 2];
     const uint32_t pixel = (uint32_t)(pixel_offset + p);
     // step 1: the clusters' weights, then the reservoir over them.  The
     // cluster loop stays a loop (one copy of the member loop in the code, so
@@ -183,8 +199,43 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
     // stay in registers through compare-and-select writes.
     float w[kMaxClusters];
     float wsum = 0.0f;
-    const float* vrow = vis + p * k;
-    if (!kSum) {
+    const float* vrow = vis + pl * k;
+    if (kTiled) {
+#pragma unroll
+      for (int t = 0; t < kMaxClusters; ++t) w[t] = 0.0f;
+      int y = 0;
+      float ch = 0.0f;
+      // cluster y is complete: its weight, in cluster order
+      auto finish = [&]() {
+        const float wy = __fmul_rn(fmaxf(__ldg(vrow + y), bits_f(kVisClampBits)), ch);
+#pragma unroll
+        for (int t = 0; t < kMaxClusters; ++t)
+          if (t == y) w[t] = wy;
+        wsum = __fadd_rn(wsum, wy);
+        ch = 0.0f;
+        ++y;
+      };
+      for (int c0 = 0; c0 < n_lights; c0 += kLightTile) {
+        const int cn = n_lights - c0 < kLightTile ? n_lights - c0 : kLightTile;
+        __syncthreads();   // the previous tile is read by every thread
+        for (int e = threadIdx.x; e < cn; e += blockDim.x) {
+          float4 l = __ldg(reinterpret_cast<const float4*>(lights) + mem[c0 + e]);
+          l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+          s_lt[e] = l;
+        }
+        __syncthreads();
+        if (live) {
+#pragma unroll 4
+          for (int i = 0; i < cn; ++i) {
+            while (c0 + i >= s_off[y + 1]) finish();
+            const float4 l = s_lt[i];
+            ch = __fadd_rn(ch, contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w));
+          }
+        }
+      }
+      if (live)
+        while (y < k) finish();
+    } else if (!kSum) {
       // visibility weights: no member loop, so the row's loads are issued
       // together (16-byte loads when the row allows) into the weights'
       // registers, and the short cluster loop is unrolled
@@ -231,6 +282,7 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
         wsum = __fadd_rn(wsum, wy);
       }
     }
+    if (!live) continue;   // the last batch: nothing to pick, no barrier follows
     const int y = cluster_reservoir(w, k, pixel, frame, view, k0, k1);
     int sel_light = -1;
     float W = 0.0f, cx = 0.0f;
@@ -288,7 +340,99 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
   }
 }
 
+// ---- temporal resampling of the cache's reservoirs (ReSTIR, Section 4.2) -----
+constexpr uint32_t kTagTemporal = 6;   // the pick between current and previous reservoir
+constexpr int kTemporalMCap = 20;      // the previous reservoir counts at most 20x the new one
+
+// p_hat(y) = c_y at the pixel, the correctly rounded float32 contribution
+// (0 for y outside [0, n_lights)).
+__device__ __forceinline__ float target_of(const float* lights, int n_lights, int y, float px,
+                                           float py, float pz, float nx, float ny, float nz) {
+  if (y < 0 || y >= n_lights) return 0.0f;
+  const float4 l = __ldg(reinterpret_cast<const float4*>(lights) + y);
+  return contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, __fmul_rn(l.w, bits_f(kInvPiBits)));
+}
+
+__global__ void __launch_bounds__(256) temporal_merge_kernel(
+    const float* __restrict__ lights, int n_lights, const float* __restrict__ spheres, int n_sph,
+    const float* __restrict__ boxes, int n_box, const float* __restrict__ pos,
+    const float* __restrict__ nrm, int64_t n, int64_t pixel_offset, uint32_t k0, uint32_t k1,
+    uint32_t frame, uint32_t view, const int32_t* __restrict__ cur_light,
+    const float* __restrict__ cur_W, const int32_t* __restrict__ prev_light,
+    const float* __restrict__ prev_W, const int32_t* __restrict__ prev_M,
+    int32_t* __restrict__ light_out, float* __restrict__ W_out, int32_t* __restrict__ M_out,
+    float* __restrict__ estimate) {
+  extern __shared__ float s_occ[];
+  float4* s_sph = reinterpret_cast<float4*>(s_occ);
+  float* s_box = s_occ + 4 * n_sph;
+  if (estimate) {
+    for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
+      s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
+    for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
+    __syncthreads();
+  }
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
+    const float nx = nrm[3 * p], ny = nrm[3 * p + 1], nz = nrm[3 * p + 2];
+    int yc = cur_light[p];
+    int yp = prev_light ? prev_light[p] : -1;
+    int Mp = prev_M ? prev_M[p] : 0;
+    Mp = Mp < 0 ? 0 : (Mp > kTemporalMCap ? kTemporalMCap : Mp);   // min(M_p, 20 M_c), M_c = 1
+    if (yc >= n_lights) yc = -1;
+    if (yp >= n_lights || Mp == 0) yp = -1;
+    const float pc = target_of(lights, n_lights, yc, px, py, pz, nx, ny, nz);
+    const float pp = target_of(lights, n_lights, yp, px, py, pz, nx, ny, nz);
+    float w[2];
+    w[0] = yc >= 0 ? __fmul_rn(__fmul_rn(1.0f, pc), cur_W[p]) : 0.0f;
+    w[1] = yp >= 0 ? __fmul_rn(__fmul_rn((float)Mp, pp), prev_W[p]) : 0.0f;
+    const uint4 r4 = philox4x32_10(make_uint4((uint32_t)(pixel_offset + p), frame, view, kTagTemporal),
+                                   k0, k1);
+    const uint32_t r[2] = {r4.x, r4.y};
+    const int j = integer_reservoir(w, 2, r);
+    const int y = j == 0 ? yc : j == 1 ? yp : -1;
+    const int M = 1 + Mp;
+    float W = 0.0f;
+    if (y >= 0) W = __fdiv_rn(__fadd_rn(w[0], w[1]), __fmul_rn((float)M, j == 0 ? pc : pp));
+    if (light_out) light_out[p] = y;
+    if (W_out) W_out[p] = W;
+    if (M_out) M_out[p] = M;
+    if (estimate) {
+      float e = 0.0f;
+      if (y >= 0) {
+        const float4 l = __ldg(reinterpret_cast<const float4*>(lights) + y);
+        if (!segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box))
+          e = __fmul_rn(j == 0 ? pc : pp, W);
+      }
+      estimate[p] = e;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_temporal_merge(const nvc_scene* sc, const float* pos, const float* nrm,
+                                  int64_t n, int64_t pixel_offset, uint64_t seed, uint32_t frame,
+                                  uint32_t view, const int32_t* cur_light, const float* cur_W,
+                                  const int32_t* prev_light, const float* prev_W,
+                                  const int32_t* prev_M, int32_t* light, float* W, int32_t* M,
+                                  float* estimate, int num_sms, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const size_t smem = estimate ? sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes)
+                               : 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(temporal_merge_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t want = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms * 8;
+  temporal_merge_kernel<<<(unsigned)(want < cap ? want : cap), 256, smem, s>>>(
+      sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes, pos, nrm, n,
+      pixel_offset, (uint32_t)seed, (uint32_t)(seed >> 32), frame, view, cur_light, cur_W,
+      prev_light, prev_W, prev_M, light, W, M, estimate);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cluster_targets(const nvc_scene* sc, const nvc_clusters* cl, const float* pos,
                                    int64_t n, uint64_t seed, uint32_t frame, float* target,
@@ -312,7 +456,7 @@ size_t sample_clustered_smem(const nvc_scene* sc, const nvc_clusters* cl) {
                      sizeof(float4) * ((kMaxClusters + 4) / 4);
   if (cl->weights == NVC_CLUSTER_WEIGHT_VISIBILITY) return occ;   // no light loop
   const size_t lt = sizeof(float) * 4 * (size_t)sc->n_lights;
-  return occ + lt <= kSmemOptin ? occ + lt : occ;
+  return occ + lt <= kSmemOptin ? occ + lt : occ + sizeof(float4) * kLightTile;
 }
 
 cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl, const float* vis,
@@ -322,12 +466,13 @@ cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl,
                                     int num_sms, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const size_t smem = sample_clustered_smem(sc, cl);
-  const bool lights_on_chip = smem > sizeof(float) * (4 * (size_t)sc->n_spheres +
-                                                      6 * (size_t)sc->n_boxes) +
-                                         sizeof(float4) * ((kMaxClusters + 4) / 4);
+  const bool lights_on_chip =
+      sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes) +
+          sizeof(float4) * ((kMaxClusters + 4) / 4) + sizeof(float) * 4 * (size_t)sc->n_lights <=
+      kSmemOptin;
   auto kern = cl->weights == NVC_CLUSTER_WEIGHT_VISIBILITY ? sample_clustered_kernel<false, false>
               : lights_on_chip                             ? sample_clustered_kernel<true, true>
-                                                           : sample_clustered_kernel<false, true>;
+                                                           : sample_clustered_kernel<false, true, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // The staged lights are shared by a CTA's threads: take the smallest CTA

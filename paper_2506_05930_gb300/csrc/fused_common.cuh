@@ -75,6 +75,9 @@ struct FusedArgs {
   // summed SM cycles of [0] encode, [1] MLP, [2] sampler, [3] whole tile
   // loop, over every group; NULL in ordinary launches
   unsigned long long* phase_cycles;
+  // resident CTAs per SM the launch may use (the autotuner's occupancy
+  // knob); 0 = as many as fit
+  int max_ctas_per_sm;
 };
 
 // ---- the encode's chunks of CH features -------------------------------------

@@ -387,7 +387,8 @@ cudaError_t launch_multi_typed(FusedArgs a, size_t smem_needed, int num_sms, cud
   }
   if (occ < 1 || occ > max_ctas) return cudaErrorInvalidConfiguration;
   const int64_t groups = (a.n_tiles + TPC - 1) / TPC;
-  const int64_t cap = (int64_t)occ * num_sms;
+  const int per_sm = a.max_ctas_per_sm > 0 && a.max_ctas_per_sm < occ ? a.max_ctas_per_sm : occ;
+  const int64_t cap = (int64_t)per_sm * num_sms;
   const int grid = (int)(groups < cap ? groups : cap);
   kern<<<grid, TPC * kTileM, smem, s>>>(a);
   return cudaGetLastError();

@@ -1012,7 +1012,8 @@ cudaError_t launch_pair_typed(const FusedArgs& a, size_t smem_needed, int num_sm
   }
   if (occ > max_ctas) return cudaErrorInvalidConfiguration;
   const int64_t n_tiles = a.n_tiles;
-  const int64_t cap = (int64_t)occ * num_sms;
+  const int per_sm = a.max_ctas_per_sm > 0 && a.max_ctas_per_sm < occ ? a.max_ctas_per_sm : occ;
+  const int64_t cap = (int64_t)per_sm * num_sms;
   const int grid = (int)(n_tiles < cap ? n_tiles : cap);
   kern<<<grid, 2 * kTileM, smem, s>>>(a);
   return cudaGetLastError();
@@ -1037,7 +1038,8 @@ cudaError_t launch_typed(const FusedArgs& a, size_t smem_needed, int num_sms, cu
   }
   if (occ > max_ctas) return cudaErrorInvalidConfiguration;
   const int64_t n_tiles = a.n_tiles;
-  const int64_t cap = (int64_t)occ * num_sms;
+  const int per_sm = a.max_ctas_per_sm > 0 && a.max_ctas_per_sm < occ ? a.max_ctas_per_sm : occ;
+  const int64_t cap = (int64_t)per_sm * num_sms;
   const int grid = (int)(n_tiles < cap ? n_tiles : cap);
   kern<<<grid, kTileM, smem, s>>>(a);
   return cudaGetLastError();
@@ -1087,7 +1089,8 @@ cudaError_t launch_ws_typed(const FusedArgs& a, size_t smem_needed, int num_sms,
   }
   if (occ > max_ctas) return cudaErrorInvalidConfiguration;
   const int64_t n_tiles = a.n_tiles;
-  const int64_t cap = (int64_t)occ * num_sms;
+  const int per_sm = a.max_ctas_per_sm > 0 && a.max_ctas_per_sm < occ ? a.max_ctas_per_sm : occ;
+  const int64_t cap = (int64_t)per_sm * num_sms;
   const int grid = (int)(n_tiles < cap ? n_tiles : cap);
   kern<<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
@@ -1226,6 +1229,7 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
   a.status = h->status;
   a.fp8_scales = h->fp8_scales;
   a.phase_cycles = phase_cycles;
+  a.max_ctas_per_sm = h->shade_ctas_per_sm;
   if (h->cfg.precision == NVC_PREC_FP8) {
     const size_t smem8 = fused_smem(h, p, &a);
     switch (h->F) {

@@ -207,6 +207,9 @@ struct nvc_handle {
   // variant (-1: the shading variant), set by nvc_autotune_infer
   int shade_variant = 0;
   int infer_variant = -1;
+  // resident CTAs per SM of the fused shading launches (0: as many as fit),
+  // the occupancy point of nvc_set_shade_plan / nvc_autotune_shade_plan
+  int shade_ctas_per_sm = 0;
   // world-space share of the training positions (nvc_set_training_placement;
   // -1: the default split, ceil(B / 2) world-space)
   int64_t n_world = -1;
@@ -339,6 +342,13 @@ cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl,
                                     int64_t pixel_offset, uint64_t seed, uint32_t frame,
                                     uint32_t view, int32_t* light, float* weight, float* estimate,
                                     int num_sms, cudaStream_t s);
+// Temporal resampling of per-pixel reservoirs (clusters.cu).
+cudaError_t launch_temporal_merge(const nvc_scene* sc, const float* pos, const float* nrm,
+                                  int64_t n, int64_t pixel_offset, uint64_t seed, uint32_t frame,
+                                  uint32_t view, const int32_t* cur_light, const float* cur_W,
+                                  const int32_t* prev_light, const float* prev_W,
+                                  const int32_t* prev_M, int32_t* light, float* W, int32_t* M,
+                                  float* estimate, int num_sms, cudaStream_t s);
 void kmeans_host(const float* lights, int n, const int32_t* init, int k, int iters,
                  int32_t* assign, double* centroids_out);
 // Training positions and their shadow-ray targets in one launch (the same

@@ -26,7 +26,8 @@ def main():
     ap.add_argument("--variant", type=int, default=7, help="fused shading variant (0-7)")
     ap.add_argument("--pretrain", type=int, default=5)
     ap.add_argument("--frames", type=int, default=3)
-    ap.add_argument("--table16", action="store_true", help="half-precision table features")
+    ap.add_argument("--table-precision", default=None, choices=["fp16", "fp32"],
+                    help="table features of the fused inference (default: the workload's)")
     args = ap.parse_args()
 
     cfg = S.config_by_name("frame_1080p")
@@ -39,8 +40,8 @@ def main():
                     torch.empty(n, device="cuda"), torch.empty(n, device="cuda"))
     cache = nvc.VisibilityCache(cfg)
     cache.set_params(S.init_params(cfg, seed=0))
-    if args.table16:
-        nvc.nvc_set_table_precision(cache.handle, "fp16")
+    if args.table_precision:
+        nvc.nvc_set_table_precision(cache.handle, args.table_precision)
     nvc.nvc_set_shade_variant(cache.handle, args.variant)
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
     for f in range(args.pretrain):

@@ -253,6 +253,28 @@ def nvc_set_table_precision(h, precision: str, stream=None):
     check(lib.nvc_set_table_precision(h, _lib.PRECISIONS[precision], _stream(stream)), h)
 
 
+def nvc_set_shade_plan(h, variant: int, ctas_per_sm: int = 0):
+    check(lib.nvc_set_shade_plan(h, ctypes.byref(_lib.NvcShadePlan(int(variant), int(ctas_per_sm)))), h)
+
+
+def nvc_autotune_shade_plan(h, scene: Scene, pos, nrm, idx=None, pdf=None, wsum=None,
+                            radiance=None, reps=5, stream=None):
+    """Times every point (variant, CTAs per SM) of the fused shading
+    kernel's tuning space on these pixels and keeps the fastest.  Returns
+    ((variant, ctas_per_sm) chosen, [((variant, ctas_per_sm), ms), ...])."""
+    cap = 64
+    chosen = _lib.NvcShadePlan()
+    pts = (_lib.NvcShadePlan * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = ctypes.c_int32()
+    check(lib.nvc_autotune_shade_plan(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0],
+                                      _ptr(idx, torch.int32, "idx"), _ptr(pdf), _ptr(wsum),
+                                      _ptr(radiance), int(reps), ctypes.byref(chosen), pts, ms, cap,
+                                      ctypes.byref(n), _stream(stream)), h)
+    tried = [((pts[i].variant, pts[i].ctas_per_sm), ms[i]) for i in range(min(n.value, cap))]
+    return (chosen.variant, chosen.ctas_per_sm), tried
+
+
 def nvc_set_shade_variant(h, variant: int):
     check(lib.nvc_set_shade_variant(h, int(variant)), h)
 
@@ -489,6 +511,22 @@ def nvc_sample_clustered(scene: Scene, clusters: Clusters, vis, pos, nrm, seed, 
                                    _ptr(estimate, name="estimate"), _stream(stream)))
 
 
+def nvc_temporal_merge(scene: Scene, pos, nrm, cur_light, cur_W, prev_light=None, prev_W=None,
+                       prev_M=None, seed=0, frame=0, view=0, pixel_offset=0, light=None, W=None,
+                       M=None, estimate=None, stream=None):
+    """Temporal resampling of the frame's cache reservoir (cur_light, cur_W)
+    with the previous frame's (prev_light, prev_W, prev_M; None: every pixel
+    disoccluded) into (light, W, M) and the one-shadow-ray estimate."""
+    check(lib.nvc_temporal_merge(scene.ref, _ptr(pos, name="pos"), _ptr(nrm, name="nrm"),
+                                 pos.shape[0], int(pixel_offset), int(seed), int(frame), int(view),
+                                 _ptr(cur_light, torch.int32, "cur_light"), _ptr(cur_W, name="cur_W"),
+                                 _ptr(prev_light, torch.int32, "prev_light"),
+                                 _ptr(prev_W, name="prev_W"), _ptr(prev_M, torch.int32, "prev_M"),
+                                 _ptr(light, torch.int32, "light"), _ptr(W, name="W"),
+                                 _ptr(M, torch.int32, "M"), _ptr(estimate, name="estimate"),
+                                 _stream(stream)))
+
+
 def nvc_infer_noalloc(cfg: NvcConfig, params, pos, vis, stream=None):
     """nvc_infer for callers that cannot allocate GPU memory: parameters come
     from the caller, the library's fixed scratch array holds the encoded
@@ -542,8 +580,9 @@ class VisibilityCache:
         self.handle = nvc_create(self.cfg)
         self.L = self.cfg.n_outputs
         self.din = self.cfg.n_levels * self.cfg.n_features
+        # a half-precision feature copy serves the tensor-core inference only
         table_precision = kw.get("table_precision", getattr(cfg, "table_precision", "fp32"))
-        if table_precision != "fp32":
+        if table_precision != "fp32" and self.cfg.precision != _lib.PRECISIONS["fp32"]:
             nvc_set_table_precision(self.handle, table_precision)
 
     def close(self):

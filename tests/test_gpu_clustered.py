@@ -89,15 +89,18 @@ def _estimate_ref(sc, pos, nrm, light, W):
 
 @pytest.mark.parametrize("n_lights,k,empty,weights",
                          [(300, 32, None, "sum"), (300, 9, 3, "sum"), (15000, 32, None, "sum"),
+                          (59000, 32, None, "sum"), (59000, 13, 5, "sum"),
                           (300, 32, None, "visibility"), (300, 9, 3, "visibility"),
                           (15000, 32, 7, "visibility")])
 def test_sample_clustered_bitexact(n_lights, k, empty, weights):
     """Light and contribution weight bit-exact against the oracle, for both
-    first-step weights; the 15,000-light cases hold more lights than shared
-    memory (lights read from global)."""
+    first-step weights.  The 15,000- and 59,000-light cases (the paper's
+    many-lights scale) hold more lights than shared memory: the summed
+    weights walk them in staged tiles, with clusters spanning tile edges."""
     sc = S.scene_many_lights(seed=4, n_lights=n_lights, n_groups=40)
     cl, off, mem = clustering(sc, k, empty=empty, iters=5, weights=weights)
-    gb = S.gbuffer_heightfield(seed=4, width=53, height=37)
+    w, h = (53, 37) if n_lights < 20000 else (23, 11)    # the oracle's [pixels, lights] arrays
+    gb = S.gbuffer_heightfield(seed=4, width=w, height=h)
     scene = nvc.Scene.from_synth(sc)
     vis = _vis(5, gb.n, k)
     light = torch.full((gb.n,), -7, dtype=torch.int32, device="cuda")

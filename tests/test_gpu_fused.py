@@ -437,3 +437,41 @@ def test_fp16_table_copy_follows_the_master():
     assert not np.array_equal(host(plain.infer(pos)), vis_trained)
     for c in (cache, fresh, plain):
         c.close()
+
+
+@pytest.mark.parametrize("name,L", [("frame_1080p", 32), ("multiview", 128)])
+def test_every_point_of_the_tuning_space_shades_identically(name, L):
+    """nvc_autotune_shade_plan searches kernel layout (tile streams per CTA,
+    levels split across threads, warp specialisation) x resident CTAs per
+    SM.  Every point it tries makes the monolithic kernel's picks; all but
+    the two-threads-per-pixel layout (whose sums are two half-sums) give
+    bit-identical pdf, sum and Neural DI too."""
+    cfg = S.config_by_name(name).with_(batch_positions=256)
+    cache, p = make(cfg, seed=2, table_scale=0.5)
+    if L == 32:
+        sc = S.scene_heightfield(seed=8, n_lights=32, n_spheres=8, n_boxes=8)
+        gb = S.gbuffer_heightfield(seed=8, width=160, height=97)
+    else:
+        sc = S.scene_unit_cube(seed=0, n_lights=128)
+        gb = S.gbuffer_points(2, 128, 81)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    chosen, tried = nvc.nvc_autotune_shade_plan(cache.handle, scene, pos, nrm, reps=2)
+    points = [pt for pt, _ in tried]
+    assert chosen in points and len(set(points)) == len(points)
+    variants = {v for v, _ in points}
+    assert variants == ({0, 1, 2, 3, 4, 5, 6, 7} if L == 32 else {0, 5})
+    assert {c for _, c in points} == {0, 1, 2, 3}
+    nvc.nvc_set_shade_plan(cache.handle, 0, 0)
+    ref = cache.shade(scene, pos, nrm, seed=3, frame=1, fused=True)
+    for v, c in points:
+        nvc.nvc_set_shade_plan(cache.handle, v, c)
+        out = cache.shade(scene, pos, nrm, seed=3, frame=1, fused=True)
+        assert torch.equal(out["idx"], ref["idx"]), (v, c)
+        for k in ("pdf", "wsum", "radiance"):
+            if v == PAIR_VARIANT:
+                np.testing.assert_allclose(host(out[k]), host(ref[k]), rtol=2 * (L - 1) * 2.0 ** -24,
+                                           atol=1e-30)
+            else:
+                assert torch.equal(out[k], ref[k]), (v, c, k)
+    cache.close()

@@ -164,6 +164,13 @@ def test_measurement_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert lib.nvc_set_training_data_fused(None, 1) == E
     assert lib.nvc_training_batch(None, None, None, None) == E
     assert lib.nvc_set_table_precision(None, 1, None) == E
+    assert lib.nvc_temporal_merge(None, None, None, 10, 0, 0, 0, 0, None, None, None, None, None,
+                                  None, None, None, None, None) == E
+    sc = _lib.NvcScene()
+    sc.n_lights, sc.lights = 4, fake
+    # a previous reservoir given in part
+    assert lib.nvc_temporal_merge(ctypes.byref(sc), fake, fake, 10, 0, 0, 0, 0, fake, fake, fake,
+                                  None, None, fake, None, None, None, None) == E
 
 
 def test_noalloc_wrapper_checks_shapes_before_launching(lib):
@@ -187,3 +194,12 @@ def test_noalloc_wrapper_checks_shapes_before_launching(lib):
     # right shapes but host tensors: refused as not CUDA, still before the call
     with pytest.raises(ValueError):
         nvc.nvc_infer_noalloc(c, good["params"], good["pos"], good["vis"])
+
+
+def test_shade_plan_entry_points_reject_bad_arguments_without_a_gpu(lib):
+    from paper_2506_05930_gb300 import _lib
+    E = _lib.NVC_ERR_INVALID_ARG
+    plan = _lib.NvcShadePlan(0, 0)
+    assert lib.nvc_set_shade_plan(None, ctypes.byref(plan)) == E
+    assert lib.nvc_autotune_shade_plan(None, None, None, None, 10, None, None, None, None, 1, None,
+                                       None, None, 0, None, None) == E

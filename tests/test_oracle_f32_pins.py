@@ -327,7 +327,7 @@ def test_fp16_table_features_are_the_rounded_table_used_exactly():
     same result as the float32-feature oracle run on a table already holding
     those rounded values, and a different one from the unrounded table."""
     from helpers import scaled_params
-    cfg = S.config_by_name("tiny_fp32").with_(table_precision="fp16")
+    cfg = S.config_by_name("tiny_fp32").with_(precision="fp16", table_precision="fp16")
     p = scaled_params(cfg, seed=4, table_scale=0.3)
     tn = cfg.n_levels * cfg.table_size * cfg.n_features
     q = p.copy()
@@ -340,3 +340,5 @@ def test_fp16_table_features_are_the_rounded_table_used_exactly():
     assert np.array_equal(v16, O.infer(cfg.with_(table_precision="fp32"), q, pos))
     v32 = O.infer(cfg.with_(table_precision="fp32"), p, pos)
     assert 0 < np.max(np.abs(v16 - v32)) < 1e-2
+    # float32 inference reads the float32 master whatever the copy's precision
+    assert np.array_equal(O.infer(cfg.with_(precision="fp32"), p, pos), v32)

@@ -778,3 +778,81 @@ def test_ris_weight_closed_forms():
     assert W1 == pytest.approx(2 * W0, rel=1e-6)
     # mean 0.625, p = 0.125: W0 = 0.625 / (0.125 * 1.0)
     assert W0 == pytest.approx(5.0, rel=1e-6)
+
+
+# ------------------------------------------- temporal resampling (ReSTIR) --
+
+def _merge_expectation(c32, V, v32, prev_M, drop_inverse_M=False):
+    """E[f(y) W] of one pixel's temporal merge, enumerated exactly over the
+    current reservoir's light i, the previous reservoir's light j (both from
+    the cache's sampler, independent) and the integer reservoir's pick."""
+    w = O.light_weights_f32(v32[None], c32[None])[0]
+    P = O.selection_law(w[None])[0]
+    wsum = np.float32(np.sum(w.astype(np.float64)))
+    L = len(c32)
+    E = 0.0
+    for i in range(L):
+        if P[i] == 0:
+            continue
+        Wi = np.float32(1.0) / np.float32(w[i] / wsum)
+        for j in range(L):
+            if P[j] == 0 and prev_M > 0:
+                continue
+            Wj = np.float32(1.0) / np.float32(w[j] / wsum) if P[j] > 0 else np.float32(0)
+            pj = P[j] if prev_M > 0 else (1.0 if j == 0 else 0.0)
+            if pj == 0:
+                continue
+            args = (c32[None], np.array([i]), np.array([Wi]), np.array([j]), np.array([Wj]),
+                    np.array([prev_M]), np.array([0]))
+            # r = 0 keeps the last candidate with q > 0; r = 2^32 - 1 the first
+            wc = np.float32(np.float32(1.0) * c32[i]) * Wi
+            wp = np.float32(np.float32(min(prev_M, 20)) * c32[j]) * Wj if prev_M > 0 else np.float32(0)
+            q = O.quantize_weights(np.array([[wc, wp]], np.float32))[0].astype(np.float64)
+            for pick_last, prob in ((True, q[1] / q.sum()), (False, q[0] / q.sum())):
+                if prob == 0:
+                    continue
+                import oracle.philox as ph
+                old = ph.stream_words
+                ph.stream_words = lambda ids, f, v, tag, m, s: np.full(
+                    (len(ids), m), 0 if pick_last else (1 << 32) - 1, np.uint64)
+                try:
+                    y, W, M = O.temporal_merge(*args[:6], args[6], 0, 0, 0)
+                finally:
+                    ph.stream_words = old
+                Wy = float(W[0]) * (float(M[0]) if drop_inverse_M else 1.0)
+                E += P[i] * pj * prob * (V[y[0]] * float(c32[y[0]]) * Wy if y[0] >= 0 else 0.0)
+    return E
+
+
+@pytest.mark.parametrize("prev_M", [0, 1, 3, 40])
+def test_temporal_merge_is_unbiased_by_exact_enumeration(prev_M):
+    """Temporal resampling of the cache's reservoirs (Sections 3.1, 4.2):
+    with the current and the previous frame's reservoir both unbiased for
+    the pixel, E[V(y) c(y) W] over every (current light, previous light,
+    pick) equals the all-lights DI sum V_i c_i, whatever the previous
+    reservoir's confidence M (0 = disoccluded, clamped at 20); dropping the
+    1/M normalisation, or the previous reservoir's weight, breaks it."""
+    rng = np.random.default_rng(11 + prev_M)
+    c32 = rng.uniform(0.1, 3.0, 6).astype(np.float32)
+    c32[2] = 0.0                                   # a back-facing light
+    V = np.array([1, 0, 1, 1, 0, 1], np.float64)   # two blocked lights
+    v32 = np.array([0.9, 0.05, 0.5, 0.8, 0.0, 0.3], np.float32)
+    exact = float(np.sum(V * c32.astype(np.float64)))
+    E = _merge_expectation(c32, V, v32, prev_M)
+    assert abs(E - exact) <= 1e-5 * exact, (E, exact)
+    if prev_M > 0:
+        wrong = _merge_expectation(c32, V, v32, prev_M, drop_inverse_M=True)
+        assert abs(wrong - exact) > 0.5 * exact
+
+
+def test_temporal_merge_special_cases():
+    """A disoccluded pixel keeps the cache's sample with its weight; a pixel
+    without any sample stays empty; the confidence adds up and is clamped."""
+    c32 = np.array([[1.0, 2.0, 0.0]], np.float32)
+    ids = np.array([7])
+    y, W, M = O.temporal_merge(c32, [1], [np.float32(1.5)], [0], [np.float32(2.0)], [0], ids, 3, 1, 0)
+    assert y[0] == 1 and W[0] == np.float32(1.5) and M[0] == 1
+    y, W, M = O.temporal_merge(c32, [-1], [np.float32(0)], [-1], [np.float32(0)], [5], ids, 3, 1, 0)
+    assert y[0] == -1 and W[0] == 0 and M[0] == 6
+    y, W, M = O.temporal_merge(c32, [0], [np.float32(1)], [1], [np.float32(1)], [100], ids, 3, 1, 0)
+    assert M[0] == 21 and y[0] in (0, 1) and W[0] > 0
