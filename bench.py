@@ -245,7 +245,7 @@ def clustered_alu_ops(n_lights, k, n_pixels):
 
 # Per-launch DRAM traffic of the dominant kernel from the ncu capture named in
 # profiles/ (None once the kernel has changed since that capture).
-KERNEL_TRAFFIC = {"fused_shade": 109.36e6, "adam": 428.34e6,
+KERNEL_TRAFFIC = {"fused_shade": 82.50e6, "adam": None,
                   # 1080p launch with the shadow ray (light, W and estimate written)
                   "sample_clustered": 336.47e6}
 
