@@ -1209,7 +1209,7 @@ nvc_status nvc_temporal_merge(const nvc_scene* scene, const float* pos, const fl
     NVC_TRY(check_ptr(nullptr, prev_M, "prev_M"));
   }
   if (!light && !W && !M && !estimate) return fail(nullptr, NVC_ERR_INVALID_ARG, "no output");
-  if (sizeof(float) * (4 * (size_t)scene->n_spheres + 6 * (size_t)scene->n_boxes) > 227 * 1024)
+  if (occluder_bytes(scene->n_spheres, scene->n_boxes) > 227 * 1024)
     return fail(nullptr, NVC_ERR_UNSUPPORTED, "too many occluders for shared memory");
   int sms = 0;
   NVC_CUDA(nullptr, current_sms(&sms));

@@ -52,12 +52,9 @@ __global__ void __launch_bounds__(256) cluster_targets_kernel(
     const float* __restrict__ boxes, int n_box, const int32_t* __restrict__ off,
     const int32_t* __restrict__ mem, int k, const float* __restrict__ pos, int64_t n,
     uint32_t k0, uint32_t k1, uint32_t frame, float* __restrict__ target) {
-  extern __shared__ float s_occ[];
-  float4* s_sph = reinterpret_cast<float4*>(s_occ);
-  float* s_box = s_occ + 4 * n_sph;
-  for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
-    s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
-  for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
+  extern __shared__ float4 s_occ[];
+  const Occluders occ =
+      stage_occluders(spheres, n_sph, boxes, n_box, s_occ, threadIdx.x, blockDim.x);
   __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * k) return;
@@ -68,7 +65,7 @@ __global__ void __launch_bounds__(256) cluster_targets_kernel(
     const int x = member_of(off, mem, y, stream_word((uint32_t)b, frame, 0u, kTagCluster, y, k0, k1));
     const float4 l = reinterpret_cast<const float4*>(lights)[x];
     const float px = pos[3 * b], py = pos[3 * b + 1], pz = pos[3 * b + 2];
-    v = segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box) ? 0.0f : 1.0f;
+    v = segment_blocked(px, py, pz, l.x, l.y, l.z, occ) ? 0.0f : 1.0f;
   }
   target[t] = v;
 }
@@ -167,9 +164,10 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
   extern __shared__ float4 s_scene4[];
   const int n_lt_s = kSmemLights ? n_lights : kTiled ? kLightTile : 0;
   float4* s_lt = s_scene4;
-  float4* s_sph = s_lt + n_lt_s;
-  int32_t* s_off = reinterpret_cast<int32_t*>(s_sph + n_sph);
-  float* s_box = reinterpret_cast<float*>(s_sph + n_sph + (kMaxClusters + 4) / 4);
+  int32_t* s_off = reinterpret_cast<int32_t*>(s_lt + n_lt_s);
+  const Occluders occ = stage_occluders(spheres, n_sph, boxes, n_box,
+                                        s_lt + n_lt_s + (kMaxClusters + 4) / 4, threadIdx.x,
+                                        blockDim.x);
   if (kSmemLights) {
     for (int e = threadIdx.x; e < n_lt_s; e += blockDim.x) {
       float4 l = reinterpret_cast<const float4*>(lights)[mem[e]];
@@ -177,10 +175,7 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
       s_lt[e] = l;
     }
   }
-  for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
-    s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
   for (int e = threadIdx.x; e <= k; e += blockDim.x) s_off[e] = off[e];
-  for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
   __syncthreads();
   // the CTA walks its pixel batches together (the tiled step 1 has block
   // barriers); a thread past the end takes part in them and writes nothing
@@ -332,8 +327,7 @@ __global__ void __launch_bounds__(1024) sample_clustered_kernel(
       float e = 0.0f;
       if (sel_light >= 0) {
         const float4 l = reinterpret_cast<const float4*>(lights)[sel_light];
-        if (!segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box))
-          e = __fmul_rn(cx, W);
+        if (!segment_blocked(px, py, pz, l.x, l.y, l.z, occ)) e = __fmul_rn(cx, W);
       }
       estimate[p] = e;
     }
@@ -362,13 +356,10 @@ __global__ void __launch_bounds__(256) temporal_merge_kernel(
     const float* __restrict__ prev_W, const int32_t* __restrict__ prev_M,
     int32_t* __restrict__ light_out, float* __restrict__ W_out, int32_t* __restrict__ M_out,
     float* __restrict__ estimate) {
-  extern __shared__ float s_occ[];
-  float4* s_sph = reinterpret_cast<float4*>(s_occ);
-  float* s_box = s_occ + 4 * n_sph;
+  extern __shared__ float4 s_occ[];
+  Occluders occ = staged_occluders(s_occ, 0, 0);
   if (estimate) {
-    for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
-      s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
-    for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
+    occ = stage_occluders(spheres, n_sph, boxes, n_box, s_occ, threadIdx.x, blockDim.x);
     __syncthreads();
   }
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
@@ -401,8 +392,7 @@ __global__ void __launch_bounds__(256) temporal_merge_kernel(
       float e = 0.0f;
       if (y >= 0) {
         const float4 l = __ldg(reinterpret_cast<const float4*>(lights) + y);
-        if (!segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box))
-          e = __fmul_rn(j == 0 ? pc : pp, W);
+        if (!segment_blocked(px, py, pz, l.x, l.y, l.z, occ)) e = __fmul_rn(j == 0 ? pc : pp, W);
       }
       estimate[p] = e;
     }
@@ -418,8 +408,7 @@ cudaError_t launch_temporal_merge(const nvc_scene* sc, const float* pos, const f
                                   const int32_t* prev_M, int32_t* light, float* W, int32_t* M,
                                   float* estimate, int num_sms, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const size_t smem = estimate ? sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes)
-                               : 0;
+  const size_t smem = estimate ? occluder_bytes(sc->n_spheres, sc->n_boxes) : 0;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(temporal_merge_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -439,7 +428,7 @@ cudaError_t launch_cluster_targets(const nvc_scene* sc, const nvc_clusters* cl, 
                                    cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t total = n * cl->k;
-  const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  const size_t smem = occluder_bytes(sc->n_spheres, sc->n_boxes);
   cluster_targets_kernel<<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
       sc->lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes, cl->offsets, cl->members,
       cl->k, pos, n, (uint32_t)seed, (uint32_t)(seed >> 32), frame, target);
@@ -452,8 +441,8 @@ cudaError_t launch_cluster_targets(const nvc_scene* sc, const nvc_clusters* cl, 
 constexpr size_t kSmemOptin = 227 * 1024;
 
 size_t sample_clustered_smem(const nvc_scene* sc, const nvc_clusters* cl) {
-  const size_t occ = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes) +
-                     sizeof(float4) * ((kMaxClusters + 4) / 4);
+  const size_t occ =
+      occluder_bytes(sc->n_spheres, sc->n_boxes) + sizeof(float4) * ((kMaxClusters + 4) / 4);
   if (cl->weights == NVC_CLUSTER_WEIGHT_VISIBILITY) return occ;   // no light loop
   const size_t lt = sizeof(float) * 4 * (size_t)sc->n_lights;
   return occ + lt <= kSmemOptin ? occ + lt : occ + sizeof(float4) * kLightTile;
@@ -467,8 +456,8 @@ cudaError_t launch_sample_clustered(const nvc_scene* sc, const nvc_clusters* cl,
   if (n == 0) return cudaSuccess;
   const size_t smem = sample_clustered_smem(sc, cl);
   const bool lights_on_chip =
-      sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes) +
-          sizeof(float4) * ((kMaxClusters + 4) / 4) + sizeof(float) * 4 * (size_t)sc->n_lights <=
+      occluder_bytes(sc->n_spheres, sc->n_boxes) + sizeof(float4) * ((kMaxClusters + 4) / 4) +
+          sizeof(float) * 4 * (size_t)sc->n_lights <=
       kSmemOptin;
   auto kern = cl->weights == NVC_CLUSTER_WEIGHT_VISIBILITY ? sample_clustered_kernel<false, false>
               : lights_on_chip                             ? sample_clustered_kernel<true, true>

@@ -21,23 +21,21 @@ namespace nvc {
 
 namespace {
 
-// Stage the occluders (and, when given, the lights with I/pi) in shared
-// memory: spheres float4, boxes 6 floats, lights float4.
-__device__ __forceinline__ void stage_scene(float* s, const float* spheres, int n_sph,
-                                            const float* boxes, int n_box, const float* lights,
-                                            int n_lights) {
-  float4* s_sph = reinterpret_cast<float4*>(s);
-  for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
-    s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
-  float4* s_lt = reinterpret_cast<float4*>(s + 4 * n_sph);
+// Stage the lights with I/pi (when given; float4) and then the occluders
+// (stage_occluders' layout) in shared memory.
+__device__ __forceinline__ Occluders stage_scene(float* s, const float* spheres, int n_sph,
+                                                 const float* boxes, int n_box,
+                                                 const float* lights, int n_lights) {
+  float4* s_lt = reinterpret_cast<float4*>(s);
   for (int e = threadIdx.x; e < n_lights; e += blockDim.x) {
     float4 l = reinterpret_cast<const float4*>(lights)[e];
     l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
     s_lt[e] = l;
   }
-  float* s_box = s + 4 * n_sph + 4 * n_lights;
-  for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
+  const Occluders occ =
+      stage_occluders(spheres, n_sph, boxes, n_box, s + 4 * n_lights, threadIdx.x, blockDim.x);
   __syncthreads();
+  return occ;
 }
 
 __global__ void __launch_bounds__(256) shade_estimate_kernel(
@@ -46,10 +44,9 @@ __global__ void __launch_bounds__(256) shade_estimate_kernel(
     const float* __restrict__ nrm, int64_t n, const int32_t* __restrict__ idx,
     const float* __restrict__ pdf, float* __restrict__ estimate, float* __restrict__ accum,
     uint32_t count) {
-  extern __shared__ float s_scene[];
-  stage_scene(s_scene, spheres, n_sph, boxes, n_box, lights, 0);
-  const float4* s_sph = reinterpret_cast<const float4*>(s_scene);
-  const float* s_box = s_scene + 4 * n_sph;
+  extern __shared__ float4 s_scene4[];
+  const Occluders occ = stage_scene(reinterpret_cast<float*>(s_scene4), spheres, n_sph, boxes,
+                                    n_box, lights, 0);
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     float e = 0.0f;
@@ -60,7 +57,7 @@ __global__ void __launch_bounds__(256) shade_estimate_kernel(
       const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
       const float c = contribution(px, py, pz, nrm[3 * p], nrm[3 * p + 1], nrm[3 * p + 2], l.x,
                                    l.y, l.z, __fmul_rn(l.w, bits_f(kInvPiBits)));
-      if (c > 0.0f && !segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box))
+      if (c > 0.0f && !segment_blocked(px, py, pz, l.x, l.y, l.z, occ))
         e = __fdiv_rn(c, pr);
     }
     if (estimate) estimate[p] = e;
@@ -79,12 +76,11 @@ __global__ void __launch_bounds__(256) exact_di_kernel(
     const float* __restrict__ lights, int L, const float* __restrict__ spheres, int n_sph,
     const float* __restrict__ boxes, int n_box, const float* __restrict__ pos,
     const float* __restrict__ nrm, int64_t n, float* __restrict__ di) {
-  extern __shared__ float s_scene[];
+  extern __shared__ float4 s_scene4[];
   const int L_s = kSmemLights ? L : 0;
-  stage_scene(s_scene, spheres, n_sph, boxes, n_box, lights, L_s);
-  const float4* s_sph = reinterpret_cast<const float4*>(s_scene);
-  const float4* s_lt = reinterpret_cast<const float4*>(s_scene + 4 * n_sph);
-  const float* s_box = s_scene + 4 * n_sph + 4 * L_s;
+  const Occluders occ = stage_scene(reinterpret_cast<float*>(s_scene4), spheres, n_sph, boxes,
+                                    n_box, lights, L_s);
+  const float4* s_lt = s_scene4;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     const float px = pos[3 * p], py = pos[3 * p + 1], pz = pos[3 * p + 2];
@@ -99,7 +95,7 @@ __global__ void __launch_bounds__(256) exact_di_kernel(
         l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
       }
       const float c = contribution(px, py, pz, nx, ny, nz, l.x, l.y, l.z, l.w);
-      if (c > 0.0f && !segment_blocked(px, py, pz, l.x, l.y, l.z, s_sph, n_sph, s_box, n_box))
+      if (c > 0.0f && !segment_blocked(px, py, pz, l.x, l.y, l.z, occ))
         sum = __fadd_rn(sum, c);
     }
     di[p] = sum;
@@ -119,7 +115,7 @@ cudaError_t launch_shade_estimate(const nvc_scene* sc, const float* pos, const f
                                   float* estimate, float* accum, uint32_t count, int num_sms,
                                   cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  const size_t smem = occluder_bytes(sc->n_spheres, sc->n_boxes);
   shade_estimate_kernel<<<grid_for(n, num_sms), 256, smem, s>>>(
       sc->lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes, pos, nrm, n, idx, pdf,
       estimate, accum, count);
@@ -129,7 +125,7 @@ cudaError_t launch_shade_estimate(const nvc_scene* sc, const float* pos, const f
 cudaError_t launch_exact_di(const nvc_scene* sc, const float* pos, const float* nrm, int64_t n,
                             float* di, int num_sms, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const size_t occ = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  const size_t occ = occluder_bytes(sc->n_spheres, sc->n_boxes);
   const size_t lt = sizeof(float) * 4 * (size_t)sc->n_lights;
   const bool on_chip = occ + lt <= 227 * 1024;
   const size_t smem = on_chip ? occ + lt : occ;

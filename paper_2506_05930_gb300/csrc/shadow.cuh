@@ -10,21 +10,117 @@
 
 namespace nvc {
 
-// The divisions are taken once per (position, light): 1/|d|^2 for the
-// spheres' closest-point parameter and 1/d per axis for the boxes' slabs;
-// each occluder then costs multiplications only.
-__device__ __forceinline__ bool sphere_blocks(float px, float py, float pz, float dx, float dy,
-                                              float dz, float inv_dd, float4 s) {
-  const float t0 = bits_f(kSegT0Bits), t1 = bits_f(kSegT1Bits);
-  const float ox = __fsub_rn(s.x, px), oy = __fsub_rn(s.y, py), oz = __fsub_rn(s.z, pz);
-  float tc = __fmul_rn(dot3_rn(ox, oy, oz, dx, dy, dz), inv_dd);
-  tc = fminf(fmaxf(tc, t0), t1);
-  const float ex = __fsub_rn(s.x, __fadd_rn(px, __fmul_rn(tc, dx)));
-  const float ey = __fsub_rn(s.y, __fadd_rn(py, __fmul_rn(tc, dy)));
-  const float ez = __fsub_rn(s.z, __fadd_rn(pz, __fmul_rn(tc, dz)));
-  return dot3_rn(ex, ey, ez, ex, ey, ez) < __fmul_rn(s.w, s.w);
+// ---- the occluders as the tests read them -----------------------------------
+// Kernels stage the scene's occluders in shared memory in this layout:
+//   sphere pairs, 32 bytes each: float4 {cx_a, cx_b, cy_a, cy_b}, float4
+//   {cz_a, cz_b, r_a^2, r_b^2} (r^2 = fl(r r)); an odd count's last slot is
+//   a sphere with r^2 = -1, which blocks nothing;
+//   boxes, 24 bytes each: (lo_x, hi_x), (lo_y, hi_y), (lo_z, hi_z).
+// So two spheres, or one slab's two planes, go through each packed float32x2
+// operation (Blackwell's add/sub/mul.rn.f32x2), each lane the correctly
+// rounded operation of the scalar test in the same order.
+struct Occluders {
+  const float4* sph;   // 2 float4 per sphere pair
+  int n_pairs;
+  const float2* box;   // 3 float2 per box
+  int n_box;
+};
+
+__host__ __device__ __forceinline__ size_t occluder_bytes(int n_sph, int n_box) {
+  return 32 * (size_t)((n_sph + 1) / 2) + 24 * (size_t)n_box;
 }
 
+// Stages the occluders at dst (16-byte aligned; occluder_bytes(...) long),
+// threads tid of nthreads sharing the work; the caller synchronises.
+__device__ __forceinline__ Occluders stage_occluders(const float* __restrict__ spheres, int n_sph,
+                                                     const float* __restrict__ boxes, int n_box,
+                                                     void* dst, int tid, int nthreads) {
+  Occluders o;
+  float* f = static_cast<float*>(dst);
+  o.sph = reinterpret_cast<const float4*>(dst);
+  o.n_pairs = (n_sph + 1) / 2;
+  for (int e = tid; e < 2 * o.n_pairs; e += nthreads) {
+    const int pair = e >> 1, lane = e & 1;
+    float4 sp = make_float4(0.0f, 0.0f, 0.0f, -1.0f);   // r^2 = -1: blocks nothing
+    if (e < n_sph) {
+      sp = reinterpret_cast<const float4*>(spheres)[e];
+      sp.w = __fmul_rn(sp.w, sp.w);
+    }
+    float* q = f + 8 * pair + lane;
+    q[0] = sp.x;
+    q[2] = sp.y;
+    q[4] = sp.z;
+    q[6] = sp.w;
+  }
+  float* b = f + 8 * o.n_pairs;
+  for (int e = tid; e < n_box; e += nthreads) {
+    const float* src = boxes + 6 * e;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      b[6 * e + 2 * a] = src[a];
+      b[6 * e + 2 * a + 1] = src[3 + a];
+    }
+  }
+  o.box = reinterpret_cast<const float2*>(b);
+  o.n_box = n_box;
+  return o;
+}
+
+// The view of occluders already staged at src (as stage_occluders left them).
+__device__ __forceinline__ Occluders staged_occluders(const void* src, int n_sph, int n_box) {
+  Occluders o;
+  o.sph = reinterpret_cast<const float4*>(src);
+  o.n_pairs = (n_sph + 1) / 2;
+  o.box = reinterpret_cast<const float2*>(static_cast<const float*>(src) + 8 * o.n_pairs);
+  o.n_box = n_box;
+  return o;
+}
+
+// ---- the tests ----------------------------------------------------------------
+// The divisions are taken once per (position, light): 1/|d|^2 for the
+// spheres' closest-point parameter and 1/d per axis for the boxes' slabs;
+// each occluder then costs multiplications only.  Sphere (c, r): the
+// segment's closest point q = x + t_c d, t_c = clamp(((c - x).d) / |d|^2,
+// t0, t1), blocks when |c - q|^2 < r^2.
+
+__device__ __forceinline__ float2 dot3_rn2(float2 ax, float2 ay, float2 az, float2 bx, float2 by,
+                                           float2 bz) {
+  return __fadd2_rn(__fadd2_rn(__fmul2_rn(ax, bx), __fmul2_rn(ay, by)), __fmul2_rn(az, bz));
+}
+
+// Two spheres A = {cx, cy} pair words, B = {cz, r^2} pair words.
+__device__ __forceinline__ bool sphere_pair_blocks(float2 px, float2 py, float2 pz, float2 dx,
+                                                   float2 dy, float2 dz, float2 inv_dd, float4 A,
+                                                   float4 B) {
+  const float t0 = bits_f(kSegT0Bits), t1 = bits_f(kSegT1Bits);
+  const float2 cx = make_float2(A.x, A.y), cy = make_float2(A.z, A.w), cz = make_float2(B.x, B.y);
+  float2 tc = __fmul2_rn(dot3_rn2(fsub2(cx, px), fsub2(cy, py), fsub2(cz, pz), dx, dy, dz), inv_dd);
+  tc.x = fminf(fmaxf(tc.x, t0), t1);
+  tc.y = fminf(fmaxf(tc.y, t0), t1);
+  const float2 ex = fsub2(cx, __fadd2_rn(px, __fmul2_rn(tc, dx)));
+  const float2 ey = fsub2(cy, __fadd2_rn(py, __fmul2_rn(tc, dy)));
+  const float2 ez = fsub2(cz, __fadd2_rn(pz, __fmul2_rn(tc, dz)));
+  const float2 e2 = dot3_rn2(ex, ey, ez, ex, ey, ez);
+  return e2.x < B.z || e2.y < B.w;
+}
+
+// Closed slab test of one box when no component of d is zero: the entry and
+// exit parameters (lo - x) / d and (hi - x) / d of every axis, two per
+// packed operation; blocked when max(t0, nearer planes) <= min(t1, farther).
+__device__ __forceinline__ bool box_blocks_oblique(float2 px, float2 py, float2 pz, float2 ix,
+                                                   float2 iy, float2 iz, const float2* b) {
+  const float2 tx = __fmul2_rn(fsub2(b[0], px), ix);
+  const float2 ty = __fmul2_rn(fsub2(b[1], py), iy);
+  const float2 tz = __fmul2_rn(fsub2(b[2], pz), iz);
+  const float tmin = fmaxf(fmaxf(fmaxf(bits_f(kSegT0Bits), fminf(tx.x, tx.y)), fminf(ty.x, ty.y)),
+                           fminf(tz.x, tz.y));
+  const float tmax = fminf(fminf(fminf(bits_f(kSegT1Bits), fmaxf(tx.x, tx.y)), fmaxf(ty.x, ty.y)),
+                           fmaxf(tz.x, tz.y));
+  return tmin <= tmax;
+}
+
+// The same test with any component of d zero: that axis only checks that x
+// lies between its planes.
 __device__ __forceinline__ void slab(float xa, float da, float inv_da, float lo, float hi,
                                      float& tmin, float& tmax, bool& miss) {
   if (da == 0.0f) {
@@ -37,35 +133,44 @@ __device__ __forceinline__ void slab(float xa, float da, float inv_da, float lo,
   tmax = fminf(tmax, fmaxf(ta, tb));
 }
 
-__device__ __forceinline__ bool box_blocks(float px, float py, float pz, float dx, float dy,
-                                           float dz, float ix, float iy, float iz,
-                                           const float* b) {
+__device__ __forceinline__ bool box_blocks_general(float px, float py, float pz, float dx, float dy,
+                                                   float dz, float ix, float iy, float iz,
+                                                   const float2* b) {
   float tmin = bits_f(kSegT0Bits), tmax = bits_f(kSegT1Bits);
   bool miss = false;
-  slab(px, dx, ix, b[0], b[3], tmin, tmax, miss);
-  slab(py, dy, iy, b[1], b[4], tmin, tmax, miss);
-  slab(pz, dz, iz, b[2], b[5], tmin, tmax, miss);
+  slab(px, dx, ix, b[0].x, b[0].y, tmin, tmax, miss);
+  slab(py, dy, iy, b[1].x, b[1].y, tmin, tmax, miss);
+  slab(pz, dz, iz, b[2].x, b[2].y, tmin, tmax, miss);
   return !miss && tmin <= tmax;
 }
 
 // Whether the segment from (px, py, pz) to the light at (lx, ly, lz) is
-// blocked by one of the staged occluders (spheres as float4 centre + radius,
-// boxes as 6 floats lo, hi).
+// blocked by one of the staged occluders.
 __device__ __forceinline__ bool segment_blocked(float px, float py, float pz, float lx, float ly,
-                                                float lz, const float4* sph, int n_sph,
-                                                const float* box, int n_box) {
+                                                float lz, const Occluders& occ) {
   const float dx = __fsub_rn(lx, px), dy = __fsub_rn(ly, py), dz = __fsub_rn(lz, pz);
   const float dd = dot3_rn(dx, dy, dz, dx, dy, dz);
+  // a zero-length segment (light on the point): t stays at t0
   const float inv_dd = dd > 0.0f ? __fdiv_rn(1.0f, dd) : 0.0f;
   const float ix = dx != 0.0f ? __fdiv_rn(1.0f, dx) : 0.0f;
   const float iy = dy != 0.0f ? __fdiv_rn(1.0f, dy) : 0.0f;
   const float iz = dz != 0.0f ? __fdiv_rn(1.0f, dz) : 0.0f;
-  bool occ = false;
-  for (int k = 0; k < n_sph && !occ; ++k)
-    occ = sphere_blocks(px, py, pz, dx, dy, dz, inv_dd, sph[k]);
-  for (int k = 0; k < n_box && !occ; ++k)
-    occ = box_blocks(px, py, pz, dx, dy, dz, ix, iy, iz, box + 6 * k);
-  return occ;
+  const float2 px2 = make_float2(px, px), py2 = make_float2(py, py), pz2 = make_float2(pz, pz);
+  const float2 dx2 = make_float2(dx, dx), dy2 = make_float2(dy, dy), dz2 = make_float2(dz, dz);
+  bool blocked = false;
+  for (int k = 0; k < occ.n_pairs && !blocked; ++k)
+    blocked = sphere_pair_blocks(px2, py2, pz2, dx2, dy2, dz2, make_float2(inv_dd, inv_dd),
+                                 occ.sph[2 * k], occ.sph[2 * k + 1]);
+  if (blocked) return true;
+  if (dx != 0.0f && dy != 0.0f && dz != 0.0f) {
+    const float2 ix2 = make_float2(ix, ix), iy2 = make_float2(iy, iy), iz2 = make_float2(iz, iz);
+    for (int k = 0; k < occ.n_box && !blocked; ++k)
+      blocked = box_blocks_oblique(px2, py2, pz2, ix2, iy2, iz2, occ.box + 3 * k);
+  } else {
+    for (int k = 0; k < occ.n_box && !blocked; ++k)
+      blocked = box_blocks_general(px, py, pz, dx, dy, dz, ix, iy, iz, occ.box + 3 * k);
+  }
+  return blocked;
 }
 
 // ---- training positions (Section 3.4) ------------------------------------------

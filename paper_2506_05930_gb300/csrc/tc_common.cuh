@@ -171,17 +171,6 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
-// a - b on both halves, each correctly rounded (sub.rn.f32x2)
-__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
-  uint64_t ua, ub, r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(ua) : "f"(a.x), "f"(a.y));
-  asm("mov.b64 %0, {%1, %2};" : "=l"(ub) : "f"(b.x), "f"(b.y));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(ua), "l"(ub));
-  float2 o;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
-  return o;
-}
-
 // ---- encode of one (pixel, level) ------------------------------------------
 // One table row of F half-precision features, widened to float32 (one 2-,
 // 4-, 8- or 16-byte load).

@@ -25,12 +25,9 @@ __global__ void __launch_bounds__(256) trace_visibility_kernel(
     const float* __restrict__ lights, int L, const float* __restrict__ spheres, int n_sph,
     const float* __restrict__ boxes, int n_box, float* __restrict__ pos, int64_t n,
     float* __restrict__ vis, PosGen gen) {
-  extern __shared__ float s_occ[];
-  float4* s_sph = reinterpret_cast<float4*>(s_occ);
-  float* s_box = s_occ + 4 * n_sph;
-  for (int e = threadIdx.x; e < n_sph; e += blockDim.x)
-    s_sph[e] = reinterpret_cast<const float4*>(spheres)[e];
-  for (int e = threadIdx.x; e < 6 * n_box; e += blockDim.x) s_box[e] = boxes[e];
+  extern __shared__ float4 s_occ[];
+  const Occluders occ =
+      stage_occluders(spheres, n_sph, boxes, n_box, s_occ, threadIdx.x, blockDim.x);
   __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * L) return;
@@ -53,19 +50,8 @@ __global__ void __launch_bounds__(256) trace_visibility_kernel(
     pz = pos[3 * p + 2];
   }
   const float4 lt = reinterpret_cast<const float4*>(lights)[i];
-  const float dx = __fsub_rn(lt.x, px), dy = __fsub_rn(lt.y, py), dz = __fsub_rn(lt.z, pz);
-  const float dd = dot3_rn(dx, dy, dz, dx, dy, dz);
-  // a zero-length segment (light on the point): t stays at t0
-  const float inv_dd = dd > 0.0f ? __fdiv_rn(1.0f, dd) : 0.0f;
-  const float ix = dx != 0.0f ? __fdiv_rn(1.0f, dx) : 0.0f;
-  const float iy = dy != 0.0f ? __fdiv_rn(1.0f, dy) : 0.0f;
-  const float iz = dz != 0.0f ? __fdiv_rn(1.0f, dz) : 0.0f;
-  bool occ = false;
-  for (int k = 0; k < n_sph && !occ; ++k)
-    occ = sphere_blocks(px, py, pz, dx, dy, dz, inv_dd, s_sph[k]);
-  for (int k = 0; k < n_box && !occ; ++k)
-    occ = box_blocks(px, py, pz, dx, dy, dz, ix, iy, iz, s_box + 6 * k);
-  vis[t] = occ ? 0.0f : 1.0f;
+  const bool blocked = segment_blocked(px, py, pz, lt.x, lt.y, lt.z, occ);
+  vis[t] = blocked ? 0.0f : 1.0f;
 }
 
 // ---- loss and its gradient at the logits ------------------------------------
@@ -294,7 +280,7 @@ cudaError_t launch_training_data(const nvc_scene* sc, const float* screen_pos, i
   if (sc->n_lights < 1)
     return launch_training_positions(sc, screen_pos, n_screen, batch, seed, frame, pos, s, n_world);
   const int64_t total = batch * sc->n_lights;
-  const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  const size_t smem = occluder_bytes(sc->n_spheres, sc->n_boxes);
   trace_visibility_kernel<true><<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
       sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes, pos, batch,
       vis, pos_gen(sc, screen_pos, n_screen, batch, seed, frame, n_world));
@@ -305,7 +291,7 @@ cudaError_t launch_trace_visibility(const nvc_scene* sc, const float* pos, int64
                                     cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t total = n * sc->n_lights;
-  const size_t smem = sizeof(float) * (4 * (size_t)sc->n_spheres + 6 * (size_t)sc->n_boxes);
+  const size_t smem = occluder_bytes(sc->n_spheres, sc->n_boxes);
   trace_visibility_kernel<false><<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
       sc->lights, sc->n_lights, sc->spheres, sc->n_spheres, sc->boxes, sc->n_boxes,
       const_cast<float*>(pos), n, vis, PosGen{});

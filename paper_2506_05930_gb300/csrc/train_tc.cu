@@ -87,7 +87,7 @@ struct TrainTcArgs {
   int n_sph, n_box;
   float* pos_out;             // [n][3]
   float* target_out;          // [n][L]
-  int occ_off;                // smem: spheres (float4), boxes (6 floats), lights (float4)
+  int occ_off;                // smem: lights (float4), then the occluders (shadow.cuh layout)
   int tgt_off;                // smem: the tile's targets, 128 x L bytes
 };
 
@@ -95,18 +95,18 @@ struct TrainTcArgs {
 // the row's position to light i against every staged occluder; the binary
 // target goes to shared memory and, for live rows, to target_out.
 __device__ __forceinline__ void trace_slice(const TrainTcArgs& a, const float* s_pos,
-                                            const float4* s_sph, const float* s_box,
-                                            const float4* s_lt, uint8_t* s_tgt, int64_t tile,
+                                            const Occluders& occ, const float4* s_lt,
+                                            uint8_t* s_tgt, int64_t tile,
                                             int r0, int r1, int t, int n_threads) {
   for (int r = r0 + t; r < r1; r += n_threads) {
     const int row = r / a.L, i = r - row * a.L;
     const int64_t sample = tile * 128 + row;
     if (sample >= a.n) continue;
     const float4 lt = s_lt[i];
-    const bool occ = segment_blocked(s_pos[3 * row], s_pos[3 * row + 1], s_pos[3 * row + 2], lt.x,
-                                     lt.y, lt.z, s_sph, a.n_sph, s_box, a.n_box);
-    s_tgt[r] = occ ? 0 : 1;
-    a.target_out[sample * a.L + i] = occ ? 0.0f : 1.0f;
+    const bool blocked = segment_blocked(s_pos[3 * row], s_pos[3 * row + 1], s_pos[3 * row + 2],
+                                         lt.x, lt.y, lt.z, occ);
+    s_tgt[r] = blocked ? 0 : 1;
+    a.target_out[sample * a.L + i] = blocked ? 0.0f : 1.0f;
   }
 }
 
@@ -159,20 +159,13 @@ __global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_c
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ double s_red[kThreads / 32];
   __shared__ float s_pos[GEN ? 3 * kTileM : 1];
-  const float4* s_sph = reinterpret_cast<const float4*>(smem + a.occ_off);
-  const float* s_box = reinterpret_cast<const float*>(smem + a.occ_off) + 4 * a.n_sph;
-  const float4* s_lt = reinterpret_cast<const float4*>(smem + a.occ_off + 16 * a.n_sph +
-                                                       ((24 * a.n_box + 15) & ~15));
+  float4* s_lt = reinterpret_cast<float4*>(smem + a.occ_off);
   uint8_t* s_tgt = smem + a.tgt_off;
+  Occluders occ = staged_occluders(s_lt + a.L, 0, 0);
   if constexpr (GEN) {
-    float4* sph = const_cast<float4*>(s_sph);
-    float* box = const_cast<float*>(s_box);
-    float4* lt = const_cast<float4*>(s_lt);
-    for (int e = threadIdx.x; e < a.n_sph; e += kThreads)
-      sph[e] = reinterpret_cast<const float4*>(a.spheres)[e];
-    for (int e = threadIdx.x; e < 6 * a.n_box; e += kThreads) box[e] = a.boxes[e];
+    occ = stage_occluders(a.spheres, a.n_sph, a.boxes, a.n_box, s_lt + a.L, threadIdx.x, kThreads);
     for (int e = threadIdx.x; e < a.L; e += kThreads)
-      lt[e] = reinterpret_cast<const float4*>(a.lights)[e];
+      s_lt[e] = reinterpret_cast<const float4*>(a.lights)[e];
   }
   uint8_t* s_w = smem;
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.bar_off);
@@ -288,7 +281,7 @@ __global__ void __launch_bounds__(kTileM * NG, 1) train_tc_kernel(const __grid_c
         // loss (layer `last`) reads them after this layer's barrier
         if (k < last) {
           const int R = kTileM * a.L;
-          trace_slice(a, s_pos, s_sph, s_box, s_lt, s_tgt, tile, R * k / last, R * (k + 1) / last, t,
+          trace_slice(a, s_pos, occ, s_lt, s_tgt, tile, R * k / last, R * (k + 1) / last, t,
                       kThreads);
         }
       }
@@ -559,7 +552,7 @@ bool plan(const nvc_handle* h, TrainTcArgs& a, size_t* smem, std::string* why,
   off += 64;
   if (gen) {
     a.occ_off = off;
-    off += 16 * gen->n_spheres + ((24 * gen->n_boxes + 15) & ~15) + 16 * h->L;
+    off += 16 * h->L + (int)((occluder_bytes(gen->n_spheres, gen->n_boxes) + 15) & ~(size_t)15);
     a.tgt_off = off;
     off += (kTileM * h->L + 15) & ~15;
   }
