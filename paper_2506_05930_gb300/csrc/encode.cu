@@ -19,7 +19,10 @@ EncodeParams encode_params(const nvc_handle* h) {
     ep.lo[d] = h->cfg.bounds_min[d];
     ep.ext[d] = h->cfg.bounds_max[d] - h->cfg.bounds_min[d];  // host float32 subtraction
   }
-  for (int l = 0; l < h->cfg.n_levels; ++l) ep.res[l] = h->res[l];
+  for (int l = 0; l < h->cfg.n_levels; ++l) {
+    ep.res[l] = h->res[l];
+    ep.resf[l] = (float)h->res[l];
+  }
   return ep;
 }
 

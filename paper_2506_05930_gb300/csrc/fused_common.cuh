@@ -133,8 +133,28 @@ __device__ __forceinline__ void encode_chunk(const EncodeParams& ep, const TT* t
 // [H, L) to the other, H = ceil(L / 2) rounded up to a multiple of 16.
 __host__ __device__ __forceinline__ int split_h(int L) { return ((((L + 1) >> 1) + 15) >> 4) << 4; }
 
+// sigma(z) = 1 / (1 + 2^(-z log2(e))) with the hardware's approximate base-2
+// exponential and reciprocal (ex2.approx, rcp.approx; subnormals flushed):
+// z -> -inf gives 2^inf = inf and 1/inf = 0, z -> +inf gives 1.
 __device__ __forceinline__ float sigmoid_fast(float z) {
-  return __fdividef(1.0f, 1.0f + __expf(-z));
+  const float t = __fmul_rn(z, -1.4426950408889634f);
+  float e, v;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(t));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(v) : "f"(__fadd_rn(e, 1.0f)));
+  return v;
+}
+
+// sigmoid_fast of two values, the multiply and the add as packed float32x2
+// operations: each lane equals sigmoid_fast of that lane.
+__device__ __forceinline__ float2 sigmoid2_fast(float2 z) {
+  const float2 t = __fmul2_rn(z, make_float2(-1.4426950408889634f, -1.4426950408889634f));
+  float2 e, v;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(t.x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(t.y));
+  const float2 d = __fadd2_rn(e, make_float2(1.0f, 1.0f));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(v.x) : "f"(d.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(v.y) : "f"(d.y));
+  return v;
 }
 
 // Exported visibilities: the sigmoid of N accumulator words (times mul)
@@ -160,14 +180,16 @@ __device__ __forceinline__ void store_sigmoid_row(float* dst, const uint32_t (&r
 
 // Unshadowed contribution of a point light (Lambertian, albedo 1):
 // (I/pi) * (n.d) / (|d| * max(|d|^2, 1e-6)) for n.d > 0, with a hardware
-// reciprocal square root.
+// reciprocal square root r of |d|^2 + 1e-30 (the 1e-30 rides in the last
+// fused multiply-add; it changes |d|^2 only below about 1e-22, where it
+// keeps r finite) and 1 / max(|d|^2, 1e-6) taken as min(r^2, 1e6).
 __device__ __forceinline__ float contribution_fast(float px, float py, float pz, float nx,
                                                    float ny, float nz, float4 l) {
   const float dx = l.x - px, dy = l.y - py, dz = l.z - pz;
-  const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float d2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-30f)));
   const float ndl = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
-  const float r = rsqrtf(fmaxf(d2, 1e-30f));
-  const float inv = d2 >= 1e-6f ? r * r : 1e6f;
+  const float r = rsqrtf(d2);
+  const float inv = fminf(r * r, 1e6f);
   return fmaxf(l.w * ndl * r * inv, 0.0f);   // n.d <= 0 gives c <= 0 -> 0
 }
 

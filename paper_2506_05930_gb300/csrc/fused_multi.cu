@@ -15,7 +15,7 @@ using namespace fz;
 
 // ---- several tiles per CTA sharing one weight copy ---------------------------
 // TPC groups of four warps.  Group g runs its own stream of 128-pixel tiles
-// (tiles blockIdx.x TPC + g + k gridDim.x TPC) the way the monolithic kernel
+// (taken one at a time from the launch's ticket counter) the way the monolithic kernel
 // does -- its own activation tile, mbarrier, TMEM columns [g C, (g + 1) C)
 // and 128-thread named barrier -- while the weight image is held once per
 // CTA for all groups.  Between the sampler's two passes the group's
@@ -53,6 +53,26 @@ __device__ __forceinline__ bool group_sync_or(int g, bool v) {
   return r != 0;
 }
 
+// Tiles are handed out at run time: each group takes its next tile from a
+// ticket counter in the handle's status words when it finishes one, so a
+// group that met cheaper tiles takes more of them and the launch ends within
+// about one tile of the mean (a fixed round-robin deal left the slowest group
+// 19% behind the mean at 1080p).  The last group to finish puts the counter
+// back to zero for the next launch.
+__device__ __forceinline__ uint32_t take_tile(int32_t* status) {
+  return atomicAdd(reinterpret_cast<uint32_t*>(status + kStTileNext), 1u);
+}
+
+__device__ __forceinline__ void finish_tiles(int32_t* status, uint32_t n_groups) {
+  __threadfence();
+  uint32_t* next = reinterpret_cast<uint32_t*>(status + kStTileNext);
+  uint32_t* done = reinterpret_cast<uint32_t*>(status + kStTileDone);
+  if (atomicAdd(done, 1u) == n_groups - 1u) {
+    atomicExch(next, 0u);
+    atomicExch(done, 0u);
+  }
+}
+
 // STAMP: the phase-profile instantiation (nvc_shade_phases).  Thread 0 of
 // each group reads the SM clock at four points of every tile -- tile start,
 // the encoded A tile complete, the output layer's accumulator read, the end
@@ -75,6 +95,7 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
   float4* s_l = reinterpret_cast<float4*>(smem + a.multi_l);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.multi_bar);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + TPC);
+  uint32_t* s_next = s_tmem + 1;         // each group's next tile
 
   for (int e = t; e < a.wimg_bytes / 16; e += kThreads)
     reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
@@ -97,6 +118,7 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(smem_u32(s_tmem), a.tmem_cols);
+  if (rw == 0) s_next[g] = take_tile(a.status);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -122,8 +144,7 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
   long long c_tile = 0, c_mark = 0;
   const long long c_loop = STAMP ? clock64() : 0;
 
-  for (int64_t tile = (int64_t)blockIdx.x * TPC + g; tile < n_tiles && !failed;
-       tile += (int64_t)gridDim.x * TPC) {
+  for (int64_t tile = s_next[g]; tile < n_tiles && !failed; tile = s_next[g]) {
     if constexpr (STAMP) c_tile = clock64();
     const ViewDesc& V = a.v[view_of(a, tile)];
     const int64_t row = (tile - V.tile_start) * kTileM + rw;
@@ -233,16 +254,18 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
               const float2 dx = __fadd2_rn(make_float2(A.x, A.y), npx);
               const float2 dy = __fadd2_rn(make_float2(A.z, A.w), npy);
               const float2 dz = __fadd2_rn(make_float2(B.x, B.y), npz);
-              const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+              const float2 d2 =
+                  __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, make_float2(1e-30f, 1e-30f))));
               const float2 ndl = __ffma2_rn(nx2, dx, __ffma2_rn(ny2, dy, __fmul2_rn(nz2, dz)));
-              const float2 rq = make_float2(rsqrtf(fmaxf(d2.x, 1e-30f)), rsqrtf(fmaxf(d2.y, 1e-30f)));
+              const float2 rq = make_float2(rsqrtf(d2.x), rsqrtf(d2.y));
               const float2 rr = __fmul2_rn(rq, rq);
-              const float2 inv = make_float2(d2.x >= 1e-6f ? rr.x : 1e6f, d2.y >= 1e-6f ? rr.y : 1e6f);
+              const float2 inv = make_float2(fminf(rr.x, 1e6f), fminf(rr.y, 1e6f));
               float2 c = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(B.z, B.w), ndl), rq), inv);
               c.x = fmaxf(c.x, 0.0f);
               c.y = fmaxf(c.y, 0.0f);
-              const float v0 = sigmoid_fast(__uint_as_float(r[j]));
-              const float v1 = sigmoid_fast(__uint_as_float(r[j + 1]));
+              const float2 v01 =
+                  sigmoid2_fast(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])));
+              const float v0 = v01.x, v1 = v01.y;
               const float2 w2 = __fmul2_rn(make_float2(fmaxf(v0, bits_f(kVisClampBits)),
                                                        fmaxf(v1, bits_f(kVisClampBits))), c);
               wmax = fmaxf(wmax, w2.x);
@@ -308,9 +331,10 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
           if (V.radiance) V.radiance[row] = di;
         }
       }
+      if (rw == 0) s_next[g] = take_tile(a.status);
       tc_fence_before();
       // also keeps the next tile's encode from overwriting weights that a
-      // slower thread of the group still reads
+      // slower thread of the group still reads, and publishes s_next[g]
       failed = group_sync_or(g, !ok);
       if constexpr (STAMP) cyc[2] += (unsigned long long)(clock64() - c_mark);
     }
@@ -324,6 +348,7 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
     }
   }
   if (failed && rw == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
+  if (rw == 0) finish_tiles(a.status, gridDim.x * TPC);
   if (failed) mbar_wait_bounded(bar, phase ^ 1u);   // let an MMA in flight land
   __syncthreads();
   if (warp == 0) {
@@ -334,7 +359,8 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
 
 // Shared-memory plan of the several-tiles-per-CTA kernel: weight image, tpc
 // activation tiles (each also holding the 128 pixels' light weights in rows
-// of 36 floats), light table, tpc mbarriers and the TMEM address word.
+// of 36 floats), light table, tpc mbarriers, the TMEM address word and the
+// groups' next-tile words.
 size_t multi_smem(const nvc_handle* h, const PackArgs& p, int tpc, FusedArgs* a = nullptr) {
   int kmax = 16;
   for (int k = 0; k < p.n_layers; ++k) kmax = p.K[k] > kmax ? p.K[k] : kmax;
@@ -348,7 +374,7 @@ size_t multi_smem(const nvc_handle* h, const PackArgs& p, int tpc, FusedArgs* a 
   off += 16 * (size_t)(h->L > 0 ? ((h->L + 1) & ~1) : 2);
   off = (off + 7) & ~(size_t)7;
   const size_t bar_off = off;
-  off += 8 * (size_t)tpc + 8;
+  off += 8 * (size_t)tpc + 8 + 4 * (size_t)tpc;
   if (a) {
     a->multi_a = (int)a_off;
     a->multi_stride = (int)stride;

@@ -88,6 +88,7 @@ struct EncodeParams {
   float lo[3];
   float ext[3];
   int res[NVC_MAX_LEVELS];
+  float resf[NVC_MAX_LEVELS];   // res as float32 (exact: res < 2^24)
 };
 
 // ---------------------------------------------------------------------------
@@ -129,6 +130,8 @@ enum StatusWord : int {
   kStFrames = 3,
   kStNonFinite = 4,   // set by the gradient kernels of the current step
   kStSkipNow = 5,     // Adam of the current step is skipped
+  kStTileNext = 6,    // shading tile scheduler: next tile ticket (0 between launches)
+  kStTileDone = 7,    // shading tile scheduler: tile streams finished (0 between launches)
   kStWords = 8
 };
 enum : int { kFlagNonFinite = 1, kFlagTimeout = 2 };

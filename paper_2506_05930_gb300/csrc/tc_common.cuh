@@ -237,7 +237,7 @@ __device__ __forceinline__ LevelCell level_cell(const EncodeParams& ep, int l, f
                                                 float z) {
   LevelCell c;
   const int n = ep.res[l];
-  const float nf = (float)n;
+  const float nf = ep.resf[l];
   int cx = __float2int_rd(__fmul_rn(x, nf)), cy = __float2int_rd(__fmul_rn(y, nf)),
       cz = __float2int_rd(__fmul_rn(z, nf));
   cx = min(cx, n - 1);
