@@ -53,26 +53,6 @@ __device__ __forceinline__ bool group_sync_or(int g, bool v) {
   return r != 0;
 }
 
-// Tiles are handed out at run time: each group takes its next tile from a
-// ticket counter in the handle's status words when it finishes one, so a
-// group that met cheaper tiles takes more of them and the launch ends within
-// about one tile of the mean (a fixed round-robin deal left the slowest group
-// 19% behind the mean at 1080p).  The last group to finish puts the counter
-// back to zero for the next launch.
-__device__ __forceinline__ uint32_t take_tile(int32_t* status) {
-  return atomicAdd(reinterpret_cast<uint32_t*>(status + kStTileNext), 1u);
-}
-
-__device__ __forceinline__ void finish_tiles(int32_t* status, uint32_t n_groups) {
-  __threadfence();
-  uint32_t* next = reinterpret_cast<uint32_t*>(status + kStTileNext);
-  uint32_t* done = reinterpret_cast<uint32_t*>(status + kStTileDone);
-  if (atomicAdd(done, 1u) == n_groups - 1u) {
-    atomicExch(next, 0u);
-    atomicExch(done, 0u);
-  }
-}
-
 // STAMP: the phase-profile instantiation (nvc_shade_phases).  Thread 0 of
 // each group reads the SM clock at four points of every tile -- tile start,
 // the encoded A tile complete, the output layer's accumulator read, the end

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
   float4* s_l = reinterpret_cast<float4*>(smem + a.mono_l);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.mono_bar);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 1);
+  uint32_t* s_next = s_tmem + 1;   // the CTA's next tile
   const int t = threadIdx.x;
   const int warp = t >> 5;
 
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(smem_u32(s_tmem), a.tmem_cols);
+  if (t == 0) *s_next = take_tile(a.status);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
   const int K0 = a.layer[0].K;
   const int64_t n_tiles = a.n_tiles;
 
-  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+  for (int64_t tile = *s_next; tile < n_tiles && !failed; tile = *s_next) {
     const ViewDesc& V = a.v[view_of(a, tile)];
     const int64_t row = (tile - V.tile_start) * kTileM + t;
     const bool live = row < V.n;
@@ -285,11 +287,13 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
           if (V.radiance) V.radiance[row] = di;
         }
       }
+      if (t == 0) *s_next = take_tile(a.status);
       tc_fence_before();
-      failed = __syncthreads_or(!ok) != 0;
+      failed = __syncthreads_or(!ok) != 0;   // also publishes *s_next
     }
   }
   if (failed && t == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
+  if (t == 0) finish_tiles(a.status, gridDim.x);
   __syncthreads();
   if (failed) mbar_wait_bounded(bar, phase ^ 1u);   // let an MMA in flight land
   if (warp == 0) {
@@ -332,6 +336,7 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
   float4* s_l = reinterpret_cast<float4*>(smem + a.mono_l);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.mono_bar);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 1);
+  uint32_t* s_next = s_tmem + 1;                                     // the CTA's next tile
   float4* s_x = reinterpret_cast<float4*>(smem + a.pair_x);          // [2][128] partials
   uint32_t* s_q = reinterpret_cast<uint32_t*>(s_x + 2 * kTileM);     // [128] Q_A
   int2* s_s = reinterpret_cast<int2*>(s_q + kTileM);                 // [128] (sel, w_sel bits) of half 1
@@ -355,6 +360,7 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(smem_u32(s_tmem), a.tmem_cols);
+  if (t == 0) *s_next = take_tile(a.status);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -376,7 +382,7 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
   const int lo = half ? H : 0;
   const int hi = half ? L : (H < L ? H : L);
 
-  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+  for (int64_t tile = *s_next; tile < n_tiles && !failed; tile = *s_next) {
     const ViewDesc& V = a.v[view_of(a, tile)];
     const int64_t row = (tile - V.tile_start) * kTileM + rw;
     const bool live = row < V.n;
@@ -571,11 +577,13 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
           if (V.radiance) V.radiance[row] = di;
         }
       }
+      if (t == 0) *s_next = take_tile(a.status);
       tc_fence_before();
-      failed = __syncthreads_or(!ok) != 0;
+      failed = __syncthreads_or(!ok) != 0;   // also publishes *s_next
     }
   }
   if (failed && t == 0) atomicOr(a.status + kStFlags, kFlagTimeout);
+  if (t == 0) finish_tiles(a.status, gridDim.x);
   __syncthreads();
   if (failed) mbar_wait_bounded(bar, phase ^ 1u);
   if (warp == 0) {
