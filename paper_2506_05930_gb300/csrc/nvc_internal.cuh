@@ -23,17 +23,25 @@ constexpr uint32_t kSegT1Bits = 0x3F7FF972u;    // 1 - 1e-4
 
 __device__ __forceinline__ float bits_f(uint32_t b) { return __uint_as_float(b); }
 
-// a - b on both halves of a float2, each a correctly rounded float32
-// subtraction (the packed sub.rn.f32x2 of sm_100 and later).
-__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
-  uint64_t ua, ub, r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(ua) : "f"(a.x), "f"(a.y));
-  asm("mov.b64 %0, {%1, %2};" : "=l"(ub) : "f"(b.x), "f"(b.y));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(ua), "l"(ub));
-  float2 o;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
-  return o;
-}
+// a - b, a + b and a * b on both halves of a float2, each a correctly
+// rounded float32 operation (the packed sub/add/mul.rn.f32x2 of sm_100 and
+// later).  Written as PTX with an explicit .rn so that no product is fused
+// into a following sum: code whose decisions must equal a scalar, one-
+// rounding-per-operation definition uses these.
+#define NVC_PACKED_OP(NAME, OP)                                                  \
+  __device__ __forceinline__ float2 NAME(float2 a, float2 b) {                   \
+    uint64_t ua, ub, r;                                                          \
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ua) : "f"(a.x), "f"(a.y));                \
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ub) : "f"(b.x), "f"(b.y));                \
+    asm(OP " %0, %1, %2;" : "=l"(r) : "l"(ua), "l"(ub));                         \
+    float2 o;                                                                    \
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));                \
+    return o;                                                                    \
+  }
+NVC_PACKED_OP(fsub2, "sub.rn.f32x2")
+NVC_PACKED_OP(fadd2_rn, "add.rn.f32x2")
+NVC_PACKED_OP(fmul2_rn, "mul.rn.f32x2")
+#undef NVC_PACKED_OP
 
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon et al., SC 2011): counter-based, one 128-bit block

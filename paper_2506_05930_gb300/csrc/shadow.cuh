@@ -16,9 +16,10 @@ namespace nvc {
 //   {cz_a, cz_b, r_a^2, r_b^2} (r^2 = fl(r r)); an odd count's last slot is
 //   a sphere with r^2 = -1, which blocks nothing;
 //   boxes, 24 bytes each: (lo_x, hi_x), (lo_y, hi_y), (lo_z, hi_z).
-// So two spheres, or one slab's two planes, go through each packed float32x2
-// operation (Blackwell's add/sub/mul.rn.f32x2), each lane the correctly
-// rounded operation of the scalar test in the same order.
+// A slab's two planes go through each packed float32x2 subtraction and
+// multiplication (Blackwell's sub/mul.rn.f32x2), each lane the correctly
+// rounded operation of the scalar test; the sphere pairs are read with two
+// 16-byte loads and tested lane by lane in scalar operations.
 struct Occluders {
   const float4* sph;   // 2 float4 per sphere pair
   int n_pairs;
@@ -83,25 +84,29 @@ __device__ __forceinline__ Occluders staged_occluders(const void* src, int n_sph
 // segment's closest point q = x + t_c d, t_c = clamp(((c - x).d) / |d|^2,
 // t0, t1), blocks when |c - q|^2 < r^2.
 
-__device__ __forceinline__ float2 dot3_rn2(float2 ax, float2 ay, float2 az, float2 bx, float2 by,
-                                           float2 bz) {
-  return __fadd2_rn(__fadd2_rn(__fmul2_rn(ax, bx), __fmul2_rn(ay, by)), __fmul2_rn(az, bz));
+// One sphere of a staged pair (lane 0 or 1), in scalar correctly rounded
+// operations: the compiler fuses a packed multiply into a following packed
+// add (one rounding instead of two) even when both carry .rn, so products
+// that feed sums stay scalar here.
+__device__ __forceinline__ bool sphere_lane_blocks(float px, float py, float pz, float dx,
+                                                   float dy, float dz, float inv_dd, float cx,
+                                                   float cy, float cz, float r2) {
+  const float t0 = bits_f(kSegT0Bits), t1 = bits_f(kSegT1Bits);
+  const float ox = __fsub_rn(cx, px), oy = __fsub_rn(cy, py), oz = __fsub_rn(cz, pz);
+  float tc = __fmul_rn(dot3_rn(ox, oy, oz, dx, dy, dz), inv_dd);
+  tc = fminf(fmaxf(tc, t0), t1);
+  const float ex = __fsub_rn(cx, __fadd_rn(px, __fmul_rn(tc, dx)));
+  const float ey = __fsub_rn(cy, __fadd_rn(py, __fmul_rn(tc, dy)));
+  const float ez = __fsub_rn(cz, __fadd_rn(pz, __fmul_rn(tc, dz)));
+  return dot3_rn(ex, ey, ez, ex, ey, ez) < r2;
 }
 
-// Two spheres A = {cx, cy} pair words, B = {cz, r^2} pair words.
-__device__ __forceinline__ bool sphere_pair_blocks(float2 px, float2 py, float2 pz, float2 dx,
-                                                   float2 dy, float2 dz, float2 inv_dd, float4 A,
+// Two spheres: A = {cx_a, cx_b, cy_a, cy_b}, B = {cz_a, cz_b, r_a^2, r_b^2}.
+__device__ __forceinline__ bool sphere_pair_blocks(float px, float py, float pz, float dx,
+                                                   float dy, float dz, float inv_dd, float4 A,
                                                    float4 B) {
-  const float t0 = bits_f(kSegT0Bits), t1 = bits_f(kSegT1Bits);
-  const float2 cx = make_float2(A.x, A.y), cy = make_float2(A.z, A.w), cz = make_float2(B.x, B.y);
-  float2 tc = __fmul2_rn(dot3_rn2(fsub2(cx, px), fsub2(cy, py), fsub2(cz, pz), dx, dy, dz), inv_dd);
-  tc.x = fminf(fmaxf(tc.x, t0), t1);
-  tc.y = fminf(fmaxf(tc.y, t0), t1);
-  const float2 ex = fsub2(cx, __fadd2_rn(px, __fmul2_rn(tc, dx)));
-  const float2 ey = fsub2(cy, __fadd2_rn(py, __fmul2_rn(tc, dy)));
-  const float2 ez = fsub2(cz, __fadd2_rn(pz, __fmul2_rn(tc, dz)));
-  const float2 e2 = dot3_rn2(ex, ey, ez, ex, ey, ez);
-  return e2.x < B.z || e2.y < B.w;
+  return sphere_lane_blocks(px, py, pz, dx, dy, dz, inv_dd, A.x, A.z, B.x, B.z) ||
+         sphere_lane_blocks(px, py, pz, dx, dy, dz, inv_dd, A.y, A.w, B.y, B.w);
 }
 
 // Closed slab test of one box when no component of d is zero: the entry and
@@ -109,9 +114,9 @@ __device__ __forceinline__ bool sphere_pair_blocks(float2 px, float2 py, float2 
 // packed operation; blocked when max(t0, nearer planes) <= min(t1, farther).
 __device__ __forceinline__ bool box_blocks_oblique(float2 px, float2 py, float2 pz, float2 ix,
                                                    float2 iy, float2 iz, const float2* b) {
-  const float2 tx = __fmul2_rn(fsub2(b[0], px), ix);
-  const float2 ty = __fmul2_rn(fsub2(b[1], py), iy);
-  const float2 tz = __fmul2_rn(fsub2(b[2], pz), iz);
+  const float2 tx = fmul2_rn(fsub2(b[0], px), ix);
+  const float2 ty = fmul2_rn(fsub2(b[1], py), iy);
+  const float2 tz = fmul2_rn(fsub2(b[2], pz), iz);
   const float tmin = fmaxf(fmaxf(fmaxf(bits_f(kSegT0Bits), fminf(tx.x, tx.y)), fminf(ty.x, ty.y)),
                            fminf(tz.x, tz.y));
   const float tmax = fminf(fminf(fminf(bits_f(kSegT1Bits), fmaxf(tx.x, tx.y)), fmaxf(ty.x, ty.y)),
@@ -156,11 +161,9 @@ __device__ __forceinline__ bool segment_blocked(float px, float py, float pz, fl
   const float iy = dy != 0.0f ? __fdiv_rn(1.0f, dy) : 0.0f;
   const float iz = dz != 0.0f ? __fdiv_rn(1.0f, dz) : 0.0f;
   const float2 px2 = make_float2(px, px), py2 = make_float2(py, py), pz2 = make_float2(pz, pz);
-  const float2 dx2 = make_float2(dx, dx), dy2 = make_float2(dy, dy), dz2 = make_float2(dz, dz);
   bool blocked = false;
   for (int k = 0; k < occ.n_pairs && !blocked; ++k)
-    blocked = sphere_pair_blocks(px2, py2, pz2, dx2, dy2, dz2, make_float2(inv_dd, inv_dd),
-                                 occ.sph[2 * k], occ.sph[2 * k + 1]);
+    blocked = sphere_pair_blocks(px, py, pz, dx, dy, dz, inv_dd, occ.sph[2 * k], occ.sph[2 * k + 1]);
   if (blocked) return true;
   if (dx != 0.0f && dy != 0.0f && dz != 0.0f) {
     const float2 ix2 = make_float2(ix, ix), iy2 = make_float2(iy, iy), iz2 = make_float2(iz, iz);

@@ -137,6 +137,49 @@ def test_trace_visibility_bitexact():
     assert 0.05 < got.mean() < 0.95
 
 
+def test_trace_visibility_bitexact_at_grazing_spheres():
+    """Segments that graze a sphere to within a few float32 ulps of its
+    radius, so the decision rests on the last bit of every rounding: the
+    kernel's decisions equal the oracle's float32 operations (each product
+    and sum rounded on its own) on every one of them."""
+    rng = np.random.default_rng(11)
+    n_sph, n_lt = 999, 8
+    lights = np.concatenate([rng.uniform(1, 9, (n_lt, 3)), np.ones((n_lt, 1))], 1).astype(np.float32)
+    pos = rng.uniform(1, 9, (n_sph + 1, 3)).astype(np.float32)
+    spheres = np.zeros((n_sph, 4), np.float32)
+    for s_ in range(n_sph):
+        p, l = pos[s_].astype(np.float64), lights[s_ % n_lt, :3].astype(np.float64)
+        d = l - p
+        u = np.cross(d, rng.standard_normal(3))
+        u /= np.linalg.norm(u)
+        rho = 0.05 + 0.2 * rng.uniform()
+        c = p + rng.uniform(0.2, 0.8) * d + rho * u
+        spheres[s_, :3] = c
+        # the exact distance of the float32 centre from the segment, then a
+        # radius within float32 rounding of it, either side
+        cc = spheres[s_, :3].astype(np.float64)
+        t = np.clip(np.dot(cc - p, d) / np.dot(d, d), 1e-4, 1 - 1e-4)
+        dist = np.linalg.norm(cc - (p + t * d))
+        spheres[s_, 3] = np.float32(dist * (1 + rng.uniform(-2e-6, 2e-6)))
+    sc = S.Scene(lights=lights, spheres=spheres, boxes=np.zeros((0, 6), np.float32),
+                 world_min=np.zeros(3, np.float32), world_max=np.full(3, 10, np.float32))
+    scene = nvc.Scene.from_synth(sc)
+    vis = torch.empty((len(pos), n_lt), device="cuda")
+    nvc.nvc_trace_visibility(scene, dev(pos), vis)
+    ref = O.visibility(pos, lights, spheres, np.zeros((0, 6), np.float32), np.float32)
+    got = host(vis)
+    assert np.array_equal(got, ref)
+    # each grazing segment against its own sphere alone: both outcomes occur,
+    # and float32 and float64 disagree on many (the decisions rest on rounding)
+    own32 = np.array([O.visibility(pos[i:i + 1], lights[i % n_lt:i % n_lt + 1], spheres[i:i + 1],
+                                   np.zeros((0, 6), np.float32), np.float32)[0, 0]
+                      for i in range(n_sph)])
+    own64 = np.array([O.visibility(pos[i:i + 1], lights[i % n_lt:i % n_lt + 1], spheres[i:i + 1],
+                                   np.zeros((0, 6), np.float32), np.float64)[0, 0]
+                      for i in range(n_sph)])
+    assert 0.2 < own32.mean() < 0.8 and (own32 != own64).mean() > 0.05
+
+
 # ------------------------------------------------- light weights and WRS --
 
 def test_light_weights_bitexact(tiny):
