@@ -368,6 +368,33 @@ def measure_phases(cache, scene, pos, nrm, view, seed, frame, shade_ms, cfg, gat
                 "its MLP phase (other tile streams of the SM run meanwhile)"}
 
 
+def measure_mlp_only(cache, cfg, n_px, stream, pk):
+    """The network alone on the tensor cores (nvc_mlp_infer_features: the
+    shading point's tile-stream kernel with its encode replaced by a read of
+    given layer-0 operands) over the frame's pixel count, random 16-bit
+    operands (133 MB at 1080p, more than L2) and sigmoid visibilities out;
+    flops over the CUDA-event time against the sustained tensor peak."""
+    import torch
+    from paper_2506_05930_gb300 import nvc
+    k0 = (cfg.n_levels * cfg.n_features + 15) // 16 * 16
+    dtype = torch.bfloat16 if cfg.precision == "bf16" else torch.float16
+    g = torch.Generator(device="cuda").manual_seed(5)
+    feat = (torch.rand((n_px, k0), device="cuda", generator=g) - 0.5).to(dtype)
+    vis = torch.empty((n_px, cfg.n_outputs), device="cuda")
+    try:
+        ms = _timed(stream, lambda k: nvc.nvc_mlp_infer_features(cache.handle, feat, vis), 20)
+    except Exception as e:
+        return {"unavailable": str(e)}
+    flops = 2 * algorithmic(cfg, n_px)["macs_per_px"] * n_px
+    tf = flops / (ms * 1e-3) / 1e12
+    del feat, vis
+    return {"workload": f"{n_px} pixels x {k0} 16-bit operands, MLP of the frame's network, "
+                        "sigmoid visibilities out",
+            "ms": ms, "tflops": tf, "peak_tflops": pk["bf16_sustained"],
+            "frac_of_tensor_peak": tf / pk["bf16_sustained"],
+            "io_bytes": n_px * (k0 * 2 + cfg.n_outputs * 4)}
+
+
 def _timed(stream, fn, n, warm=3):
     """Mean milliseconds of fn(k) over n calls on `stream` (CUDA events),
     after `warm` untimed calls."""
@@ -759,6 +786,7 @@ def run_ours(args):
         sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
         phases = measure_phases(cache, scene, pos, nrm, view, seed, f0 + args.steps, stage_ms[3],
                                 cfg, gather, peaks(), sm_mhz)
+    mlp_only = measure_mlp_only(cache, cfg, P, stream, peaks()) if rank == 0 and fused else None
 
     # end to end through the public API with host buffers
     pin_pos = torch.from_numpy(gb.pos).pin_memory()
@@ -900,6 +928,10 @@ def run_ours(args):
             "achieved_tflops": phases["mlp"]["tflops"], "peak_tflops": pk["bf16_sustained"],
             "frac": phases["mlp"]["frac_of_tensor_peak"], "phase_share": phases["share"]["mlp"],
             "per_tile_frac": phases["mlp"]["per_tile_frac"]}
+    if mlp_only and "tflops" in mlp_only:
+        shade_view["views"]["mlp_only_launch_vs_tensor"] = {
+            "achieved_tflops": mlp_only["tflops"], "peak_tflops": pk["bf16_sustained"],
+            "frac": mlp_only["frac_of_tensor_peak"], "ms": mlp_only["ms"]}
     roof = shade_view if stage_ms[3] >= stage_ms[2] else adam_view
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world,
@@ -927,6 +959,7 @@ def run_ours(args):
         "l2_gather_peak_gbs": gather["row8"]["useful_gbs"] if gather else None,
         "gather_bench": gather,
         "shade_phases": phases,
+        "mlp_only": mlp_only,
     }
     if base:
         line["fp32_unfused_baseline"] = base

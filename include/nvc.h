@@ -198,6 +198,18 @@ nvc_status nvc_encode(nvc_handle* h, const float* pos, int64_t n, float* feat,
 nvc_status nvc_infer(nvc_handle* h, const float* pos, int64_t n, float* vis,
                      void* stream);
 
+/* The network alone on given encodings (Section 3.3's MLP, sigmoid
+ * outputs), on the tensor cores: feat (device, 16-byte aligned) holds
+ * [n][k0] 16-bit operands in the handle's precision (FP16 or BF16), k0 =
+ * levels*F rounded up to a multiple of 16 (columns past levels*F zero;
+ * another k0 is NVC_ERR_INVALID_ARG); vis
+ * (device [n][L]) receives the visibilities.  The tile-stream shading
+ * kernel runs with its encode replaced by a read of feat: this measures the
+ * MLP's tensor-core throughput apart from the encode and the sampler.
+ * NVC_ERR_UNSUPPORTED for FP32 or E4M3 operands or n_outputs > 32. */
+nvc_status nvc_mlp_infer_features(nvc_handle* h, const void* feat, int64_t n, int32_t k0,
+                                  float* vis, void* stream);
+
 /* ---- light sampling (Sections 3.1, 3.2) -------------------------------- */
 
 /* Light weights: c (device [n][L]) = unshadowed contribution of each point

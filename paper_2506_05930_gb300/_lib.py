@@ -99,6 +99,7 @@ PROTOTYPES = {
     "nvc_autotune_shade": (c_int32, [_vp, _scp, _vp, _vp, c_int64, _vp, _vp, _vp, _vp, c_int32,
                                      POINTER(c_int32), POINTER(c_double), _vp]),
     "nvc_set_shade_variant": (c_int32, [_vp, c_int32]),
+    "nvc_mlp_infer_features": (c_int32, [_vp, _vp, c_int64, c_int32, _vp, _vp]),
     "nvc_set_shade_plan": (c_int32, [_vp, POINTER(NvcShadePlan)]),
     "nvc_autotune_shade_plan": (c_int32, [_vp, _scp, _vp, _vp, c_int64, _vp, _vp, _vp, _vp, c_int32,
                                           POINTER(NvcShadePlan), POINTER(NvcShadePlan),

@@ -530,6 +530,27 @@ nvc_status nvc_infer(nvc_handle* h, const float* pos, int64_t n, float* vis, voi
   return NVC_OK;
 }
 
+nvc_status nvc_mlp_infer_features(nvc_handle* h, const void* feat, int64_t n, int32_t k0,
+                                  float* vis, void* stream) {
+  if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
+  if (h->cfg.precision != NVC_PREC_FP16 && h->cfg.precision != NVC_PREC_BF16)
+    return fail(h, NVC_ERR_UNSUPPORTED, "feature inference needs FP16 or BF16 operands");
+  if (h->L > 32) return fail(h, NVC_ERR_UNSUPPORTED, "feature inference needs n_outputs <= 32");
+  if (k0 != (h->din + 15) / 16 * 16)
+    return fail(h, NVC_ERR_INVALID_ARG, "feat rows must hold %d operands", (h->din + 15) / 16 * 16);
+  if (n < 0) return fail(h, NVC_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NVC_OK;
+  NVC_TRY(check_ptr(h, feat, "feat", 16));
+  NVC_TRY(check_ptr(h, vis, "vis"));
+  std::string why;
+  if (!fused_supported(h, &why)) return fail(h, NVC_ERR_UNSUPPORTED, "%s", why.c_str());
+  const FusedView v{nullptr, nullptr, n, 0, 0, nullptr, nullptr, nullptr, nullptr, vis, nullptr};
+  NVC_CUDA(h, launch_shade_fused_views(h, nullptr, &v, 1, 0, 0, (cudaStream_t)stream, nullptr,
+                                       static_cast<const uint16_t*>(feat)));
+  count_launches(h, 1);
+  return NVC_OK;
+}
+
 nvc_status nvc_light_weights(const nvc_scene* scene, const float* pos, const float* nrm,
                              const float* vis, int64_t n, float* c, float* w, void* stream) {
   NVC_TRY(check_scene(nullptr, scene, 0));

@@ -78,6 +78,9 @@ struct FusedArgs {
   // resident CTAs per SM the launch may use (the autotuner's occupancy
   // knob); 0 = as many as fit
   int max_ctas_per_sm;
+  // MLP-only launches (nvc_mlp_infer_features): the layer-0 operands,
+  // [n][layer[0].K] 16-bit values, read instead of encoding; NULL otherwise
+  const uint16_t* feat16;
 };
 
 // ---- the encode's chunks of CH features -------------------------------------

@@ -53,12 +53,14 @@ __device__ __forceinline__ bool group_sync_or(int g, bool v) {
   return r != 0;
 }
 
+// FEAT: the MLP-only instantiation (nvc_mlp_infer_features): the tile's
+// layer-0 operands are read from a.feat16 instead of encoded.
 // STAMP: the phase-profile instantiation (nvc_shade_phases).  Thread 0 of
 // each group reads the SM clock at four points of every tile -- tile start,
 // the encoded A tile complete, the output layer's accumulator read, the end
 // of the tile's sampler -- and adds the phases' cycles to a.phase_cycles
 // once at exit; outputs are the same as the plain instantiation's.
-template <int F, int PREC, int TPC, bool FULL, bool STAMP>
+template <int F, int PREC, int TPC, bool FULL, bool STAMP, bool FEAT = false>
 __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
     fused_shade_multi_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int kThreads = kTileM * TPC;
@@ -130,13 +132,18 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
     const int64_t row = (tile - V.tile_start) * kTileM + rw;
     const bool live = row < V.n;
     float px = 0.f, py = 0.f, pz = 0.f;
-    if (live) {
+    if (live && !FEAT) {
       px = __ldg(V.pos + 3 * row);
       py = __ldg(V.pos + 3 * row + 1);
       pz = __ldg(V.pos + 3 * row + 2);
     }
     // ---- encode ------------------------------------------------------------
-    {
+    if constexpr (FEAT) {
+      const uint4* src = reinterpret_cast<const uint4*>(a.feat16 + row * K0);
+      for (int c = 0; c < K0 / CH; ++c)
+        *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, 2)) =
+            live ? __ldg(src + c) : make_uint4(0u, 0u, 0u, 0u);
+    } else {
       const float x = normalise(px, a.ep.lo[0], a.ep.ext[0]);
       const float y = normalise(py, a.ep.lo[1], a.ep.ext[1]);
       const float z = normalise(pz, a.ep.lo[2], a.ep.ext[2]);
@@ -204,7 +211,28 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
         cyc[1] += (unsigned long long)(c - c_mark);
         c_mark = c;
       }
-      if (V.vis_out) {
+      if (V.vis_out && L == 32 && (reinterpret_cast<uintptr_t>(V.vis_out) & 15) == 0) {
+        // the tile's 128 x 32 visibilities are one contiguous block: staged
+        // in the idle activation tile (row rw's float4 q at slot q ^ (rw & 7),
+        // so a warp's writes spread over the banks), then stored by the
+        // group in consecutive 16-byte pieces
+        float4* s_v = reinterpret_cast<float4*>(s_a);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          s_v[rw * 8 + (q ^ (rw & 7))] =
+              make_float4(sigmoid_fast(__uint_as_float(r[4 * q])),
+                          sigmoid_fast(__uint_as_float(r[4 * q + 1])),
+                          sigmoid_fast(__uint_as_float(r[4 * q + 2])),
+                          sigmoid_fast(__uint_as_float(r[4 * q + 3])));
+        group_sync(g);
+        const int64_t row0 = (tile - V.tile_start) * kTileM;
+        float4* dst = reinterpret_cast<float4*>(V.vis_out + row0 * 32);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) {
+          const int e = rw + k2 * kTileM, rr = e >> 3, q = e & 7;
+          if (row0 + rr < V.n) dst[e] = s_v[rr * 8 + (q ^ (rr & 7))];
+        }
+      } else if (V.vis_out) {
         if (live) {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
@@ -374,6 +402,9 @@ cudaError_t launch_multi_typed(FusedArgs a, size_t smem_needed, int num_sms, cud
   if (a.phase_cycles)
     kern = full ? fused_shade_multi_kernel<F, PREC, TPC, true, true>
                 : fused_shade_multi_kernel<F, PREC, TPC, false, true>;
+  if (a.feat16)
+    kern = full ? fused_shade_multi_kernel<F, PREC, TPC, true, false, true>
+                : fused_shade_multi_kernel<F, PREC, TPC, false, false, true>;
   a.multi_cols = (int)a.tmem_cols;              // per group
   a.tmem_cols = a.tmem_cols * (uint32_t)TPC;    // per CTA (a power of two)
   if (a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;

@@ -1176,9 +1176,10 @@ bool fused_supported(const nvc_handle* h, std::string* why) {
 cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
                                      const FusedView* views, int n_views, uint64_t seed,
                                      uint32_t frame, cudaStream_t s,
-                                     unsigned long long* phase_cycles) {
+                                     unsigned long long* phase_cycles, const uint16_t* feat16) {
   // views beyond one launch's table go to further launches
   if (n_views > kMaxViews) {
+    if (feat16) return cudaErrorInvalidValue;   // one view of features per launch
     cudaError_t e = launch_shade_fused_views(h, sc, views, kMaxViews, seed, frame, s, phase_cycles);
     if (e != cudaSuccess) return e;
     return launch_shade_fused_views(h, sc, views + kMaxViews, n_views - kMaxViews, seed, frame, s,
@@ -1238,6 +1239,14 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
   a.fp8_scales = h->fp8_scales;
   a.phase_cycles = phase_cycles;
   a.max_ctas_per_sm = h->shade_ctas_per_sm;
+  a.feat16 = feat16;
+  if (feat16) {
+    // the MLP-only launch runs the tile-stream kernel (two streams per CTA
+    // when the handle's shading point is variant 6, else four)
+    if (h->cfg.precision == NVC_PREC_FP8 || h->L > 32) return cudaErrorInvalidValue;
+    return launch_shade_multi(a, h, p, h->shade_variant == kShadeMulti2 ? 2 : 4,
+                              h->cfg.precision == NVC_PREC_BF16, s);
+  }
   if (h->cfg.precision == NVC_PREC_FP8) {
     const size_t smem8 = fused_smem(h, p, &a);
     switch (h->F) {

@@ -343,7 +343,8 @@ struct FusedView {
 cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
                                      const FusedView* views, int n_views, uint64_t seed,
                                      uint32_t frame, cudaStream_t s,
-                                     unsigned long long* phase_cycles = nullptr);
+                                     unsigned long long* phase_cycles = nullptr,
+                                     const uint16_t* feat16 = nullptr);
 
 // train_tc.cu
 bool train_tc_supported(const nvc_handle* h, std::string* why);

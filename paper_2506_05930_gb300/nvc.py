@@ -171,6 +171,19 @@ def nvc_encode(h, pos, feat, stream=None):
                          _stream(stream)), h)
 
 
+def nvc_mlp_infer_features(h, feat, vis, stream=None):
+    """feat: CUDA [n][K0] float16 or bfloat16 tensor (the handle's operand
+    type), vis: CUDA [n][L] float32."""
+    if not isinstance(feat, torch.Tensor) or not feat.is_cuda or feat.dim() != 2:
+        raise ValueError("feat must be a 2-D CUDA tensor")
+    if feat.dtype not in (torch.float16, torch.bfloat16) or not feat.is_contiguous():
+        raise ValueError("feat must be contiguous float16 or bfloat16")
+    if vis.shape[0] != feat.shape[0]:
+        raise ValueError("feat and vis must have the same number of rows")
+    check(lib.nvc_mlp_infer_features(h, feat.data_ptr(), feat.shape[0], feat.shape[1],
+                                     _ptr(vis, name="vis"), _stream(stream)), h)
+
+
 def nvc_infer(h, pos, vis, stream=None):
     check(lib.nvc_infer(h, _ptr(pos, name="pos"), pos.shape[0], _ptr(vis, name="vis"),
                         _stream(stream)), h)

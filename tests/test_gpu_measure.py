@@ -73,3 +73,36 @@ def test_gather_bench_sums_rows_of_the_table(row_bytes):
     s = sink.cpu().numpy()
     assert len(np.unique(s)) > n_threads // 2
     assert s.min() >= 0 and s.max() <= rows * row_bytes / 4 * n_floats
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_mlp_on_given_features_matches_oracle(precision):
+    """The MLP-only launch (the network's throughput apart from the encode):
+    sigmoid(MLP(feat)) of given 16-bit operands, within the FP16/BF16 bound
+    of the float64 oracle on the same operands, over a ragged last tile;
+    both tile-stream layouts give the same bits; a wrong row width is an
+    argument error."""
+    from oracle import nvc as O
+    cfg = cfg_frame(precision=precision, batch_positions=256)
+    cache = nvc.VisibilityCache(cfg)
+    p = scaled_params(cfg, seed=3, table_scale=0.5)
+    cache.set_params(p)
+    n, k0 = 5000, 32
+    rng = np.random.default_rng(7)
+    dtype = torch.float16 if precision == "fp16" else torch.bfloat16
+    feat = torch.as_tensor(rng.uniform(-0.6, 0.6, (n, k0)).astype(np.float32)).to("cuda", dtype)
+    outs = []
+    for variant in (7, 6):
+        nvc.nvc_set_shade_variant(cache.handle, variant)
+        vis = torch.full((n, cfg.n_outputs), -1.0, device="cuda")
+        nvc.nvc_mlp_infer_features(cache.handle, feat, vis)
+        outs.append(vis.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    _, Ws = O.split_params(cfg, p)
+    logits, _, _ = O.mlp_forward(Ws, feat.float().cpu().numpy().astype(np.float64), cfg.leaky_slope)
+    ref = 1.0 / (1.0 + np.exp(-logits))
+    tol = 2e-3 if precision == "fp16" else 2e-2
+    assert np.max(np.abs(outs[0] - ref)) < tol
+    with pytest.raises(_lib.NVCError):
+        nvc.nvc_mlp_infer_features(cache.handle, feat[:, :16].contiguous(), vis)
+    cache.close()
