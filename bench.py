@@ -247,7 +247,7 @@ def clustered_alu_ops(n_lights, k, n_pixels):
 # profiles/ (None once the kernel has changed since that capture).
 KERNEL_TRAFFIC = {"fused_shade": 83.67e6, "adam": None,
                   # 1080p launch with the shadow ray (light, W and estimate written)
-                  "sample_clustered": None}
+                  "sample_clustered": 336.44e6}
 
 
 # ------------------------------------------------------------- our arm ----

@@ -78,8 +78,9 @@ def test_gather_bench_sums_rows_of_the_table(row_bytes):
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
 def test_mlp_on_given_features_matches_oracle(precision):
     """The MLP-only launch (the network's throughput apart from the encode):
-    sigmoid(MLP(feat)) of given 16-bit operands, within the FP16/BF16 bound
-    of the float64 oracle on the same operands, over a ragged last tile;
+    sigmoid(MLP(feat)) of given 16-bit operands, within about three times the
+    measured FP16/BF16 error of the float64 oracle on the same operands, over
+    a ragged last tile;
     both tile-stream layouts give the same bits; a wrong row width is an
     argument error."""
     from oracle import nvc as O
@@ -101,7 +102,8 @@ def test_mlp_on_given_features_matches_oracle(precision):
     _, Ws = O.split_params(cfg, p)
     logits, _, _ = O.mlp_forward(Ws, feat.float().cpu().numpy().astype(np.float64), cfg.leaky_slope)
     ref = 1.0 / (1.0 + np.exp(-logits))
-    tol = 2e-3 if precision == "fp16" else 2e-2
+    # measured on GB300: max 9.2e-5 (FP16), 8.4e-4 (BF16); bounds about 3x that
+    tol = 3e-4 if precision == "fp16" else 2.5e-3
     assert np.max(np.abs(outs[0] - ref)) < tol
     with pytest.raises(_lib.NVCError):
         nvc.nvc_mlp_infer_features(cache.handle, feat[:, :16].contiguous(), vis)
