@@ -1110,8 +1110,11 @@ static nvc_status train_step_impl(nvc_handle* h, const nvc_scene* scene, const f
   NVC_TRY(train_forward_backward(h, scene, screen_pos, n_screen, seed, frame, s, clusters));
   StageScope sc(h, s, 2);
   NVC_CUDA(h, launch_adam(h, loss_out, true, s));
-  NVC_CUDA(h, launch_pack_mlp(h, s));
-  count_launches(h, 2 + (h->mlp_packed ? 1 : 0));
+  // the Adam kernel rewrites a 16-bit weight image itself; E4M3 repacks
+  MlpImageMap mp;
+  const bool in_adam = mlp_image_map(h, &mp);
+  if (!in_adam) NVC_CUDA(h, launch_pack_mlp(h, s));
+  count_launches(h, 2 + (h->mlp_packed && !in_adam ? 1 : 0));
   return NVC_OK;
 }
 

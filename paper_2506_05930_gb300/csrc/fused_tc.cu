@@ -1113,6 +1113,24 @@ size_t mlp_packed_bytes(const nvc_handle* h) {
   return (size_t)p.byte_off[p.n_layers];
 }
 
+bool mlp_image_map(const nvc_handle* h, MlpImageMap* m) {
+  if (!h->mlp_packed || h->cfg.precision == NVC_PREC_FP8 || h->cfg.precision == NVC_PREC_FP32)
+    return false;
+  PackArgs p{};
+  layer_geometry(h, p);
+  m->n_layers = p.n_layers;
+  for (int k = 0; k < p.n_layers; ++k) {
+    m->w_off[k] = p.w_off[k];
+    m->K_real[k] = p.K_real[k];
+    m->K[k] = p.K[k];
+    m->byte_off[k] = p.byte_off[k];
+  }
+  m->w_off[p.n_layers] = p.w_off[p.n_layers - 1] + (int64_t)p.N_real[p.n_layers - 1] *
+                                                       p.K_real[p.n_layers - 1];
+  m->bf16 = h->cfg.precision == NVC_PREC_BF16;
+  return true;
+}
+
 cudaError_t launch_pack_mlp(nvc_handle* h, cudaStream_t s) {
   if (!h->mlp_packed) return cudaSuccess;
   PackArgs p{};

@@ -157,6 +157,19 @@ enum ShadeVariant : int {
   kShadeVariants = 8
 };
 
+// Where each MLP weight sits in the tensor cores' 16-bit weight image (the
+// layout pack_mlp_kernel writes): layer k's W[n][kk] (parameter w_off[k] +
+// n K_real + kk) is element ((n/8) (K/8) + kk/8) 64 + (n%8) 8 + kk%8 of the
+// layer's block at byte_off[k].  The Adam kernel uses it to refresh the
+// image from the updated weights in the same pass.
+struct MlpImageMap {
+  int n_layers;
+  int64_t w_off[NVC_MAX_HIDDEN_LAYERS + 2];   // [n_layers] = end of the last layer
+  int K_real[NVC_MAX_HIDDEN_LAYERS + 1], K[NVC_MAX_HIDDEN_LAYERS + 1];
+  int byte_off[NVC_MAX_HIDDEN_LAYERS + 1];
+  int bf16;
+};
+
 // Adam scalars written on the device each step.
 struct AdamScalars {
   float lr_over_bc1;     // lr / (1 - b1^t)
@@ -315,6 +328,10 @@ cudaError_t launch_finish_gradient(nvc_handle* h, float* grad_out, double* loss_
 
 // fused_tc.cu
 cudaError_t launch_pack_mlp(nvc_handle* h, cudaStream_t s);
+// The image map of the handle's 16-bit weight image; false when there is
+// none to keep (float32 inference, or E4M3, whose per-layer scales need
+// the whole layer).
+bool mlp_image_map(const nvc_handle* h, MlpImageMap* m);
 // Refreshes the half-precision table copy from the master (no-op without one).
 cudaError_t launch_pack_table(nvc_handle* h, cudaStream_t s);
 bool fused_supported(const nvc_handle* h, std::string* why);

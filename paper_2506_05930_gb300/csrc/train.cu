@@ -170,15 +170,31 @@ __device__ __forceinline__ bool nonzero4(float4 g) {
   return g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f;
 }
 
+// Element j (an MLP weight) of the 16-bit weight image, set to v.
+__device__ __forceinline__ void set_image(const MlpImageMap& mp, uint8_t* img, int64_t j, float v) {
+  int k = 0;
+  while (k + 1 < mp.n_layers && j >= mp.w_off[k + 1]) ++k;
+  const int64_t lj = j - mp.w_off[k];
+  const int n = (int)(lj / mp.K_real[k]), kk = (int)(lj - (int64_t)n * mp.K_real[k]);
+  const int local = ((((n >> 3) * (mp.K[k] >> 3)) + (kk >> 3)) << 6) + ((n & 7) << 3) + (kk & 7);
+  if (mp.bf16)
+    reinterpret_cast<__nv_bfloat16*>(img + mp.byte_off[k])[local] = __float2bfloat16_rn(v);
+  else
+    reinterpret_cast<__half*>(img + mp.byte_off[k])[local] = __float2half_rn(v);
+}
+
 // table16 (may be NULL): the half-precision copy of the first 4 n_table4
-// parameters (the hash table), rewritten from the updated values.
+// parameters (the hash table), rewritten from the updated values.  img (may
+// be NULL): the tensor cores' 16-bit weight image, whose MLP weights are
+// rewritten from the updated values (the separate packing pass's job).
 __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
                                                    float* __restrict__ grad,
                                                    float* __restrict__ m, float* __restrict__ v,
                                                    int64_t n4, int64_t n, float beta1,
                                                    float beta2, float eps,
                                                    const AdamScalars* __restrict__ scp,
-                                                   uint2* __restrict__ table16, int64_t n_table4) {
+                                                   uint2* __restrict__ table16, int64_t n_table4,
+                                                   MlpImageMap mp, uint8_t* __restrict__ img) {
   const AdamScalars sc = *scp;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,6 +238,11 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
         table16[ee] = make_uint2(*reinterpret_cast<const uint32_t*>(&a),
                                  *reinterpret_cast<const uint32_t*>(&b));
       }
+      if (img != nullptr && 4 * ee >= mp.w_off[0] && 4 * ee < mp.w_off[mp.n_layers]) {
+        const float tv[4] = {th[u].x, th[u].y, th[u].z, th[u].w};
+        for (int c = 0; c < 4; ++c)
+          if (4 * ee + c < mp.w_off[mp.n_layers]) set_image(mp, img, 4 * ee + c, tv[c]);
+      }
       __stcs(m4 + ee, mm[u]);
       __stcs(v4 + ee, vv[u]);
       if (nonzero4(g[u])) __stcs(g4 + ee, zero);
@@ -231,6 +252,8 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
     const float g = grad[e];
     grad[e] = 0.0f;
     adam_scalar(theta[e], g, m[e], v[e], sc, beta1, beta2, eps);
+    if (img != nullptr && e >= mp.w_off[0] && e < mp.w_off[mp.n_layers])
+      set_image(mp, img, e, theta[e]);
   }
 }
 
@@ -322,9 +345,11 @@ cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_
   if (e != cudaSuccess || !apply) return e;
   const int64_t n4 = h->n_params / 4;
   const int blocks = h->num_sms * 8;
+  MlpImageMap mp{};
+  uint8_t* img = mlp_image_map(h, &mp) ? static_cast<uint8_t*>(h->mlp_packed) : nullptr;
   adam_kernel<<<blocks, 256, 0, s>>>(h->params, h->grad, h->adam_m, h->adam_v, n4, h->n_params,
                                      c.beta1, c.beta2, c.eps, h->adam_scalars,
-                                     reinterpret_cast<uint2*>(h->table16), h->n_table / 4);
+                                     reinterpret_cast<uint2*>(h->table16), h->n_table / 4, mp, img);
   return cudaGetLastError();
 }
 

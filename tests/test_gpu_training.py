@@ -246,3 +246,34 @@ def test_fused_training_data_steps_and_frames_train():
         cache.close()
     np.testing.assert_allclose(losses[True], losses[False], rtol=1e-3)
     assert losses[True][-1] < losses[True][0]
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_adam_refreshes_the_weight_image_and_table_copy(precision):
+    """The Adam kernel writes the tensor cores' 16-bit weight image and the
+    half-precision table copy from the updated weights (no separate packing
+    pass): after training steps, shading equals that of a fresh handle given
+    the same state (whose image and copy are packed from it), bit for bit."""
+    from helpers import cfg_frame, scaled_params
+    cfg = cfg_frame(precision=precision, train_precision="fp16", batch_positions=256)
+    sc = S.scene_heightfield(seed=3, n_lights=32, n_spheres=16, n_boxes=16)
+    gb = S.gbuffer_heightfield(seed=3, width=97, height=61)
+    scene = nvc.Scene.from_synth(sc)
+    pos = torch.from_numpy(gb.pos).cuda()
+    nrm = torch.from_numpy(gb.nrm).cuda()
+    a = nvc.VisibilityCache(cfg)
+    a.set_params(scaled_params(cfg, seed=4, table_scale=0.5))
+    for f in range(3):
+        a.train_step(scene, pos, 1, f)
+    p, m, v = a.state()
+    b = nvc.VisibilityCache(cfg)
+    b.set_params(p, m, v, step=a.counters()["step"])
+    for cache in (a, b):
+        nvc.nvc_set_shade_variant(cache.handle, 7)
+    oa = a.shade(scene, pos, nrm, seed=2, frame=5, fused=True)
+    ob = b.shade(scene, pos, nrm, seed=2, frame=5, fused=True)
+    for k in oa:
+        assert torch.equal(oa[k], ob[k]), k
+    assert a.counters()["step"] == 3
+    a.close()
+    b.close()
