@@ -303,7 +303,7 @@ nvc_status nvc_create(const nvc_config* cfg, nvc_handle** out) {
       (e = dalloc(&h->t_logits, B * h->L)) ||
       (e = dalloc(&h->t_delta, (size_t)h->n_layers * B * maxdim)) ||
       (e = dalloc(&h->t_dfeat, B * h->din)) || (e = dalloc(&h->loss_partials, 256)) ||
-      (e = dalloc(&h->status, kStWords)) || (e = dalloc(&h->adam_scalars, 1)) ||
+      (e = dalloc(&h->status, kStWords)) ||
       (e = dalloc(&h->phase_cycles, 4)))
     return cleanup_fail(e, "cudaMalloc");
   h->n_loss_partials = 256;
@@ -367,7 +367,6 @@ void nvc_destroy(nvc_handle* h) {
   cudaFree(h->loss_partials);
   cudaFree(h->status);
   cudaFree(h->phase_cycles);
-  cudaFree(h->adam_scalars);
   cudaFree(h->fp8_scales);
   cudaFree(h->s_feat);
   cudaFree(h->s_vis);
@@ -1114,7 +1113,7 @@ static nvc_status train_step_impl(nvc_handle* h, const nvc_scene* scene, const f
   MlpImageMap mp;
   const bool in_adam = mlp_image_map(h, &mp);
   if (!in_adam) NVC_CUDA(h, launch_pack_mlp(h, s));
-  count_launches(h, 2 + (h->mlp_packed && !in_adam ? 1 : 0));
+  count_launches(h, 1 + (h->mlp_packed && !in_adam ? 1 : 0));
   return NVC_OK;
 }
 

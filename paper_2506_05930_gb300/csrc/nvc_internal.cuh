@@ -140,7 +140,8 @@ enum StatusWord : int {
   kStSkipNow = 5,     // Adam of the current step is skipped
   kStTileNext = 6,    // shading tile scheduler: next tile ticket (0 between launches)
   kStTileDone = 7,    // shading tile scheduler: tile streams finished (0 between launches)
-  kStWords = 8
+  kStAdamDone = 8,    // Adam CTAs finished (0 between launches)
+  kStWords = 16
 };
 enum : int { kFlagNonFinite = 1, kFlagTimeout = 2 };
 
@@ -232,7 +233,6 @@ struct nvc_handle {
   int loss_blocks = 0;                  // partials written by the last training pass
   int32_t* status = nullptr;            // nvc::kStWords
   unsigned long long* phase_cycles = nullptr;   // [4], nvc_shade_phases
-  nvc::AdamScalars* adam_scalars = nullptr;
 
   // staging of the unfused shading path
   int64_t stage_pixels = 0;

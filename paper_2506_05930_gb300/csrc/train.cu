@@ -113,39 +113,67 @@ __device__ __forceinline__ double pow_int(double b, int t) {
   return r;
 }
 
-// Prologue (one warp): loss = sum of partials / count; decide whether this
-// step applies (all gradients finite); step counter, bias corrections and
-// the scheduled learning rate.
-__global__ void adam_prologue_kernel(const double* __restrict__ partials, int n_partials,
-                                     double inv_count, double* loss_out, int32_t* status,
-                                     AdamScalars* sc, int apply, int schedule, float lr0,
-                                     float lr_end, int ramp, double beta1, double beta2,
-                                     float inv_scale) {
+// The step's constants, read from the loss partials and the status words
+// (not changed here): loss = sum of partials (lane-strided over one warp,
+// then a shuffle tree) x inv_count; whether the step applies (all gradients
+// finite); step t, bias corrections and the scheduled learning rate.
+struct StepPlan {
+  AdamScalars sc;
+  double loss_sum;
+  int t;
+  bool nonfinite;
+};
+
+struct StepArgs {
+  const double* partials;
+  int n_partials;
+  int schedule, ramp;
+  float lr0, lr_end, inv_scale;
+  double beta1, beta2;
+};
+
+// Called by all 32 lanes of one warp; lane 0's result is the plan.
+__device__ __forceinline__ StepPlan plan_step(const StepArgs& a, const int32_t* status) {
+  StepPlan pl{};
   double s = 0.0;
-  for (int i = threadIdx.x; i < n_partials; i += 32) s += partials[i];
+  for (int i = threadIdx.x & 31; i < a.n_partials; i += 32) s += a.partials[i];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (threadIdx.x != 0) return;
-  if (loss_out) *loss_out = s * inv_count;
-  const bool nonfinite = status[kStNonFinite] != 0;
+  pl.loss_sum = s;
+  pl.nonfinite = status[kStNonFinite] != 0;
+  pl.t = status[kStStep] + 1;
+  double lr = a.lr0;
+  if (a.schedule == NVC_LR_RAMP) {
+    const int k = pl.t - 1 < a.ramp ? pl.t - 1 : a.ramp;
+    lr = (double)a.lr0 + ((double)a.lr_end - (double)a.lr0) * (double)k / (double)a.ramp;
+  }
+  pl.sc.lr_over_bc1 = (float)(lr / (1.0 - pow_int(a.beta1, pl.t)));
+  pl.sc.inv_bc2 = (float)(1.0 / (1.0 - pow_int(a.beta2, pl.t)));
+  pl.sc.inv_scale = a.inv_scale;
+  pl.sc.skip = pl.nonfinite ? 1 : 0;
+  return pl;
+}
+
+// The step's bookkeeping, once: the loss, the non-finite flag cleared for
+// the next step, and either the step count or the skip count and flag.
+__device__ __forceinline__ void commit_step(const StepPlan& pl, bool apply, double inv_count,
+                                            double* loss_out, int32_t* status) {
+  if (loss_out) *loss_out = pl.loss_sum * inv_count;
   status[kStNonFinite] = 0;
   if (!apply) return;
-  if (nonfinite) {
+  if (pl.nonfinite) {
     status[kStSkipped] += 1;
     status[kStFlags] |= kFlagNonFinite;
-    sc->skip = 1;
-    return;
+  } else {
+    status[kStStep] = pl.t;
   }
-  const int t = status[kStStep] + 1;
-  status[kStStep] = t;
-  double lr = lr0;
-  if (schedule == NVC_LR_RAMP) {
-    const int k = t - 1 < ramp ? t - 1 : ramp;
-    lr = (double)lr0 + ((double)lr_end - (double)lr0) * (double)k / (double)ramp;
-  }
-  sc->lr_over_bc1 = (float)(lr / (1.0 - pow_int(beta1, t)));
-  sc->inv_bc2 = (float)(1.0 / (1.0 - pow_int(beta2, t)));
-  sc->inv_scale = inv_scale;
-  sc->skip = 0;
+}
+
+// Prologue alone (one warp), for the gradient-only calls: the loss and the
+// non-finite flag, no update.
+__global__ void adam_prologue_kernel(StepArgs a, double inv_count, double* loss_out,
+                                     int32_t* status) {
+  const StepPlan pl = plan_step(a, status);
+  if (threadIdx.x == 0) commit_step(pl, false, inv_count, loss_out, status);
 }
 
 // theta -= (lr / bc1) m / (sqrt(v / bc2) + eps), after m, v updates with the
@@ -183,29 +211,17 @@ __device__ __forceinline__ void set_image(const MlpImageMap& mp, uint8_t* img, i
     reinterpret_cast<__half*>(img + mp.byte_off[k])[local] = __float2half_rn(v);
 }
 
-// table16 (may be NULL): the half-precision copy of the first 4 n_table4
-// parameters (the hash table), rewritten from the updated values.  img (may
-// be NULL): the tensor cores' 16-bit weight image, whose MLP weights are
-// rewritten from the updated values (the separate packing pass's job).
-__global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
-                                                   float* __restrict__ grad,
-                                                   float* __restrict__ m, float* __restrict__ v,
-                                                   int64_t n4, int64_t n, float beta1,
-                                                   float beta2, float eps,
-                                                   const AdamScalars* __restrict__ scp,
-                                                   uint2* __restrict__ table16, int64_t n_table4,
-                                                   MlpImageMap mp, uint8_t* __restrict__ img) {
-  const AdamScalars sc = *scp;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// The update proper (sc.skip == 0): grid-stride over float4 groups, two at
+// a time, then the tail scalars.
+__device__ __forceinline__ void adam_update(float* __restrict__ theta, float* __restrict__ grad,
+                                            float* __restrict__ m, float* __restrict__ v,
+                                            int64_t n4, int64_t n, float beta1, float beta2,
+                                            float eps, const AdamScalars& sc,
+                                            uint2* __restrict__ table16, int64_t n_table4,
+                                            const MlpImageMap& mp, uint8_t* __restrict__ img,
+                                            int64_t t0, int64_t stride) {
   float4* g4 = reinterpret_cast<float4*>(grad);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (sc.skip) {
-    for (int64_t e = t0; e < n4; e += stride)
-      if (nonzero4(g4[e])) g4[e] = zero;
-    for (int64_t e = 4 * n4 + t0; e < n; e += stride) grad[e] = 0.0f;
-    return;
-  }
   float4* th4 = reinterpret_cast<float4*>(theta);
   float4* m4 = reinterpret_cast<float4*>(m);
   float4* v4 = reinterpret_cast<float4*>(v);
@@ -256,6 +272,52 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
       set_image(mp, img, e, theta[e]);
   }
 }
+
+// table16 (may be NULL): the half-precision copy of the first 4 n_table4
+// parameters (the hash table), rewritten from the updated values.  img (may
+// be NULL): the tensor cores' 16-bit weight image, whose MLP weights are
+// rewritten from the updated values (the separate packing pass's job).
+__global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
+                                                   float* __restrict__ grad,
+                                                   float* __restrict__ m, float* __restrict__ v,
+                                                   int64_t n4, int64_t n, float beta1,
+                                                   float beta2, float eps,
+                                                   StepArgs step, double inv_count,
+                                                   double* loss_out, int32_t* status,
+                                                   uint2* __restrict__ table16, int64_t n_table4,
+                                                   MlpImageMap mp, uint8_t* __restrict__ img) {
+  // every CTA plans the step from the same inputs (warp 0); the last CTA to
+  // finish commits its bookkeeping, after every CTA has read the status
+  __shared__ StepPlan s_plan;
+  if (threadIdx.x < 32) {
+    const StepPlan pl = plan_step(step, status);
+    if (threadIdx.x == 0) s_plan = pl;
+  }
+  __syncthreads();
+  const AdamScalars sc = s_plan.sc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float4* g4 = reinterpret_cast<float4*>(grad);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (sc.skip) {
+    for (int64_t e = t0; e < n4; e += stride)
+      if (nonzero4(g4[e])) g4[e] = zero;
+    for (int64_t e = 4 * n4 + t0; e < n; e += stride) grad[e] = 0.0f;
+  } else {
+    adam_update(theta, grad, m, v, n4, n, beta1, beta2, eps, sc, table16, n_table4, mp, img,
+                t0, stride);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    uint32_t* done = reinterpret_cast<uint32_t*>(status + kStAdamDone);
+    if (atomicAdd(done, 1u) == gridDim.x - 1) {
+      commit_step(s_plan, true, inv_count, loss_out, status);
+      atomicExch(done, 0u);
+    }
+  }
+}
+
 
 // Copy (and unscale) the accumulated gradient out, clearing it.
 __global__ void take_gradient_kernel(float* __restrict__ grad, float* __restrict__ out, int64_t n,
@@ -336,19 +398,28 @@ cudaError_t launch_loss_grad(nvc_handle* h, int64_t n, cudaStream_t s) {
 cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_t s) {
   const nvc_config& c = h->cfg;
   const double inv_count = 1.0 / ((double)h->B * (double)h->L);
-  const int n_partials = h->loss_blocks > 0 ? h->loss_blocks : kLossBlocks;
-  adam_prologue_kernel<<<1, 32, 0, s>>>(h->loss_partials, n_partials, inv_count, loss_out,
-                                        h->status, h->adam_scalars, apply ? 1 : 0, c.lr_schedule,
-                                        c.lr, c.lr_end, c.lr_ramp_steps, (double)c.beta1,
-                                        (double)c.beta2, 1.0f / c.loss_scale);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !apply) return e;
+  StepArgs a{};
+  a.partials = h->loss_partials;
+  a.n_partials = h->loss_blocks > 0 ? h->loss_blocks : kLossBlocks;
+  a.schedule = c.lr_schedule;
+  a.ramp = c.lr_ramp_steps;
+  a.lr0 = c.lr;
+  a.lr_end = c.lr_end;
+  a.inv_scale = 1.0f / c.loss_scale;
+  a.beta1 = (double)c.beta1;
+  a.beta2 = (double)c.beta2;
+  if (!apply) {
+    adam_prologue_kernel<<<1, 32, 0, s>>>(a, inv_count, loss_out, h->status);
+    return cudaGetLastError();
+  }
+  // the step's loss, skip decision and scalars are derived inside the
+  // update kernel (one launch)
   const int64_t n4 = h->n_params / 4;
   const int blocks = h->num_sms * 8;
   MlpImageMap mp{};
   uint8_t* img = mlp_image_map(h, &mp) ? static_cast<uint8_t*>(h->mlp_packed) : nullptr;
   adam_kernel<<<blocks, 256, 0, s>>>(h->params, h->grad, h->adam_m, h->adam_v, n4, h->n_params,
-                                     c.beta1, c.beta2, c.eps, h->adam_scalars,
+                                     c.beta1, c.beta2, c.eps, a, inv_count, loss_out, h->status,
                                      reinterpret_cast<uint2*>(h->table16), h->n_table / 4, mp, img);
   return cudaGetLastError();
 }
