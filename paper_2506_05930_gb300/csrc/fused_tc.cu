@@ -233,6 +233,15 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
             for (int j = 0; j < 32; ++j)
               if (c0 + j < L) V.w_out[row * L + c0 + j] = wreg[j];
           }
+          if (!LSMALL) {
+            // the weights replace their logits in the (now read) output
+            // accumulator, so the pick pass reads them instead of computing
+            // them again
+            uint32_t wb[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) wb[j] = __float_as_uint(wreg[j]);
+            tmem_st32(t_lane + (uint32_t)c0, wb);
+          }
         }
         int sel = -1;
         float wsel = 0.0f;
@@ -259,12 +268,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
               const int i = c0 + j;
               if (i < L) {
                 float w = wreg[j];
-                if (!LSMALL) {
-                  const float v = sigmoid_fast(__uint_as_float(r[j]) * outmul);
-                  w = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)) *
-                                    contribution_fast(px, py, pz, nx, ny, nz, s_l[i]),
-                                qs.pre);
-                }
+                if (!LSMALL) w = __fmul_rn(__uint_as_float(r[j]), qs.pre);
                 if ((i & 3) == 0)
                   rr = philox_keyed(make_uint4(pixel, a.frame, V.view,
                                                ((uint32_t)(i >> 2) << 4) | kTagWrs),
@@ -487,6 +491,15 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
             for (int j = 0; j < 16; ++j)
               if (c0 + j < hi) V.w_out[row * L + c0 + j] = wreg[j];
           }
+          if (!HSMALL) {
+            // the weights replace their logits in this half's (now read)
+            // accumulator columns, so the later passes read them instead of
+            // computing them again
+            uint32_t wb[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) wb[j] = __float_as_uint(wreg[j]);
+            tmem_st16(t_lane + (uint32_t)c0, wb);
+          }
         }
         // exchange 1: the other half's max, sum and DI
         s_x[half * kTileM + rw] = make_float4(wmax, sum, di, 0.0f);
@@ -517,10 +530,7 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
                 const int i = c0 + j;
                 if (i < hi) {
                   float w = wreg[j];
-                  if (!HSMALL)
-                    w = __fmul_rn(fmaxf(sigmoid_fast(__uint_as_float(r[j])), bits_f(kVisClampBits)) *
-                                      contribution_fast(px, py, pz, nx, ny, nz, s_l[i]),
-                                  qs.pre);
+                  if (!HSMALL) w = __fmul_rn(__uint_as_float(r[j]), qs.pre);
                   QA += quantize_scaled(w, qs.scale);
                 }
               }
@@ -544,10 +554,7 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
               const int i = c0 + j;
               if (i < hi) {
                 float w = wreg[j];
-                if (!HSMALL)
-                  w = __fmul_rn(fmaxf(sigmoid_fast(__uint_as_float(r[j])), bits_f(kVisClampBits)) *
-                                    contribution_fast(px, py, pz, nx, ny, nz, s_l[i]),
-                                qs.pre);
+                if (!HSMALL) w = __fmul_rn(__uint_as_float(r[j]), qs.pre);
                 if ((i & 3) == 0)
                   rr = philox_keyed(make_uint4(pixel, a.frame, V.view,
                                                ((uint32_t)(i >> 2) << 4) | kTagWrs),
