@@ -219,6 +219,44 @@ __device__ __forceinline__ float contribution_fast(float px, float py, float pz,
   return fmaxf(l.w * ndl * r * inv, 0.0f);   // n.d <= 0 gives c <= 0 -> 0
 }
 
+// contribution_fast of two lights at once, lane by lane the same operations
+// (x - p as x + (-p)), from a light table staged in pairs, coordinate-major:
+// A = {x, x', y, y'}, B = {z, z', I/pi, I'/pi} (stage_light_pairs).
+__device__ __forceinline__ float2 contribution2_fast(float2 npx, float2 npy, float2 npz,
+                                                     float2 nx2, float2 ny2, float2 nz2,
+                                                     float4 A, float4 B) {
+  const float2 dx = __fadd2_rn(make_float2(A.x, A.y), npx);
+  const float2 dy = __fadd2_rn(make_float2(A.z, A.w), npy);
+  const float2 dz = __fadd2_rn(make_float2(B.x, B.y), npz);
+  const float2 d2 =
+      __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, make_float2(1e-30f, 1e-30f))));
+  const float2 ndl = __ffma2_rn(nx2, dx, __ffma2_rn(ny2, dy, __fmul2_rn(nz2, dz)));
+  const float2 rq = make_float2(rsqrtf(d2.x), rsqrtf(d2.y));
+  const float2 rr = __fmul2_rn(rq, rq);
+  const float2 inv = make_float2(fminf(rr.x, 1e6f), fminf(rr.y, 1e6f));
+  float2 c = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(B.z, B.w), ndl), rq), inv);
+  c.x = fmaxf(c.x, 0.0f);   // n.d <= 0 gives c <= 0 -> 0
+  c.y = fmaxf(c.y, 0.0f);
+  return c;
+}
+
+// Stages the L lights (float4 x, y, z, I) as pairs for contribution2_fast,
+// I scaled by 1/pi; an odd count's last slot is zero.  Threads t of
+// nthreads share the work; the caller synchronises.
+__device__ __forceinline__ void stage_light_pairs(float4* s_pairs, const float* lights, int L,
+                                                  int t, int nthreads) {
+  const int Lp = (L + 1) & ~1;
+  for (int e = t; e < Lp; e += nthreads) {
+    float4 l = e < L ? reinterpret_cast<const float4*>(lights)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
+    float* q = reinterpret_cast<float*>(s_pairs) + (e >> 1) * 8 + (e & 1);
+    q[0] = l.x;
+    q[2] = l.y;
+    q[4] = l.z;
+    q[6] = l.w;
+  }
+}
+
 // Per-pixel scales for q = max(1, floor(w 2^(23 - e))), e = ilogb(wmax), by
 // exact multiplications only: when wmax < 2^-104 the weights are first
 // multiplied by 2^64 (a power of two, so exact, and every w <= wmax stays

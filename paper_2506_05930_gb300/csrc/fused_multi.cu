@@ -81,20 +81,7 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
 
   for (int e = t; e < a.wimg_bytes / 16; e += kThreads)
     reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
-  if (a.lights) {
-    // lights in pairs, coordinate-major: {x_j, x_j+1, y_j, y_j+1},
-    // {z_j, z_j+1, I_j/pi, I_j+1/pi}; an odd count's last slot is zero
-    const int Lp = (a.L + 1) & ~1;
-    for (int e = t; e < Lp; e += kThreads) {
-      float4 l = e < a.L ? reinterpret_cast<const float4*>(a.lights)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-      l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
-      float* q = reinterpret_cast<float*>(s_l) + (e >> 1) * 8 + (e & 1);
-      q[0] = l.x;
-      q[2] = l.y;
-      q[4] = l.z;
-      q[6] = l.w;
-    }
-  }
+  if (a.lights) stage_light_pairs(s_l, a.lights, a.L, t, kThreads);
   if (t == 0) {
     for (int gg = 0; gg < TPC; ++gg) mbar_init(smem_u32(s_bar + gg), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -258,19 +245,8 @@ __global__ void __launch_bounds__(kTileM * TPC, TPC == 2 ? 3 : 2)
             w4[up * 2] = 0.0f;
             w4[up * 2 + 1] = 0.0f;
             if (j < L) {
-              const float4 A = s_l[j], B = s_l[j + 1];   // pair j/2: {x, y}, {z, I/pi}
-              const float2 dx = __fadd2_rn(make_float2(A.x, A.y), npx);
-              const float2 dy = __fadd2_rn(make_float2(A.z, A.w), npy);
-              const float2 dz = __fadd2_rn(make_float2(B.x, B.y), npz);
-              const float2 d2 =
-                  __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, make_float2(1e-30f, 1e-30f))));
-              const float2 ndl = __ffma2_rn(nx2, dx, __ffma2_rn(ny2, dy, __fmul2_rn(nz2, dz)));
-              const float2 rq = make_float2(rsqrtf(d2.x), rsqrtf(d2.y));
-              const float2 rr = __fmul2_rn(rq, rq);
-              const float2 inv = make_float2(fminf(rr.x, 1e6f), fminf(rr.y, 1e6f));
-              float2 c = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(B.z, B.w), ndl), rq), inv);
-              c.x = fmaxf(c.x, 0.0f);
-              c.y = fmaxf(c.y, 0.0f);
+              // pair j/2 of the staged table
+              const float2 c = contribution2_fast(npx, npy, npz, nx2, ny2, nz2, s_l[j], s_l[j + 1]);
               const float2 v01 =
                   sigmoid2_fast(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])));
               const float v0 = v01.x, v1 = v01.y;

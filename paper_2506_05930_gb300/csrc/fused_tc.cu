@@ -54,13 +54,7 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
 
   for (int e = t; e < a.wimg_bytes / 16; e += kTileM)
     reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
-  if (a.lights) {
-    for (int e = t; e < a.L; e += kTileM) {
-      float4 l = reinterpret_cast<const float4*>(a.lights)[e];
-      l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
-      s_l[e] = l;
-    }
-  }
+  if (a.lights) stage_light_pairs(s_l, a.lights, a.L, t, kTileM);
   const uint32_t bar = smem_u32(s_bar);
   if (t == 0) {
     mbar_init(bar, 1);
@@ -211,22 +205,35 @@ __global__ void __launch_bounds__(kTileM, 5) fused_shade_kernel(const __grid_con
         }
         float wreg[32];
         float wmax = 0.0f, sum = 0.0f, di = 0.0f;
+        const float2 npx = make_float2(-px, -px), npy = make_float2(-py, -py),
+                     npz = make_float2(-pz, -pz);
+        const float2 nx2 = make_float2(nx, nx), ny2 = make_float2(ny, ny), nz2 = make_float2(nz, nz);
         for (int c0 = 0; c0 < L; c0 += 32) {
           uint32_t r[32];
           tmem_ld32(t_lane + (uint32_t)c0, r);
+          // two lights per packed operation (pair (c0 + j) / 2 of the table)
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < 32; j += 2) {
             const int i = c0 + j;
-            float w = 0.0f;
+            wreg[j] = 0.0f;
+            wreg[j + 1] = 0.0f;
             if (i < L) {
-              const float v = sigmoid_fast(__uint_as_float(r[j]) * outmul);
-              const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
-              w = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), c);
-              wmax = fmaxf(wmax, w);
-              sum += w;
-              di = fmaf(v, c, di);
+              const float2 c = contribution2_fast(npx, npy, npz, nx2, ny2, nz2, s_l[i], s_l[i + 1]);
+              const float v0 = sigmoid_fast(__uint_as_float(r[j]) * outmul);
+              const float w0 = __fmul_rn(fmaxf(v0, bits_f(kVisClampBits)), c.x);
+              wmax = fmaxf(wmax, w0);
+              sum += w0;
+              di = fmaf(v0, c.x, di);
+              wreg[j] = w0;
+              if (i + 1 < L) {
+                const float v1 = sigmoid_fast(__uint_as_float(r[j + 1]) * outmul);
+                const float w1 = __fmul_rn(fmaxf(v1, bits_f(kVisClampBits)), c.y);
+                wmax = fmaxf(wmax, w1);
+                sum += w1;
+                di = fmaf(v1, c.y, di);
+                wreg[j + 1] = w1;
+              }
             }
-            wreg[j] = w;
           }
           if (V.w_out != nullptr && live) {
 #pragma unroll
@@ -351,13 +358,7 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
 
   for (int e = t; e < a.wimg_bytes / 16; e += kThreads)
     reinterpret_cast<uint4*>(s_w)[e] = a.wimg[e];
-  if (a.lights) {
-    for (int e = t; e < a.L; e += kThreads) {
-      float4 l = reinterpret_cast<const float4*>(a.lights)[e];
-      l.w = __fmul_rn(l.w, bits_f(kInvPiBits));
-      s_l[e] = l;
-    }
-  }
+  if (a.lights) stage_light_pairs(s_l, a.lights, a.L, t, kThreads);
   const uint32_t bar = smem_u32(s_bar);
   if (t == 0) {
     mbar_init(bar, 1);
@@ -469,22 +470,35 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
         }
         float wreg[16];
         float wmax = 0.0f, sum = 0.0f, di = 0.0f;
+        const float2 npx = make_float2(-px, -px), npy = make_float2(-py, -py),
+                     npz = make_float2(-pz, -pz);
+        const float2 nx2 = make_float2(nx, nx), ny2 = make_float2(ny, ny), nz2 = make_float2(nz, nz);
         for (int c0 = lo; c0 < hi; c0 += 16) {
           uint32_t r[16];
           tmem_ld16(t_lane + (uint32_t)c0, r);
+          // two lights per packed operation (pair (c0 + j) / 2 of the table)
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < 16; j += 2) {
             const int i = c0 + j;
-            float w = 0.0f;
+            wreg[j] = 0.0f;
+            wreg[j + 1] = 0.0f;
             if (i < hi) {
-              const float v = sigmoid_fast(__uint_as_float(r[j]));
-              const float c = contribution_fast(px, py, pz, nx, ny, nz, s_l[i]);
-              w = __fmul_rn(fmaxf(v, bits_f(kVisClampBits)), c);
-              wmax = fmaxf(wmax, w);
-              sum += w;
-              di = fmaf(v, c, di);
+              const float2 c = contribution2_fast(npx, npy, npz, nx2, ny2, nz2, s_l[i], s_l[i + 1]);
+              const float2 v01 =
+                  sigmoid2_fast(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])));
+              const float w0 = __fmul_rn(fmaxf(v01.x, bits_f(kVisClampBits)), c.x);
+              wmax = fmaxf(wmax, w0);
+              sum += w0;
+              di = fmaf(v01.x, c.x, di);
+              wreg[j] = w0;
+              if (i + 1 < hi) {
+                const float w1 = __fmul_rn(fmaxf(v01.y, bits_f(kVisClampBits)), c.y);
+                wmax = fmaxf(wmax, w1);
+                sum += w1;
+                di = fmaf(v01.y, c.y, di);
+                wreg[j + 1] = w1;
+              }
             }
-            wreg[j] = w;
           }
           if (V.w_out != nullptr && live) {
 #pragma unroll
@@ -988,7 +1002,7 @@ size_t fused_smem(const nvc_handle* h, const PackArgs& p, FusedArgs* a = nullptr
   off += (size_t)kTileM * kmax * p.esize;
   off = (off + 15) & ~(size_t)15;
   const size_t l_off = off;
-  off += 16 * (size_t)(h->L > 0 ? h->L : 1);
+  off += 16 * (size_t)(h->L > 0 ? ((h->L + 1) & ~1) : 2);   // lights in pairs
   const size_t bar_off = off;
   off += 64;
   if (a) {
