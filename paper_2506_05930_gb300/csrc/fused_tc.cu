@@ -349,8 +349,8 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 1);
   uint32_t* s_next = s_tmem + 1;                                     // the CTA's next tile
   float4* s_x = reinterpret_cast<float4*>(smem + a.pair_x);          // [2][128] partials
-  uint32_t* s_q = reinterpret_cast<uint32_t*>(s_x + 2 * kTileM);     // [128] Q_A
-  int2* s_s = reinterpret_cast<int2*>(s_q + kTileM);                 // [128] (sel, w_sel bits) of half 1
+  uint32_t* s_q = reinterpret_cast<uint32_t*>(s_x + 2 * kTileM);     // [2][128] parts of Q_A
+  int2* s_s = reinterpret_cast<int2*>(s_q + 2 * kTileM);             // [128] (sel, w_sel bits) of half 1
   const int t = threadIdx.x;
   const int warp = t >> 5;
   const int rw = t & (kTileM - 1);
@@ -515,9 +515,12 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
             tmem_st16(t_lane + (uint32_t)c0, wb);
           }
         }
-        // exchange 1: the other half's max, sum and DI
+        // exchange 1: the other half's max, sum and DI (and, with the
+        // weights in TMEM, the other half's columns for exchange 2)
         s_x[half * kTileM + rw] = make_float4(wmax, sum, di, 0.0f);
+        if (!HSMALL) tc_fence_before();
         pair_sync(warp);
+        if (!HSMALL) tc_fence_after();
         const float4 o = s_x[(half ^ 1) * kTileM + rw];
         wmax = fmaxf(wmax, o.x);
         const float sumA = half ? o.y : sum, sumB = half ? sum : o.y;
@@ -531,9 +534,25 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
 #pragma unroll
           for (int j = 0; j < 16; ++j) wreg[j] = __fmul_rn(wreg[j], qs.pre);
         }
-        // this half's integer weight total (exchange 2 hands Q_A to half 1)
+        // the first half's integer weight total Q_A (exchange 2 hands it to
+        // half 1).  With the weights in TMEM both halves share the sum:
+        // half h quantizes the first half's chunks h, h + 2, ...
         uint32_t Q = 0;
-        if (half == 0) {
+        if (!HSMALL) {
+          const int hiA = H < L ? H : L;
+          uint32_t part = 0;
+          for (int c0 = half * 16; c0 < hiA; c0 += 32) {
+            uint32_t r[16];
+            tmem_ld16(t_lane + (uint32_t)c0, r);
+            if (active) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (c0 + j < hiA)
+                  part += quantize_scaled(__fmul_rn(__uint_as_float(r[j]), qs.pre), qs.scale);
+            }
+          }
+          s_q[half * kTileM + rw] = part;
+        } else if (half == 0) {
           uint32_t QA = 0;
           for (int c0 = lo; c0 < hi; c0 += 16) {
             uint32_t r[16];
@@ -553,7 +572,7 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
           s_q[rw] = QA;
         }
         pair_sync(warp);
-        if (half == 1) Q = s_q[rw];
+        if (half == 1) Q = HSMALL ? s_q[rw] : s_q[rw] + s_q[kTileM + rw];
         // the pick over this half's lights, prefix sums continuing from Q
         int sel = -1;
         float wsel = 0.0f;
@@ -1014,12 +1033,12 @@ size_t fused_smem(const nvc_handle* h, const PackArgs& p, FusedArgs* a = nullptr
 }
 
 // The monolithic plan followed by the exchange area of the two-threads-per-
-// pixel kernel: partials [2][128] float4, Q_A [128] uint32, pick [128] int2.
+// pixel kernel: partials [2][128] float4, Q_A parts [2][128] uint32, pick [128] int2.
 size_t pair_smem(const nvc_handle* h, const PackArgs& p, FusedArgs* a = nullptr) {
   size_t off = fused_smem(h, p, a);
   off = (off + 15) & ~(size_t)15;
   if (a) a->pair_x = (int)off;
-  return off + 2 * kTileM * 16 + kTileM * 4 + kTileM * 8;
+  return off + 2 * kTileM * 16 + 2 * kTileM * 4 + kTileM * 8;
 }
 
 template <int F, int PREC>
