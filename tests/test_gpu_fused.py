@@ -273,13 +273,15 @@ def test_every_shade_variant_gives_identical_outputs(cfg_name):
     assert ms[chosen] == min(m for m in ms if m > 0)
 
 
-@pytest.mark.parametrize("L", [4, 48, 128, 256])
+@pytest.mark.parametrize("L", [4, 48, 128, 201, 256])
 def test_two_threads_per_pixel_variant_across_light_counts(L):
     """Variant 5 splits the lights at H = ceil(L/2) rounded up to 16: for
     L = 4 the second thread has no lights, for 48 the first has two 16-light
-    chunks, 128 and 256 take the recomputing path (256 TMEM columns).  Its
-    picks equal the monolithic kernel's, its sums agree to rounding, and the
-    picks are the oracle's on the kernel's own weights."""
+    chunks; 128, 201 and 256 keep the weights in TMEM between the sampler's
+    passes (201: odd, so the paired light table ends in a padding slot and
+    the last chunks are ragged), as the monolithic kernel does above 32
+    lights.  Its picks equal the monolithic kernel's, its sums agree to
+    rounding, and the picks are the oracle's on the kernel's own weights."""
     cfg = S.config_by_name("frame_1080p").with_(n_outputs=L, precision="fp16", batch_positions=256)
     sc = S.scene_heightfield(seed=4, n_lights=L, n_spheres=8, n_boxes=8)
     gb = S.gbuffer_heightfield(seed=4, width=97, height=61)
