@@ -561,7 +561,7 @@ def measure_precisions(stream):
             nvc.nvc_calibrate(cache.handle, pos[::4096][:1024].contiguous())
         if not fused:
             nvc.nvc_set_staging(cache.handle, P)
-        elif prec != "fp8":
+        else:
             chosen, _ = nvc.nvc_autotune_shade_plan(cache.handle, scene, pos, nrm, reps=2, **out)
         ms = _timed(stream, lambda f: nvc.nvc_shade(cache.handle, scene, pos, nrm, 3, f, 0, 0,
                                                     fused=fused, stream=s, **out), 5, warm=2)

@@ -365,7 +365,9 @@ nvc_status nvc_autotune_shade_plan(nvc_handle* h, const nvc_scene* scene, const 
                                    nvc_shade_plan* chosen, nvc_shade_plan* points, double* ms,
                                    int32_t max_points, int32_t* n_points, void* stream);
 
-/* Selects the fused shading kernel variant (0 .. NVC_SHADE_VARIANTS-1). */
+/* Selects the fused shading kernel variant (0 .. NVC_SHADE_VARIANTS-1).
+ * NVC_ERR_UNSUPPORTED for variants 1-4, 6 and 7 with n_outputs > 32, and for
+ * any but 0 and 5 with E4M3 operands. */
 nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant);
 
 /* ---- the shading pass (Section 3.1) and exact direct illumination -------- */

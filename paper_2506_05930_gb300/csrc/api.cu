@@ -729,8 +729,8 @@ nvc_status nvc_shade_phases(nvc_handle* h, const nvc_scene* scene, const float* 
 static nvc_status check_variant(nvc_handle* h, int32_t variant) {
   if (variant < 0 || variant >= kShadeVariants)
     return fail(h, NVC_ERR_INVALID_ARG, "variant out of range");
-  if (variant != kShadeMono && h->cfg.precision == NVC_PREC_FP8)
-    return fail(h, NVC_ERR_UNSUPPORTED, "E4M3 operands run the monolithic variant only");
+  if (variant != kShadeMono && variant != kShadePair && h->cfg.precision == NVC_PREC_FP8)
+    return fail(h, NVC_ERR_UNSUPPORTED, "E4M3 operands run variants 0 and 5 only");
   if (variant != kShadeMono && variant != kShadePair && h->L > 32)
     return fail(h, NVC_ERR_UNSUPPORTED, "variants 1-4, 6 and 7 need n_outputs <= 32");
   return NVC_OK;
@@ -815,8 +815,8 @@ nvc_status nvc_set_shade_variant(nvc_handle* h, int32_t variant) {
   if (!h) return fail(nullptr, NVC_ERR_INVALID_ARG, "handle is NULL");
   if (variant < 0 || variant >= kShadeVariants)
     return fail(h, NVC_ERR_INVALID_ARG, "variant out of range");
-  if (variant != kShadeMono && h->cfg.precision == NVC_PREC_FP8)
-    return fail(h, NVC_ERR_UNSUPPORTED, "E4M3 operands run the monolithic variant only");
+  if (variant != kShadeMono && variant != kShadePair && h->cfg.precision == NVC_PREC_FP8)
+    return fail(h, NVC_ERR_UNSUPPORTED, "E4M3 operands run variants 0 and 5 only");
   if (variant != kShadeMono && variant != kShadePair && h->L > 32)
     return fail(h, NVC_ERR_UNSUPPORTED, "variants 1-4, 6 and 7 need n_outputs <= 32");
   h->shade_variant = variant;
@@ -846,7 +846,7 @@ nvc_status nvc_autotune_infer(nvc_handle* h, const float* pos, int64_t n, float*
   double best_ms = 0.0;
   cudaError_t err = cudaSuccess;
   for (int v = 0; v < kShadeVariants && err == cudaSuccess; ++v) {
-    if (v != kShadeMono && h->cfg.precision == NVC_PREC_FP8) continue;
+    if (v != kShadeMono && v != kShadePair && h->cfg.precision == NVC_PREC_FP8) continue;
     if (v != kShadeMono && v != kShadePair && h->L > 32) continue;
     h->shade_variant = v;
     if (launch_shade_fused(h, nullptr, pos, nullptr, n, 0, 0, 0, 0, nullptr, nullptr, nullptr,
@@ -895,7 +895,7 @@ nvc_status nvc_autotune_shade(nvc_handle* h, const nvc_scene* scene, const float
   double best_ms = 0.0;
   for (int v = 0; v < kShadeVariants; ++v) {
     if (ms_out) ms_out[v] = -1.0;
-    if (v != kShadeMono && h->cfg.precision == NVC_PREC_FP8) continue;
+    if (v != kShadeMono && v != kShadePair && h->cfg.precision == NVC_PREC_FP8) continue;
     if (v != kShadeMono && v != kShadePair && h->L > 32) continue;
     h->shade_variant = v;
     cudaError_t e = launch_shade_fused(h, scene, pos, nrm, n, 1, 0, 0, 0, idx, pdf, wsum,

@@ -377,8 +377,22 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
   uint32_t phase = 0;
   bool failed = false;
 
-  constexpr int CH = 8;    // 16-bit operands: 8 per 16-byte core-matrix row
-  constexpr int KS = 16;
+  constexpr bool kF8 = PREC == NVC_PREC_FP8;
+  constexpr int CH = kF8 ? 16 : 8;     // operand elements per 16-byte core-matrix row
+  constexpr int ES = kF8 ? 1 : 2;      // bytes per operand element
+  constexpr int KS = kF8 ? 32 : 16;    // K per MMA instruction
+  // E4M3: layer k's accumulator times s_mult[k] is the next layer's scaled
+  // input (or, for the last layer, the logit), as in the monolithic kernel
+  __shared__ float s_mult[kMaxLayers];
+  float s_in0 = 1.0f;
+  if constexpr (kF8) {
+    const float* sa = a.fp8_scales;
+    const float* sw = a.fp8_scales + kMaxLayers;
+    s_in0 = sa[0];
+    if (t < a.n_layers)
+      s_mult[t] = (t + 1 < a.n_layers ? sa[t + 1] : 1.0f) / (sa[t] * sw[t]);
+    __syncthreads();
+  }
   const int din = a.ep.n_levels * F;
   const int K0 = a.layer[0].K;
   const int64_t n_tiles = a.n_tiles;
@@ -406,7 +420,8 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
         for (int c = half; c < K0 / CH; c += 2) {
           float fv[CH];
           encode_chunk<F, false, CH>(a.ep, tab, c, din, x, y, z, live, fv);
-          *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, 2)) = pack_chunk<PREC, CH>(fv, 1.0f);
+          *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c * CH, K0, ES)) =
+              pack_chunk<PREC, CH>(fv, s_in0);
         }
       };
       if (a.table16)
@@ -423,11 +438,16 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
       const LayerDesc ld = a.layer[k];
       if (t == 0) {
         tc_fence_after();
-        const uint32_t sbo = (uint32_t)ld.K * 16u;
+        const uint32_t sbo = (uint32_t)ld.K * 8u * ES;
         const uint32_t wb = w_base + (uint32_t)ld.w_byte_off;
-        for (int kk = 0; kk < ld.K / KS; ++kk)
-          mma_f16(tmem, smem_desc(a_base + kk * 256, 128, sbo), smem_desc(wb + kk * 256, 128, sbo),
-                  ld.idesc, kk > 0 ? 1u : 0u);
+        for (int kk = 0; kk < ld.K / KS; ++kk) {
+          if constexpr (kF8)
+            mma_f8(tmem, smem_desc(a_base + kk * 256, 128, sbo), smem_desc(wb + kk * 256, 128, sbo),
+                   ld.idesc, kk > 0 ? 1u : 0u);
+          else
+            mma_f16(tmem, smem_desc(a_base + kk * 256, 128, sbo),
+                    smem_desc(wb + kk * 256, 128, sbo), ld.idesc, kk > 0 ? 1u : 0u);
+        }
         mma_commit(bar);
       }
       const bool ok = mbar_wait_bounded(bar, phase);
@@ -438,14 +458,32 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
         for (int c0 = half * 32; c0 < ld.N; c0 += 64) {
           uint32_t r[32];
           tmem_ld32(t_lane + (uint32_t)c0, r);
+          if constexpr (kF8) {
+            // leaky ReLU is positively homogeneous: leaky(m z) = m leaky(z)
+            const float m = s_mult[k];
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            uint4 pk;
-            pk.x = leaky2<PREC>(r[g * 8 + 0], r[g * 8 + 1], a.slope);
-            pk.y = leaky2<PREC>(r[g * 8 + 2], r[g * 8 + 3], a.slope);
-            pk.z = leaky2<PREC>(r[g * 8 + 4], r[g * 8 + 5], a.slope);
-            pk.w = leaky2<PREC>(r[g * 8 + 6], r[g * 8 + 7], a.slope);
-            if (c0 + g * 8 < Kn) *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c0 + g * 8, Kn, 2)) = pk;
+            for (int g = 0; g < 2; ++g) {
+              float v[16];
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                const float zz = __uint_as_float(r[g * 16 + q]) * m;
+                v[q] = fmaxf(zz, a.slope * zz);
+              }
+              if (c0 + g * 16 < Kn)
+                *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c0 + g * 16, Kn, 1)) =
+                    pack_chunk<PREC, 16>(v, 1.0f);
+            }
+          } else {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              uint4 pk;
+              pk.x = leaky2<PREC>(r[g * 8 + 0], r[g * 8 + 1], a.slope);
+              pk.y = leaky2<PREC>(r[g * 8 + 2], r[g * 8 + 3], a.slope);
+              pk.z = leaky2<PREC>(r[g * 8 + 4], r[g * 8 + 5], a.slope);
+              pk.w = leaky2<PREC>(r[g * 8 + 6], r[g * 8 + 7], a.slope);
+              if (c0 + g * 8 < Kn)
+                *reinterpret_cast<uint4*>(s_a + cm_offset(rw, c0 + g * 8, Kn, 2)) = pk;
+            }
           }
         }
         fence_async_smem();
@@ -455,11 +493,12 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
       }
 
       // ---- output layer: this half's lights -----------------------------------
+      const float outmul = kF8 ? s_mult[a.n_layers - 1] : 1.0f;
       if (V.vis_out) {
         for (int c0 = lo; c0 < hi; c0 += 16) {
           uint32_t r[16];
           tmem_ld16(t_lane + (uint32_t)c0, r);
-          if (live) store_sigmoid_row<16>(V.vis_out + row * L + c0, r, hi - c0, 1.0f);
+          if (live) store_sigmoid_row<16>(V.vis_out + row * L + c0, r, hi - c0, outmul);
         }
       } else {
         float nx = 0.f, ny = 0.f, nz = 0.f;
@@ -484,8 +523,9 @@ __global__ void __launch_bounds__(2 * kTileM, 3) fused_shade_pair_kernel(const _
             wreg[j + 1] = 0.0f;
             if (i < hi) {
               const float2 c = contribution2_fast(npx, npy, npz, nx2, ny2, nz2, s_l[i], s_l[i + 1]);
-              const float2 v01 =
-                  sigmoid2_fast(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])));
+              float2 z01 = make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1]));
+              if constexpr (kF8) z01 = __fmul2_rn(z01, make_float2(outmul, outmul));
+              const float2 v01 = sigmoid2_fast(z01);
               const float w0 = __fmul_rn(fmaxf(v01.x, bits_f(kVisClampBits)), c.x);
               wmax = fmaxf(wmax, w0);
               sum += w0;
@@ -1304,6 +1344,16 @@ cudaError_t launch_shade_fused_views(const nvc_handle* h, const nvc_scene* sc,
     if (h->cfg.precision == NVC_PREC_FP8 || h->L > 32) return cudaErrorInvalidValue;
     return launch_shade_multi(a, h, p, h->shade_variant == kShadeMulti2 ? 2 : 4,
                               h->cfg.precision == NVC_PREC_BF16, s);
+  }
+  if (h->cfg.precision == NVC_PREC_FP8 && h->shade_variant == kShadePair) {
+    const size_t smem_p8 = pair_smem(h, p, &a);
+    switch (h->F) {
+      case 1: return launch_pair_typed<1, NVC_PREC_FP8>(a, smem_p8, h->num_sms, s);
+      case 2: return launch_pair_typed<2, NVC_PREC_FP8>(a, smem_p8, h->num_sms, s);
+      case 4: return launch_pair_typed<4, NVC_PREC_FP8>(a, smem_p8, h->num_sms, s);
+      case 8: return launch_pair_typed<8, NVC_PREC_FP8>(a, smem_p8, h->num_sms, s);
+    }
+    return cudaErrorInvalidValue;
   }
   if (h->cfg.precision == NVC_PREC_FP8) {
     const size_t smem8 = fused_smem(h, p, &a);

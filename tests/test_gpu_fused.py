@@ -303,6 +303,35 @@ def test_two_threads_per_pixel_variant_across_light_counts(L):
     assert np.array_equal(host(out["idx"]), idx)
 
 
+@pytest.mark.parametrize("L", [32, 256])
+def test_e4m3_two_threads_per_pixel_equals_monolithic(L):
+    """With E4M3 operands the two-threads-per-pixel kernel (variant 5) runs
+    the same scaled encode, MMAs and epilogues as the monolithic kernel:
+    visibilities and picks bit for bit, sums to rounding."""
+    cfg = S.config_by_name("frame_1080p").with_(n_outputs=L, precision="fp8",
+                                                train_precision="fp32", batch_positions=256)
+    sc = S.scene_heightfield(seed=6, n_lights=L, n_spheres=8, n_boxes=8)
+    gb = S.gbuffer_heightfield(seed=6, width=97, height=61)
+    cache, _ = make(cfg, seed=2, table_scale=0.5)
+    scene = nvc.Scene.from_synth(sc)
+    pos, nrm = dev(gb.pos), dev(gb.nrm)
+    nvc.nvc_calibrate(cache.handle, pos[:256])          # at most batch_positions samples
+    outs = []
+    for v in (0, PAIR_VARIANT):
+        nvc.nvc_set_shade_variant(cache.handle, v)
+        outs.append((cache.shade(scene, pos, nrm, seed=4, frame=2, pixel_offset=7, fused=True),
+                     cache.infer(pos)))
+    (ref, vref), (out, vout) = outs
+    assert torch.equal(vout, vref)
+    assert torch.equal(out["idx"], ref["idx"])
+    assert (host(out["idx"]) >= 0).mean() > 0.5
+    for k in ("pdf", "wsum", "radiance"):
+        _assert_resummed(out[k], ref[k], L)
+    with pytest.raises(nvc.NVCError):
+        nvc.nvc_set_shade_variant(cache.handle, 7)
+    cache.close()
+
+
 def _views(gbs):
     out = []
     for v, gb in enumerate(gbs):
