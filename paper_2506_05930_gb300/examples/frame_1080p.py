@@ -1,5 +1,5 @@
 """The 1080p frame workload (Sections 3.1-3.4): the heightfield + boxes view
-with 32 point lights, trained online for a few frames and then rendered as
+with 32 point lights (or --lights), trained online for a few frames and then rendered as
 whole frames (training step, fused inference + WRS + Neural DI), with the
 time of each stage printed (CUDA events).
 
@@ -23,6 +23,8 @@ def main():
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--variant", type=int, default=7, help="fused shading variant (0-7)")
+    ap.add_argument("--lights", type=int, default=32,
+                    help="point lights = network outputs (above 32: variant 0 or 5)")
     ap.add_argument("--pretrain", type=int, default=5)
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--warm", type=int, default=0,
@@ -31,8 +33,8 @@ def main():
                     help="table features of the fused inference (default: the workload's)")
     args = ap.parse_args()
 
-    cfg = S.config_by_name("frame_1080p")
-    sc = S.scene_heightfield(seed=1, n_lights=32, n_spheres=32, n_boxes=32)
+    cfg = S.config_by_name("frame_1080p").with_(n_outputs=args.lights)
+    sc = S.scene_heightfield(seed=1, n_lights=args.lights, n_spheres=32, n_boxes=32)
     gb = S.gbuffer_heightfield(seed=1, width=args.width, height=args.height)
     scene = nvc.Scene.from_synth(sc)
     n = gb.n
