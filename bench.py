@@ -245,9 +245,9 @@ def clustered_alu_ops(n_lights, k, n_pixels):
 
 # Per-launch DRAM traffic of the dominant kernel from the ncu capture named in
 # profiles/ (None once the kernel has changed since that capture).
-KERNEL_TRAFFIC = {"fused_shade": 83.67e6, "adam": None,
+KERNEL_TRAFFIC = {"fused_shade": 83.04e6, "adam": None,
                   # 1080p launch with the shadow ray (light, W and estimate written)
-                  "sample_clustered": 336.44e6}
+                  "sample_clustered": 336.78e6}
 
 
 # ------------------------------------------------------------- our arm ----
