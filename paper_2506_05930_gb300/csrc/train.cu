@@ -415,7 +415,11 @@ cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_
   // the step's loss, skip decision and scalars are derived inside the
   // update kernel (one launch)
   const int64_t n4 = h->n_params / 4;
-  const int blocks = h->num_sms * 8;
+  // two float4 groups per thread and pass: no more CTAs than that covers
+  // (a small table would otherwise pay for 8 CTAs per SM that each plan the
+  // step and find no work)
+  const int64_t want = (n4 + 2 * 256 - 1) / (2 * 256);
+  const int blocks = (int)(want < 1 ? 1 : want < h->num_sms * 8 ? want : h->num_sms * 8);
   MlpImageMap mp{};
   uint8_t* img = mlp_image_map(h, &mp) ? static_cast<uint8_t*>(h->mlp_packed) : nullptr;
   adam_kernel<<<blocks, 256, 0, s>>>(h->params, h->grad, h->adam_m, h->adam_v, n4, h->n_params,
