@@ -212,7 +212,11 @@ def algorithmic(cfg, n_pixels):
     F, Lv, L = cfg.n_features, cfg.n_levels, cfg.n_outputs
     dims = [cfg.n_inputs, *cfg.hidden, L]
     macs = sum(a * b for a, b in zip(dims[:-1], dims[1:]))
-    n_params = cfg.n_levels * cfg.table_size * F + macs
+    n_table = cfg.n_levels * cfg.table_size * F
+    n_params = n_table + macs
+    # the half-precision feature copy the fused inference reads is rewritten
+    # by the same Adam pass, 2 B per table parameter
+    table16 = cfg.table_precision != "fp32" and cfg.precision != "fp32"
     alu_px = (ALU_OPS["normalise"]
               + Lv * (ALU_OPS["level_base"] + ALU_OPS["level_per_feature"] * F)
               + ALU_OPS["hidden_value"] * sum(cfg.hidden)
@@ -222,7 +226,8 @@ def algorithmic(cfg, n_pixels):
         shade_flops=2.0 * macs * n_pixels,                  # MLP contraction
         shade_hbm_bytes=40.0 * n_pixels,                    # pos+nrm in, idx/pdf/wsum/DI out
         shade_gather_bytes=Lv * 8 * F * 4.0 * n_pixels,     # useful table bytes gathered
-        adam_bytes=28.5 * n_params,                         # read theta,m,v,g; write theta,m,v; clear touched g
+        # read theta,m,v,g; write theta,m,v; clear touched g; the FP16 copy
+        adam_bytes=28.5 * n_params + (2.0 * n_table if table16 else 0.0),
         n_params=n_params, macs_per_px=macs, alu_ops_per_px=alu_px)
 
 
@@ -244,8 +249,9 @@ def clustered_alu_ops(n_lights, k, n_pixels):
 
 
 # Per-launch DRAM traffic of the dominant kernel from the ncu capture named in
-# profiles/ (None once the kernel has changed since that capture).
-KERNEL_TRAFFIC = {"fused_shade": 83.04e6, "adam": None,
+# profiles/ (None once the kernel has changed since that capture); the fused
+# shading kernel's by variant (the 1080p frame's launch).
+KERNEL_TRAFFIC = {"fused_shade": {6: 78.68e6, 7: 83.04e6}, "adam": 461.3e6,
                   # 1080p launch with the shadow ray (light, W and estimate written)
                   "sample_clustered": 336.78e6}
 
@@ -897,7 +903,8 @@ def run_ours(args):
                   "bound": "alu", "achieved": alg["shade_alu_ops"] / shade_s / 1e12,
                   "peak": peak_alu / 1e12, "unit": "Tops/s",
                   "peak_source": "152 SMs x 128 lanes x 2070 MHz (max SM clock)",
-                  "traffic": KERNEL_TRAFFIC["fused_shade"]}
+                  "traffic": KERNEL_TRAFFIC["fused_shade"].get(
+                      tune["chosen"]["variant"] if tune else None)}
     if not fused:
         shade_view["kernel"] = "shade (encode, MLP, WRS+DI kernels)"
         shade_view["traffic"] = None

@@ -283,6 +283,8 @@ nvc_status nvc_create(const nvc_config* cfg, nvc_handle** out) {
   if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) !=
       cudaSuccess)
     return cleanup_fail(e, "cudaDeviceGetAttribute");
+  if ((e = adam_occupancy(&h->adam_ctas_per_sm)) != cudaSuccess)
+    return cleanup_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (mlp_fwd_smem_bytes(h) > (size_t)smem_optin) {

@@ -194,6 +194,7 @@ struct nvc_handle {
   int w_in[NVC_MAX_HIDDEN_LAYERS + 1] = {};
   int device = 0;
   int num_sms = 0;
+  int adam_ctas_per_sm = 0;   // resident Adam CTAs per SM (occupancy query at create)
 
   // parameters and optimiser state (float32, n_params each)
   float* params = nullptr;
@@ -323,6 +324,8 @@ cudaError_t launch_trace_visibility(const nvc_scene* sc, const float* pos, int64
                                     float* vis, cudaStream_t s);
 cudaError_t launch_loss_grad(nvc_handle* h, int64_t n, cudaStream_t s);
 cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_t s);
+// Resident CTAs per SM of the Adam update (256 threads), for a one-wave grid.
+cudaError_t adam_occupancy(int* ctas_per_sm);
 cudaError_t launch_finish_gradient(nvc_handle* h, float* grad_out, double* loss_out,
                                    cudaStream_t s);
 

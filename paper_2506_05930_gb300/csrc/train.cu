@@ -179,10 +179,10 @@ __global__ void adam_prologue_kernel(StepArgs a, double inv_count, double* loss_
 // theta -= (lr / bc1) m / (sqrt(v / bc2) + eps), after m, v updates with the
 // unscaled gradient; the gradient buffer is cleared for the next step.
 // HBM-bound: each thread issues all loads of two float4 groups before any
-// arithmetic; m and v stream (evict-first), theta is stored normally so the
-// updated table is still in L2 when the shading kernel gathers from it, and
-// gradient entries already zero (table rows no sample touched) are not
-// rewritten.
+// arithmetic; m and v stream (evict-first), theta and its half-precision
+// copy are stored normally so the table the shading kernel gathers from is
+// still in L2, and gradient entries already zero (table rows no sample
+// touched) are not rewritten.
 __device__ __forceinline__ void adam_scalar(float& th, float g, float& mm, float& vv,
                                             const AdamScalars& sc, float beta1, float beta2,
                                             float eps) {
@@ -211,15 +211,37 @@ __device__ __forceinline__ void set_image(const MlpImageMap& mp, uint8_t* img, i
     reinterpret_cast<__half*>(img + mp.byte_off[k])[local] = __float2half_rn(v);
 }
 
+// One thread's two float4 groups of an iteration: e, and e + stride when
+// that is below n4.
+struct AdamGroups {
+  float4 g[2], th[2], mm[2], vv[2];
+};
+
+__device__ __forceinline__ void adam_load(AdamGroups& q, const float4* g4, const float4* th4,
+                                          const float4* m4, const float4* v4, int64_t e,
+                                          int64_t e1, bool two) {
+  q.g[0] = __ldcs(g4 + e);
+  q.th[0] = th4[e];
+  q.mm[0] = __ldcs(m4 + e);
+  q.vv[0] = __ldcs(v4 + e);
+  if (two) {
+    q.g[1] = __ldcs(g4 + e1);
+    q.th[1] = th4[e1];
+    q.mm[1] = __ldcs(m4 + e1);
+    q.vv[1] = __ldcs(v4 + e1);
+  }
+}
+
 // The update proper (sc.skip == 0): grid-stride over float4 groups, two at
-// a time, then the tail scalars.
+// a time, then the tail scalars.  q holds the first iteration's groups
+// (e = t0), loaded by the caller before the step's scalars were known.
 __device__ __forceinline__ void adam_update(float* __restrict__ theta, float* __restrict__ grad,
                                             float* __restrict__ m, float* __restrict__ v,
                                             int64_t n4, int64_t n, float beta1, float beta2,
                                             float eps, const AdamScalars& sc,
                                             uint2* __restrict__ table16, int64_t n_table4,
                                             const MlpImageMap& mp, uint8_t* __restrict__ img,
-                                            int64_t t0, int64_t stride) {
+                                            int64_t t0, int64_t stride, AdamGroups& q) {
   float4* g4 = reinterpret_cast<float4*>(grad);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   float4* th4 = reinterpret_cast<float4*>(theta);
@@ -228,17 +250,11 @@ __device__ __forceinline__ void adam_update(float* __restrict__ theta, float* __
   for (int64_t e = t0; e < n4; e += 2 * stride) {
     const int64_t e1 = e + stride;
     const bool two = e1 < n4;
-    float4 g[2], th[2], mm[2], vv[2];
-    g[0] = __ldcs(g4 + e);
-    th[0] = th4[e];
-    mm[0] = __ldcs(m4 + e);
-    vv[0] = __ldcs(v4 + e);
-    if (two) {
-      g[1] = __ldcs(g4 + e1);
-      th[1] = th4[e1];
-      mm[1] = __ldcs(m4 + e1);
-      vv[1] = __ldcs(v4 + e1);
-    }
+    if (e != t0) adam_load(q, g4, th4, m4, v4, e, e1, two);
+    float4 (&g)[2] = q.g;
+    float4 (&th)[2] = q.th;
+    float4 (&mm)[2] = q.mm;
+    float4 (&vv)[2] = q.vv;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (u == 1 && !two) break;
@@ -286,6 +302,16 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
                                                    double* loss_out, int32_t* status,
                                                    uint2* __restrict__ table16, int64_t n_table4,
                                                    MlpImageMap mp, uint8_t* __restrict__ img) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float4* g4 = reinterpret_cast<float4*>(grad);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  // the first iteration's loads go out before the step is planned, so the
+  // planning warp's latency hides behind them
+  AdamGroups q;
+  if (t0 < n4)
+    adam_load(q, g4, reinterpret_cast<const float4*>(theta), reinterpret_cast<const float4*>(m),
+              reinterpret_cast<const float4*>(v), t0, t0 + stride, t0 + stride < n4);
   // every CTA plans the step from the same inputs (warp 0); the last CTA to
   // finish commits its bookkeeping, after every CTA has read the status
   __shared__ StepPlan s_plan;
@@ -295,17 +321,13 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
   }
   __syncthreads();
   const AdamScalars sc = s_plan.sc;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  float4* g4 = reinterpret_cast<float4*>(grad);
-  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   if (sc.skip) {
     for (int64_t e = t0; e < n4; e += stride)
       if (nonzero4(g4[e])) g4[e] = zero;
     for (int64_t e = 4 * n4 + t0; e < n; e += stride) grad[e] = 0.0f;
   } else {
     adam_update(theta, grad, m, v, n4, n, beta1, beta2, eps, sc, table16, n_table4, mp, img,
-                t0, stride);
+                t0, stride, q);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -418,14 +440,21 @@ cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_
   // two float4 groups per thread and pass: no more CTAs than that covers
   // (a small table would otherwise pay for 8 CTAs per SM that each plan the
   // step and find no work)
+  // and no more than one resident wave, so every CTA plans the step once, at
+  // the start, while its first loads are in flight
   const int64_t want = (n4 + 2 * 256 - 1) / (2 * 256);
-  const int blocks = (int)(want < 1 ? 1 : want < h->num_sms * 8 ? want : h->num_sms * 8);
+  const int64_t cap = (int64_t)h->num_sms * (h->adam_ctas_per_sm > 0 ? h->adam_ctas_per_sm : 1);
+  const int blocks = (int)(want < 1 ? 1 : want < cap ? want : cap);
   MlpImageMap mp{};
   uint8_t* img = mlp_image_map(h, &mp) ? static_cast<uint8_t*>(h->mlp_packed) : nullptr;
   adam_kernel<<<blocks, 256, 0, s>>>(h->params, h->grad, h->adam_m, h->adam_v, n4, h->n_params,
                                      c.beta1, c.beta2, c.eps, a, inv_count, loss_out, h->status,
                                      reinterpret_cast<uint2*>(h->table16), h->n_table / 4, mp, img);
   return cudaGetLastError();
+}
+
+cudaError_t adam_occupancy(int* ctas_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, adam_kernel, 256, 0);
 }
 
 cudaError_t launch_finish_gradient(nvc_handle* h, float* grad_out, double* loss_out,
