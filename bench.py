@@ -394,11 +394,18 @@ def measure_mlp_only(cache, cfg, n_px, stream, pk):
     flops = 2 * algorithmic(cfg, n_px)["macs_per_px"] * n_px
     tf = flops / (ms * 1e-3) / 1e12
     del feat, vis
+    # operands in and float32 visibilities out: at the copy peak this I/O
+    # takes longer than the contraction at the tensor peak, so HBM bounds
+    # the launch
+    io = n_px * (k0 * 2 + cfg.n_outputs * 4)
+    io_gbs = io / (ms * 1e-3) / 1e9
     return {"workload": f"{n_px} pixels x {k0} 16-bit operands, MLP of the frame's network, "
                         "sigmoid visibilities out",
             "ms": ms, "tflops": tf, "peak_tflops": pk["bf16_sustained"],
             "frac_of_tensor_peak": tf / pk["bf16_sustained"],
-            "io_bytes": n_px * (k0 * 2 + cfg.n_outputs * 4)}
+            "io_bytes": io, "io_gbs": io_gbs, "peak_hbm_gbs": pk["hbm"],
+            "frac_of_hbm": io_gbs / pk["hbm"],
+            "bound": "hbm" if io / pk["hbm"] > flops / (pk["bf16_sustained"] * 1e3) else "tensor"}
 
 
 def _timed(stream, fn, n, warm=3):
@@ -938,7 +945,8 @@ def run_ours(args):
     if mlp_only and "tflops" in mlp_only:
         shade_view["views"]["mlp_only_launch_vs_tensor"] = {
             "achieved_tflops": mlp_only["tflops"], "peak_tflops": pk["bf16_sustained"],
-            "frac": mlp_only["frac_of_tensor_peak"], "ms": mlp_only["ms"]}
+            "frac": mlp_only["frac_of_tensor_peak"], "ms": mlp_only["ms"],
+            "bound": mlp_only["bound"], "io_frac_of_hbm": mlp_only["frac_of_hbm"]}
     roof = shade_view if stage_ms[3] >= stage_ms[2] else adam_view
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world,

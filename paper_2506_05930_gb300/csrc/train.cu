@@ -211,29 +211,34 @@ __device__ __forceinline__ void set_image(const MlpImageMap& mp, uint8_t* img, i
     reinterpret_cast<__half*>(img + mp.byte_off[k])[local] = __float2half_rn(v);
 }
 
-// One thread's two float4 groups of an iteration: e, and e + stride when
-// that is below n4.
+// A thread loads kAdamGroups float4 groups (e, e + stride, ...) before any
+// arithmetic; the launch keeps at most kAdamCtaCap CTAs of 256 threads per
+// SM (0: all that fit).  Two groups and two CTAs (16 warps per SM) was the
+// fastest point of the 1080p table's update: 1 to 8 groups at 8 to 32 warps
+// per SM all took longer.
+constexpr int kAdamGroups = 2;
+constexpr int kAdamCtaCap = 2;
+
 struct AdamGroups {
-  float4 g[2], th[2], mm[2], vv[2];
+  float4 g[kAdamGroups], th[kAdamGroups], mm[kAdamGroups], vv[kAdamGroups];
 };
 
 __device__ __forceinline__ void adam_load(AdamGroups& q, const float4* g4, const float4* th4,
                                           const float4* m4, const float4* v4, int64_t e,
-                                          int64_t e1, bool two) {
-  q.g[0] = __ldcs(g4 + e);
-  q.th[0] = th4[e];
-  q.mm[0] = __ldcs(m4 + e);
-  q.vv[0] = __ldcs(v4 + e);
-  if (two) {
-    q.g[1] = __ldcs(g4 + e1);
-    q.th[1] = th4[e1];
-    q.mm[1] = __ldcs(m4 + e1);
-    q.vv[1] = __ldcs(v4 + e1);
+                                          int64_t stride, int64_t n4) {
+#pragma unroll
+  for (int u = 0; u < kAdamGroups; ++u) {
+    const int64_t eu = e + u * stride;
+    if (u > 0 && eu >= n4) break;
+    q.g[u] = __ldcs(g4 + eu);
+    q.th[u] = th4[eu];
+    q.mm[u] = __ldcs(m4 + eu);
+    q.vv[u] = __ldcs(v4 + eu);
   }
 }
 
-// The update proper (sc.skip == 0): grid-stride over float4 groups, two at
-// a time, then the tail scalars.  q holds the first iteration's groups
+// The update proper (sc.skip == 0): grid-stride over float4 groups,
+// kAdamGroups at a time, then the tail scalars.  q holds the first iteration's groups
 // (e = t0), loaded by the caller before the step's scalars were known.
 __device__ __forceinline__ void adam_update(float* __restrict__ theta, float* __restrict__ grad,
                                             float* __restrict__ m, float* __restrict__ v,
@@ -247,22 +252,20 @@ __device__ __forceinline__ void adam_update(float* __restrict__ theta, float* __
   float4* th4 = reinterpret_cast<float4*>(theta);
   float4* m4 = reinterpret_cast<float4*>(m);
   float4* v4 = reinterpret_cast<float4*>(v);
-  for (int64_t e = t0; e < n4; e += 2 * stride) {
-    const int64_t e1 = e + stride;
-    const bool two = e1 < n4;
-    if (e != t0) adam_load(q, g4, th4, m4, v4, e, e1, two);
-    float4 (&g)[2] = q.g;
-    float4 (&th)[2] = q.th;
-    float4 (&mm)[2] = q.mm;
-    float4 (&vv)[2] = q.vv;
+  for (int64_t e = t0; e < n4; e += kAdamGroups * stride) {
+    if (e != t0) adam_load(q, g4, th4, m4, v4, e, stride, n4);
+    float4 (&g)[kAdamGroups] = q.g;
+    float4 (&th)[kAdamGroups] = q.th;
+    float4 (&mm)[kAdamGroups] = q.mm;
+    float4 (&vv)[kAdamGroups] = q.vv;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      if (u == 1 && !two) break;
+    for (int u = 0; u < kAdamGroups; ++u) {
+      const int64_t ee = e + u * stride;
+      if (u > 0 && ee >= n4) break;
       adam_scalar(th[u].x, g[u].x, mm[u].x, vv[u].x, sc, beta1, beta2, eps);
       adam_scalar(th[u].y, g[u].y, mm[u].y, vv[u].y, sc, beta1, beta2, eps);
       adam_scalar(th[u].z, g[u].z, mm[u].z, vv[u].z, sc, beta1, beta2, eps);
       adam_scalar(th[u].w, g[u].w, mm[u].w, vv[u].w, sc, beta1, beta2, eps);
-      const int64_t ee = u == 0 ? e : e1;
       th4[ee] = th[u];
       if (table16 != nullptr && ee < n_table4) {
         const __half2 a = __floats2half2_rn(th[u].x, th[u].y);
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ theta,
   AdamGroups q;
   if (t0 < n4)
     adam_load(q, g4, reinterpret_cast<const float4*>(theta), reinterpret_cast<const float4*>(m),
-              reinterpret_cast<const float4*>(v), t0, t0 + stride, t0 + stride < n4);
+              reinterpret_cast<const float4*>(v), t0, stride, n4);
   // every CTA plans the step from the same inputs (warp 0); the last CTA to
   // finish commits its bookkeeping, after every CTA has read the status
   __shared__ StepPlan s_plan;
@@ -437,13 +440,14 @@ cudaError_t launch_adam(nvc_handle* h, double* loss_out, bool apply, cudaStream_
   // the step's loss, skip decision and scalars are derived inside the
   // update kernel (one launch)
   const int64_t n4 = h->n_params / 4;
-  // two float4 groups per thread and pass: no more CTAs than that covers
-  // (a small table would otherwise pay for 8 CTAs per SM that each plan the
-  // step and find no work)
-  // and no more than one resident wave, so every CTA plans the step once, at
-  // the start, while its first loads are in flight
-  const int64_t want = (n4 + 2 * 256 - 1) / (2 * 256);
-  const int64_t cap = (int64_t)h->num_sms * (h->adam_ctas_per_sm > 0 ? h->adam_ctas_per_sm : 1);
+  // kAdamGroups float4 groups per thread and pass: no more CTAs than that
+  // covers (a small table would otherwise pay for CTAs that each plan the
+  // step and find no work), and no more than one resident wave, so every CTA
+  // plans the step once, at the start, while its first loads are in flight
+  const int64_t want = (n4 + kAdamGroups * 256 - 1) / (kAdamGroups * 256);
+  int per_sm = h->adam_ctas_per_sm > 0 ? h->adam_ctas_per_sm : 1;
+  if (kAdamCtaCap > 0 && per_sm > kAdamCtaCap) per_sm = kAdamCtaCap;
+  const int64_t cap = (int64_t)h->num_sms * per_sm;
   const int blocks = (int)(want < 1 ? 1 : want < cap ? want : cap);
   MlpImageMap mp{};
   uint8_t* img = mlp_image_map(h, &mp) ? static_cast<uint8_t*>(h->mlp_packed) : nullptr;
