@@ -251,7 +251,7 @@ def clustered_alu_ops(n_lights, k, n_pixels):
 # Per-launch DRAM traffic of the dominant kernel from the ncu capture named in
 # profiles/ (None once the kernel has changed since that capture); the fused
 # shading kernel's by variant (the 1080p frame's launch).
-KERNEL_TRAFFIC = {"fused_shade": {6: 78.68e6, 7: 83.04e6}, "adam": 461.3e6,
+KERNEL_TRAFFIC = {"fused_shade": {6: 78.75e6, 7: 83.04e6}, "adam": 460.4e6,
                   # 1080p launch with the shadow ray (light, W and estimate written)
                   "sample_clustered": 336.78e6}
 
