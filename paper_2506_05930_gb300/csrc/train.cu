@@ -238,8 +238,9 @@ __device__ __forceinline__ void adam_load(AdamGroups& q, const float4* g4, const
 }
 
 // The update proper (sc.skip == 0): grid-stride over float4 groups,
-// kAdamGroups at a time, then the tail scalars.  q holds the first iteration's groups
-// (e = t0), loaded by the caller before the step's scalars were known.
+// kAdamGroups at a time, then the tail scalars.  q holds the first
+// iteration's groups (e = t0), loaded by the caller before the step's
+// scalars were known.
 __device__ __forceinline__ void adam_update(float* __restrict__ theta, float* __restrict__ grad,
                                             float* __restrict__ m, float* __restrict__ v,
                                             int64_t n4, int64_t n, float beta1, float beta2,
