@@ -47,6 +47,63 @@ def _ptr(t: Optional[torch.Tensor], dtype=torch.float32, name="tensor"):
     return t.data_ptr()
 
 
+# The C entry points take bare pointers and sizes, so a tensor shorter than
+# the extent a call reads or writes would let a kernel run past it.  The
+# wrappers check every tensor's extent against the call's n, the handle's
+# shapes (recorded here by nvc_create) and the scene's light count before
+# anything is launched.
+@dataclass(frozen=True)
+class HandleShapes:
+    n_outputs: int      # L: visibilities per position
+    enc_width: int      # levels x features
+    n_params: int
+    precision: int      # _lib.PRECISIONS value of the inference operands
+    batch: int          # training positions per step
+
+
+_HANDLE_SHAPES: dict = {}
+
+
+def _shapes(h) -> Optional[HandleShapes]:
+    return _HANDLE_SHAPES.get(h.value if isinstance(h, ctypes.c_void_p) else h)
+
+
+def _rows(t, cols: int, name: str) -> int:
+    """n of a [n, cols] tensor (the row count a call is given)."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dim() != 2 or t.shape[1] != cols:
+        raise ValueError(f"{name} must be [n, {cols}], got {tuple(t.shape)}")
+    return int(t.shape[0])
+
+
+def _holds(t, count: int, name: str):
+    """A tensor the call reads or writes `count` elements of (None passes)."""
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.numel() < count:
+        raise ValueError(f"{name} holds {t.numel()} elements; the call uses {count}")
+
+
+def _outputs_per_pixel(h) -> Optional[int]:
+    s = _shapes(h)
+    return None if s is None else s.n_outputs
+
+
+def _pixels(pos, nrm=None, per_pixel=(), name="pos") -> int:
+    """n from pos [n, 3]; nrm holds n rows of 3, the per-pixel tensors n
+    elements."""
+    n = _rows(pos, 3, name)
+    if nrm is not None:
+        if _rows(nrm, 3, "nrm") < n:
+            raise ValueError(f"nrm has {nrm.shape[0]} rows, pos {n}")
+    for t, nm in per_pixel:
+        _holds(t, n, nm)
+    return n
+
+
 def make_config(cfg=None, **kw) -> NvcConfig:
     """nvc_config from an object/dict with the fields of the workload sets
     (``hidden`` is a tuple of equal widths) plus keyword overrides."""
@@ -132,10 +189,15 @@ def nvc_level_resolution(cfg: NvcConfig, level: int) -> int:
 def nvc_create(cfg: NvcConfig):
     h = ctypes.c_void_p()
     check(lib.nvc_create(ctypes.byref(cfg), ctypes.byref(h)))
+    _HANDLE_SHAPES[h.value] = HandleShapes(
+        n_outputs=int(cfg.n_outputs), enc_width=int(cfg.n_levels * cfg.n_features),
+        n_params=nvc_param_count(cfg), precision=int(cfg.precision),
+        batch=int(cfg.batch_positions))
     return h
 
 
 def nvc_destroy(h):
+    _HANDLE_SHAPES.pop(h.value if isinstance(h, ctypes.c_void_p) else h, None)
     lib.nvc_destroy(h)
 
 
@@ -143,16 +205,26 @@ def nvc_last_error(h=None) -> str:
     return lib.nvc_last_error(h).decode(errors="replace")
 
 
+def _params_like(h, tensors):
+    s = _shapes(h)
+    if s is not None:
+        for t, name in tensors:
+            _holds(t, s.n_params, name)
+
+
 def nvc_set_state(h, params, adam_m=None, adam_v=None, step=0, stream=None):
+    _params_like(h, ((params, "params"), (adam_m, "adam_m"), (adam_v, "adam_v")))
     check(lib.nvc_set_state(h, _ptr(params, name="params"), _ptr(adam_m, name="adam_m"),
                             _ptr(adam_v, name="adam_v"), int(step), _stream(stream)), h)
 
 
 def nvc_set_params(h, params, stream=None):
+    _params_like(h, ((params, "params"),))
     check(lib.nvc_set_params(h, _ptr(params, name="params"), _stream(stream)), h)
 
 
 def nvc_get_state(h, params=None, adam_m=None, adam_v=None, stream=None):
+    _params_like(h, ((params, "params"), (adam_m, "adam_m"), (adam_v, "adam_v")))
     check(lib.nvc_get_state(h, _ptr(params), _ptr(adam_m), _ptr(adam_v), _stream(stream)), h)
 
 
@@ -167,6 +239,10 @@ def nvc_sync_status(h, stream=None) -> dict:
 
 
 def nvc_encode(h, pos, feat, stream=None):
+    n = _pixels(pos)
+    s = _shapes(h)
+    if s is not None:
+        _holds(feat, n * s.enc_width, "feat")
     check(lib.nvc_encode(h, _ptr(pos, name="pos"), pos.shape[0], _ptr(feat, name="feat"),
                          _stream(stream)), h)
 
@@ -180,22 +256,40 @@ def nvc_mlp_infer_features(h, feat, vis, stream=None):
         raise ValueError("feat must be contiguous float16 or bfloat16")
     if vis.shape[0] != feat.shape[0]:
         raise ValueError("feat and vis must have the same number of rows")
+    s = _shapes(h)
+    if s is not None:
+        _holds(vis, feat.shape[0] * s.n_outputs, "vis")
+        want = {_lib.PRECISIONS["fp16"]: torch.float16, _lib.PRECISIONS["bf16"]: torch.bfloat16}
+        if s.precision in want and feat.dtype != want[s.precision]:
+            raise TypeError(f"feat must be {want[s.precision]} for this handle")
     check(lib.nvc_mlp_infer_features(h, feat.data_ptr(), feat.shape[0], feat.shape[1],
                                      _ptr(vis, name="vis"), _stream(stream)), h)
 
 
 def nvc_infer(h, pos, vis, stream=None):
+    n = _pixels(pos)
+    L = _outputs_per_pixel(h)
+    if L is not None:
+        _holds(vis, n * L, "vis")
     check(lib.nvc_infer(h, _ptr(pos, name="pos"), pos.shape[0], _ptr(vis, name="vis"),
                         _stream(stream)), h)
 
 
 def nvc_light_weights(scene: Scene, pos, nrm, vis, c, w=None, stream=None):
+    n = _pixels(pos, nrm)
+    L = scene.struct.n_lights
+    for t, name in ((vis, "vis"), (c, "c"), (w, "w")):
+        _holds(t, n * L, name)
     check(lib.nvc_light_weights(scene.ref, _ptr(pos), _ptr(nrm), _ptr(vis), pos.shape[0],
                                 _ptr(c), _ptr(w), _stream(stream)))
 
 
 def nvc_wrs_from_weights(w, seed, frame, view=0, pixel_offset=0, idx=None, pdf=None,
                          wsum=None, stream=None):
+    if not isinstance(w, torch.Tensor) or w.dim() != 2:
+        raise ValueError("w must be a [n, n_lights] tensor")
+    for t, name in ((idx, "idx"), (pdf, "pdf"), (wsum, "wsum")):
+        _holds(t, w.shape[0], name)
     check(lib.nvc_wrs_from_weights(_ptr(w, name="w"), w.shape[0], w.shape[1], int(seed),
                                    int(frame), int(view), int(pixel_offset),
                                    _ptr(idx, torch.int32, "idx"), _ptr(pdf), _ptr(wsum),
@@ -204,6 +298,7 @@ def nvc_wrs_from_weights(w, seed, frame, view=0, pixel_offset=0, idx=None, pdf=N
 
 def nvc_wrs_sample(h, scene: Scene, pos, nrm, seed, frame, view=0, pixel_offset=0, idx=None,
                    pdf=None, wsum=None, stream=None):
+    _pixels(pos, nrm, ((idx, "idx"), (pdf, "pdf"), (wsum, "wsum")))
     check(lib.nvc_wrs_sample(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0], int(seed),
                              int(frame), int(view), int(pixel_offset),
                              _ptr(idx, torch.int32, "idx"), _ptr(pdf), _ptr(wsum),
@@ -211,12 +306,14 @@ def nvc_wrs_sample(h, scene: Scene, pos, nrm, seed, frame, view=0, pixel_offset=
 
 
 def nvc_direct_illum(h, scene: Scene, pos, nrm, radiance, stream=None):
+    _pixels(pos, nrm, ((radiance, "radiance"),))
     check(lib.nvc_direct_illum(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0],
                                _ptr(radiance), _stream(stream)), h)
 
 
 def nvc_shade(h, scene: Scene, pos, nrm, seed, frame, view=0, pixel_offset=0, idx=None,
               pdf=None, wsum=None, radiance=None, fused=True, stream=None):
+    _pixels(pos, nrm, ((idx, "idx"), (pdf, "pdf"), (wsum, "wsum"), (radiance, "radiance")))
     check(lib.nvc_shade(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0], int(seed),
                         int(frame), int(view), int(pixel_offset),
                         _ptr(idx, torch.int32, "idx"), _ptr(pdf), _ptr(wsum), _ptr(radiance),
@@ -224,6 +321,10 @@ def nvc_shade(h, scene: Scene, pos, nrm, seed, frame, view=0, pixel_offset=0, id
 
 
 def nvc_sampler_weights(h, scene: Scene, pos, nrm, w, stream=None):
+    n = _pixels(pos, nrm)
+    L = _outputs_per_pixel(h)
+    if L is not None:
+        _holds(w, n * L, "w")
     check(lib.nvc_sampler_weights(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0], _ptr(w),
                                   _stream(stream)), h)
 
@@ -235,6 +336,7 @@ def nvc_autotune_shade(h, scene: Scene, pos, nrm, idx=None, pdf=None, wsum=None,
                        reps=5, stream=None):
     """Times the fused shading kernel's variants on these pixels and keeps
     the fastest.  Returns (chosen variant, [ms per launch or -1])."""
+    _pixels(pos, nrm, ((idx, "idx"), (pdf, "pdf"), (wsum, "wsum"), (radiance, "radiance")))
     chosen = ctypes.c_int32()
     ms = (ctypes.c_double * SHADE_VARIANTS)()
     check(lib.nvc_autotune_shade(h, scene.ref, _ptr(pos), _ptr(nrm), pos.shape[0],
@@ -248,6 +350,10 @@ def nvc_autotune_infer(h, pos, vis, reps=5, stream=None):
     """Times nvc_infer under each fused-kernel variant (vis is scratch) and
     keeps the fastest for this handle's nvc_infer.  Returns (chosen variant,
     [ms per call or -1])."""
+    n = _pixels(pos)
+    L = _outputs_per_pixel(h)
+    if L is not None:
+        _holds(vis, n * L, "vis")
     chosen = ctypes.c_int32()
     ms = (ctypes.c_double * SHADE_VARIANTS)()
     check(lib.nvc_autotune_infer(h, _ptr(pos, name="pos"), pos.shape[0], _ptr(vis, name="vis"),
@@ -257,6 +363,7 @@ def nvc_autotune_infer(h, pos, vis, reps=5, stream=None):
 
 def nvc_calibrate(h, pos, stream=None):
     """Per-tensor E4M3 activation scales from a float32 pass over pos."""
+    _pixels(pos)
     check(lib.nvc_calibrate(h, _ptr(pos, name="pos"), pos.shape[0], _stream(stream)), h)
 
 
@@ -275,6 +382,7 @@ def nvc_autotune_shade_plan(h, scene: Scene, pos, nrm, idx=None, pdf=None, wsum=
     """Times every point (variant, CTAs per SM) of the fused shading
     kernel's tuning space on these pixels and keeps the fastest.  Returns
     ((variant, ctas_per_sm) chosen, [((variant, ctas_per_sm), ms), ...])."""
+    _pixels(pos, nrm, ((idx, "idx"), (pdf, "pdf"), (wsum, "wsum"), (radiance, "radiance")))
     cap = 64
     chosen = _lib.NvcShadePlan()
     pts = (_lib.NvcShadePlan * cap)()
@@ -296,6 +404,7 @@ def nvc_shade_phases(h, scene: Scene, pos, nrm, seed=0, frame=0, idx=None, pdf=N
                      radiance=None, stream=None):
     """One instrumented fused shading launch (variants 6 and 7): returns the
     summed SM cycles of [encode, MLP, sampler, whole tile loop]."""
+    _pixels(pos, nrm, ((idx, "idx"), (pdf, "pdf"), (wsum, "wsum"), (radiance, "radiance")))
     cyc = (ctypes.c_double * 4)()
     check(lib.nvc_shade_phases(h, scene.ref, _ptr(pos, name="pos"), _ptr(nrm, name="nrm"),
                                pos.shape[0], int(seed), int(frame),
@@ -317,19 +426,23 @@ def nvc_gather_bench(table, row_bytes, n_threads, rows_per_thread, sink, seed=0,
 
 
 def nvc_trace_visibility(scene: Scene, pos, vis, stream=None):
+    n = _pixels(pos)
+    _holds(vis, n * scene.struct.n_lights, "vis")
     check(lib.nvc_trace_visibility(scene.ref, _ptr(pos), pos.shape[0], _ptr(vis),
                                    _stream(stream)))
 
 
 def nvc_training_positions(scene: Scene, screen_pos, batch, seed, frame, pos, stream=None):
-    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    n_screen = 0 if screen_pos is None else _rows(screen_pos, 3, "screen_pos")
+    _holds(pos, int(batch) * 3, "pos")
     check(lib.nvc_training_positions(scene.ref, _ptr(screen_pos), n_screen, int(batch),
                                      int(seed), int(frame), _ptr(pos), _stream(stream)))
 
 
 def nvc_training_positions_split(scene: Scene, screen_pos, batch, n_world, seed, frame, pos,
                                  stream=None):
-    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    n_screen = 0 if screen_pos is None else _rows(screen_pos, 3, "screen_pos")
+    _holds(pos, int(batch) * 3, "pos")
     check(lib.nvc_training_positions_split(scene.ref, _ptr(screen_pos), n_screen, int(batch),
                                            int(n_world), int(seed), int(frame), _ptr(pos),
                                            _stream(stream)))
@@ -343,6 +456,10 @@ def nvc_set_training_data_fused(h, fused: bool):
 
 def nvc_training_batch(h, pos=None, target=None, stream=None):
     """Copies the last training step's positions [B, 3] and targets [B, L] out."""
+    s = _shapes(h)
+    if s is not None:
+        _holds(pos, s.batch * 3, "pos")
+        _holds(target, s.batch * s.n_outputs, "target")
     check(lib.nvc_training_batch(h, _ptr(pos, name="pos"), _ptr(target, name="target"),
                                  _stream(stream)), h)
 
@@ -352,24 +469,34 @@ def nvc_set_training_placement(h, n_world: int):
 
 
 def nvc_train_step(h, scene: Scene, screen_pos, seed, frame, loss_out=None, stream=None):
-    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    n_screen = 0 if screen_pos is None else _rows(screen_pos, 3, "screen_pos")
     check(lib.nvc_train_step(h, scene.ref, _ptr(screen_pos), n_screen, int(seed), int(frame),
                              _ptr(loss_out, torch.float64, "loss_out"), _stream(stream)), h)
 
 
 def nvc_train_gradient(h, scene: Scene, screen_pos, seed, frame, grad, loss_out=None,
                        stream=None):
-    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    n_screen = 0 if screen_pos is None else _rows(screen_pos, 3, "screen_pos")
+    _params_like(h, ((grad, "grad"),))
     check(lib.nvc_train_gradient(h, scene.ref, _ptr(screen_pos), n_screen, int(seed),
                                  int(frame), _ptr(grad), _ptr(loss_out, torch.float64),
                                  _stream(stream)), h)
 
 
 def nvc_mlp_forward(h, pos, logits, stream=None):
+    n = _pixels(pos)
+    L = _outputs_per_pixel(h)
+    if L is not None:
+        _holds(logits, n * L, "logits")
     check(lib.nvc_mlp_forward(h, _ptr(pos), pos.shape[0], _ptr(logits), _stream(stream)), h)
 
 
 def nvc_mlp_backward(h, pos, dlogits, grad, stream=None):
+    n = _pixels(pos)
+    L = _outputs_per_pixel(h)
+    if L is not None:
+        _holds(dlogits, n * L, "dlogits")
+    _params_like(h, ((grad, "grad"),))
     check(lib.nvc_mlp_backward(h, _ptr(pos), pos.shape[0], _ptr(dlogits), _ptr(grad),
                                _stream(stream)), h)
 
@@ -385,7 +512,12 @@ class View:
     wsum: Optional[torch.Tensor] = None
     radiance: Optional[torch.Tensor] = None
 
+    def check_extents(self):
+        _pixels(self.pos, self.nrm, ((self.idx, "idx"), (self.pdf, "pdf"), (self.wsum, "wsum"),
+                                     (self.radiance, "radiance")))
+
     def struct(self) -> NvcView:
+        self.check_extents()
         v = NvcView()
         v.pos = _ptr(self.pos)
         v.nrm = _ptr(self.nrm)
@@ -421,6 +553,7 @@ def _host_ptr(t: Optional[torch.Tensor], dtype=torch.float32, name="tensor"):
 
 
 def _host_view(v: "View") -> NvcView:
+    v.check_extents()
     s = NvcView()
     s.pos = _host_ptr(v.pos, name="pos")
     s.nrm = _host_ptr(v.nrm, name="nrm")
@@ -453,6 +586,7 @@ def nvc_shade_estimate(scene: Scene, pos, nrm, idx, pdf, estimate=None, accum=No
                        stream=None):
     """V c / pdf for each pixel's sampled light (one shadow ray), and/or its
     running mean over `count` frames into `accum`."""
+    _pixels(pos, nrm, ((idx, "idx"), (pdf, "pdf"), (estimate, "estimate"), (accum, "accum")))
     check(lib.nvc_shade_estimate(scene.ref, _ptr(pos, name="pos"), _ptr(nrm, name="nrm"),
                                  pos.shape[0], _ptr(idx, torch.int32, "idx"), _ptr(pdf, name="pdf"),
                                  _ptr(estimate, name="estimate"), _ptr(accum, name="accum"),
@@ -461,6 +595,7 @@ def nvc_shade_estimate(scene: Scene, pos, nrm, idx, pdf, estimate=None, accum=No
 
 def nvc_exact_di(scene: Scene, pos, nrm, di, stream=None):
     """Sum over all lights of V_i c_i, one shadow ray per (pixel, light)."""
+    _pixels(pos, nrm, ((di, "di"),))
     check(lib.nvc_exact_di(scene.ref, _ptr(pos, name="pos"), _ptr(nrm, name="nrm"), pos.shape[0],
                            _ptr(di, name="di"), _stream(stream)))
 
@@ -504,19 +639,23 @@ class Clusters:
 
 def nvc_train_step_clustered(h, scene: Scene, clusters: Clusters, screen_pos, seed, frame,
                              loss_out=None, stream=None):
-    n_screen = 0 if screen_pos is None else screen_pos.shape[0]
+    n_screen = 0 if screen_pos is None else _rows(screen_pos, 3, "screen_pos")
     check(lib.nvc_train_step_clustered(h, scene.ref, clusters.ref, _ptr(screen_pos), n_screen,
                                        int(seed), int(frame), _ptr(loss_out, torch.float64, "loss_out"),
                                        _stream(stream)), h)
 
 
 def nvc_cluster_targets(scene: Scene, clusters: Clusters, pos, seed, frame, target, stream=None):
+    n = _pixels(pos)
+    _holds(target, n * clusters.struct.k, "target")
     check(lib.nvc_cluster_targets(scene.ref, clusters.ref, _ptr(pos, name="pos"), pos.shape[0],
                                   int(seed), int(frame), _ptr(target, name="target"), _stream(stream)))
 
 
 def nvc_sample_clustered(scene: Scene, clusters: Clusters, vis, pos, nrm, seed, frame, view=0,
                          pixel_offset=0, light=None, weight=None, estimate=None, stream=None):
+    n = _pixels(pos, nrm, ((light, "light"), (weight, "weight"), (estimate, "estimate")))
+    _holds(vis, n * clusters.struct.k, "vis")
     check(lib.nvc_sample_clustered(scene.ref, clusters.ref, _ptr(vis, name="vis"),
                                    _ptr(pos, name="pos"), _ptr(nrm, name="nrm"), pos.shape[0],
                                    int(pixel_offset), int(seed), int(frame), int(view),
@@ -530,6 +669,9 @@ def nvc_temporal_merge(scene: Scene, pos, nrm, cur_light, cur_W, prev_light=None
     """Temporal resampling of the frame's cache reservoir (cur_light, cur_W)
     with the previous frame's (prev_light, prev_W, prev_M; None: every pixel
     disoccluded) into (light, W, M) and the one-shadow-ray estimate."""
+    _pixels(pos, nrm, ((cur_light, "cur_light"), (cur_W, "cur_W"), (prev_light, "prev_light"),
+                       (prev_W, "prev_W"), (prev_M, "prev_M"), (light, "light"), (W, "W"),
+                       (M, "M"), (estimate, "estimate")))
     check(lib.nvc_temporal_merge(scene.ref, _ptr(pos, name="pos"), _ptr(nrm, name="nrm"),
                                  pos.shape[0], int(pixel_offset), int(seed), int(frame), int(view),
                                  _ptr(cur_light, torch.int32, "cur_light"), _ptr(cur_W, name="cur_W"),
