@@ -92,6 +92,13 @@ def _outputs_per_pixel(h) -> Optional[int]:
     return None if s is None else s.n_outputs
 
 
+def _cluster_count(clusters) -> int:
+    """k for the extent checks; a k outside 1..32 is left to the library,
+    which rejects it."""
+    k = int(clusters.struct.k)
+    return k if 1 <= k <= 32 else 0
+
+
 def _pixels(pos, nrm=None, per_pixel=(), name="pos") -> int:
     """n from pos [n, 3]; nrm holds n rows of 3, the per-pixel tensors n
     elements."""
@@ -647,7 +654,7 @@ def nvc_train_step_clustered(h, scene: Scene, clusters: Clusters, screen_pos, se
 
 def nvc_cluster_targets(scene: Scene, clusters: Clusters, pos, seed, frame, target, stream=None):
     n = _pixels(pos)
-    _holds(target, n * clusters.struct.k, "target")
+    _holds(target, n * _cluster_count(clusters), "target")
     check(lib.nvc_cluster_targets(scene.ref, clusters.ref, _ptr(pos, name="pos"), pos.shape[0],
                                   int(seed), int(frame), _ptr(target, name="target"), _stream(stream)))
 
@@ -655,7 +662,7 @@ def nvc_cluster_targets(scene: Scene, clusters: Clusters, pos, seed, frame, targ
 def nvc_sample_clustered(scene: Scene, clusters: Clusters, vis, pos, nrm, seed, frame, view=0,
                          pixel_offset=0, light=None, weight=None, estimate=None, stream=None):
     n = _pixels(pos, nrm, ((light, "light"), (weight, "weight"), (estimate, "estimate")))
-    _holds(vis, n * clusters.struct.k, "vis")
+    _holds(vis, n * _cluster_count(clusters), "vis")
     check(lib.nvc_sample_clustered(scene.ref, clusters.ref, _ptr(vis, name="vis"),
                                    _ptr(pos, name="pos"), _ptr(nrm, name="nrm"), pos.shape[0],
                                    int(pixel_offset), int(seed), int(frame), int(view),
